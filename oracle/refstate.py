@@ -1,0 +1,58 @@
+"""Hydrostatic reference state (Eqs. rho_split, theta_split, p_split, hydro_bal).
+
+Sec. 2 splits rho, theta and p into a z-only hydrostatic part plus a
+fluctuation, with dp0/dz = -rho0 g.  The paper takes the background from a
+sounding that is not available; the reference state used here is the
+constant Brunt-Vaisala-frequency atmosphere (theta0(0) = theta_s, buoyancy
+frequency N_bv), written in closed form:
+
+    theta0(z) = theta_s exp(N_bv^2 z / g)
+    pi0(z)    = 1 + g^2 / (c_p theta_s N_bv^2) (exp(-N_bv^2 z / g) - 1)
+    p0        = p00 pi0^(c_p / R_d)
+    rho0      = p00 pi0^(c_v / R_d) / (R_d theta0)
+    (rho theta)0 = rho0 theta0
+
+which satisfies c_p theta0 dpi0/dz = -g, i.e. dp0/dz = -rho0 g exactly, and the
+ideal gas law p = rho R_d T with T = theta pi, pi = (p / p00)^(R_d / c_p)
+(Sec. 2).
+
+Test infrastructure only (see oracle/__init__.py).
+"""
+import numpy as np
+
+
+class Params:
+    """Physical constants (Sec. 2: g = 9.81; the gas constants are unstated
+    in the paper, the values below are the ones used throughout)."""
+
+    def __init__(self, g=9.81, R_d=287.0, c_p=1004.0, p00=1.0e5, f=5.0e-5,
+                 theta_s=300.0, N_bv=0.01):
+        self.g, self.R_d, self.c_p, self.p00 = g, R_d, c_p, p00
+        self.c_v = c_p - R_d
+        self.gamma = c_p / self.c_v
+        self.f, self.theta_s, self.N_bv = f, theta_s, N_bv
+
+
+def reference_state(z, prm):
+    """theta0, pi0, p0, rho0, (rho theta)0 and d theta0/dz at heights z."""
+    z = np.asarray(z, dtype=np.float64)
+    g, N2 = prm.g, prm.N_bv ** 2
+    theta0 = prm.theta_s * np.exp(N2 * z / g)
+    pi0 = 1.0 + g * g / (prm.c_p * prm.theta_s * N2) * (np.exp(-N2 * z / g) - 1.0)
+    p0 = prm.p00 * pi0 ** (prm.c_p / prm.R_d)
+    rho0 = prm.p00 * pi0 ** (prm.c_v / prm.R_d) / (prm.R_d * theta0)
+    rhotheta0 = rho0 * theta0
+    dtheta0 = theta0 * N2 / g
+    return dict(theta0=theta0, pi0=pi0, p0=p0, rho0=rho0,
+                rhotheta0=rhotheta0, dtheta0=dtheta0)
+
+
+def pressure_perturbation(rhotheta_pert, rhotheta0, p0, gamma):
+    """p' = p - p0 with p = p00 (R_d rho theta / p00)^gamma.
+
+    Since p0 = p00 (R_d (rho theta)0 / p00)^gamma:
+        p' = p0 ((1 + (rho theta)'/(rho theta)0)^gamma - 1)
+           = p0 expm1(gamma log1p((rho theta)' / (rho theta)0)),
+    which is exactly zero for a zero perturbation.
+    """
+    return p0 * np.expm1(gamma * np.log1p(rhotheta_pert / rhotheta0))

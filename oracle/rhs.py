@@ -1,0 +1,102 @@
+"""Right-hand side of the split dry Euler equations on the CG spectral-element mesh.
+
+Two equation sets share one discretisation (Sec. 3):
+
+* "C" (conservative): state (rho', rho u, rho v, rho w, (rho theta)'), the
+  flux form of Eqs. mass_split / mom_split / ent_split (multiply the velocity
+  and theta equations by rho and use the mass equation):
+      d rho'/dt          = -div(rho u)
+      d (rho u)/dt       = -div(rho u (x) u + p' I) - rho' g e_z + f (rho v, -rho u, 0)
+      d (rho theta)'/dt  = -div(rho theta u)
+* "NC" (the paper's non-conservative set, Eqs. mass_split..ent_split):
+  state (rho', u, v, w, theta'),
+      d rho'/dt   = -div(rho u)
+      d u/dt      = -u.grad u - grad p' / rho + (rho'/rho) g k + f (v, -u, 0)
+      d theta'/dt = -u.grad theta0 - u.grad theta'
+  with k = (0, 0, -1) (Sec. 2).  The f-plane Coriolis term is not in the
+  paper's equations; it is added with the parameter f (zero turns it off).
+
+In both, p' = p0 expm1(gamma log1p((rho theta)'/(rho theta)0)).
+
+Discretisation: the divergence terms are taken in weak form,
+    r_l = sum_k w_k J grad psi_l(x_k) . F(x_k)   (+ boundary terms, see below),
+the remaining (source, advective and pressure-gradient) terms in collocated
+strong form, r_l = w_l J s_l.  The element residuals are assembled with the
+modified DSS of Sec. 3.1, R = Q^T r, and divided by the lumped mass built the
+same way, M = Q^T (w J).  Lateral boundaries are periodic (Sec. 4); top and
+bottom are rigid lids: the vertical-momentum (or w) tendency is set to zero
+at the lid nodes, which also removes the lid boundary integrals because the
+normal mass, momentum and theta fluxes vanish there with w = 0.
+
+Test infrastructure only (see oracle/__init__.py).
+"""
+import numpy as np
+
+from .refstate import reference_state, pressure_perturbation
+
+FIELDS_C = ("rho'", "rho u", "rho v", "rho w", "(rho theta)'")
+FIELDS_NC = ("rho'", "u", "v", "w", "theta'")
+
+
+def element_residual(mesh, qL, prm, eqset="C"):
+    """Element-local residuals r_L, shape (5, Ne, P), from local values qL."""
+    if eqset not in ("C", "NC"):
+        raise ValueError(eqset)
+    z = mesh.X[:, :, 2]
+    ref = reference_state(z, prm)
+    rho0, p0, rt0 = ref["rho0"], ref["p0"], ref["rhotheta0"]
+    theta0, dth0 = ref["theta0"], ref["dtheta0"]
+    g, f, gamma = prm.g, prm.f, prm.gamma
+    wJ = mesh.wJ
+    r = np.zeros_like(qL)
+    for lev in np.unique(mesh.level):
+        es = np.nonzero(mesh.level == lev)[0]
+        G = mesh.element_ops(int(lev))
+        q = qL[:, es, :]
+        rp = q[0]
+        rho = rho0[es] + rp
+        W_ = wJ[es]
+
+        def weak(F):
+            # sum_k wJ_k sum_d G_d[k, l] F_d[k]
+            return sum((W_ * F[d]) @ G[d] for d in range(3))
+
+        def grad(phi):
+            return [phi @ G[d].T for d in range(3)]
+
+        if eqset == "C":
+            U, V, Wm, Tp = q[1], q[2], q[3], q[4]
+            u, v, w = U / rho, V / rho, Wm / rho
+            pp = pressure_perturbation(Tp, rt0[es], p0[es], gamma)
+            rt = rt0[es] + Tp
+            r[0, es] = weak((U, V, Wm))
+            r[1, es] = weak((U * u + pp, U * v, U * w)) + W_ * (f * V)
+            r[2, es] = weak((V * u, V * v + pp, V * w)) + W_ * (-f * U)
+            r[3, es] = weak((Wm * u, Wm * v, Wm * w + pp)) + W_ * (-rp * g)
+            r[4, es] = weak((rt * u, rt * v, rt * w))
+        else:
+            u, v, w, thp = q[1], q[2], q[3], q[4]
+            rtp = rho0[es] * thp + rp * (theta0[es] + thp)
+            pp = pressure_perturbation(rtp, rt0[es], p0[es], gamma)
+            r[0, es] = weak((rho * u, rho * v, rho * w))
+            gu, gv, gw, gp, gt = grad(u), grad(v), grad(w), grad(pp), grad(thp)
+            adv = lambda gq: u * gq[0] + v * gq[1] + w * gq[2]
+            su = -adv(gu) - gp[0] / rho + f * v
+            sv = -adv(gv) - gp[1] / rho - f * u
+            sw = -adv(gw) - gp[2] / rho - (rp / rho) * g
+            st = -w * dth0[es] - adv(gt)
+            r[1, es] = W_ * su
+            r[2, es] = W_ * sv
+            r[3, es] = W_ * sw
+            r[4, es] = W_ * st
+    return r
+
+
+def rhs(mesh, qG, prm, eqset="C"):
+    """Tendency dq_G/dt = (Q^T r_L) / M with the lid condition, shape (5, NG)."""
+    qL = mesh.to_local(qG)
+    r = element_residual(mesh, qL, prm, eqset)
+    R = mesh.assemble(r)
+    T = R / mesh.M[None, :]
+    T[3, mesh.z_bottom | mesh.z_top] = 0.0
+    return T
