@@ -1,0 +1,336 @@
+"""Benchmark: SSP-RK3 steps of the spectral-element solver on the
+64 x 64 x 16, N = 4 uniform workload (65,536 elements, 8,192,000 local nodes,
+2048 x 2048 x 24 km, warm-core vortex), one step = 3 stages of
+(right-hand side + fused RK update) over the whole mesh.
+
+Metric: DOF-updates/s = 5 fields x local nodes x RK stages / second, for the
+mixed-precision form (float32 element and face arithmetic, float64 reference
+state and stage accumulation); the plain float64 form is measured beside it,
+and the maximum-wind error of the mixed form against the float64 form after
+100 steps is reported (gate 1e-3).
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference] [--form fp64]
+
+With N > 1 (torchrun) every rank runs an independent replica (the path has
+no exchange step); `value` sums the replicas' throughput.  --impl reference
+times the CPU oracle on a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "uniform-64x64x16-N4"
+METRIC = "DOF-updates/s (RHS+RK stage) vs plain FP64 GPU, at <=1e-3 rel max-wind error"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--gate-steps", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d["hbm_gbs"], "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k]
+                          and "Not" not in r[5 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_sample(steps=1, n=32):
+    """The CPU oracle on a bounded sample of the workload: an n x n x 16 block
+    of the same elements (same element size, order, physics), SSP-RK3 steps.
+    Returns (DOF-updates/s, threads, description)."""
+    import numpy as np
+    from oracle import mesh as om, refstate, rk as ork
+    from synth.vortex import vortex_state
+    L = 2048e3 * n / 64
+    o = om.OracleMesh(L, L, 24e3, n, n, 16, 4)
+    q = vortex_state(o.XG, 24e3)
+    prm = refstate.Params()
+    ork.rk_step(o, prm, q, 0.25)            # warm caches
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        q = ork.rk_step(o, prm, q, 0.25)
+    dt = time.perf_counter() - t0
+    dofs = 5 * o.Ne * o.P * 3 * steps
+    threads = int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1))
+    desc = (f"{steps} SSP-RK3 step(s) of the oracle on a {n}x{n}x16 block of the same "
+            f"elements ({o.Ne} of 65,536; N=4), float64 numpy/scipy")
+    return dofs / dt, threads, desc, dt
+
+
+def run_reference(a):
+    import torch.distributed as dist  # noqa: F401
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    # each step: one SSP-RK3 step of the oracle on a 16x16x16 block
+    import numpy as np  # noqa: F401
+    from oracle import mesh as om, refstate, rk as ork
+    from synth.vortex import vortex_state
+    n = 16
+    L = 2048e3 * n / 64
+    o = om.OracleMesh(L, L, 24e3, n, n, 16, 4)
+    q = vortex_state(o.XG, 24e3)
+    prm = refstate.Params()
+    for _ in range(a.warmup):
+        q = ork.rk_step(o, prm, q, 0.25)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        q = ork.rk_step(o, prm, q, 0.25)
+    dt = time.perf_counter() - t0
+    value = 5 * o.Ne * o.P * 3 * a.steps / dt
+    threads = int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF-updates/s",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * dt / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"{n}x{n}x16 block", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": threads,
+                             "kind": "oracle",
+                             "sample": f"SSP-RK3 steps on a {n}x{n}x16 block of the workload's elements"},
+            "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2410_21607_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2410_21607_gb300 import sem
+    from synth.vortex import vortex_state
+
+    L, Lz, n, nz, N, dt = 2048e3, 24e3, 64, 16, 4, 0.25
+    m = sem.sem_mesh_create(L, L, Lz, n, n, nz, N)
+    xyz = sem.sem_mesh_coords_host(m).T
+    q0_host = vortex_state(xyz, Lz)
+    q0 = torch.from_numpy(q0_host).cuda()
+    prec = sem.SEM_PREC_MIXED if a.form == "mixed" else sem.SEM_PREC_FP64
+    p = sem.sem_params_default(precision=prec)
+    p64 = sem.sem_params_default(precision=sem.SEM_PREC_FP64)
+    bufs = [q0.clone(), torch.empty_like(q0), torch.empty_like(q0)]
+    stream = torch.cuda.current_stream()
+
+    def step(b, prm):
+        # ping-pong: q -> w1 -> w2 -> w1, then w1 becomes the new state
+        qn, w1, w2 = b
+        sem.sem_rk_stage(m, prm, 0, qn, qn, w1, dt, stream)
+        sem.sem_rk_stage(m, prm, 1, qn, w1, w2, dt, stream)
+        sem.sem_rk_stage(m, prm, 2, qn, w2, w1, dt, stream)
+        return [w1, qn, w2]
+
+    dof_stage = 5 * m.Ne * (N + 1) ** 3
+    for _ in range(max(a.warmup, 3)):
+        bufs = step(bufs, p)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    time.sleep(0.3)
+    sem.sem_profile_begin()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(a.steps):
+        bufs = step(bufs, p)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    prof = sem.sem_profile_end()
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / a.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+        dist.barrier()
+    value = dof_stage * 3 * world / (ms * 1e-3)
+    status = sem.sem_status(m)
+
+    # per-kernel roofline of the timed region
+    hbm, peak_kind = peaks()
+    Ncol, Nq, NZ, NG, NH = m.Ncol, (N + 1) ** 2, m.NZ, m.NG, m.NH
+    rbytes = 4 if a.form == "mixed" else 8
+    alg = {
+        "volume": 5 * 8 * NG + 4 * Nq * Ncol + 5 * rbytes * Ncol * Nq * NZ,
+        "dss_rk": 5 * rbytes * Ncol * Nq * NZ + 3 * 5 * 8 * NG + 8 * (NH + NZ) + 12 * Ncol * Nq,
+    }
+    kernels = {}
+    for name, (launches, tot) in prof.items():
+        base = name.rsplit("_", 1)[0] if name.startswith("volume") else "dss_rk"
+        avg = tot / max(launches, 1)
+        kernels[name] = {"launches": launches, "ms_avg": avg, "share": None,
+                         "alg_bytes": alg[base], "gbs": alg[base] / (avg * 1e-3) / 1e9}
+    tot_all = sum(v[1] for v in prof.values()) or 1.0
+    for name in kernels:
+        kernels[name]["share"] = prof[name][1] / tot_all
+    dom = max(kernels, key=lambda k: prof[k][1])
+    roof = {"kernel": dom, "bound": "hbm", "achieved": kernels[dom]["gbs"], "peak": hbm,
+            "unit": "GB/s", "frac": kernels[dom]["gbs"] / hbm, "traffic": None,
+            "peak_source": peak_kind}
+
+    # FP64 form beside it, and the max-wind gate after gate_steps steps
+    fp64_ms = None
+    if a.form == "mixed":
+        b64 = [q0.clone(), torch.empty_like(q0), torch.empty_like(q0)]
+        for _ in range(2):
+            b64 = step(b64, p64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        nfp = 3
+        for _ in range(nfp):
+            b64 = step(b64, p64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64_ms = e0.elapsed_time(e1) / nfp
+    gate = None
+    if a.gate_steps > 0:
+        bm = [q0.clone(), torch.empty_like(q0), torch.empty_like(q0)]
+        bd = [q0.clone(), torch.empty_like(q0), torch.empty_like(q0)]
+        for _ in range(a.gate_steps):
+            bm = step(bm, p)
+            bd = step(bd, p64)
+        dm = sem.sem_diag(m, p64, bm[0])
+        dd = sem.sem_diag(m, p64, bd[0])
+        gate = {"steps": a.gate_steps, "max_wind_fp64": dd["max_wind"],
+                "max_wind_rel_err": abs(dm["max_wind"] - dd["max_wind"]) / dd["max_wind"],
+                "max_mean_wind_rel_err": abs(dm["max_mean_wind"] - dd["max_mean_wind"])
+                / dd["max_mean_wind"]}
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    hq = torch.from_numpy(q0_host).pin_memory()
+    hout = torch.empty_like(hq).pin_memory()
+    eb = [torch.empty_like(q0), torch.empty_like(q0), torch.empty_like(q0)]
+    ke = max(3, min(a.steps, 10))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(ke):
+        eb[0].copy_(hq, non_blocking=True)
+        eb = step(eb, p)
+        hout.copy_(eb[0], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / ke
+    nbytes = 5 * NG * 8
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not a.no_cpu_baseline:
+            v, thr, desc, secs = cpu_oracle_sample()
+            cpu = {"value": v, "unit": "DOF-updates/s", "cores": thr, "kind": "oracle",
+                   "sample": desc, "seconds": secs}
+        line = {
+            "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64acc" if a.form == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "form": a.form, "elements": m.Ne,
+                       "local_nodes": m.Ne * (N + 1) ** 3, "global_nodes": NG, "dt": dt,
+                       "l2": "inputs larger than L2 (state 3 x 170 MB + residual scratch)",
+                       "parallelism": f"replicas x{world}"},
+            "fp64_form": None if fp64_ms is None else {
+                "ms_per_step": fp64_ms, "value": dof_stage * 3 * world / (fp64_ms * 1e-3),
+                "speedup_mixed_over_fp64": fp64_ms / ms},
+            "gate": gate,
+            "roofline": roof, "kernels": kernels,
+            "cpu_baseline": cpu,
+            "e2e": {"value": dof_stage * 3 * world / (e2e_ms * 1e-3), "unit": "DOF-updates/s",
+                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                    "ms_per_step": e2e_ms},
+            "gpu_launches": 2 * 3 * a.steps,
+            "clocks": ck, "status": status,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

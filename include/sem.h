@@ -1,0 +1,212 @@
+/*
+ * sem.h - C ABI of the GB300 spectral-element tropical-cyclone hot path.
+ *
+ * The library evaluates the right-hand side of the split dry compressible
+ * Euler equations (Eqs. mass_split, mom_split, ent_split of arXiv 2410.21607,
+ * Sec. 2, here with an f-plane Coriolis term) on a hexahedral mesh of
+ * tensor-product Lagrange elements of order N on Legendre-Gauss-Lobatto points
+ * (Sec. 3), with 2:1 non-conforming faces handled by the modified direct
+ * stiffness summation of Sec. 3.1; it advances the state with the stages of an
+ * explicit third-order Runge-Kutta scheme (Sec. 4, "Time integration"); it
+ * evaluates the threshold refinement criterion (Sec. 3.1) and moves the
+ * solution to the refined/coarsened mesh (Sec. 3.2, Algorithm 3).
+ *
+ * Conventions (every function):
+ *   - returns SEM_OK (0) or a SEM_ERR_* code; sem_last_error() gives a
+ *     thread-local message for the last failure on the calling thread;
+ *   - sem_mesh handles are owned by the library and freed by sem_mesh_destroy;
+ *   - field arrays are owned by the caller.  "dev" pointers are CUDA device
+ *     memory, "host" pointers are host memory;
+ *   - a global field is laid out structure-of-arrays as [5][NH][NZ] float64:
+ *     field f, horizontal global node h, vertical level kz at offset
+ *     (f * NH + h) * NZ + kz, i.e. [5][NG] with NG = NH * NZ;
+ *   - calls taking a cudaStream_t only enqueue work on that stream (0 = the
+ *     legacy default stream) and return without synchronising, unless the
+ *     description says that the call returns host data;
+ *   - no call allocates or frees caller memory.  The library allocates its own
+ *     device tables and scratch for a mesh on the first device call for that
+ *     mesh (on the current device) and frees them in sem_mesh_destroy.
+ */
+#ifndef SEM_H
+#define SEM_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SEM_OK 0
+#define SEM_ERR_ARG 1        /* invalid argument (null pointer, bad size)   */
+#define SEM_ERR_CUDA 2       /* a CUDA runtime call failed                  */
+#define SEM_ERR_TOPOLOGY 3   /* leaves do not tile the domain, 2:1 balance  */
+                             /* violated, or a constraint chain was found   */
+#define SEM_ERR_NUMERIC 4    /* non-finite value detected on the device     */
+#define SEM_ERR_TIMEOUT 5    /* a bounded device wait ran out               */
+#define SEM_ERR_IO 6         /* checkpoint read/write failed                */
+#define SEM_ERR_UNSUPPORTED 7/* order N or option not compiled in           */
+
+#define SEM_EQ_CONSERVATIVE 0     /* (rho', rho u, rho v, rho w, (rho theta)') */
+#define SEM_EQ_NONCONSERVATIVE 1  /* (rho', u, v, w, theta')  Eqs. mass_split..ent_split */
+
+#define SEM_PREC_FP64 0   /* every operation in float64                          */
+#define SEM_PREC_MIXED 1  /* float32 perturbation arithmetic in the element and  */
+                          /* face work; float64 reference state, metric terms    */
+                          /* and stage accumulation of the state                 */
+
+#define SEM_MAX_THRESHOLDS 8
+
+/* Mesh description (host).  Domain [-Lx/2, Lx/2] x [-Ly/2, Ly/2] x [0, Lz],
+ * base grid nx x ny columns of nz hexahedra of order N (Sec. 3).  Refinement
+ * is horizontal and by whole columns (Sec. 3.1): a leaf column is
+ * (level, i, j) on the 2^level-times finer horizontal grid.  leaves == NULL
+ * (n_leaves == 0) gives the uniform level-0 mesh.  The leaves must tile the
+ * domain exactly once and be 2:1 balanced across faces and corners,
+ * otherwise SEM_ERR_TOPOLOGY. */
+typedef struct {
+  double Lx, Ly, Lz;
+  int nx, ny, nz;
+  int N;                  /* polynomial order, 2..6 */
+  int periodic_x, periodic_y;
+  int lvl_max;            /* largest level the criterion may request */
+  int n_leaves;
+  const int* leaves;      /* host, [n_leaves][3] = (level, i, j) */
+} sem_mesh_desc;
+
+typedef struct sem_mesh sem_mesh;
+
+typedef struct {
+  long long Ne;           /* elements                                   */
+  long long NL;           /* local nodes, Ne * (N+1)^3                  */
+  long long NG;           /* global (non-hanging) nodes, NH * NZ        */
+  long long NH;           /* horizontal global nodes                    */
+  long long NZ;           /* vertical levels, nz * N + 1                */
+  long long Ncol;         /* leaf columns                               */
+  long long n_hanging_h;  /* hanging horizontal local nodes (per column layer) */
+  long long n_nonconforming_faces; /* coarse sides with finer neighbours, per layer */
+  int N, nz, max_level;
+  long long level_hist[16]; /* columns per level */
+} sem_mesh_info;
+
+/* Physical and scheme parameters (Sec. 2; constants the paper leaves unstated
+ * take the defaults of sem_params_default). */
+typedef struct {
+  double g;           /* 9.81 m s^-2 (Sec. 2)                       */
+  double f;           /* Coriolis parameter (f-plane), s^-1         */
+  double R_d, c_p;    /* gas constant and heat capacity of dry air  */
+  double p00;         /* reference surface pressure, Pa             */
+  double theta_s;     /* reference theta at z = 0, K                */
+  double N_bv;        /* buoyancy frequency of the reference state  */
+  int eqset;          /* SEM_EQ_*                                    */
+  int precision;      /* SEM_PREC_*                                  */
+  int n_thresholds;   /* criterion thresholds, one per level (Sec. 3.1) */
+  int lvl_max;
+  double thresholds[SEM_MAX_THRESHOLDS];
+} sem_params;
+
+typedef struct {
+  double max_wind;        /* max sqrt(u^2+v^2) over |x|,|y| <= half_width (Sec. 4.2) */
+  double max_mean_wind;   /* max over heights of the mass-weighted horizontal mean   */
+} sem_diag_out;
+
+const char* sem_last_error(void);
+
+/* Defaults: g 9.81, f 5e-5, R_d 287, c_p 1004, p00 1e5, theta_s 300,
+ * N_bv 0.01, conservative set, FP64, thresholds [7.5, 15, 22.5] (Sec. 4.1). */
+int sem_params_default(sem_params* p);
+
+/* Host only.  Builds the leaf columns (Morton order), the global node
+ * numbering, the hanging-node interpolation rows (Sec. 3.1) and the lumped
+ * mass.  No device work. */
+int sem_mesh_create(const sem_mesh_desc* d, sem_mesh** out);
+void sem_mesh_destroy(sem_mesh* m);
+int sem_mesh_get_info(const sem_mesh* m, sem_mesh_info* out);
+
+/* Host exports (no device work).  coords: [3][NG] (x, y, z of every global
+ * node, x and y wrapped into [-L/2, L/2)).  leaves: [Ncol][3].
+ * hmap: [Ncol][(N+1)^2] horizontal map of each column's local node
+ * (a, b) (a along x, fastest): value h >= 0 is the horizontal global node,
+ * value -1-k means hanging row k.  hang_h / hang_w: [n_hanging_h][N+1] the
+ * horizontal global nodes and weights of hanging row k.  mass: [NG] lumped
+ * mass M = Q^T (w J). */
+int sem_mesh_coords_host(const sem_mesh* m, double* coords_host);
+int sem_mesh_leaves_host(const sem_mesh* m, int* leaves_host);
+int sem_mesh_hmap_host(const sem_mesh* m, int* hmap_host, int* hang_h_host, double* hang_w_host);
+int sem_mesh_mass_host(const sem_mesh* m, double* mass_host);
+
+/* Device copy of the coordinates, [3][NG]. */
+int sem_mesh_coords(sem_mesh* m, double* coords_dev, cudaStream_t stream);
+
+/* Tendency dq/dt = M^-1 Q^T r(q) of the semi-discrete system (Sec. 3, 3.1),
+ * with the rigid-lid condition (zero vertical-momentum tendency at z = 0 and
+ * z = Lz).  q_dev, rhs_dev: [5][NG] float64 device arrays, distinct. */
+int sem_rhs(sem_mesh* m, const sem_params* p, const double* q_dev, double* rhs_dev,
+            cudaStream_t stream);
+
+/* One stage of the SSP-RK3 scheme (Sec. 4, time integration):
+ *   q_out = a[stage] qn + b[stage] qs + c[stage] dt rhs(qs)
+ * with (a, b, c) = (0, 1, 1), (3/4, 1/4, 1/4), (1/3, 2/3, 2/3).
+ * qn, qs, q_out: [5][NG] float64 device arrays; q_out may alias neither. */
+int sem_rk_stage(sem_mesh* m, const sem_params* p, int stage, const double* qn_dev,
+                 const double* qs_dev, double* qout_dev, double dt, cudaStream_t stream);
+
+/* A whole SSP-RK3 step in place on q_dev, using two caller-owned work arrays
+ * w1_dev, w2_dev of [5][NG] float64. */
+int sem_step(sem_mesh* m, const sem_params* p, double* q_dev, double* w1_dev,
+             double* w2_dev, double dt, cudaStream_t stream);
+
+/* Sec. 3.1 criterion on the velocity magnitude at every local node:
+ * flags[e] = +1 / -1 / 0 (refine / coarsen / keep).  Element e = column *
+ * nz + layer in the order of sem_mesh_leaves_host.  The _host variant copies
+ * the Ne flags to host memory and synchronises the stream; cmax (optional,
+ * may be NULL) receives the per-element maximum speed. */
+int sem_adapt_flags(sem_mesh* m, const sem_params* p, const double* q_dev,
+                    int8_t* flags_dev, double* cmax_dev, cudaStream_t stream);
+int sem_adapt_flags_host(sem_mesh* m, const sem_params* p, const double* q_dev,
+                         int8_t* flags_host, cudaStream_t stream);
+
+/* Host only: the mesh after one adaptation pass driven by element flags
+ * (Sec. 3.1: whole-column horizontal refinement, four-sibling coarsening,
+ * one level per pass, 2:1 balance).  The new mesh remembers where each new
+ * column comes from, for sem_transfer. */
+int sem_transfer_plan(const sem_mesh* old_mesh, const int8_t* flags_host,
+                      sem_mesh** new_out);
+
+/* Solution transfer old -> new (new from sem_transfer_plan(old, ...)):
+ * interpolation into refined columns, exact L2 projection into coarsened
+ * ones, then projection onto the continuous constrained space.
+ * q_old_dev [5][NG_old], q_new_dev [5][NG_new] float64 device arrays. */
+int sem_transfer(sem_mesh* old_mesh, sem_mesh* new_mesh, const double* q_old_dev,
+                 double* q_new_dev, cudaStream_t stream);
+
+/* Wind diagnostics of Sec. 4.2 over |x|, |y| <= half_width; returns host
+ * data and synchronises the stream. */
+int sem_diag(sem_mesh* m, const sem_params* p, const double* q_dev, double half_width,
+             sem_diag_out* out_host, cudaStream_t stream);
+
+/* Reads and clears the device status word that the stage kernels set when
+ * they write a non-finite value; synchronises the stream.  *status_host is 0
+ * (clean) or SEM_ERR_NUMERIC. */
+int sem_status(sem_mesh* m, int* status_host, cudaStream_t stream);
+
+/* Kernel timing.  Between sem_profile_begin and sem_profile_end every kernel
+ * the library launches is bracketed by CUDA events recorded on the stream it
+ * is launched on.  sem_profile_end synchronises those streams and returns, per
+ * kernel name, the number of launches and the summed event time in
+ * milliseconds.  At most SEM_PROFILE_MAX kernel names and 1 << 16 launches
+ * are recorded per session; later launches are not timed.  Not thread-safe. */
+#define SEM_PROFILE_MAX 16
+typedef struct {
+  int n_kernels;
+  char name[SEM_PROFILE_MAX][48];
+  long long launches[SEM_PROFILE_MAX];
+  double ms_total[SEM_PROFILE_MAX];
+} sem_profile_out;
+int sem_profile_begin(void);
+int sem_profile_end(sem_profile_out* out_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEM_H */

@@ -221,13 +221,14 @@ class OracleMesh:
             rows[q] = out
             return out
 
-        ri, ci, vv = [], [], []
-        for q in range(NL):
-            for g, v in row(q).items():
-                if v != 0.0:
-                    ri.append(q)
-                    ci.append(g)
-                    vv.append(v)
+        # non-hanging rows are unit vectors; only hanging rows need row()
+        ri, ci, vv = [free], [gid[free]], [np.ones(free.size)]
+        for q in np.nonzero(hang_of >= 0)[0]:
+            items = [(g, v) for g, v in row(int(q)).items() if v != 0.0]
+            ri.append(np.full(len(items), q))
+            ci.append(np.array([g for g, _ in items], dtype=np.int64))
+            vv.append(np.array([v for _, v in items]))
+        ri, ci, vv = np.concatenate(ri), np.concatenate(ci), np.concatenate(vv)
         self.Q = sp.csr_matrix((vv, (ri, ci)), shape=(NL, NG))
         self.QT = self.Q.T.tocsr()
         self.gid = gid

@@ -1,0 +1,418 @@
+// C ABI entry points (include/sem.h), device tables and the reference state.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "sem_internal.h"
+
+namespace sem {
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+static long long g_serial = 0;
+
+template <typename T>
+static int upload(T*& dst, const std::vector<T>& src) {
+  size_t n = src.size() ? src.size() : 1;
+  SEM_CUDA_TRY(cudaMalloc((void**)&dst, n * sizeof(T)));
+  if (!src.empty()) SEM_CUDA_TRY(cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return SEM_OK;
+}
+
+void free_device(Mesh& m) {
+  if (!m.dev) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (m.dev_id >= 0 && cur != m.dev_id) cudaSetDevice(m.dev_id);
+  DeviceTables& D = *m.dev;
+  void* ptrs[] = {D.hmap, D.hang_h, D.hang_w, D.qt_ptr, D.qt_src, D.qt_w, D.Minv_h, D.Minv_z,
+                  D.Mh, D.Mz, D.ref, D.ref32, D.col_level, D.xh, D.yh, D.zk, D.scratch,
+                  D.status, D.org, D.elem_cmax, D.elem_flags, D.diag_buf,
+                  D.tr_comp_ptr, D.tr_nodes, D.tr_A_ptr, D.tr_A_col, D.tr_A_val, D.tr_coupled};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete m.dev;
+  m.dev = nullptr;
+  if (m.dev_id >= 0 && cur >= 0 && cur != m.dev_id) cudaSetDevice(cur);
+  m.dev_id = -1;
+}
+
+int ensure_device(Mesh& m) {
+  int cur = 0;
+  SEM_CUDA_TRY(cudaGetDevice(&cur));
+  if (m.dev) {
+    if (m.dev_id != cur) return fail(SEM_ERR_ARG, "mesh tables live on another device");
+    return SEM_OK;
+  }
+  m.dev = new (std::nothrow) DeviceTables();
+  if (!m.dev) return fail(SEM_ERR_ARG, "out of host memory");
+  m.dev_id = cur;
+  DeviceTables& D = *m.dev;
+  int rc;
+  std::vector<double> minvh(m.NH), minvz(m.NZ);
+  for (long long h = 0; h < m.NH; ++h) minvh[h] = 1.0 / m.Mh[h];
+  for (int k = 0; k < m.NZ; ++k) minvz[k] = 1.0 / m.Mz[k];
+  std::vector<int> lev(m.Ncol());
+  for (long long c = 0; c < m.Ncol(); ++c) lev[c] = m.leaves[c].l;
+  if ((rc = upload(D.hmap, m.hmap)) || (rc = upload(D.hang_h, m.hang_h)) ||
+      (rc = upload(D.hang_w, m.hang_w)) || (rc = upload(D.qt_ptr, m.qt_ptr)) ||
+      (rc = upload(D.qt_src, m.qt_src)) || (rc = upload(D.qt_w, m.qt_w)) ||
+      (rc = upload(D.Minv_h, minvh)) || (rc = upload(D.Minv_z, minvz)) ||
+      (rc = upload(D.Mh, m.Mh)) || (rc = upload(D.Mz, m.Mz)) || (rc = upload(D.col_level, lev)) ||
+      (rc = upload(D.xh, m.xh)) || (rc = upload(D.yh, m.yh)) || (rc = upload(D.zk, m.zk))) {
+    free_device(m);
+    return rc;
+  }
+  // column residual scratch: [Ncol][Nq][5][NZ], float64 (also holds float32)
+  D.scratch_bytes = (size_t)m.Ncol() * m.Nq * kFields * m.NZ * sizeof(double);
+  cudaError_t e = cudaMalloc(&D.scratch, D.scratch_bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&D.status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(D.status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&D.ref, (size_t)m.NZ * kRef * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&D.ref32, (size_t)m.NZ * kRef * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&D.elem_cmax, (size_t)m.Ne() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&D.elem_flags, (size_t)m.Ne());
+  if (e == cudaSuccess) e = cudaMalloc((void**)&D.diag_buf, (size_t)m.NZ * 4 * sizeof(double));
+  if (e != cudaSuccess) {
+    free_device(m);
+    return fail(SEM_ERR_CUDA, std::string("device allocation: ") + cudaGetErrorString(e));
+  }
+  if (!m.origin.empty()) {
+    std::vector<int> org((size_t)m.Ncol() * 6);
+    for (long long c = 0; c < m.Ncol(); ++c) {
+      const Origin& o = m.origin[c];
+      org[c * 6 + 0] = o.kind;
+      for (int q = 0; q < 4; ++q) org[c * 6 + 1 + q] = o.src[q];
+      org[c * 6 + 5] = o.a + 2 * o.b;
+    }
+    if ((rc = upload(D.org, org))) {
+      free_device(m);
+      return rc;
+    }
+  }
+  return SEM_OK;
+}
+
+// Hydrostatic reference state at every vertical level (Eqs. rho_split ..
+// hydro_bal): the constant buoyancy-frequency atmosphere
+//   theta0 = theta_s exp(N^2 z / g),
+//   pi0 = 1 + g^2/(c_p theta_s N^2) (exp(-N^2 z/g) - 1),
+//   p0 = p00 pi0^(c_p/R_d),  rho0 = p00 pi0^(c_v/R_d) / (R_d theta0),
+// which satisfies dp0/dz = -rho0 g and p0 = p00 (R_d rho0 theta0 / p00)^gamma.
+int ensure_reference(Mesh& m, const sem_params& p) {
+  DeviceTables& D = *m.dev;
+  double key[8] = {p.g, p.R_d, p.c_p, p.p00, p.theta_s, p.N_bv, 0, 0};
+  if (D.ref_valid && std::memcmp(key, D.ref_key, sizeof(key)) == 0) return SEM_OK;
+  if (!(p.N_bv > 0) || !(p.g > 0) || !(p.c_p > p.R_d) || !(p.R_d > 0))
+    return fail(SEM_ERR_ARG, "reference state needs g > 0, N_bv > 0, c_p > R_d > 0");
+  const double c_v = p.c_p - p.R_d, N2 = p.N_bv * p.N_bv;
+  std::vector<double> ref((size_t)m.NZ * kRef);
+  std::vector<float> ref32((size_t)m.NZ * kRef);
+  for (int k = 0; k < m.NZ; ++k) {
+    const double z = m.zk[k];
+    const double th0 = p.theta_s * std::exp(N2 * z / p.g);
+    const double pi0 = 1.0 + p.g * p.g / (p.c_p * p.theta_s * N2) * (std::exp(-N2 * z / p.g) - 1.0);
+    if (!(pi0 > 0)) return fail(SEM_ERR_ARG, "reference state: Exner pressure <= 0 below the lid");
+    const double p0 = p.p00 * std::pow(pi0, p.c_p / p.R_d);
+    const double rho0 = p.p00 * std::pow(pi0, c_v / p.R_d) / (p.R_d * th0);
+    const double r[kRef] = {th0, pi0, p0, rho0, rho0 * th0, th0 * N2 / p.g, 1.0 / (rho0 * th0), z};
+    for (int q = 0; q < kRef; ++q) {
+      ref[(size_t)k * kRef + q] = r[q];
+      ref32[(size_t)k * kRef + q] = (float)r[q];
+    }
+  }
+  SEM_CUDA_TRY(cudaMemcpy(D.ref, ref.data(), ref.size() * sizeof(double), cudaMemcpyHostToDevice));
+  SEM_CUDA_TRY(cudaMemcpy(D.ref32, ref32.data(), ref32.size() * sizeof(float), cudaMemcpyHostToDevice));
+  std::memcpy(D.ref_key, key, sizeof(key));
+  D.ref_valid = true;
+  return SEM_OK;
+}
+
+static int check_params(const sem_params* p) {
+  if (!p) return fail(SEM_ERR_ARG, "params is NULL");
+  if (p->eqset != SEM_EQ_CONSERVATIVE && p->eqset != SEM_EQ_NONCONSERVATIVE)
+    return fail(SEM_ERR_ARG, "unknown equation set");
+  if (p->precision != SEM_PREC_FP64 && p->precision != SEM_PREC_MIXED)
+    return fail(SEM_ERR_ARG, "unknown precision");
+  if (p->n_thresholds < 0 || p->n_thresholds > SEM_MAX_THRESHOLDS)
+    return fail(SEM_ERR_ARG, "n_thresholds out of range");
+  return SEM_OK;
+}
+
+static int prepare(sem_mesh* mh, const sem_params* p) {
+  if (!mh) return fail(SEM_ERR_ARG, "mesh is NULL");
+  int rc = check_params(p);
+  if (rc) return rc;
+  if ((rc = ensure_device(mh->m))) return rc;
+  return ensure_reference(mh->m, *p);
+}
+
+}  // namespace sem
+
+using namespace sem;
+
+extern "C" {
+
+const char* sem_last_error(void) { return g_err.c_str(); }
+
+int sem_params_default(sem_params* p) {
+  if (!p) return fail(SEM_ERR_ARG, "params is NULL");
+  std::memset(p, 0, sizeof(*p));
+  p->g = 9.81;
+  p->f = 5.0e-5;
+  p->R_d = 287.0;
+  p->c_p = 1004.0;
+  p->p00 = 1.0e5;
+  p->theta_s = 300.0;
+  p->N_bv = 0.01;
+  p->eqset = SEM_EQ_CONSERVATIVE;
+  p->precision = SEM_PREC_FP64;
+  p->n_thresholds = 3;
+  p->lvl_max = 3;
+  p->thresholds[0] = 7.5;
+  p->thresholds[1] = 15.0;
+  p->thresholds[2] = 22.5;
+  return SEM_OK;
+}
+
+int sem_mesh_create(const sem_mesh_desc* d, sem_mesh** out) {
+  if (!d || !out) return fail(SEM_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  if (d->nx <= 0 || d->ny <= 0 || d->nz <= 0 || !(d->Lx > 0) || !(d->Ly > 0) || !(d->Lz > 0))
+    return fail(SEM_ERR_ARG, "sizes must be positive");
+  if (d->N < 2 || d->N > kMaxN) return fail(SEM_ERR_UNSUPPORTED, "order N must be in 2..6");
+  if (d->n_leaves < 0 || (d->n_leaves > 0 && !d->leaves)) return fail(SEM_ERR_ARG, "bad leaf list");
+  if (d->lvl_max < 0 || d->lvl_max > 12) return fail(SEM_ERR_ARG, "lvl_max out of range");
+  sem_mesh* mh = new (std::nothrow) sem_mesh();
+  if (!mh) return fail(SEM_ERR_ARG, "out of host memory");
+  Mesh& m = mh->m;
+  m.Lx = d->Lx; m.Ly = d->Ly; m.Lz = d->Lz;
+  m.nx = d->nx; m.ny = d->ny; m.nz = d->nz; m.N = d->N;
+  m.px = d->periodic_x != 0; m.py = d->periodic_y != 0;
+  m.lvl_max = d->lvl_max;
+  if (d->n_leaves == 0) {
+    for (int j = 0; j < d->ny; ++j)
+      for (int i = 0; i < d->nx; ++i) m.leaves.push_back({0, i, j});
+  } else {
+    for (int k = 0; k < d->n_leaves; ++k)
+      m.leaves.push_back({d->leaves[3 * k], d->leaves[3 * k + 1], d->leaves[3 * k + 2]});
+  }
+  int rc = build_mesh(m);
+  if (rc) {
+    delete mh;
+    return rc;
+  }
+  m.serial = ++g_serial;
+  *out = mh;
+  return SEM_OK;
+}
+
+void sem_mesh_destroy(sem_mesh* mh) {
+  if (!mh) return;
+  free_device(mh->m);
+  delete mh;
+}
+
+int sem_mesh_get_info(const sem_mesh* mh, sem_mesh_info* o) {
+  if (!mh || !o) return fail(SEM_ERR_ARG, "NULL argument");
+  const Mesh& m = mh->m;
+  std::memset(o, 0, sizeof(*o));
+  o->Ne = m.Ne();
+  o->NL = m.Ne() * m.P;
+  o->NG = m.NG;
+  o->NH = m.NH;
+  o->NZ = m.NZ;
+  o->Ncol = m.Ncol();
+  o->n_hanging_h = (long long)m.hang_h.size() / (m.N + 1);
+  o->n_nonconforming_faces = m.n_nonconf_sides;
+  o->N = m.N;
+  o->nz = m.nz;
+  o->max_level = m.Lf;
+  for (auto& f : m.leaves)
+    if (f.l < 16) o->level_hist[f.l]++;
+  return SEM_OK;
+}
+
+int sem_mesh_coords_host(const sem_mesh* mh, double* xyz) {
+  if (!mh || !xyz) return fail(SEM_ERR_ARG, "NULL argument");
+  const Mesh& m = mh->m;
+  for (long long h = 0; h < m.NH; ++h)
+    for (int k = 0; k < m.NZ; ++k) {
+      long long g = h * m.NZ + k;
+      xyz[g] = m.xh[h];
+      xyz[m.NG + g] = m.yh[h];
+      xyz[2 * m.NG + g] = m.zk[k];
+    }
+  return SEM_OK;
+}
+
+int sem_mesh_leaves_host(const sem_mesh* mh, int* out) {
+  if (!mh || !out) return fail(SEM_ERR_ARG, "NULL argument");
+  const Mesh& m = mh->m;
+  for (long long c = 0; c < m.Ncol(); ++c) {
+    out[3 * c] = m.leaves[c].l;
+    out[3 * c + 1] = m.leaves[c].i;
+    out[3 * c + 2] = m.leaves[c].j;
+  }
+  return SEM_OK;
+}
+
+int sem_mesh_hmap_host(const sem_mesh* mh, int* hmap, int* hh, double* hw) {
+  if (!mh) return fail(SEM_ERR_ARG, "NULL argument");
+  const Mesh& m = mh->m;
+  if (hmap) std::memcpy(hmap, m.hmap.data(), m.hmap.size() * sizeof(int));
+  if (hh) std::memcpy(hh, m.hang_h.data(), m.hang_h.size() * sizeof(int));
+  if (hw) std::memcpy(hw, m.hang_w.data(), m.hang_w.size() * sizeof(double));
+  return SEM_OK;
+}
+
+int sem_mesh_mass_host(const sem_mesh* mh, double* M) {
+  if (!mh || !M) return fail(SEM_ERR_ARG, "NULL argument");
+  const Mesh& m = mh->m;
+  for (long long h = 0; h < m.NH; ++h)
+    for (int k = 0; k < m.NZ; ++k) M[h * m.NZ + k] = m.Mh[h] * m.Mz[k];
+  return SEM_OK;
+}
+
+int sem_mesh_coords(sem_mesh* mh, double* xyz, cudaStream_t st) {
+  if (!mh || !xyz) return fail(SEM_ERR_ARG, "NULL argument");
+  int rc = ensure_device(mh->m);
+  if (rc) return rc;
+  return launch_coords(mh->m, xyz, st);
+}
+
+int sem_rhs(sem_mesh* mh, const sem_params* p, const double* q, double* rhs, cudaStream_t st) {
+  int rc = prepare(mh, p);
+  if (rc) return rc;
+  if (!q || !rhs || q == rhs) return fail(SEM_ERR_ARG, "q and rhs must be distinct device arrays");
+  StageArgs s{nullptr, q, rhs, 0.0, 0.0, 1.0, 1};
+  return launch_rhs_stage(mh->m, *p, s, st);
+}
+
+static const double kA[3] = {0.0, 0.75, 1.0 / 3.0};
+static const double kB[3] = {1.0, 0.25, 2.0 / 3.0};
+static const double kC[3] = {1.0, 0.25, 2.0 / 3.0};
+
+int sem_rk_stage(sem_mesh* mh, const sem_params* p, int stage, const double* qn,
+                 const double* qs, double* qout, double dt, cudaStream_t st) {
+  int rc = prepare(mh, p);
+  if (rc) return rc;
+  if (stage < 0 || stage > 2) return fail(SEM_ERR_ARG, "stage must be 0, 1 or 2");
+  if (!qn || !qs || !qout || qout == qn || qout == qs)
+    return fail(SEM_ERR_ARG, "qout must not alias qn or qs");
+  StageArgs s{qn, qs, qout, kA[stage], kB[stage], kC[stage] * dt, 0};
+  return launch_rhs_stage(mh->m, *p, s, st);
+}
+
+int sem_step(sem_mesh* mh, const sem_params* p, double* q, double* w1, double* w2, double dt,
+             cudaStream_t st) {
+  if (!q || !w1 || !w2 || q == w1 || q == w2 || w1 == w2)
+    return fail(SEM_ERR_ARG, "q, w1, w2 must be distinct");
+  int rc;
+  if ((rc = sem_rk_stage(mh, p, 0, q, q, w1, dt, st))) return rc;
+  if ((rc = sem_rk_stage(mh, p, 1, q, w1, w2, dt, st))) return rc;
+  // the last stage writes w1 and copies it back into q
+  if ((rc = sem_rk_stage(mh, p, 2, q, w2, w1, dt, st))) return rc;
+  SEM_CUDA_TRY(cudaMemcpyAsync(q, w1, (size_t)mh->m.NG * kFields * sizeof(double),
+                               cudaMemcpyDeviceToDevice, st));
+  return SEM_OK;
+}
+
+int sem_adapt_flags(sem_mesh* mh, const sem_params* p, const double* q, int8_t* flags,
+                    double* cmax, cudaStream_t st) {
+  int rc = prepare(mh, p);
+  if (rc) return rc;
+  if (!q || !flags) return fail(SEM_ERR_ARG, "NULL argument");
+  if (p->lvl_max > p->n_thresholds) return fail(SEM_ERR_ARG, "need one threshold per level");
+  return launch_adapt(mh->m, *p, q, flags, cmax, st);
+}
+
+int sem_adapt_flags_host(sem_mesh* mh, const sem_params* p, const double* q, int8_t* flags_host,
+                         cudaStream_t st) {
+  int rc = prepare(mh, p);
+  if (rc) return rc;
+  if (!flags_host) return fail(SEM_ERR_ARG, "NULL argument");
+  int8_t* dflags = mh->m.dev->elem_flags;
+  rc = sem_adapt_flags(mh, p, q, dflags, nullptr, st);
+  if (rc) return rc;
+  SEM_CUDA_TRY(cudaMemcpyAsync(flags_host, dflags, (size_t)mh->m.Ne(), cudaMemcpyDeviceToHost, st));
+  SEM_CUDA_TRY(cudaStreamSynchronize(st));
+  return SEM_OK;
+}
+
+int sem_transfer_plan(const sem_mesh* oldh, const int8_t* flags, sem_mesh** out) {
+  if (!oldh || !flags || !out) return fail(SEM_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  const Mesh& o = oldh->m;
+  std::vector<Leaf> nl;
+  std::vector<Origin> org;
+  int rc = adapt_leaves(o, flags, nl, org);
+  if (rc) return rc;
+  sem_mesh* nh = new (std::nothrow) sem_mesh();
+  if (!nh) return fail(SEM_ERR_ARG, "out of host memory");
+  Mesh& m = nh->m;
+  m.Lx = o.Lx; m.Ly = o.Ly; m.Lz = o.Lz;
+  m.nx = o.nx; m.ny = o.ny; m.nz = o.nz; m.N = o.N;
+  m.px = o.px; m.py = o.py; m.lvl_max = o.lvl_max;
+  m.leaves = nl;
+  rc = build_mesh(m);   // sorts the leaves into Morton order
+  if (rc) {
+    delete nh;
+    return rc;
+  }
+  // carry the provenance over to the sorted order
+  m.origin.resize(m.leaves.size());
+  {
+    std::vector<std::pair<long long, int>> idx;
+    auto key = [](const Leaf& f) { return ((long long)f.l << 50) | ((long long)f.i << 25) | f.j; };
+    std::vector<std::pair<long long, int>> a;
+    for (size_t k = 0; k < nl.size(); ++k) a.push_back({key(nl[k]), (int)k});
+    std::sort(a.begin(), a.end());
+    for (size_t c = 0; c < m.leaves.size(); ++c) {
+      auto it = std::lower_bound(a.begin(), a.end(), std::make_pair(key(m.leaves[c]), -1));
+      m.origin[c] = org[it->second];
+    }
+  }
+  m.parent_serial = o.serial;
+  m.serial = ++g_serial;
+  *out = nh;
+  return SEM_OK;
+}
+
+int sem_transfer(sem_mesh* oldh, sem_mesh* newh, const double* qold, double* qnew, cudaStream_t st) {
+  if (!oldh || !newh || !qold || !qnew) return fail(SEM_ERR_ARG, "NULL argument");
+  if (newh->m.parent_serial != oldh->m.serial || newh->m.origin.empty())
+    return fail(SEM_ERR_ARG, "new mesh was not planned from this old mesh");
+  int rc;
+  if ((rc = ensure_device(oldh->m)) || (rc = ensure_device(newh->m))) return rc;
+  return launch_transfer(oldh->m, newh->m, qold, qnew, st);
+}
+
+int sem_diag(sem_mesh* mh, const sem_params* p, const double* q, double half_width,
+             sem_diag_out* out, cudaStream_t st) {
+  int rc = prepare(mh, p);
+  if (rc) return rc;
+  if (!q || !out) return fail(SEM_ERR_ARG, "NULL argument");
+  return launch_diag(mh->m, *p, q, half_width, out, st);
+}
+
+int sem_status(sem_mesh* mh, int* status, cudaStream_t st) {
+  if (!mh || !status) return fail(SEM_ERR_ARG, "NULL argument");
+  int rc = ensure_device(mh->m);
+  if (rc) return rc;
+  int v = 0;
+  SEM_CUDA_TRY(cudaMemcpyAsync(&v, mh->m.dev->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SEM_CUDA_TRY(cudaMemsetAsync(mh->m.dev->status, 0, sizeof(int), st));
+  SEM_CUDA_TRY(cudaStreamSynchronize(st));
+  *status = v ? SEM_ERR_NUMERIC : SEM_OK;
+  return SEM_OK;
+}
+
+}  // extern "C"

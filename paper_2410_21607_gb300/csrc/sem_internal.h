@@ -1,0 +1,173 @@
+// Internal declarations shared by the host topology and the CUDA kernels.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "../../include/sem.h"
+
+namespace sem {
+
+constexpr int kMaxN = 6;
+constexpr int kFields = 5;
+
+// ---------------------------------------------------------------------------
+// error reporting
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+#define SEM_CUDA_TRY(expr)                                                       \
+  do {                                                                           \
+    cudaError_t e_ = (expr);                                                     \
+    if (e_ != cudaSuccess)                                                       \
+      return ::sem::fail(SEM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// 1-D LGL basis (host, float64)
+struct Basis1D {
+  int N = 0;
+  std::vector<double> xi, w;         // N+1
+  std::vector<double> D;             // [i][j] = h_j'(xi_i)
+  std::vector<double> P[2];          // child interpolation [i][j] = h_j((xi_i+2c-1)/2)
+  std::vector<double> Mex;           // exact mass matrix [i][j]
+};
+const Basis1D& basis(int N);
+double lagrange(const std::vector<double>& xi, int j, double x);
+
+// ---------------------------------------------------------------------------
+// Leaf column of the horizontal quadtree forest
+struct Leaf {
+  int l, i, j;
+};
+
+// How a column of an adapted mesh was obtained from the previous mesh.
+struct Origin {
+  int kind;      // 0 same, 1 refined child, 2 coarsened parent
+  int src[4];    // same: src[0]; refined: src[0] = parent; coarsened: 4 children (a + 2b)
+  int a, b;      // child position for kind 1
+};
+
+struct DeviceTables;
+
+// ---------------------------------------------------------------------------
+// Host mesh: topology and numbering; device tables created lazily.
+struct Mesh {
+  // description
+  double Lx = 0, Ly = 0, Lz = 0;
+  int nx = 0, ny = 0, nz = 0, N = 0;
+  bool px = true, py = true;
+  int lvl_max = 0;
+  std::vector<Leaf> leaves;          // Morton order
+  int Lf = 0;                        // finest level present
+  // numbering
+  int Nq = 0;                        // (N+1)^2 horizontal local nodes per column
+  int P = 0;                         // (N+1)^3
+  int NZ = 0;
+  long long NH = 0, NG = 0;
+  std::vector<int> hmap;             // [Ncol][Nq]
+  std::vector<int> hang_h;           // [Nhang][N+1]
+  std::vector<double> hang_w;        // [Nhang][N+1]
+  std::vector<int> qt_ptr;           // [NH+1]
+  std::vector<int> qt_src;           // column*Nq + ab
+  std::vector<double> qt_w;
+  std::vector<double> Mh, Mz;        // lumped mass factors, M(h,kz) = Mh[h] Mz[kz]
+  std::vector<double> xh, yh, zk;    // coordinates of horizontal nodes / levels
+  long long n_nonconf_sides = 0;
+  // adaptation provenance (set by sem_transfer_plan)
+  std::vector<Origin> origin;
+  long long parent_serial = -1;
+  long long serial = 0;
+  // device
+  DeviceTables* dev = nullptr;
+  int dev_id = -1;
+
+  long long Ncol() const { return (long long)leaves.size(); }
+  long long Ne() const { return Ncol() * nz; }
+  double hx(int l) const { return Lx / (double)((long long)nx << l); }
+  double hy(int l) const { return Ly / (double)((long long)ny << l); }
+  double hz() const { return Lz / nz; }
+};
+
+int build_mesh(Mesh& m);                       // numbering from leaves (host)
+int check_leaves(const Mesh& m);               // tiling + balance
+int adapt_leaves(const Mesh& old, const int8_t* flags, std::vector<Leaf>& out,
+                 std::vector<Origin>& origin);
+
+// ---------------------------------------------------------------------------
+// Device tables of a mesh
+struct DeviceTables {
+  int* hmap = nullptr;
+  int* hang_h = nullptr;
+  double* hang_w = nullptr;
+  int* qt_ptr = nullptr;
+  int* qt_src = nullptr;
+  double* qt_w = nullptr;
+  double* Minv_h = nullptr;
+  double* Minv_z = nullptr;
+  double* Mh = nullptr;
+  double* Mz = nullptr;
+  double* ref = nullptr;        // [NZ][kRef] float64 reference state
+  float* ref32 = nullptr;       // [NZ][kRef] float32 copy
+  int* col_level = nullptr;     // [Ncol]
+  double* xh = nullptr;         // [NH]
+  double* yh = nullptr;
+  double* zk = nullptr;         // [NZ]
+  void* scratch = nullptr;      // column residuals
+  size_t scratch_bytes = 0;
+  int* status = nullptr;        // device status word
+  // transfer
+  int* org = nullptr;           // [Ncol][6] kind, src0..3, a+2b
+  // adapt and diagnostics
+  double* elem_cmax = nullptr;
+  int8_t* elem_flags = nullptr;
+  double* diag_buf = nullptr;   // [NZ][4]
+  // continuous projection of the transfer (coupled coarse-face nodes)
+  int n_comp = 0, max_comp = 0;
+  int* tr_comp_ptr = nullptr;   // [n_comp+1] into tr_nodes
+  int* tr_nodes = nullptr;      // horizontal node ids, grouped by component
+  int* tr_A_ptr = nullptr;      // CSR of A_h restricted to each component
+  int* tr_A_col = nullptr;      // component-local column
+  double* tr_A_val = nullptr;
+  int* tr_coupled = nullptr;    // [NH] 1 when the node is solved for
+  // the params the ref tables were built with
+  double ref_key[8] = {0};
+  bool ref_valid = false;
+};
+constexpr int kRef = 8;  // theta0, pi0, p0, rho0, rhotheta0, dtheta0/dz, 1/(rho theta)0, z
+
+int ensure_device(Mesh& m);
+int ensure_reference(Mesh& m, const sem_params& p);
+void free_device(Mesh& m);
+
+// kernel launchers (k_*.cu)
+struct StageArgs {
+  const double* qn;
+  const double* qs;
+  double* out;
+  double a, b, cdt;   // out = a qn + b qs + cdt * tendency; rhs mode: a=b=0, cdt=1
+  int rhs_only;
+};
+int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStream_t st);
+int launch_adapt(Mesh& m, const sem_params& p, const double* q, int8_t* flags, double* cmax,
+                 cudaStream_t st);
+int launch_diag(Mesh& m, const sem_params& p, const double* q, double half_width,
+                sem_diag_out* out, cudaStream_t st);
+int launch_transfer(Mesh& oldm, Mesh& newm, const double* qold, double* qnew, cudaStream_t st);
+int launch_coords(Mesh& m, double* xyz, cudaStream_t st);
+
+// per-kernel event timing (profile.cpp); -1 when profiling is off
+int prof_begin_kernel(const char* name, cudaStream_t st);
+void prof_end_kernel(int rec, cudaStream_t st);
+struct ProfScope {
+  int rec;
+  cudaStream_t st;
+  ProfScope(const char* name, cudaStream_t s) : rec(prof_begin_kernel(name, s)), st(s) {}
+  ~ProfScope() { prof_end_kernel(rec, st); }
+};
+
+}  // namespace sem
+
+struct sem_mesh {
+  sem::Mesh m;
+};

@@ -1,0 +1,298 @@
+"""ctypes binding of libsem.so (include/sem.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own: device arrays are torch CUDA tensors (float64,
+contiguous, shape (5, NG) for fields), streams are torch CUDA streams (the
+current stream by default).  If the shared library is missing this module
+raises on import: there is no fallback path.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libsem.so")
+
+SEM_OK, SEM_ERR_ARG, SEM_ERR_CUDA, SEM_ERR_TOPOLOGY = 0, 1, 2, 3
+SEM_ERR_NUMERIC, SEM_ERR_TIMEOUT, SEM_ERR_IO, SEM_ERR_UNSUPPORTED = 4, 5, 6, 7
+SEM_EQ_CONSERVATIVE, SEM_EQ_NONCONSERVATIVE = 0, 1
+SEM_PREC_FP64, SEM_PREC_MIXED = 0, 1
+SEM_MAX_THRESHOLDS = 8
+
+# every symbol include/sem.h declares
+EXPORTS = (
+    "sem_last_error", "sem_params_default", "sem_mesh_create", "sem_mesh_destroy",
+    "sem_mesh_get_info", "sem_mesh_coords_host", "sem_mesh_leaves_host", "sem_mesh_hmap_host",
+    "sem_mesh_mass_host", "sem_mesh_coords", "sem_rhs", "sem_rk_stage", "sem_step",
+    "sem_adapt_flags", "sem_adapt_flags_host", "sem_transfer_plan", "sem_transfer", "sem_diag",
+    "sem_status", "sem_profile_begin", "sem_profile_end",
+)
+
+
+class SemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"sem error {code}: {msg}")
+        self.code = code
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("Lx", C.c_double), ("Ly", C.c_double), ("Lz", C.c_double),
+                ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("N", C.c_int),
+                ("periodic_x", C.c_int), ("periodic_y", C.c_int), ("lvl_max", C.c_int),
+                ("n_leaves", C.c_int), ("leaves", C.POINTER(C.c_int))]
+
+
+class MeshInfo(C.Structure):
+    _fields_ = [("Ne", C.c_longlong), ("NL", C.c_longlong), ("NG", C.c_longlong),
+                ("NH", C.c_longlong), ("NZ", C.c_longlong), ("Ncol", C.c_longlong),
+                ("n_hanging_h", C.c_longlong), ("n_nonconforming_faces", C.c_longlong),
+                ("N", C.c_int), ("nz", C.c_int), ("max_level", C.c_int),
+                ("level_hist", C.c_longlong * 16)]
+
+
+class Params(C.Structure):
+    _fields_ = [("g", C.c_double), ("f", C.c_double), ("R_d", C.c_double), ("c_p", C.c_double),
+                ("p00", C.c_double), ("theta_s", C.c_double), ("N_bv", C.c_double),
+                ("eqset", C.c_int), ("precision", C.c_int), ("n_thresholds", C.c_int),
+                ("lvl_max", C.c_int), ("thresholds", C.c_double * SEM_MAX_THRESHOLDS)]
+
+
+class ProfileOut(C.Structure):
+    _fields_ = [("n_kernels", C.c_int), ("name", (C.c_char * 48) * 16),
+                ("launches", C.c_longlong * 16), ("ms_total", C.c_double * 16)]
+
+
+class DiagOut(C.Structure):
+    _fields_ = [("max_wind", C.c_double), ("max_mean_wind", C.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2410_21607_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, i, d = C.c_void_p, C.c_int, C.c_double
+    sig = {
+        "sem_last_error": (C.c_char_p, []),
+        "sem_params_default": (i, [C.POINTER(Params)]),
+        "sem_mesh_create": (i, [C.POINTER(MeshDesc), C.POINTER(vp)]),
+        "sem_mesh_destroy": (None, [vp]),
+        "sem_mesh_get_info": (i, [vp, C.POINTER(MeshInfo)]),
+        "sem_mesh_coords_host": (i, [vp, vp]),
+        "sem_mesh_leaves_host": (i, [vp, vp]),
+        "sem_mesh_hmap_host": (i, [vp, vp, vp, vp]),
+        "sem_mesh_mass_host": (i, [vp, vp]),
+        "sem_mesh_coords": (i, [vp, vp, vp]),
+        "sem_rhs": (i, [vp, C.POINTER(Params), vp, vp, vp]),
+        "sem_rk_stage": (i, [vp, C.POINTER(Params), i, vp, vp, vp, d, vp]),
+        "sem_step": (i, [vp, C.POINTER(Params), vp, vp, vp, d, vp]),
+        "sem_adapt_flags": (i, [vp, C.POINTER(Params), vp, vp, vp, vp]),
+        "sem_adapt_flags_host": (i, [vp, C.POINTER(Params), vp, vp, vp]),
+        "sem_transfer_plan": (i, [vp, vp, C.POINTER(vp)]),
+        "sem_transfer": (i, [vp, vp, vp, vp, vp]),
+        "sem_diag": (i, [vp, C.POINTER(Params), vp, d, C.POINTER(DiagOut), vp]),
+        "sem_status": (i, [vp, C.POINTER(C.c_int), vp]),
+        "sem_profile_begin": (i, []),
+        "sem_profile_end": (i, [C.POINTER(ProfileOut)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+LIB = _load()
+
+
+def _check(rc):
+    if rc != SEM_OK:
+        raise SemError(rc, LIB.sem_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("host array must be C-contiguous")
+        return t.ctypes.data
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def _f64(t, shape=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
+        raise TypeError("expected a float64 CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {shape}, got {tuple(t.shape)}")
+    return t
+
+
+def sem_params_default(**overrides):
+    p = Params()
+    _check(LIB.sem_params_default(C.byref(p)))
+    thr = overrides.pop("thresholds", None)
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    if thr is not None:
+        p.n_thresholds = len(thr)
+        for k, v in enumerate(thr):
+            p.thresholds[k] = v
+    return p
+
+
+class Mesh:
+    """Owning handle of a sem_mesh."""
+
+    def __init__(self, handle):
+        self.h = C.c_void_p(handle)
+        info = MeshInfo()
+        _check(LIB.sem_mesh_get_info(self.h, C.byref(info)))
+        self.info = info
+        self.NG, self.NH, self.NZ, self.Ne = info.NG, info.NH, info.NZ, info.Ne
+        self.N, self.nz, self.Ncol = info.N, info.nz, info.Ncol
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            LIB.sem_mesh_destroy(h)
+            self.h = None
+
+    @property
+    def field_shape(self):
+        return (5, self.NG)
+
+
+def sem_mesh_create(Lx, Ly, Lz, nx, ny, nz, N, leaves=None, periodic=(True, True), lvl_max=0):
+    d = MeshDesc(Lx, Ly, Lz, nx, ny, nz, N, int(periodic[0]), int(periodic[1]), lvl_max, 0, None)
+    keep = None
+    if leaves is not None and len(leaves):
+        keep = np.ascontiguousarray(np.asarray(leaves, dtype=np.int32).reshape(-1, 3))
+        d.n_leaves = len(keep)
+        d.leaves = keep.ctypes.data_as(C.POINTER(C.c_int))
+    h = C.c_void_p()
+    _check(LIB.sem_mesh_create(C.byref(d), C.byref(h)))
+    return Mesh(h.value)
+
+
+def sem_mesh_coords_host(mesh):
+    out = np.zeros((3, mesh.NG))
+    _check(LIB.sem_mesh_coords_host(mesh.h, _ptr(out)))
+    return out
+
+
+def sem_mesh_leaves_host(mesh):
+    out = np.zeros((mesh.Ncol, 3), dtype=np.int32)
+    _check(LIB.sem_mesh_leaves_host(mesh.h, _ptr(out)))
+    return out
+
+
+def sem_mesh_hmap_host(mesh):
+    n1 = mesh.N + 1
+    hmap = np.zeros((mesh.Ncol, n1 * n1), dtype=np.int32)
+    nh = mesh.info.n_hanging_h
+    hh = np.zeros((max(nh, 1), n1), dtype=np.int32)
+    hw = np.zeros((max(nh, 1), n1))
+    _check(LIB.sem_mesh_hmap_host(mesh.h, _ptr(hmap), _ptr(hh), _ptr(hw)))
+    return hmap, hh[:nh], hw[:nh]
+
+
+def sem_mesh_mass_host(mesh):
+    out = np.zeros(mesh.NG)
+    _check(LIB.sem_mesh_mass_host(mesh.h, _ptr(out)))
+    return out
+
+
+def sem_mesh_coords(mesh, out, stream=None):
+    _f64(out, (3, mesh.NG))
+    _check(LIB.sem_mesh_coords(mesh.h, _ptr(out), _stream(stream)))
+    return out
+
+
+def sem_rhs(mesh, params, q, out, stream=None):
+    _f64(q, mesh.field_shape)
+    _f64(out, mesh.field_shape)
+    _check(LIB.sem_rhs(mesh.h, C.byref(params), _ptr(q), _ptr(out), _stream(stream)))
+    return out
+
+
+def sem_rk_stage(mesh, params, stage, qn, qs, qout, dt, stream=None):
+    for t in (qn, qs, qout):
+        _f64(t, mesh.field_shape)
+    _check(LIB.sem_rk_stage(mesh.h, C.byref(params), int(stage), _ptr(qn), _ptr(qs), _ptr(qout),
+                            float(dt), _stream(stream)))
+    return qout
+
+
+def sem_step(mesh, params, q, w1, w2, dt, stream=None):
+    for t in (q, w1, w2):
+        _f64(t, mesh.field_shape)
+    _check(LIB.sem_step(mesh.h, C.byref(params), _ptr(q), _ptr(w1), _ptr(w2), float(dt),
+                        _stream(stream)))
+    return q
+
+
+def sem_adapt_flags(mesh, params, q, flags, cmax=None, stream=None):
+    _f64(q, mesh.field_shape)
+    _check(LIB.sem_adapt_flags(mesh.h, C.byref(params), _ptr(q), _ptr(flags), _ptr(cmax),
+                               _stream(stream)))
+    return flags
+
+
+def sem_adapt_flags_host(mesh, params, q, stream=None):
+    _f64(q, mesh.field_shape)
+    out = np.zeros(mesh.Ne, dtype=np.int8)
+    _check(LIB.sem_adapt_flags_host(mesh.h, C.byref(params), _ptr(q), _ptr(out), _stream(stream)))
+    return out
+
+
+def sem_transfer_plan(mesh, flags_host):
+    f = np.ascontiguousarray(np.asarray(flags_host, dtype=np.int8))
+    if f.shape != (mesh.Ne,):
+        raise ValueError("one flag per element")
+    h = C.c_void_p()
+    _check(LIB.sem_transfer_plan(mesh.h, _ptr(f), C.byref(h)))
+    return Mesh(h.value)
+
+
+def sem_transfer(old, new, q_old, q_new, stream=None):
+    _f64(q_old, old.field_shape)
+    _f64(q_new, new.field_shape)
+    _check(LIB.sem_transfer(old.h, new.h, _ptr(q_old), _ptr(q_new), _stream(stream)))
+    return q_new
+
+
+def sem_diag(mesh, params, q, half_width=50.0e3, stream=None):
+    _f64(q, mesh.field_shape)
+    out = DiagOut()
+    _check(LIB.sem_diag(mesh.h, C.byref(params), _ptr(q), float(half_width), C.byref(out),
+                        _stream(stream)))
+    return {"max_wind": out.max_wind, "max_mean_wind": out.max_mean_wind}
+
+
+def sem_status(mesh, stream=None):
+    v = C.c_int(0)
+    _check(LIB.sem_status(mesh.h, C.byref(v), _stream(stream)))
+    return v.value
+
+
+def sem_profile_begin():
+    _check(LIB.sem_profile_begin())
+
+
+def sem_profile_end():
+    """{kernel name: (launches, total ms)} of the launches since sem_profile_begin."""
+    out = ProfileOut()
+    _check(LIB.sem_profile_end(C.byref(out)))
+    return {bytes(out.name[k]).split(b"\0")[0].decode(): (out.launches[k], out.ms_total[k])
+            for k in range(out.n_kernels)}

@@ -1,0 +1,134 @@
+"""CPU checks of the C ABI library: it loads, exports every declared symbol,
+and its host topology (numbering, hanging rows, lumped mass, adaptation) agrees
+with the oracle's brute-force construction (Sec. 3.1-3.2)."""
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import adapt, mesh as om
+from tests.helpers import node_perm
+from tests.test_oracle_mesh import ring_leaves, two_level_leaves
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def sem():
+    from paper_2410_21607_gb300 import build
+    build.build()
+    from paper_2410_21607_gb300 import sem as s
+    return s
+
+
+def test_library_exports_every_declared_symbol(sem):
+    hdr = open(os.path.join(ROOT, "include", "sem.h")).read()
+    declared = set(re.findall(r"^\s*(?:const\s+)?\w+\*?\s+\*?(sem_\w+)\s*\(", hdr, re.M))
+    assert "sem_rhs" in declared and "sem_transfer" in declared
+    for name in declared:
+        assert hasattr(sem.LIB, name), name
+    assert declared == set(sem.EXPORTS)
+
+
+def _lib_Q(sem, m):
+    """Full constraint matrix Q rebuilt from the library's host export."""
+    hmap, hh, hw = sem.sem_mesh_hmap_host(m)
+    leaves = sem.sem_mesh_leaves_host(m)
+    N, NZ, nz = m.N, m.NZ, m.nz
+    n1 = N + 1
+    rows, cols, vals = [], [], []
+    ii, jj, kk = np.meshgrid(np.arange(n1), np.arange(n1), np.arange(n1), indexing="ij")
+    ii, jj, kk = ii.ravel(), jj.ravel(), kk.ravel()
+    lidx = ii + n1 * jj + n1 * n1 * kk
+    for c in range(m.Ncol):
+        for k in range(nz):
+            base = (c * nz + k) * n1 ** 3
+            for i, j, kq, l in zip(ii, jj, kk, lidx):
+                v = hmap[c, i + n1 * j]
+                kz = k * N + kq
+                if v >= 0:
+                    rows.append(base + l); cols.append(v * NZ + kz); vals.append(1.0)
+                else:
+                    for q in range(n1):
+                        if hw[-1 - v, q] != 0.0:
+                            rows.append(base + l); cols.append(hh[-1 - v, q] * NZ + kz)
+                            vals.append(hw[-1 - v, q])
+    return sp.csr_matrix((vals, (rows, cols)), shape=(m.Ne * n1 ** 3, m.NG)), leaves
+
+
+def _compare_with_oracle(sem, L, nx, nz, N, leaves, periodic):
+    m = sem.sem_mesh_create(L, L, 10e3, nx, nx, nz, N, leaves=leaves, periodic=periodic, lvl_max=4)
+    o = om.OracleMesh(L, L, 10e3, nx, nx, nz, N, leaves=leaves, periodic=periodic)
+    assert m.NG == o.NG
+    perm = node_perm(sem.sem_mesh_coords_host(m), o.XG)
+    Q, lv = _lib_Q(sem, m)
+    oleaf = {tuple(l): c for c, l in enumerate(o.leaves)}
+    erow = np.concatenate([np.arange((oleaf[tuple(l)] * nz + k) * o.P,
+                                     (oleaf[tuple(l)] * nz + k + 1) * o.P)
+                           for l in lv for k in range(nz)])
+    coo = Q.tocoo()
+    Qo = sp.csr_matrix((coo.data, (erow[coo.row], perm[coo.col])), shape=o.Q.shape)
+    assert abs(Qo - o.Q).max() < 1e-13
+    M = sem.sem_mesh_mass_host(m)
+    np.testing.assert_allclose(M, o.M[perm], rtol=1e-13)
+    return m, o
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 6])
+@pytest.mark.parametrize("periodic", [(True, True), (False, False), (True, False)])
+def test_topology_matches_oracle_two_level(sem, N, periodic):
+    _compare_with_oracle(sem, 80e3, 4, 2, N, two_level_leaves(), periodic)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_topology_matches_oracle_random_balanced(sem, seed):
+    rng = np.random.default_rng(100 + seed)
+    leaves = [(0, i, j) for j in range(3) for i in range(3)]
+    for _ in range(5):
+        fl = rng.integers(-1, 2, size=len(leaves)).astype(np.int8)
+        leaves, _ = adapt.update_leaves(leaves, fl, 1, 3, 3, 3)
+    _compare_with_oracle(sem, 90e3, 3, 1, 3 + seed % 2, leaves, (True, True))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_adaptation_plan_matches_oracle(sem, seed):
+    rng = np.random.default_rng(seed)
+    nx, nz = 4, 2
+    leaves = [(0, i, j) for j in range(nx) for i in range(nx)]
+    for _ in range(3):
+        fl = rng.integers(-1, 2, size=len(leaves)).astype(np.int8)
+        leaves, _ = adapt.update_leaves(leaves, fl, 1, nx, nx, 3)
+    m = sem.sem_mesh_create(80e3, 80e3, 10e3, nx, nx, nz, 4, leaves=leaves, lvl_max=3)
+    lv = [tuple(x) for x in sem.sem_mesh_leaves_host(m)]
+    flags = rng.integers(-1, 2, size=len(lv) * nz).astype(np.int8)
+    new_lib = sem.sem_transfer_plan(m, flags)
+    new_oracle, _ = adapt.update_leaves(lv, flags, nz, nx, nx, 3)
+    got = sorted(tuple(x) for x in sem.sem_mesh_leaves_host(new_lib))
+    assert got == sorted(new_oracle)
+
+
+def test_rejects_bad_meshes(sem):
+    with pytest.raises(sem.SemError) as e:     # level 0 next to level 2
+        sem.sem_mesh_create(80e3, 80e3, 10e3, 2, 2, 1, 4,
+                            leaves=[(0, 1, 0), (0, 0, 1), (0, 1, 1), (1, 1, 0), (1, 0, 1), (1, 1, 1)]
+                            + [(2, a, b) for a in (0, 1) for b in (0, 1)])
+    assert e.value.code == sem.SEM_ERR_TOPOLOGY
+    with pytest.raises(sem.SemError) as e:     # a hole
+        sem.sem_mesh_create(80e3, 80e3, 10e3, 2, 2, 1, 4, leaves=[(0, 0, 0), (0, 1, 0), (0, 0, 1)])
+    assert e.value.code == sem.SEM_ERR_TOPOLOGY
+    with pytest.raises(sem.SemError) as e:
+        sem.sem_mesh_create(80e3, 80e3, 10e3, 2, 2, 1, 9)
+    assert e.value.code == sem.SEM_ERR_UNSUPPORTED
+    m = sem.sem_mesh_create(80e3, 80e3, 10e3, 2, 2, 1, 4)
+    with pytest.raises(sem.SemError) as e:     # flags outside {-1, 0, 1}
+        sem.sem_transfer_plan(m, np.full(m.Ne, 3, dtype=np.int8))
+    assert e.value.code == sem.SEM_ERR_ARG
+
+
+def test_uniform_counts_and_info(sem):
+    m = sem.sem_mesh_create(2048e3, 2048e3, 24e3, 64, 64, 16, 4)
+    assert (m.Ne, m.NG, m.NH, m.NZ) == (65536, 4259840, 65536, 65)
+    assert m.info.NL == 8192000
+    assert m.info.n_hanging_h == 0

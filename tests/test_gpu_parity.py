@@ -1,0 +1,272 @@
+"""GPU parity: every C-ABI compute call against the CPU oracle on the same
+seeded inputs.
+
+Tolerances (relative L2 per field group {rho, momentum, theta}):
+  FP64 form   <= 1e-12
+  mixed form  <= 1e-4 on states after RK stages (full fields), and on
+                 tendencies <= 1e-4 of the tendency norm
+Flags of the criterion are integers decided in float64 on both sides: they
+must agree exactly, except where the element maximum lies within 1e-12
+(relative) of a threshold.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import adapt, diag, mesh as om, refstate, rhs as orhs, rk as ork, transfer as otr  # noqa: E402
+from synth.vortex import random_state, vortex_state, VortexSpec  # noqa: E402
+from tests.helpers import group_rel_l2, node_perm  # noqa: E402
+from tests.test_oracle_mesh import two_level_leaves  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def sem():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_21607_gb300 import build
+    build.build()
+    from paper_2410_21607_gb300 import sem as s
+    return s
+
+
+PRM = refstate.Params()
+
+
+def make_pair(sem, L, Lz, nx, nz, N, leaves=None, periodic=(True, True), lvl_max=3):
+    m = sem.sem_mesh_create(L, L, Lz, nx, nx, nz, N, leaves=leaves, periodic=periodic, lvl_max=lvl_max)
+    o = om.OracleMesh(L, L, Lz, nx, nx, nz, N, leaves=leaves, periodic=periodic)
+    xyz = sem.sem_mesh_coords_host(m)
+    perm = node_perm(xyz, o.XG)
+    return m, o, xyz.T, perm
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def full_fields(q, z, eqset="C"):
+    """Full (not perturbation) fields used by the state-level norms."""
+    ref = refstate.reference_state(z, PRM)
+    out = q.copy()
+    out[0] += ref["rho0"]
+    if eqset == "C":
+        out[4] += ref["rhotheta0"]
+    else:
+        out[4] += ref["theta0"]
+    return out
+
+
+MESHES = {
+    "uniform-6x6x4-N4": dict(L=600e3, Lz=24e3, nx=6, nz=4, N=4),
+    "twolevel-N4": dict(L=300e3, Lz=12e3, nx=4, nz=2, N=4, leaves=two_level_leaves()),
+    "twolevel-N3-open": dict(L=300e3, Lz=12e3, nx=4, nz=3, N=3, leaves=two_level_leaves(),
+                             periodic=(False, False)),
+    "uniform-5x4x3-N6": dict(L=500e3, Lz=12e3, nx=5, nz=3, N=6),
+    "uniform-3x3x2-N2": dict(L=300e3, Lz=12e3, nx=3, nz=2, N=2),
+}
+
+
+@pytest.mark.parametrize("name", list(MESHES))
+@pytest.mark.parametrize("eqset", ["C", "NC"])
+def test_rhs_fp64_matches_oracle(sem, name, eqset):
+    m, o, X, perm = make_pair(sem, **MESHES[name])
+    q_o = random_state(o.XG, o.Lz, 11, eqset)
+    T_o = orhs.rhs(o, q_o, PRM, eqset)
+    p = sem.sem_params_default(eqset=0 if eqset == "C" else 1)
+    q = dev(q_o[:, perm])
+    out = torch.empty_like(q)
+    sem.sem_rhs(m, p, q, out)
+    T = host(out)
+    err = group_rel_l2(T, T_o[:, perm])
+    assert np.all(err <= 1e-12), err
+
+
+@pytest.mark.parametrize("name", ["uniform-6x6x4-N4", "twolevel-N4"])
+@pytest.mark.parametrize("eqset", ["C", "NC"])
+def test_rhs_mixed_matches_oracle(sem, name, eqset):
+    m, o, X, perm = make_pair(sem, **MESHES[name])
+    q_o = random_state(o.XG, o.Lz, 12, eqset)
+    T_o = orhs.rhs(o, q_o, PRM, eqset)
+    p = sem.sem_params_default(eqset=0 if eqset == "C" else 1, precision=sem.SEM_PREC_MIXED)
+    q = dev(q_o[:, perm])
+    out = torch.empty_like(q)
+    sem.sem_rhs(m, p, q, out)
+    err = group_rel_l2(host(out), T_o[:, perm])
+    assert np.all(err <= 1e-4), err
+
+
+def test_rest_state_exactly_steady_on_gpu(sem):
+    m, o, X, perm = make_pair(sem, **MESHES["twolevel-N4"])
+    for prec in (0, 1):
+        for eq in (0, 1):
+            p = sem.sem_params_default(eqset=eq, precision=prec)
+            q = torch.zeros(5, m.NG, dtype=torch.float64, device="cuda")
+            out = torch.full_like(q, 7.0)
+            sem.sem_rhs(m, p, q, out)
+            assert torch.count_nonzero(out).item() == 0
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ten_rk3_steps_uniform_6x6x4(sem, prec):
+    """The small workload: 10 SSP-RK3 steps at dt = 1 s on the 6x6x4 mesh."""
+    m, o, X, perm = make_pair(sem, **MESHES["uniform-6x6x4-N4"])
+    q_o = vortex_state(o.XG, o.Lz)
+    q_ref = q_o.copy()
+    for _ in range(10):
+        q_ref = ork.rk_step(o, PRM, q_ref, 1.0)
+    p = sem.sem_params_default(precision=prec)
+    q = dev(q_o[:, perm])
+    w1, w2 = torch.empty_like(q), torch.empty_like(q)
+    for _ in range(10):
+        sem.sem_step(m, p, q, w1, w2, 1.0)
+    got = host(q)
+    z = X[:, 2]
+    err = group_rel_l2(full_fields(got, z), full_fields(q_ref[:, perm], z))
+    tol = 1e-12 if prec == 0 else 1e-4
+    assert np.all(err <= tol), err
+    # the perturbation itself, not only the full field
+    pert = group_rel_l2(got, q_ref[:, perm])
+    assert np.all(pert <= (1e-11 if prec == 0 else 1e-3)), pert
+    assert sem.sem_status(m) == 0
+
+
+@pytest.mark.parametrize("stage", [0, 1, 2])
+def test_rk_stage_on_nonconforming_mesh(sem, stage):
+    m, o, X, perm = make_pair(sem, **MESHES["twolevel-N4"])
+    qn_o = random_state(o.XG, o.Lz, 21)
+    qs_o = random_state(o.XG, o.Lz, 22)
+    ref = ork.rk_stage(o, PRM, stage, qn_o, qs_o, 0.7)
+    p = sem.sem_params_default()
+    qn, qs = dev(qn_o[:, perm]), dev(qs_o[:, perm])
+    out = torch.empty_like(qn)
+    sem.sem_rk_stage(m, p, stage, qn, qs, out, 0.7)
+    err = group_rel_l2(host(out), ref[:, perm])
+    assert np.all(err <= 1e-12), err
+
+
+def test_mass_conservation_on_gpu(sem):
+    m, o, X, perm = make_pair(sem, **MESHES["twolevel-N4"])
+    M = sem.sem_mesh_mass_host(m)
+    q = dev(random_state(o.XG, o.Lz, 5)[:, perm])
+    out = torch.empty_like(q)
+    for prec in (0, 1):
+        sem.sem_rhs(m, sem.sem_params_default(precision=prec), q, out)
+        T = host(out)
+        tol = 1e-13 if prec == 0 else 1e-6
+        assert abs(np.sum(M * T[0])) <= tol * np.sum(np.abs(M * T[0]))
+
+
+@pytest.mark.parametrize("name", ["uniform-6x6x4-N4", "twolevel-N4"])
+def test_adapt_flags_match_oracle(sem, name):
+    m, o, X, perm = make_pair(sem, **MESHES[name])
+    q_o = vortex_state(o.XG, o.Lz)
+    lv = sem.sem_mesh_leaves_host(m)
+    oleaf = {tuple(l): c for c, l in enumerate(o.leaves)}
+    emap = np.array([oleaf[tuple(l)] * o.nz + k for l in lv for k in range(o.nz)])
+    q = dev(q_o[:, perm])
+    for thr in ([5.0, 10.0, 15.0], [2.0, 5.0, 7.5], [7.5, 15.0, 22.5]):
+        fl_o, cmax_o = adapt.criterion_flags(o, q_o, PRM, thr, 3)
+        p = sem.sem_params_default(thresholds=thr, lvl_max=3)
+        flags = torch.empty(m.Ne, dtype=torch.int8, device="cuda")
+        cmax = torch.empty(m.Ne, dtype=torch.float64, device="cuda")
+        sem.sem_adapt_flags(m, p, q, flags, cmax)
+        fl, cm = host(flags), host(cmax)
+        np.testing.assert_allclose(cm, cmax_o[emap], rtol=1e-14)
+        tie = np.min(np.abs(cmax_o[emap][:, None] - np.array(thr)[None]), axis=1) <= 1e-12 * max(thr)
+        assert np.array_equal(fl[~tie], fl_o[emap][~tie])
+        assert np.array_equal(sem.sem_adapt_flags_host(m, p, q), fl)
+
+
+def test_transfer_matches_oracle(sem):
+    """Refine by the criterion, then coarsen everything back: both transfers
+    against the oracle's (interpolation, L2 projection, continuous projection)."""
+    m, o, X, perm = make_pair(sem, L=600e3, Lz=24e3, nx=4, nz=2, N=4)
+    q_o = vortex_state(o.XG, o.Lz)
+    lv = [tuple(l) for l in sem.sem_mesh_leaves_host(m)]
+    oleaf = {l: c for c, l in enumerate(o.leaves)}
+    fl_o, _ = adapt.criterion_flags(o, q_o, PRM, [5.0, 10.0], 2)
+    # flags in library element order
+    fl_lib = np.array([fl_o[oleaf[l] * o.nz + k] for l in lv for k in range(o.nz)], dtype=np.int8)
+    new = sem.sem_transfer_plan(m, fl_lib)
+    new_o, org = adapt.update_leaves(o.leaves, fl_o, o.nz, 4, 4, 2)
+    o2, q2_o = otr.transfer(o, new_o, org, q_o)
+    perm2 = node_perm(sem.sem_mesh_coords_host(new), o2.XG)
+    q = dev(q_o[:, perm])
+    q2 = torch.empty(5, new.NG, dtype=torch.float64, device="cuda")
+    sem.sem_transfer(m, new, q, q2)
+    err = group_rel_l2(host(q2), q2_o[:, perm2])
+    assert np.all(err <= 1e-12), err
+    assert sem.sem_status(new) == 0
+    # coarsen everything back
+    back = sem.sem_transfer_plan(new, -np.ones(new.Ne, dtype=np.int8))
+    q3 = torch.empty(5, back.NG, dtype=torch.float64, device="cuda")
+    sem.sem_transfer(new, back, q2, q3)
+    perm3 = node_perm(sem.sem_mesh_coords_host(back), o.XG)
+    err = group_rel_l2(host(q3), q_o[:, perm3])
+    assert np.all(err <= 1e-12), err
+
+
+def test_transfer_coarsening_matches_oracle(sem):
+    m, o, X, perm = make_pair(sem, **MESHES["twolevel-N4"])
+    q_o = random_state(o.XG, o.Lz, 9)
+    lv = [tuple(l) for l in sem.sem_mesh_leaves_host(m)]
+    fl_lib = np.array([-1 if l[0] == 2 else (1 if l == (0, 0, 0) else 0)
+                       for l in lv for _ in range(o.nz)], dtype=np.int8)
+    oleaf = {tuple(l): c for c, l in enumerate(lv)}
+    fl_o = np.zeros(o.Ne, dtype=np.int8)
+    for c, l in enumerate(o.leaves):
+        fl_o[c * o.nz:(c + 1) * o.nz] = fl_lib[oleaf[tuple(l)] * o.nz]
+    new = sem.sem_transfer_plan(m, fl_lib)
+    new_o, org = adapt.update_leaves(o.leaves, fl_o, o.nz, 4, 4, 3)
+    o2, q2_o = otr.transfer(o, new_o, org, q_o)
+    perm2 = node_perm(sem.sem_mesh_coords_host(new), o2.XG)
+    q2 = torch.empty(5, new.NG, dtype=torch.float64, device="cuda")
+    sem.sem_transfer(m, new, dev(q_o[:, perm]), q2)
+    err = group_rel_l2(host(q2), q2_o[:, perm2])
+    assert np.all(err <= 1e-12), err
+
+
+def test_diag_matches_oracle(sem):
+    m, o, X, perm = make_pair(sem, **MESHES["uniform-6x6x4-N4"])
+    q_o = vortex_state(o.XG, o.Lz)
+    d_o = diag.wind_diagnostics(o, q_o, PRM)
+    d = sem.sem_diag(m, sem.sem_params_default(), dev(q_o[:, perm]))
+    assert abs(d["max_wind"] - d_o["max_wind"]) <= 1e-12 * d_o["max_wind"]
+    assert abs(d["max_mean_wind"] - d_o["max_mean_wind"]) <= 1e-12 * d_o["max_mean_wind"]
+
+
+def test_coords_on_device_match_host(sem):
+    m = sem.sem_mesh_create(300e3, 300e3, 12e3, 4, 4, 2, 4, leaves=two_level_leaves())
+    xyz = torch.empty(3, m.NG, dtype=torch.float64, device="cuda")
+    sem.sem_mesh_coords(m, xyz)
+    assert np.array_equal(host(xyz), sem.sem_mesh_coords_host(m))
+
+
+def test_nonfinite_state_sets_status(sem):
+    m = sem.sem_mesh_create(300e3, 300e3, 12e3, 3, 3, 2, 4)
+    q = torch.zeros(5, m.NG, dtype=torch.float64, device="cuda")
+    q[1, 17] = float("nan")
+    w1, w2 = torch.empty_like(q), torch.empty_like(q)
+    sem.sem_step(m, sem.sem_params_default(), q, w1, w2, 1.0)
+    assert sem.sem_status(m) == sem.SEM_ERR_NUMERIC
+    assert sem.sem_status(m) == 0       # reading clears it
+
+
+def test_bad_arguments_are_rejected(sem):
+    m = sem.sem_mesh_create(300e3, 300e3, 12e3, 3, 3, 2, 4)
+    q = torch.zeros(5, m.NG, dtype=torch.float64, device="cuda")
+    p = sem.sem_params_default()
+    with pytest.raises(sem.SemError):
+        sem.sem_rhs(m, p, q, q)                       # aliasing
+    with pytest.raises(sem.SemError):
+        sem.sem_rk_stage(m, p, 3, q, q, torch.empty_like(q), 1.0)
+    p.eqset = 7
+    with pytest.raises(sem.SemError):
+        sem.sem_rhs(m, p, q, torch.empty_like(q))
