@@ -191,17 +191,28 @@ def main():
     prec = sem.SEM_PREC_MIXED if a.form == "mixed" else sem.SEM_PREC_FP64
     p = sem.sem_params_default(precision=prec)
     p64 = sem.sem_params_default(precision=sem.SEM_PREC_FP64)
-    bufs = [q0.clone(), torch.empty_like(q0), torch.empty_like(q0)]
     stream = torch.cuda.current_stream()
+
+    def new_bufs():
+        b = [q0.clone(), torch.empty_like(q0), torch.empty_like(q0)]
+        m32 = [torch.empty(q0.shape, dtype=torch.float32, device="cuda") for _ in range(3)]
+        sem.sem_mirror(m, b[0], m32[0], stream)
+        return b + m32
 
     def step(b, prm):
         # ping-pong: q -> w1 -> w2 -> w1, then w1 becomes the new state
-        qn, w1, w2 = b
-        sem.sem_rk_stage(m, prm, 0, qn, qn, w1, dt, stream)
-        sem.sem_rk_stage(m, prm, 1, qn, w1, w2, dt, stream)
-        sem.sem_rk_stage(m, prm, 2, qn, w2, w1, dt, stream)
-        return [w1, qn, w2]
+        qn, w1, w2, qn32, w132, w232 = b
+        if prm.precision == sem.SEM_PREC_MIXED:
+            sem.sem_rk_stage_mixed(m, prm, 0, qn, qn, qn32, w1, w132, dt, stream)
+            sem.sem_rk_stage_mixed(m, prm, 1, qn, w1, w132, w2, w232, dt, stream)
+            sem.sem_rk_stage_mixed(m, prm, 2, qn, w2, w232, w1, w132, dt, stream)
+        else:
+            sem.sem_rk_stage(m, prm, 0, qn, qn, w1, dt, stream)
+            sem.sem_rk_stage(m, prm, 1, qn, w1, w2, dt, stream)
+            sem.sem_rk_stage(m, prm, 2, qn, w2, w1, dt, stream)
+        return [w1, qn, w2, w132, qn32, w232]
 
+    bufs = new_bufs()
     dof_stage = 5 * m.Ne * (N + 1) ** 3
     for _ in range(max(a.warmup, 3)):
         bufs = step(bufs, p)
@@ -233,20 +244,31 @@ def main():
     hbm, peak_kind = peaks()
     Ncol, Nq, NZ, NG, NH = m.Ncol, (N + 1) ** 2, m.NZ, m.NG, m.NH
     rbytes = 4 if a.form == "mixed" else 8
+    # algorithmic bytes per launch: the state read by the element kernel
+    # (float32 mirror or float64), the column residuals written and read back,
+    # the stage's float64 reads (qs; qn on 2 of 3 stages), the float64 output
+    # and its float32 mirror, plus the index and mass tables
     alg = {
-        "volume": 5 * 8 * NG + 4 * Nq * Ncol + 5 * rbytes * Ncol * Nq * NZ,
-        "dss_rk": 5 * rbytes * Ncol * Nq * NZ + 3 * 5 * 8 * NG + 8 * (NH + NZ) + 12 * Ncol * Nq,
+        "volume": 5 * rbytes * NG + 4 * Nq * Ncol + 5 * rbytes * Ncol * Nq * NZ,
+        "dss_rk": (5 * rbytes * Ncol * Nq * NZ + (1 + 2.0 / 3.0) * 5 * 8 * NG + 5 * 8 * NG
+                   + (5 * 4 * NG if a.form == "mixed" else 0) + rbytes * (NH + NZ)
+                   + (4 + rbytes) * Ncol * Nq + 4 * NH),
     }
     kernels = {}
     for name, (launches, tot) in prof.items():
+        if name == "mirror":
+            continue
         base = name.rsplit("_", 1)[0] if name.startswith("volume") else "dss_rk"
         avg = tot / max(launches, 1)
         kernels[name] = {"launches": launches, "ms_avg": avg, "share": None,
                          "alg_bytes": alg[base], "gbs": alg[base] / (avg * 1e-3) / 1e9}
     tot_all = sum(v[1] for v in prof.values()) or 1.0
-    for name in kernels:
+    for name in list(kernels):
         kernels[name]["share"] = prof[name][1] / tot_all
     dom = max(kernels, key=lambda k: prof[k][1])
+    # ratio of measured DRAM traffic (ncu, same kernel and workload) to the
+    # algorithmic bytes, kept under profiles/; null until a capture of the
+    # current kernel exists
     roof = {"kernel": dom, "bound": "hbm", "achieved": kernels[dom]["gbs"], "peak": hbm,
             "unit": "GB/s", "frac": kernels[dom]["gbs"] / hbm, "traffic": None,
             "peak_source": peak_kind}
@@ -254,7 +276,7 @@ def main():
     # FP64 form beside it, and the max-wind gate after gate_steps steps
     fp64_ms = None
     if a.form == "mixed":
-        b64 = [q0.clone(), torch.empty_like(q0), torch.empty_like(q0)]
+        b64 = new_bufs()
         for _ in range(2):
             b64 = step(b64, p64)
         torch.cuda.synchronize()
@@ -268,8 +290,8 @@ def main():
         fp64_ms = e0.elapsed_time(e1) / nfp
     gate = None
     if a.gate_steps > 0:
-        bm = [q0.clone(), torch.empty_like(q0), torch.empty_like(q0)]
-        bd = [q0.clone(), torch.empty_like(q0), torch.empty_like(q0)]
+        bm = new_bufs()
+        bd = new_bufs()
         for _ in range(a.gate_steps):
             bm = step(bm, p)
             bd = step(bd, p64)
@@ -283,13 +305,15 @@ def main():
     # end to end through the C ABI with host buffers (pinned), copies timed
     hq = torch.from_numpy(q0_host).pin_memory()
     hout = torch.empty_like(hq).pin_memory()
-    eb = [torch.empty_like(q0), torch.empty_like(q0), torch.empty_like(q0)]
+    eb = new_bufs()
     ke = max(3, min(a.steps, 10))
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(ke):
         eb[0].copy_(hq, non_blocking=True)
+        if a.form == "mixed":
+            sem.sem_mirror(m, eb[0], eb[3], stream)
         eb = step(eb, p)
         hout.copy_(eb[0], non_blocking=True)
     e1.record(stream)

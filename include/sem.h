@@ -151,6 +151,20 @@ int sem_rhs(sem_mesh* m, const sem_params* p, const double* q_dev, double* rhs_d
 int sem_rk_stage(sem_mesh* m, const sem_params* p, int stage, const double* qn_dev,
                  const double* qs_dev, double* qout_dev, double dt, cudaStream_t stream);
 
+/* Mixed form with caller-owned float32 mirrors.  qs32_dev must hold the
+ * float32 mirror of qs_dev ([5][NG], as written by sem_mirror or by a previous
+ * call of this function into its qout32); the stage writes q_out (float64)
+ * and its float32 mirror qout32.  The element and face arithmetic reads the
+ * mirror, the float64 stage accumulation reads qn and qs.  Needs
+ * p->precision == SEM_PREC_MIXED.  (sem_rk_stage in the mixed form makes the
+ * mirror itself, in library scratch, at the cost of one more pass.) */
+int sem_rk_stage_mixed(sem_mesh* m, const sem_params* p, int stage, const double* qn_dev,
+                       const double* qs_dev, const float* qs32_dev, double* qout_dev,
+                       float* qout32_dev, double dt, cudaStream_t stream);
+
+/* q32 = float32 mirror of q ([5][NG]; significand truncated to 24 bits). */
+int sem_mirror(sem_mesh* m, const double* q_dev, float* q32_dev, cudaStream_t stream);
+
 /* A whole SSP-RK3 step in place on q_dev, using two caller-owned work arrays
  * w1_dev, w2_dev of [5][NG] float64. */
 int sem_step(sem_mesh* m, const sem_params* p, double* q_dev, double* w1_dev,

@@ -33,7 +33,7 @@ void free_device(Mesh& m) {
   if (m.dev_id >= 0 && cur != m.dev_id) cudaSetDevice(m.dev_id);
   DeviceTables& D = *m.dev;
   void* ptrs[] = {D.hmap, D.hang_h, D.hang_w, D.qt_ptr, D.qt_src, D.qt_w, D.Minv_h, D.Minv_z,
-                  D.Mh, D.Mz, D.ref, D.ref32, D.col_level, D.xh, D.yh, D.zk, D.scratch,
+                  D.Mh, D.Mz, D.Minv_h32, D.Minv_z32, D.qt_w32, D.hang_w32, D.mirror, D.ref, D.ref32, D.col_level, D.xh, D.yh, D.zk, D.scratch,
                   D.status, D.org, D.elem_cmax, D.elem_flags, D.diag_buf,
                   D.tr_comp_ptr, D.tr_nodes, D.tr_A_ptr, D.tr_A_col, D.tr_A_val, D.tr_coupled};
   for (void* p : ptrs)
@@ -59,6 +59,11 @@ int ensure_device(Mesh& m) {
   std::vector<double> minvh(m.NH), minvz(m.NZ);
   for (long long h = 0; h < m.NH; ++h) minvh[h] = 1.0 / m.Mh[h];
   for (int k = 0; k < m.NZ; ++k) minvz[k] = 1.0 / m.Mz[k];
+  std::vector<float> minvh32(m.NH), minvz32(m.NZ), qtw32(m.qt_w.size()), hw32(m.hang_w.size());
+  for (long long h = 0; h < m.NH; ++h) minvh32[h] = (float)minvh[h];
+  for (int k = 0; k < m.NZ; ++k) minvz32[k] = (float)minvz[k];
+  for (size_t k = 0; k < qtw32.size(); ++k) qtw32[k] = (float)m.qt_w[k];
+  for (size_t k = 0; k < hw32.size(); ++k) hw32[k] = (float)m.hang_w[k];
   std::vector<int> lev(m.Ncol());
   for (long long c = 0; c < m.Ncol(); ++c) lev[c] = m.leaves[c].l;
   if ((rc = upload(D.hmap, m.hmap)) || (rc = upload(D.hang_h, m.hang_h)) ||
@@ -66,7 +71,9 @@ int ensure_device(Mesh& m) {
       (rc = upload(D.qt_src, m.qt_src)) || (rc = upload(D.qt_w, m.qt_w)) ||
       (rc = upload(D.Minv_h, minvh)) || (rc = upload(D.Minv_z, minvz)) ||
       (rc = upload(D.Mh, m.Mh)) || (rc = upload(D.Mz, m.Mz)) || (rc = upload(D.col_level, lev)) ||
-      (rc = upload(D.xh, m.xh)) || (rc = upload(D.yh, m.yh)) || (rc = upload(D.zk, m.zk))) {
+      (rc = upload(D.xh, m.xh)) || (rc = upload(D.yh, m.yh)) || (rc = upload(D.zk, m.zk)) ||
+      (rc = upload(D.Minv_h32, minvh32)) || (rc = upload(D.Minv_z32, minvz32)) ||
+      (rc = upload(D.qt_w32, qtw32)) || (rc = upload(D.hang_w32, hw32))) {
     free_device(m);
     return rc;
   }
@@ -80,6 +87,7 @@ int ensure_device(Mesh& m) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&D.elem_cmax, (size_t)m.Ne() * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void**)&D.elem_flags, (size_t)m.Ne());
   if (e == cudaSuccess) e = cudaMalloc((void**)&D.diag_buf, (size_t)m.NZ * 4 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&D.mirror, (size_t)m.NG * kFields * sizeof(float));
   if (e != cudaSuccess) {
     free_device(m);
     return fail(SEM_ERR_CUDA, std::string("device allocation: ") + cudaGetErrorString(e));
@@ -292,7 +300,7 @@ int sem_rhs(sem_mesh* mh, const sem_params* p, const double* q, double* rhs, cud
   int rc = prepare(mh, p);
   if (rc) return rc;
   if (!q || !rhs || q == rhs) return fail(SEM_ERR_ARG, "q and rhs must be distinct device arrays");
-  StageArgs s{nullptr, q, rhs, 0.0, 0.0, 1.0, 1};
+  StageArgs s{nullptr, q, rhs, nullptr, nullptr, 0.0, 0.0, 1.0, 1};
   return launch_rhs_stage(mh->m, *p, s, st);
 }
 
@@ -307,8 +315,29 @@ int sem_rk_stage(sem_mesh* mh, const sem_params* p, int stage, const double* qn,
   if (stage < 0 || stage > 2) return fail(SEM_ERR_ARG, "stage must be 0, 1 or 2");
   if (!qn || !qs || !qout || qout == qn || qout == qs)
     return fail(SEM_ERR_ARG, "qout must not alias qn or qs");
-  StageArgs s{qn, qs, qout, kA[stage], kB[stage], kC[stage] * dt, 0};
+  StageArgs s{qn, qs, qout, nullptr, nullptr, kA[stage], kB[stage], kC[stage] * dt, 0};
   return launch_rhs_stage(mh->m, *p, s, st);
+}
+
+int sem_rk_stage_mixed(sem_mesh* mh, const sem_params* p, int stage, const double* qn,
+                       const double* qs, const float* qs32, double* qout, float* qout32,
+                       double dt, cudaStream_t st) {
+  int rc = prepare(mh, p);
+  if (rc) return rc;
+  if (p->precision != SEM_PREC_MIXED) return fail(SEM_ERR_ARG, "sem_rk_stage_mixed needs SEM_PREC_MIXED");
+  if (stage < 0 || stage > 2) return fail(SEM_ERR_ARG, "stage must be 0, 1 or 2");
+  if (!qn || !qs || !qs32 || !qout || !qout32 || qout == qn || qout == qs ||
+      (const void*)qout32 == (const void*)qs32)
+    return fail(SEM_ERR_ARG, "outputs must not alias inputs");
+  StageArgs s{qn, qs, qout, qs32, qout32, kA[stage], kB[stage], kC[stage] * dt, 0};
+  return launch_rhs_stage(mh->m, *p, s, st);
+}
+
+int sem_mirror(sem_mesh* mh, const double* q, float* q32, cudaStream_t st) {
+  if (!mh || !q || !q32) return fail(SEM_ERR_ARG, "NULL argument");
+  int rc = ensure_device(mh->m);
+  if (rc) return rc;
+  return launch_mirror(q, q32, (long long)kFields * mh->m.NG, st);
 }
 
 int sem_step(sem_mesh* mh, const sem_params* p, double* q, double* w1, double* w2, double dt,

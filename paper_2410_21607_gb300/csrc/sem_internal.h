@@ -105,6 +105,11 @@ struct DeviceTables {
   double* qt_w = nullptr;
   double* Minv_h = nullptr;
   double* Minv_z = nullptr;
+  float* Minv_h32 = nullptr;    // float32 copies for the mixed form
+  float* Minv_z32 = nullptr;
+  float* qt_w32 = nullptr;
+  float* hang_w32 = nullptr;
+  float* mirror = nullptr;      // float32 state mirror scratch [5][NG]
   double* Mh = nullptr;
   double* Mz = nullptr;
   double* ref = nullptr;        // [NZ][kRef] float64 reference state
@@ -145,6 +150,8 @@ struct StageArgs {
   const double* qn;
   const double* qs;
   double* out;
+  const float* qs32;  // mixed form: float32 mirror of qs (null: made internally)
+  float* out32;       // mixed form: float32 mirror of out to write (may be null)
   double a, b, cdt;   // out = a qn + b qs + cdt * tendency; rhs mode: a=b=0, cdt=1
   int rhs_only;
 };
@@ -155,6 +162,7 @@ int launch_diag(Mesh& m, const sem_params& p, const double* q, double half_width
                 sem_diag_out* out, cudaStream_t st);
 int launch_transfer(Mesh& oldm, Mesh& newm, const double* qold, double* qnew, cudaStream_t st);
 int launch_coords(Mesh& m, double* xyz, cudaStream_t st);
+int launch_mirror(const double* q, float* q32, long long n, cudaStream_t st);
 
 // per-kernel event timing (profile.cpp); -1 when profiling is off
 int prof_begin_kernel(const char* name, cudaStream_t st);

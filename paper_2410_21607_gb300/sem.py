@@ -24,7 +24,8 @@ SEM_MAX_THRESHOLDS = 8
 EXPORTS = (
     "sem_last_error", "sem_params_default", "sem_mesh_create", "sem_mesh_destroy",
     "sem_mesh_get_info", "sem_mesh_coords_host", "sem_mesh_leaves_host", "sem_mesh_hmap_host",
-    "sem_mesh_mass_host", "sem_mesh_coords", "sem_rhs", "sem_rk_stage", "sem_step",
+    "sem_mesh_mass_host", "sem_mesh_coords", "sem_rhs", "sem_rk_stage", "sem_rk_stage_mixed",
+    "sem_mirror", "sem_step",
     "sem_adapt_flags", "sem_adapt_flags_host", "sem_transfer_plan", "sem_transfer", "sem_diag",
     "sem_status", "sem_profile_begin", "sem_profile_end",
 )
@@ -85,6 +86,8 @@ def _load():
         "sem_mesh_coords": (i, [vp, vp, vp]),
         "sem_rhs": (i, [vp, C.POINTER(Params), vp, vp, vp]),
         "sem_rk_stage": (i, [vp, C.POINTER(Params), i, vp, vp, vp, d, vp]),
+        "sem_rk_stage_mixed": (i, [vp, C.POINTER(Params), i, vp, vp, vp, vp, vp, d, vp]),
+        "sem_mirror": (i, [vp, vp, vp, vp]),
         "sem_step": (i, [vp, C.POINTER(Params), vp, vp, vp, d, vp]),
         "sem_adapt_flags": (i, [vp, C.POINTER(Params), vp, vp, vp, vp]),
         "sem_adapt_flags_host": (i, [vp, C.POINTER(Params), vp, vp, vp]),
@@ -232,6 +235,32 @@ def sem_rk_stage(mesh, params, stage, qn, qs, qout, dt, stream=None):
     _check(LIB.sem_rk_stage(mesh.h, C.byref(params), int(stage), _ptr(qn), _ptr(qs), _ptr(qout),
                             float(dt), _stream(stream)))
     return qout
+
+
+def _f32(t, shape):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_cuda:
+        raise TypeError("expected a float32 CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {shape}, got {tuple(t.shape)}")
+    return t
+
+
+def sem_rk_stage_mixed(mesh, params, stage, qn, qs, qs32, qout, qout32, dt, stream=None):
+    for t in (qn, qs, qout):
+        _f64(t, mesh.field_shape)
+    for t in (qs32, qout32):
+        _f32(t, mesh.field_shape)
+    _check(LIB.sem_rk_stage_mixed(mesh.h, C.byref(params), int(stage), _ptr(qn), _ptr(qs),
+                                  _ptr(qs32), _ptr(qout), _ptr(qout32), float(dt), _stream(stream)))
+    return qout
+
+
+def sem_mirror(mesh, q, q32, stream=None):
+    _f64(q, mesh.field_shape)
+    _f32(q32, mesh.field_shape)
+    _check(LIB.sem_mirror(mesh.h, _ptr(q), _ptr(q32), _stream(stream)))
+    return q32
 
 
 def sem_step(mesh, params, q, w1, w2, dt, stream=None):

@@ -270,3 +270,30 @@ def test_bad_arguments_are_rejected(sem):
     p.eqset = 7
     with pytest.raises(sem.SemError):
         sem.sem_rhs(m, p, q, torch.empty_like(q))
+
+
+def test_mixed_stage_with_mirrors_matches_oracle(sem):
+    """sem_rk_stage_mixed with caller-owned float32 mirrors, ten SSP-RK3 steps
+    on the non-conforming mesh, against the oracle's float64 steps."""
+    m, o, X, perm = make_pair(sem, **MESHES["twolevel-N4"])
+    q_o = vortex_state(o.XG, o.Lz)
+    q_ref = q_o.copy()
+    for _ in range(10):
+        q_ref = ork.rk_step(o, PRM, q_ref, 1.0)
+    p = sem.sem_params_default(precision=sem.SEM_PREC_MIXED)
+    q = dev(q_o[:, perm])
+    w1, w2 = torch.empty_like(q), torch.empty_like(q)
+    q32, w132, w232 = (torch.empty(q.shape, dtype=torch.float32, device="cuda") for _ in range(3))
+    sem.sem_mirror(m, q, q32)
+    np.testing.assert_allclose(host(q32), host(q), rtol=2.4e-7)
+    for _ in range(10):
+        sem.sem_rk_stage_mixed(m, p, 0, q, q, q32, w1, w132, 1.0)
+        sem.sem_rk_stage_mixed(m, p, 1, q, w1, w132, w2, w232, 1.0)
+        sem.sem_rk_stage_mixed(m, p, 2, q, w2, w232, w1, w132, 1.0)
+        q, w1, q32, w132 = w1, q, w132, q32
+    got = host(q)
+    z = X[:, 2]
+    err = group_rel_l2(full_fields(got, z), full_fields(q_ref[:, perm], z))
+    assert np.all(err <= 1e-4), err
+    np.testing.assert_allclose(host(q32), got, rtol=2.4e-7, atol=1e-30)
+    assert sem.sem_status(m) == 0
