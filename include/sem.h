@@ -144,6 +144,32 @@ int sem_mesh_coords(sem_mesh* m, double* coords_dev, cudaStream_t stream);
 int sem_rhs(sem_mesh* m, const sem_params* p, const double* q_dev, double* rhs_dev,
             cudaStream_t stream);
 
+/* sem_rhs without any device allocation.
+ *
+ * For callers that may not allocate device memory when they evaluate the
+ * right-hand side: for example code that runs while another allocator (a
+ * framework's caching allocator or a memory pool) has reserved all free device
+ * memory, so that a new cudaMalloc would fail, or real-time and certified
+ * code that forbids device allocation after start-up.  The paper has no
+ * counterpart; it is an interface addition of this library.
+ *
+ * Same inputs, outputs and result as sem_rhs.  Instead of the mesh's own
+ * residual scratch it uses one fixed device array of 16 MiB built into the
+ * library (every GPU that loads the library holds it until the process
+ * exits), so it serves meshes with Ncol * (N+1)^2 * 5 * NZ * 8 <= 16 MiB
+ * (about 1,000 columns of 16 layers at N = 4); larger meshes get SEM_ERR_ARG
+ * before any device work.  The call itself allocates nothing: the mesh must
+ * already have its device tables, made by any earlier device call on it (for
+ * example sem_mesh_coords), else SEM_ERR_ARG.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress, kept per
+ * device); make that first call before any stream capture.  All calls share
+ * the one array and every element of it that a call reads is first written
+ * by the same call, so nothing needs clearing between calls; calls that
+ * overlap on the GPU (on different streams, or from several threads) race on
+ * the array and must be serialised by the caller. */
+int sem_rhs_noalloc(sem_mesh* m, const sem_params* p, const double* q_dev, double* rhs_dev,
+                    cudaStream_t stream);
+
 /* One stage of the SSP-RK3 scheme (Sec. 4, time integration):
  *   q_out = a[stage] qn + b[stage] qs + c[stage] dt rhs(qs)
  * with (a, b, c) = (0, 1, 1), (3/4, 1/4, 1/4), (1/3, 2/3, 2/3).

@@ -16,6 +16,7 @@
 // float for the mixed form (perturbation arithmetic in float32; reference
 // state and metric terms from float64 tables; stage accumulation in float64).
 #include <cstdio>
+#include <mutex>
 
 #include "sem_internal.h"
 
@@ -490,7 +491,7 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
   }
   VolArgs A;
   A.q = mixed ? (const void*)qs32 : (const void*)s.qs;
-  A.rc = D.scratch;
+  A.rc = s.scratch ? s.scratch : D.scratch;
   A.hmap = D.hmap;
   A.hang_h = D.hang_h;
   A.hang_w = mixed ? (const void*)D.hang_w32 : (const void*)D.hang_w;
@@ -533,7 +534,7 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
   }
   SEM_CUDA_TRY(cudaGetLastError());
   DssArgs B;
-  B.rc = D.scratch;
+  B.rc = s.scratch ? s.scratch : D.scratch;
   B.qt_ptr = D.qt_ptr;
   B.qt_src = D.qt_src;
   B.qt_w = mixed ? (const void*)D.qt_w32 : (const void*)D.qt_w;
@@ -563,3 +564,61 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
 }
 
 }  // namespace sem
+
+// ---------------------------------------------------------------------------
+// Allocation-free right-hand side (sem_rhs_noalloc).
+//
+// Its column-residual scratch is this file-scope device array instead of
+// memory the library allocates per mesh.  Every GPU that loads the library
+// holds the array until the process exits.  Host code cannot use the array's
+// name as a device address (on the host it names a stand-in object), so the
+// device address is looked up once per device with cudaGetSymbolAddress, with
+// that device current, and passed to the kernels.
+namespace sem {
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchBytes / sizeof(double)];
+constexpr int kNoAllocMaxDevices = 64;
+static void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+static std::mutex g_noalloc_mu;
+
+static int noalloc_scratch_address(int dev, void** out) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(SEM_ERR_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(SEM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return SEM_OK;
+}
+}  // namespace sem
+
+extern "C" int sem_rhs_noalloc(sem_mesh* mh, const sem_params* p, const double* q, double* rhs,
+                               cudaStream_t st) {
+  using namespace sem;
+  if (!mh || !p || !q || !rhs || q == rhs) return fail(SEM_ERR_ARG, "NULL or aliased argument");
+  if ((p->eqset != SEM_EQ_CONSERVATIVE && p->eqset != SEM_EQ_NONCONSERVATIVE) ||
+      (p->precision != SEM_PREC_FP64 && p->precision != SEM_PREC_MIXED))
+    return fail(SEM_ERR_ARG, "unknown equation set or precision");
+  Mesh& m = mh->m;
+  const size_t need = (size_t)m.Ncol() * m.Nq * kFields * m.NZ * sizeof(double);
+  if (need > kNoAllocScratchBytes)
+    return fail(SEM_ERR_ARG, "mesh too large for sem_rhs_noalloc: needs " + std::to_string(need) +
+                                 " bytes of scratch, the fixed maximum is " +
+                                 std::to_string(kNoAllocScratchBytes));
+  int dev = 0;
+  SEM_CUDA_TRY(cudaGetDevice(&dev));
+  if (!m.dev)
+    return fail(SEM_ERR_ARG, "the mesh has no device tables yet: make another device call on it "
+                             "first (for example sem_mesh_coords)");
+  if (m.dev_id != dev) return fail(SEM_ERR_ARG, "mesh tables live on another device");
+  int rc = ensure_reference(m, *p);
+  if (rc) return rc;
+  void* scratch = nullptr;
+  if ((rc = noalloc_scratch_address(dev, &scratch))) return rc;
+  StageArgs s{nullptr, q, rhs, nullptr, nullptr, 0.0, 0.0, 1.0, 1, scratch};
+  return launch_rhs_stage(m, *p, s, st);
+}

@@ -154,6 +154,7 @@ struct StageArgs {
   float* out32;       // mixed form: float32 mirror of out to write (may be null)
   double a, b, cdt;   // out = a qn + b qs + cdt * tendency; rhs mode: a=b=0, cdt=1
   int rhs_only;
+  void* scratch;      // column-residual scratch; null: the mesh's own
 };
 int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStream_t st);
 int launch_adapt(Mesh& m, const sem_params& p, const double* q, int8_t* flags, double* cmax,

@@ -24,7 +24,8 @@ SEM_MAX_THRESHOLDS = 8
 EXPORTS = (
     "sem_last_error", "sem_params_default", "sem_mesh_create", "sem_mesh_destroy",
     "sem_mesh_get_info", "sem_mesh_coords_host", "sem_mesh_leaves_host", "sem_mesh_hmap_host",
-    "sem_mesh_mass_host", "sem_mesh_coords", "sem_rhs", "sem_rk_stage", "sem_rk_stage_mixed",
+    "sem_mesh_mass_host", "sem_mesh_coords", "sem_rhs", "sem_rhs_noalloc", "sem_rk_stage",
+    "sem_rk_stage_mixed",
     "sem_mirror", "sem_step",
     "sem_adapt_flags", "sem_adapt_flags_host", "sem_transfer_plan", "sem_transfer", "sem_diag",
     "sem_status", "sem_profile_begin", "sem_profile_end",
@@ -85,6 +86,7 @@ def _load():
         "sem_mesh_mass_host": (i, [vp, vp]),
         "sem_mesh_coords": (i, [vp, vp, vp]),
         "sem_rhs": (i, [vp, C.POINTER(Params), vp, vp, vp]),
+        "sem_rhs_noalloc": (i, [vp, C.POINTER(Params), vp, vp, vp]),
         "sem_rk_stage": (i, [vp, C.POINTER(Params), i, vp, vp, vp, d, vp]),
         "sem_rk_stage_mixed": (i, [vp, C.POINTER(Params), i, vp, vp, vp, vp, vp, d, vp]),
         "sem_mirror": (i, [vp, vp, vp, vp]),
@@ -226,6 +228,16 @@ def sem_rhs(mesh, params, q, out, stream=None):
     _f64(q, mesh.field_shape)
     _f64(out, mesh.field_shape)
     _check(LIB.sem_rhs(mesh.h, C.byref(params), _ptr(q), _ptr(out), _stream(stream)))
+    return out
+
+
+def sem_rhs_noalloc(mesh, params, q, out, stream=None):
+    """sem_rhs with the library's fixed 16 MiB device scratch instead of the
+    mesh's own: for callers that may not allocate device memory at this point.
+    The mesh needs its device tables already (any earlier device call)."""
+    _f64(q, mesh.field_shape)
+    _f64(out, mesh.field_shape)
+    _check(LIB.sem_rhs_noalloc(mesh.h, C.byref(params), _ptr(q), _ptr(out), _stream(stream)))
     return out
 
 
