@@ -195,24 +195,29 @@ def main():
 
     def new_bufs():
         b = [q0.clone(), torch.empty_like(q0), torch.empty_like(q0)]
-        m32 = [torch.empty(q0.shape, dtype=torch.float32, device="cuda") for _ in range(3)]
+        m32 = [torch.empty(q0.shape, dtype=torch.float32, device="cuda"),
+               torch.empty((10, q0.shape[1]), dtype=torch.float32, device="cuda")]
         sem.sem_mirror(m, b[0], m32[0], stream)
         return b + m32
 
     def step(b, prm):
-        # ping-pong: q -> w1 -> w2 -> w1, then w1 becomes the new state
-        qn, w1, w2, qn32, w132, w232 = b
+        qn, w1, w2, q32, work = b
         if prm.precision == sem.SEM_PREC_MIXED:
-            sem.sem_rk_stage_mixed(m, prm, 0, qn, qn, qn32, w1, w132, dt, stream)
-            sem.sem_rk_stage_mixed(m, prm, 1, qn, w1, w132, w2, w232, dt, stream)
-            sem.sem_rk_stage_mixed(m, prm, 2, qn, w2, w232, w1, w132, dt, stream)
-        else:
-            sem.sem_rk_stage(m, prm, 0, qn, qn, w1, dt, stream)
-            sem.sem_rk_stage(m, prm, 1, qn, w1, w2, dt, stream)
-            sem.sem_rk_stage(m, prm, 2, qn, w2, w1, dt, stream)
-        return [w1, qn, w2, w132, qn32, w232]
+            # increment form: float32 stage increments, float64 state update
+            sem.sem_step_mixed(m, prm, qn, q32, work, dt, stream)
+            return b
+        # float64 form, ping-pong: q -> w1 -> w2 -> w1, then w1 is the state
+        sem.sem_rk_stage(m, prm, 0, qn, qn, w1, dt, stream)
+        sem.sem_rk_stage(m, prm, 1, qn, w1, w2, dt, stream)
+        sem.sem_rk_stage(m, prm, 2, qn, w2, w1, dt, stream)
+        return [w1, qn, w2, q32, work]
 
     bufs = new_bufs()
+    tune = None
+    if a.form == "mixed":
+        rows, chosen = sem.sem_autotune(m, p, bufs[3], 5, stream)
+        tune = {"variants": [{"layers_per_cta": r[0], "min_ctas_per_sm": r[1], "ms": r[2]}
+                             for r in rows], "chosen": chosen}
     dof_stage = 5 * m.Ne * (N + 1) ** 3
     for _ in range(max(a.warmup, 3)):
         bufs = step(bufs, p)
@@ -248,17 +253,24 @@ def main():
     # (float32 mirror or float64), the column residuals written and read back,
     # the stage's float64 reads (qs; qn on 2 of 3 stages), the float64 output
     # and its float32 mirror, plus the index and mass tables
+    NZr = (NZ + 3) // 4 * 4
     alg = {
         "volume": 5 * rbytes * NG + 4 * Nq * Ncol + 5 * rbytes * Ncol * Nq * NZ,
+        # float64 form: residual read, qs and (2 of 3 stages) qn read, output write
         "dss_rk": (5 * rbytes * Ncol * Nq * NZ + (1 + 2.0 / 3.0) * 5 * 8 * NG + 5 * 8 * NG
-                   + (5 * 4 * NG if a.form == "mixed" else 0) + rbytes * (NH + NZ)
-                   + (4 + rbytes) * Ncol * Nq + 4 * NH),
+                   + rbytes * (NH + NZ) + (4 + rbytes) * Ncol * Nq + 4 * NH),
+        # increment form, averaged over its 3 stages: residual read; stage 0
+        # writes d and a mirror and reads the mirror of q_n (12 B/value),
+        # stage 1 also reads d (16 B), stage 2 reads d and q, writes q and its
+        # mirror (24 B)
+        "dss_inc": (5 * 4 * Ncol * Nq * NZ + 5 * NG * (12 + 16 + 24) / 3.0
+                    + 4 * (NH + NZ) + 8 * Ncol * Nq + 4 * NH),
     }
     kernels = {}
     for name, (launches, tot) in prof.items():
         if name == "mirror":
             continue
-        base = name.rsplit("_", 1)[0] if name.startswith("volume") else "dss_rk"
+        base = name.rsplit("_", 1)[0]
         avg = tot / max(launches, 1)
         kernels[name] = {"launches": launches, "ms_avg": avg, "share": None,
                          "alg_bytes": alg[base], "gbs": alg[base] / (avg * 1e-3) / 1e9}
@@ -341,12 +353,12 @@ def main():
                 "ms_per_step": fp64_ms, "value": dof_stage * 3 * world / (fp64_ms * 1e-3),
                 "speedup_mixed_over_fp64": fp64_ms / ms},
             "gate": gate,
-            "roofline": roof, "kernels": kernels,
+            "roofline": roof, "kernels": kernels, "autotune": tune,
             "cpu_baseline": cpu,
             "e2e": {"value": dof_stage * 3 * world / (e2e_ms * 1e-3), "unit": "DOF-updates/s",
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                     "ms_per_step": e2e_ms},
-            "gpu_launches": 2 * 3 * a.steps,
+            "gpu_launches": sum(v[0] for v in prof.values()),
             "clocks": ck, "status": status,
         }
         print(json.dumps(line), flush=True)

@@ -156,7 +156,8 @@ int sem_rhs(sem_mesh* m, const sem_params* p, const double* q_dev, double* rhs_d
  * Same inputs, outputs and result as sem_rhs.  Instead of the mesh's own
  * residual scratch it uses one fixed device array of 16 MiB built into the
  * library (every GPU that loads the library holds it until the process
- * exits), so it serves meshes with Ncol * (N+1)^2 * 5 * NZ * 8 <= 16 MiB
+ * exits), so it serves meshes with Ncol * (N+1)^2 * 5 * NZ4 * 8 <= 16 MiB
+ * (NZ4 = NZ rounded up to a multiple of 4)
  * (about 1,000 columns of 16 layers at N = 4); larger meshes get SEM_ERR_ARG
  * before any device work.  The call itself allocates nothing: the mesh must
  * already have its device tables, made by any earlier device call on it (for
@@ -187,6 +188,18 @@ int sem_rk_stage(sem_mesh* m, const sem_params* p, int stage, const double* qn_d
 int sem_rk_stage_mixed(sem_mesh* m, const sem_params* p, int stage, const double* qn_dev,
                        const double* qs_dev, const float* qs32_dev, double* qout_dev,
                        float* qout32_dev, double dt, cudaStream_t stream);
+
+/* A whole SSP-RK3 step of the mixed form, conservative set, in increment
+ * form: with d_s = q_s - q_n,
+ *   d_1 = dt L(q_n), d_2 = (d_1 + dt L(q_1)) / 4, d_3 = 2 (d_2 + dt L(q_2)) / 3,
+ *   q_{n+1} = q_n + d_3,
+ * which is the Shu-Osher SSP-RK3 step rewritten exactly.  The increments d_s
+ * are float32, the state q (float64, [5][NG]) is updated in place with one
+ * float64 addition per value, and q32 (its float32 mirror, [5][NG], from
+ * sem_mirror or the previous step) is updated with it.  work32_dev is
+ * caller-owned float32 scratch of 2 * 5 * NG values. */
+int sem_step_mixed(sem_mesh* m, const sem_params* p, double* q_dev, float* q32_dev,
+                   float* work32_dev, double dt, cudaStream_t stream);
 
 /* q32 = float32 mirror of q ([5][NG]; significand truncated to 24 bits). */
 int sem_mirror(sem_mesh* m, const double* q_dev, float* q32_dev, cudaStream_t stream);
@@ -229,6 +242,24 @@ int sem_diag(sem_mesh* m, const sem_params* p, const double* q_dev, double half_
  * they write a non-finite value; synchronises the stream.  *status_host is 0
  * (clean) or SEM_ERR_NUMERIC. */
 int sem_status(sem_mesh* m, int* status_host, cudaStream_t stream);
+
+/* Autotuner of the mixed-form element kernel.  Times every launch variant
+ * compiled for the mesh's order (layers of a column per CTA, and the number
+ * of CTAs per SM the register budget is sized for) on the float32 state
+ * mirror q32_dev, `reps` launches each after two warm-up launches, keeps the
+ * fastest for this mesh (used by sem_rk_stage, sem_rk_stage_mixed and
+ * sem_step_mixed afterwards) and reports all timings.  Synchronises the
+ * stream; overwrites the mesh's residual scratch. */
+#define SEM_TUNE_MAX 16
+typedef struct {
+  int n_variants;
+  int chosen;                          /* index into the arrays below */
+  int layers_per_cta[SEM_TUNE_MAX];
+  int min_ctas_per_sm[SEM_TUNE_MAX];
+  double ms[SEM_TUNE_MAX];             /* mean event time per launch */
+} sem_tune_out;
+int sem_autotune(sem_mesh* m, const sem_params* p, const float* q32_dev, int reps,
+                 sem_tune_out* out_host, cudaStream_t stream);
 
 /* Kernel timing.  Between sem_profile_begin and sem_profile_end every kernel
  * the library launches is bracketed by CUDA events recorded on the stream it

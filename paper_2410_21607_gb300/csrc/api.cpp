@@ -77,8 +77,8 @@ int ensure_device(Mesh& m) {
     free_device(m);
     return rc;
   }
-  // column residual scratch: [Ncol][Nq][5][NZ], float64 (also holds float32)
-  D.scratch_bytes = (size_t)m.Ncol() * m.Nq * kFields * m.NZ * sizeof(double);
+  // column residual scratch: [Ncol][Nq][5][NZr], float64 (also holds float32)
+  D.scratch_bytes = (size_t)m.Ncol() * m.Nq * kFields * m.NZr() * sizeof(double);
   cudaError_t e = cudaMalloc(&D.scratch, D.scratch_bytes);
   if (e == cudaSuccess) e = cudaMalloc((void**)&D.status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(D.status, 0, sizeof(int));
@@ -331,6 +331,26 @@ int sem_rk_stage_mixed(sem_mesh* mh, const sem_params* p, int stage, const doubl
     return fail(SEM_ERR_ARG, "outputs must not alias inputs");
   StageArgs s{qn, qs, qout, qs32, qout32, kA[stage], kB[stage], kC[stage] * dt, 0};
   return launch_rhs_stage(mh->m, *p, s, st);
+}
+
+int sem_step_mixed(sem_mesh* mh, const sem_params* p, double* q, float* q32, float* work32,
+                   double dt, cudaStream_t st) {
+  int rc = prepare(mh, p);
+  if (rc) return rc;
+  if (p->precision != SEM_PREC_MIXED || p->eqset != SEM_EQ_CONSERVATIVE)
+    return fail(SEM_ERR_ARG, "sem_step_mixed needs SEM_PREC_MIXED and the conservative set");
+  if (!q || !q32 || !work32) return fail(SEM_ERR_ARG, "NULL argument");
+  if (mh->m.NG * kFields >= (1ll << 31)) return fail(SEM_ERR_ARG, "mesh too large for 32-bit indexing");
+  return launch_step_mixed(mh->m, *p, q, q32, work32, dt, st);
+}
+
+int sem_autotune(sem_mesh* mh, const sem_params* p, const float* q32, int reps, sem_tune_out* out,
+                 cudaStream_t st) {
+  int rc = prepare(mh, p);
+  if (rc) return rc;
+  if (!q32 || !out || reps < 1) return fail(SEM_ERR_ARG, "bad argument");
+  std::memset(out, 0, sizeof(*out));
+  return autotune_pencil(mh->m, *p, q32, reps, out, st);
 }
 
 int sem_mirror(sem_mesh* mh, const double* q, float* q32, cudaStream_t st) {

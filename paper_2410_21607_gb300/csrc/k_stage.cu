@@ -91,6 +91,7 @@ struct VolArgs {
   const int* col_level;
   const double* ref;
   int Ncol, nz, NZ;
+  int NZr;              // level stride of the column residuals (NZ rounded up to 4)
   long long NH, NG;
   double Lx, Ly, Lz;
   int nx, ny;
@@ -293,9 +294,9 @@ volume_column(const VolArgs A) {
 #pragma unroll
         for (int fl = 0; fl < kFields; ++fl) sC[k & 1][fl][ab] = r[fl];
       } else {
-        R* dst = rc + ((long long)((long long)col * Nq + ab) * kFields) * A.NZ + kz;
+        R* dst = rc + ((long long)((long long)col * Nq + ab) * kFields) * A.NZr + kz;
 #pragma unroll
-        for (int fl = 0; fl < kFields; ++fl) dst[(long long)fl * A.NZ] = r[fl];
+        for (int fl = 0; fl < kFields; ++fl) dst[(long long)fl * A.NZr] = r[fl];
       }
     }
     __syncthreads();
@@ -350,7 +351,7 @@ struct DssArgs {
   double a, b, cdt;
   int rhs_only;
   long long NH, NG;
-  int NZ;
+  int NZ, NZr;
   int* status;
 };
 
@@ -371,9 +372,9 @@ __global__ void __launch_bounds__(256) dss_stage_fp64(const DssArgs A) {
     double acc[kFields] = {0, 0, 0, 0, 0};
     for (int e = beg; e < end; ++e) {
       const double w = __ldg(qtw + e);
-      const double* p = rc + (long long)__ldg(A.qt_src + e) * kFields * A.NZ + kz;
+      const double* p = rc + (long long)__ldg(A.qt_src + e) * kFields * A.NZr + kz;
 #pragma unroll
-      for (int fl = 0; fl < kFields; ++fl) acc[fl] = fma(w, p[(long long)fl * A.NZ], acc[fl]);
+      for (int fl = 0; fl < kFields; ++fl) acc[fl] = fma(w, p[(long long)fl * A.NZr], acc[fl]);
     }
 #pragma unroll
     for (int fl = 0; fl < kFields; ++fl) {
@@ -414,9 +415,9 @@ __global__ void __launch_bounds__(256) dss_stage_mixed(const DssArgs A) {
     float acc[kFields] = {0, 0, 0, 0, 0};
     for (int e = beg; e < end; ++e) {
       const float w = __ldg(qtw + e);
-      const float* p = rc + (long long)__ldg(A.qt_src + e) * kFields * A.NZ + kz;
+      const float* p = rc + (long long)__ldg(A.qt_src + e) * kFields * A.NZr + kz;
 #pragma unroll
-      for (int fl = 0; fl < kFields; ++fl) acc[fl] = fmaf(w, p[(long long)fl * A.NZ], acc[fl]);
+      for (int fl = 0; fl < kFields; ++fl) acc[fl] = fmaf(w, p[(long long)fl * A.NZr], acc[fl]);
     }
 #pragma unroll
     for (int fl = 0; fl < kFields; ++fl) {
@@ -462,36 +463,254 @@ static void launch_volume_n(const VolArgs& A, int eq, bool mixed, cudaStream_t s
   }
 }
 
-static int grid_cap(long long work) {
-  int dev = 0, nsm = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  long long blocks = (work + 255) / 256;
-  long long cap = (long long)nsm * 8;
-  return (int)(blocks < cap ? (blocks > 0 ? blocks : 1) : cap);
+// ---------------------------------------------------------------------------
+// Mixed form, conservative set: z-pencil element kernel.
+//
+// One CTA per leaf column; thread (ab, kk) owns the N+1 nodes of the vertical
+// line (a, b) of layer k = chunk * KL + kk, so consecutive threads walk up a
+// column's z-lines and their loads and stores are contiguous.  The z-direction
+// contraction runs on the thread's own registers; the x and y flux components
+// go to shared memory with the nodes of a z-line side by side, so that one
+// 64-bit shared load feeds a packed float32x2 FMA for two nodes.  The face
+// shared by consecutive layers is summed inside the CTA (vertical DSS), as in
+// volume_column.  Arithmetic: float32; geometry and reference state come from
+// tables computed in float64.
+template <int N, int KL, int MB>
+__global__ void __launch_bounds__(KL * (N + 1) * (N + 1), MB)
+volume_pencil_mixed(const VolArgs A) {
+  constexpr int n1 = N + 1, Nq = n1 * n1, CP = (n1 + 1) / 2, CW = 2 * CP;
+  constexpr int SXY = kFields * KL * Nq * CW;  // floats per flux direction
+  extern __shared__ __align__(16) float smem[];
+  float* sX = smem;                    // [f][kk][j][m][c]
+  float* sY = sX + SXY;                // [f][kk][i][m][c]
+  float* sT = sY + SXY;                // [f][kk][ab]: top-face residual
+  float* sP = sT + kFields * KL * Nq;  // [f][ab]: carry between chunks
+  const int t = threadIdx.x;
+  const int kk = t % KL, ab = t / KL;
+  const int i = ab % n1, j = ab / n1;
+  const int col = blockIdx.x;
+  const int lev = A.col_level[col];
+  const float* geo = A.geof[lev];
+  const float sx = geo[4], sy = geo[5], sz = geo[6], J = geo[3];
+  const int hm = A.hmap[(long long)col * Nq + ab];
+  const float* q = (const float*)A.q;
+  const float* hw = (const float*)A.hang_w;
+  float Dwi[n1], Dwj[n1];
+#pragma unroll
+  for (int m = 0; m < n1; ++m) {
+    Dwi[m] = c_Dwf[N][i * n1 + m];
+    Dwj[m] = c_Dwf[N][j * n1 + m];
+  }
+  const float wi = c_wf[N][i], wj = c_wf[N][j];
+  const float g = A.gf, fc = A.ff, gam = A.gammaf;
+  float* rc = (float*)A.rc;
+  const int nchunk = (A.nz + KL - 1) / KL;
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const int k = ch * KL + kk;
+    const bool act = k < A.nz;
+    const int kz0 = k * N;
+    float2 r[kFields][CP];
+#pragma unroll
+    for (int f = 0; f < kFields; ++f)
+#pragma unroll
+      for (int p = 0; p < CP; ++p) r[f][p] = make_float2(0.f, 0.f);
+    float* myX = sX + ((0 * KL + kk) * n1 + j) * n1 * CW + i * CW;  // + f * KL*Nq*CW + c
+    float* myY = sY + ((0 * KL + kk) * n1 + i) * n1 * CW + j * CW;
+    constexpr int FS = KL * Nq * CW;                               // field stride
+    if (act) {
+#pragma unroll
+      for (int c = 0; c < n1; ++c) {
+        float v[kFields];
+        const int kz = kz0 + c;
+        if (hm >= 0) {
+          const float* pq = q + (long long)hm * A.NZ + kz;
+#pragma unroll
+          for (int f = 0; f < kFields; ++f) v[f] = __ldg(pq + (long long)f * A.NG);
+        } else {
+          const int hk = -1 - hm;
+#pragma unroll
+          for (int f = 0; f < kFields; ++f) v[f] = 0.f;
+#pragma unroll
+          for (int m = 0; m < n1; ++m) {
+            const float wm = __ldg(hw + hk * n1 + m);
+            const float* pq = q + (long long)__ldg(A.hang_h + hk * n1 + m) * A.NZ + kz;
+#pragma unroll
+            for (int f = 0; f < kFields; ++f) v[f] = fmaf(wm, __ldg(pq + (long long)f * A.NG), v[f]);
+          }
+        }
+        const float* rf = A.ref32 + (long long)kz * kRef;
+        const float p0 = __ldg(rf + 2), rho0 = __ldg(rf + 3), rt0 = __ldg(rf + 4), inv_rt0 = __ldg(rf + 6);
+        const float rp = v[0], U = v[1], V = v[2], W = v[3], Tp = v[4];
+        const float inv = __frcp_rn(rho0 + rp);
+        const float u = U * inv, vv = V * inv, w = W * inv;
+        const float pp = p0 * expm1f(gam * log1pf(Tp * inv_rt0));
+        const float rt = rt0 + Tp;
+        const float wc = c_wf[N][c];
+        const float ax = wj * wc * sx, ay = wi * wc * sy, az = wi * wj * sz;
+        myX[0 * FS + c] = U * ax;
+        myX[1 * FS + c] = (U * u + pp) * ax;
+        myX[2 * FS + c] = V * u * ax;
+        myX[3 * FS + c] = W * u * ax;
+        myX[4 * FS + c] = rt * u * ax;
+        myY[0 * FS + c] = V * ay;
+        myY[1 * FS + c] = U * vv * ay;
+        myY[2 * FS + c] = (V * vv + pp) * ay;
+        myY[3 * FS + c] = W * vv * ay;
+        myY[4 * FS + c] = rt * vv * ay;
+        // z contraction on registers as a rank-1 update per node:
+        // r[c'] += Dw[c'][c] Fz[c] for every node c' of the z-line
+        const float fzv[kFields] = {W * az, U * w * az, V * w * az, (W * w + pp) * az, rt * w * az};
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) {
+          const float2 fm = make_float2(fzv[f], fzv[f]);
+#pragma unroll
+          for (int p = 0; p < CP; ++p) {
+            const float d0 = c_Dwf[N][(2 * p) * n1 + c];
+            const float d1 = (2 * p + 1 < n1) ? c_Dwf[N][(2 * p + 1) * n1 + c] : 0.f;
+            r[f][p] = __ffma2_rn(make_float2(d0, d1), fm, r[f][p]);
+          }
+        }
+        // sources: Coriolis on rho u, rho v; buoyancy on rho w
+        const float wJ = wi * wj * wc * J;
+        float* rr = reinterpret_cast<float*>(&r[0][0]);
+        rr[(1 * CP * 2) + c] += wJ * (fc * V);
+        rr[(2 * CP * 2) + c] += wJ * (-fc * U);
+        rr[(3 * CP * 2) + c] += wJ * (-rp * g);
+      }
+      if (n1 < CW) {
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) {
+          myX[f * FS + n1] = 0.f;
+          myY[f * FS + n1] = 0.f;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int f = 0; f < kFields; ++f)
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+          myX[f * FS + c] = 0.f;
+          myY[f * FS + c] = 0.f;
+        }
+    }
+    __syncthreads();
+    // x and y contractions from shared memory, two nodes per packed FMA
+    const float* rowX = sX + ((0 * KL + kk) * n1 + j) * n1 * CW;  // + f*FS + m*CW + c
+    const float* rowY = sY + ((0 * KL + kk) * n1 + i) * n1 * CW;
+#pragma unroll
+    for (int f = 0; f < kFields; ++f)
+#pragma unroll
+      for (int m = 0; m < n1; ++m) {
+        const float2 dx = make_float2(Dwi[m], Dwi[m]);
+        const float2 dy = make_float2(Dwj[m], Dwj[m]);
+#pragma unroll
+        for (int p = 0; p < CP; ++p) {
+          const float2 vx = *reinterpret_cast<const float2*>(rowX + f * FS + m * CW + 2 * p);
+          const float2 vy = *reinterpret_cast<const float2*>(rowY + f * FS + m * CW + 2 * p);
+          r[f][p] = __ffma2_rn(dx, vx, r[f][p]);
+          r[f][p] = __ffma2_rn(dy, vy, r[f][p]);
+        }
+      }
+    // vertical DSS: the top node of layer k and the bottom node of layer k+1
+    float* rr = reinterpret_cast<float*>(&r[0][0]);
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) sT[(f * KL + kk) * Nq + ab] = rr[f * CP * 2 + N];
+    if (kk == 0 && ch > 0) {
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) rr[f * CP * 2] += sP[f * Nq + ab];
+    }
+    __syncthreads();
+    if (kk > 0) {
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) rr[f * CP * 2] += sT[(f * KL + kk - 1) * Nq + ab];
+    }
+    if (kk == KL - 1) {
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) sP[f * Nq + ab] = rr[f * CP * 2 + N];
+    }
+    if (act) {
+      float* dst = rc + ((long long)((long long)col * Nq + ab) * kFields) * A.NZr + kz0;
+      const bool top = (k == A.nz - 1);
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) {
+        float* df = dst + (long long)f * A.NZr;
+        if (N == 4) {
+          *reinterpret_cast<float4*>(df) = make_float4(rr[f * CP * 2 + 0], rr[f * CP * 2 + 1],
+                                                       rr[f * CP * 2 + 2], rr[f * CP * 2 + 3]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < N; ++c) df[c] = rr[f * CP * 2 + c];
+        }
+        if (top) df[N] = rr[f * CP * 2 + N];
+      }
+    }
+    __syncthreads();
+  }
 }
 
-int launch_mirror(const double* q, float* q32, long long n, cudaStream_t st) {
-  ProfScope ps("mirror", st);
-  mirror_kernel<<<grid_cap(n), 256, 0, st>>>(q, q32, n);
-  SEM_CUDA_TRY(cudaGetLastError());
+template <int N, int KL>
+static size_t pencil_smem() {
+  constexpr int n1 = N + 1, Nq = n1 * n1, CW = 2 * ((n1 + 1) / 2);
+  return sizeof(float) * (2 * kFields * KL * Nq * CW + kFields * KL * Nq + kFields * Nq);
+}
+
+template <int N, int KL, int MB>
+static int launch_pencil(const VolArgs& A, cudaStream_t st) {
+  const size_t sm = pencil_smem<N, KL>();
+  static bool attr = false;
+  if (!attr) {
+    SEM_CUDA_TRY(cudaFuncSetAttribute(volume_pencil_mixed<N, KL, MB>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr = true;
+  }
+  ProfScope ps("volume_mixed", st);
+  volume_pencil_mixed<N, KL, MB><<<A.Ncol, KL * (N + 1) * (N + 1), sm, st>>>(A);
   return SEM_OK;
 }
 
-int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStream_t st) {
-  int rc = upload_basis_constants();
-  if (rc) return rc;
-  DeviceTables& D = *m.dev;
-  const bool mixed = p.precision == SEM_PREC_MIXED;
-  const float* qs32 = s.qs32;
-  if (mixed && !qs32) {
-    // no caller mirror: make one in the mesh scratch
-    if ((rc = launch_mirror(s.qs, D.mirror, (long long)kFields * m.NG, st))) return rc;
-    qs32 = D.mirror;
+// Launch variants of the pencil kernel: layers per CTA (KL) and the minimum
+// resident CTAs per SM the register allocation is sized for (MB).  The
+// autotuner (sem_autotune) times them on a mesh and keeps the fastest.
+struct PencilVariant {
+  int N, KL, MB;
+  int (*launch)(const VolArgs&, cudaStream_t);
+};
+static const PencilVariant kPencil[] = {
+    {2, 8, 4, launch_pencil<2, 8, 4>},   {2, 16, 2, launch_pencil<2, 16, 2>},
+    {3, 8, 3, launch_pencil<3, 8, 3>},   {3, 16, 2, launch_pencil<3, 16, 2>},
+    {4, 4, 8, launch_pencil<4, 4, 8>},   {4, 8, 2, launch_pencil<4, 8, 2>},
+    {4, 8, 4, launch_pencil<4, 8, 4>},   {4, 16, 1, launch_pencil<4, 16, 1>},
+    {4, 16, 2, launch_pencil<4, 16, 2>}, {5, 8, 1, launch_pencil<5, 8, 1>},
+    {5, 8, 2, launch_pencil<5, 8, 2>},   {6, 4, 2, launch_pencil<6, 4, 2>},
+    {6, 8, 1, launch_pencil<6, 8, 1>},
+};
+constexpr int kNumPencil = sizeof(kPencil) / sizeof(kPencil[0]);
+
+// default choice before tuning: the most layers per CTA that fit nz
+static int pencil_default(int N, int nz) {
+  int best = -1;
+  for (int v = 0; v < kNumPencil; ++v) {
+    if (kPencil[v].N != N) continue;
+    if (best < 0) { best = v; continue; }
+    const PencilVariant& a = kPencil[v];
+    const PencilVariant& b = kPencil[best];
+    const int fa = a.KL <= nz, fb = b.KL <= nz;
+    if (fa != fb ? fa > fb : (a.KL != b.KL ? (fa ? a.KL > b.KL : a.KL < b.KL) : a.MB > b.MB)) best = v;
   }
+  return best;
+}
+
+static int launch_pencil_n(const VolArgs& A, int N, int nz, cudaStream_t st, int variant = -1) {
+  if (variant < 0 || variant >= kNumPencil || kPencil[variant].N != N) variant = pencil_default(N, nz);
+  if (variant < 0) return fail(SEM_ERR_UNSUPPORTED, "order N not compiled");
+  return kPencil[variant].launch(A, st);
+}
+
+static VolArgs make_vol_args(Mesh& m, const sem_params& p, const void* q, bool mixed, void* scratch) {
+  DeviceTables& D = *m.dev;
   VolArgs A;
-  A.q = mixed ? (const void*)qs32 : (const void*)s.qs;
-  A.rc = s.scratch ? s.scratch : D.scratch;
+  A.q = q;
+  A.rc = scratch ? scratch : D.scratch;
   A.hmap = D.hmap;
   A.hang_h = D.hang_h;
   A.hang_w = mixed ? (const void*)D.hang_w32 : (const void*)D.hang_w;
@@ -501,6 +720,7 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
   A.Ncol = (int)m.Ncol();
   A.nz = m.nz;
   A.NZ = m.NZ;
+  A.NZr = m.NZr();
   A.NH = m.NH;
   A.NG = m.NG;
   A.Lx = m.Lx;
@@ -523,8 +743,189 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
       A.geof[l][k] = (float)g[k];
     }
   }
+  return A;
+}
+
+static int grid_cap(long long work) {
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  long long blocks = (work + 255) / 256;
+  long long cap = (long long)nsm * 8;
+  return (int)(blocks < cap ? (blocks > 0 ? blocks : 1) : cap);
+}
+
+// ---------------------------------------------------------------------------
+// Mixed form, increment form of the SSP-RK3 step (sem_step_mixed).
+//
+// With d_s = q_s - q_n the three stages are
+//   d_1 = dt L(q_n),  d_2 = 1/4 d_1 + 1/4 dt L(q_1),  d_3 = 2/3 d_2 + 2/3 dt L(q_2),
+//   q_{n+1} = q_n + d_3.
+// The increments are float32; the state q_n is float64 and receives one
+// float64 addition per value and step.  Stages 0 and 1 write d and the
+// float32 mirror q_n32 + d of the next stage state; stage 2 writes q_{n+1} and
+// its mirror.
+struct IncArgs {
+  const float* rc;
+  const int* qt_ptr;
+  const int* qt_src;
+  const float* qt_w;
+  const float* Minv_h;
+  const float* Minv_z;
+  const float* q32;   // mirror of q_n
+  float* d;           // increment, updated in place
+  float* qs32;        // stages 0, 1: mirror of the next stage state
+  double* q;          // stage 2: float64 state, updated in place
+  float* q32_out;     // stage 2: mirror of q_{n+1}
+  float cdt, bcoef;
+  int NG, NZ, NZr;
+  int* status;
+};
+
+template <int STAGE>
+__global__ void __launch_bounds__(256) dss_inc(const IncArgs A) {
+  int bad = 0;
+  for (int gidx = blockIdx.x * blockDim.x + threadIdx.x; gidx < A.NG; gidx += gridDim.x * blockDim.x) {
+    const int h = (int)((unsigned)gidx / (unsigned)A.NZ);
+    const int kz = gidx - h * A.NZ;
+    const int beg = __ldg(A.qt_ptr + h), end = __ldg(A.qt_ptr + h + 1);
+    const float s = A.cdt * (__ldg(A.Minv_h + h) * __ldg(A.Minv_z + kz));
+    const bool lid = (kz == 0) || (kz == A.NZ - 1);
+    float acc[kFields] = {0, 0, 0, 0, 0};
+    for (int e = beg; e < end; ++e) {
+      const float w = __ldg(A.qt_w + e);
+      const float* p = A.rc + (long long)__ldg(A.qt_src + e) * kFields * A.NZr + kz;
+#pragma unroll
+      for (int fl = 0; fl < kFields; ++fl) acc[fl] = fmaf(w, __ldg(p + fl * A.NZr), acc[fl]);
+    }
+#pragma unroll
+    for (int fl = 0; fl < kFields; ++fl) {
+      const long long o = (long long)fl * A.NG + gidx;
+      const float inc = (fl == 3 && lid) ? 0.f : acc[fl] * s;
+      const float dn = (STAGE == 0) ? inc : fmaf(A.bcoef, A.d[o], inc);
+      if (STAGE < 2) {
+        A.d[o] = dn;
+        A.qs32[o] = __ldg(A.q32 + o) + dn;
+      } else {
+        const double qv = A.q[o] + f2d_bits(dn);
+        A.q[o] = qv;
+        A.q32_out[o] = d2f_bits(qv);
+        bad |= nonfinite_bits(qv);
+      }
+    }
+  }
+  if (STAGE == 2 && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(A.status, 1);
+}
+
+int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float* work32, double dt,
+                      cudaStream_t st) {
+  int rc = upload_basis_constants();
+  if (rc) return rc;
+  DeviceTables& D = *m.dev;
+  float* d = work32;
+  float* qs32 = work32 + (size_t)kFields * m.NG;
+  for (int stage = 0; stage < 3; ++stage) {
+    // element work on the stage state's mirror
+    VolArgs A = make_vol_args(m, p, stage == 0 ? (const void*)q32 : (const void*)qs32, true, nullptr);
+    if ((rc = launch_pencil_n(A, m.N, m.nz, st, m.pencil_variant))) return rc;
+    SEM_CUDA_TRY(cudaGetLastError());
+    IncArgs B;
+    B.rc = (const float*)D.scratch;
+    B.qt_ptr = D.qt_ptr;
+    B.qt_src = D.qt_src;
+    B.qt_w = D.qt_w32;
+    B.Minv_h = D.Minv_h32;
+    B.Minv_z = D.Minv_z32;
+    B.q32 = q32;
+    B.d = d;
+    B.qs32 = qs32;
+    B.q = q;
+    B.q32_out = q32;
+    const double cs[3] = {1.0, 0.25, 2.0 / 3.0};
+    B.cdt = (float)(cs[stage] * dt);
+    B.bcoef = (float)cs[stage];
+    B.NG = (int)m.NG;
+    B.NZ = m.NZ;
+    B.NZr = m.NZr();
+    B.status = D.status;
+    ProfScope ps("dss_inc_mixed", st);
+    const int blocks = grid_cap(m.NG);
+    if (stage == 0) dss_inc<0><<<blocks, 256, 0, st>>>(B);
+    else if (stage == 1) dss_inc<1><<<blocks, 256, 0, st>>>(B);
+    else dss_inc<2><<<blocks, 256, 0, st>>>(B);
+    SEM_CUDA_TRY(cudaGetLastError());
+  }
+  return SEM_OK;
+}
+
+// Autotuner: time every pencil variant compiled for the mesh's order on the
+// given state (float32 mirror) and keep the fastest for this mesh.
+int autotune_pencil(Mesh& m, const sem_params& p, const float* q32, int reps, sem_tune_out* out,
+                    cudaStream_t st) {
+  int rc = upload_basis_constants();
+  if (rc) return rc;
+  VolArgs A = make_vol_args(m, p, q32, true, nullptr);
+  cudaEvent_t e0, e1;
+  SEM_CUDA_TRY(cudaEventCreate(&e0));
+  SEM_CUDA_TRY(cudaEventCreate(&e1));
+  int best = -1;
+  float best_ms = 0.f;
+  out->n_variants = 0;
+  for (int v = 0; v < kNumPencil && out->n_variants < SEM_TUNE_MAX; ++v) {
+    if (kPencil[v].N != m.N) continue;
+    for (int w = 0; w < 2; ++w) kPencil[v].launch(A, st);
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps; ++r) kPencil[v].launch(A, st);
+    cudaEventRecord(e1, st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return fail(SEM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    const int k = out->n_variants++;
+    out->layers_per_cta[k] = kPencil[v].KL;
+    out->min_ctas_per_sm[k] = kPencil[v].MB;
+    out->ms[k] = ms;
+    if (best < 0 || ms < best_ms) {
+      best = v;
+      best_ms = ms;
+      out->chosen = k;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best < 0) return fail(SEM_ERR_UNSUPPORTED, "no variant for this order");
+  m.pencil_variant = best;
+  return SEM_OK;
+}
+
+int launch_mirror(const double* q, float* q32, long long n, cudaStream_t st) {
+  ProfScope ps("mirror", st);
+  mirror_kernel<<<grid_cap(n), 256, 0, st>>>(q, q32, n);
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
+
+int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStream_t st) {
+  int rc = upload_basis_constants();
+  if (rc) return rc;
+  DeviceTables& D = *m.dev;
+  const bool mixed = p.precision == SEM_PREC_MIXED;
+  const float* qs32 = s.qs32;
+  if (mixed && !qs32) {
+    // no caller mirror: make one in the mesh scratch
+    if ((rc = launch_mirror(s.qs, D.mirror, (long long)kFields * m.NG, st))) return rc;
+    qs32 = D.mirror;
+  }
+  VolArgs A = make_vol_args(m, p, mixed ? (const void*)qs32 : (const void*)s.qs, mixed, s.scratch);
   const int eq = p.eqset;
-  switch (m.N) {
+  if (mixed && eq == SEM_EQ_CONSERVATIVE) {
+    if ((rc = launch_pencil_n(A, m.N, m.nz, st, m.pencil_variant))) return rc;
+  } else switch (m.N) {
     case 2: launch_volume_n<2>(A, eq, mixed, st); break;
     case 3: launch_volume_n<3>(A, eq, mixed, st); break;
     case 4: launch_volume_n<4>(A, eq, mixed, st); break;
@@ -551,6 +952,7 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
   B.NH = m.NH;
   B.NG = m.NG;
   B.NZ = m.NZ;
+  B.NZr = m.NZr();
   B.status = D.status;
   {
     ProfScope ps(mixed ? "dss_rk_mixed" : "dss_rk_fp64", st);
@@ -604,7 +1006,7 @@ extern "C" int sem_rhs_noalloc(sem_mesh* mh, const sem_params* p, const double* 
       (p->precision != SEM_PREC_FP64 && p->precision != SEM_PREC_MIXED))
     return fail(SEM_ERR_ARG, "unknown equation set or precision");
   Mesh& m = mh->m;
-  const size_t need = (size_t)m.Ncol() * m.Nq * kFields * m.NZ * sizeof(double);
+  const size_t need = (size_t)m.Ncol() * m.Nq * kFields * m.NZr() * sizeof(double);
   if (need > kNoAllocScratchBytes)
     return fail(SEM_ERR_ARG, "mesh too large for sem_rhs_noalloc: needs " + std::to_string(need) +
                                  " bytes of scratch, the fixed maximum is " +

@@ -78,6 +78,8 @@ struct Mesh {
   std::vector<Origin> origin;
   long long parent_serial = -1;
   long long serial = 0;
+  // element-kernel launch variant chosen by the autotuner (-1: default)
+  int pencil_variant = -1;
   // device
   DeviceTables* dev = nullptr;
   int dev_id = -1;
@@ -87,6 +89,7 @@ struct Mesh {
   double hx(int l) const { return Lx / (double)((long long)nx << l); }
   double hy(int l) const { return Ly / (double)((long long)ny << l); }
   double hz() const { return Lz / nz; }
+  int NZr() const { return (NZ + 3) & ~3; }  // level stride of the column residual scratch
 };
 
 int build_mesh(Mesh& m);                       // numbering from leaves (host)
@@ -164,6 +167,10 @@ int launch_diag(Mesh& m, const sem_params& p, const double* q, double half_width
 int launch_transfer(Mesh& oldm, Mesh& newm, const double* qold, double* qnew, cudaStream_t st);
 int launch_coords(Mesh& m, double* xyz, cudaStream_t st);
 int launch_mirror(const double* q, float* q32, long long n, cudaStream_t st);
+int autotune_pencil(Mesh& m, const sem_params& p, const float* q32, int reps, sem_tune_out* out,
+                    cudaStream_t st);
+int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float* work32, double dt,
+                      cudaStream_t st);
 
 // per-kernel event timing (profile.cpp); -1 when profiling is off
 int prof_begin_kernel(const char* name, cudaStream_t st);

@@ -26,9 +26,9 @@ EXPORTS = (
     "sem_mesh_get_info", "sem_mesh_coords_host", "sem_mesh_leaves_host", "sem_mesh_hmap_host",
     "sem_mesh_mass_host", "sem_mesh_coords", "sem_rhs", "sem_rhs_noalloc", "sem_rk_stage",
     "sem_rk_stage_mixed",
-    "sem_mirror", "sem_step",
+    "sem_mirror", "sem_step", "sem_step_mixed",
     "sem_adapt_flags", "sem_adapt_flags_host", "sem_transfer_plan", "sem_transfer", "sem_diag",
-    "sem_status", "sem_profile_begin", "sem_profile_end",
+    "sem_status", "sem_profile_begin", "sem_profile_end", "sem_autotune",
 )
 
 
@@ -65,6 +65,11 @@ class ProfileOut(C.Structure):
                 ("launches", C.c_longlong * 16), ("ms_total", C.c_double * 16)]
 
 
+class TuneOut(C.Structure):
+    _fields_ = [("n_variants", C.c_int), ("chosen", C.c_int), ("layers_per_cta", C.c_int * 16),
+                ("min_ctas_per_sm", C.c_int * 16), ("ms", C.c_double * 16)]
+
+
 class DiagOut(C.Structure):
     _fields_ = [("max_wind", C.c_double), ("max_mean_wind", C.c_double)]
 
@@ -90,6 +95,7 @@ def _load():
         "sem_rk_stage": (i, [vp, C.POINTER(Params), i, vp, vp, vp, d, vp]),
         "sem_rk_stage_mixed": (i, [vp, C.POINTER(Params), i, vp, vp, vp, vp, vp, d, vp]),
         "sem_mirror": (i, [vp, vp, vp, vp]),
+        "sem_step_mixed": (i, [vp, C.POINTER(Params), vp, vp, vp, d, vp]),
         "sem_step": (i, [vp, C.POINTER(Params), vp, vp, vp, d, vp]),
         "sem_adapt_flags": (i, [vp, C.POINTER(Params), vp, vp, vp, vp]),
         "sem_adapt_flags_host": (i, [vp, C.POINTER(Params), vp, vp, vp]),
@@ -98,6 +104,7 @@ def _load():
         "sem_diag": (i, [vp, C.POINTER(Params), vp, d, C.POINTER(DiagOut), vp]),
         "sem_status": (i, [vp, C.POINTER(C.c_int), vp]),
         "sem_profile_begin": (i, []),
+        "sem_autotune": (i, [vp, C.POINTER(Params), vp, i, C.POINTER(TuneOut), vp]),
         "sem_profile_end": (i, [C.POINTER(ProfileOut)]),
     }
     for name, (res, args) in sig.items():
@@ -268,6 +275,15 @@ def sem_rk_stage_mixed(mesh, params, stage, qn, qs, qs32, qout, qout32, dt, stre
     return qout
 
 
+def sem_step_mixed(mesh, params, q, q32, work32, dt, stream=None):
+    _f64(q, mesh.field_shape)
+    _f32(q32, mesh.field_shape)
+    _f32(work32, (2 * 5, mesh.NG))
+    _check(LIB.sem_step_mixed(mesh.h, C.byref(params), _ptr(q), _ptr(q32), _ptr(work32),
+                              float(dt), _stream(stream)))
+    return q
+
+
 def sem_mirror(mesh, q, q32, stream=None):
     _f64(q, mesh.field_shape)
     _f32(q32, mesh.field_shape)
@@ -337,3 +353,14 @@ def sem_profile_end():
     _check(LIB.sem_profile_end(C.byref(out)))
     return {bytes(out.name[k]).split(b"\0")[0].decode(): (out.launches[k], out.ms_total[k])
             for k in range(out.n_kernels)}
+
+
+def sem_autotune(mesh, params, q32, reps=5, stream=None):
+    """Time the element-kernel variants on this mesh and keep the fastest.
+    Returns [(layers_per_cta, min_ctas_per_sm, ms)] and the chosen index."""
+    _f32(q32, mesh.field_shape)
+    out = TuneOut()
+    _check(LIB.sem_autotune(mesh.h, C.byref(params), _ptr(q32), int(reps), C.byref(out),
+                            _stream(stream)))
+    rows = [(out.layers_per_cta[k], out.min_ctas_per_sm[k], out.ms[k]) for k in range(out.n_variants)]
+    return rows, out.chosen

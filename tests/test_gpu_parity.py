@@ -297,3 +297,50 @@ def test_mixed_stage_with_mirrors_matches_oracle(sem):
     assert np.all(err <= 1e-4), err
     np.testing.assert_allclose(host(q32), got, rtol=2.4e-7, atol=1e-30)
     assert sem.sem_status(m) == 0
+
+
+@pytest.mark.parametrize("name", ["uniform-6x6x4-N4", "twolevel-N4", "uniform-3x3x2-N2", "uniform-5x4x3-N6"])
+def test_step_mixed_increment_form_matches_oracle(sem, name):
+    """sem_step_mixed (float32 stage increments, one float64 accumulation per
+    step) against ten float64 oracle steps."""
+    m, o, X, perm = make_pair(sem, **MESHES[name])
+    q_o = vortex_state(o.XG, o.Lz)
+    dt = 1.0 if name != "uniform-5x4x3-N6" else 0.5
+    q_ref = q_o.copy()
+    for _ in range(10):
+        q_ref = ork.rk_step(o, PRM, q_ref, dt)
+    p = sem.sem_params_default(precision=sem.SEM_PREC_MIXED)
+    q = dev(q_o[:, perm])
+    q32 = torch.empty(q.shape, dtype=torch.float32, device="cuda")
+    work = torch.empty((10, m.NG), dtype=torch.float32, device="cuda")
+    sem.sem_mirror(m, q, q32)
+    for _ in range(10):
+        sem.sem_step_mixed(m, p, q, q32, work, dt)
+    got = host(q)
+    z = X[:, 2]
+    err = group_rel_l2(full_fields(got, z), full_fields(q_ref[:, perm], z))
+    assert np.all(err <= 1e-4), err
+    pert = group_rel_l2(got, q_ref[:, perm])
+    assert np.all(pert <= 1e-3), pert
+    np.testing.assert_allclose(host(q32), got, rtol=2.4e-7, atol=1e-30)
+    assert sem.sem_status(m) == 0
+
+
+def test_autotune_then_step_parity(sem):
+    """Every element-kernel variant the autotuner times gives the same
+    (correct) step: tune, then check the increment-form step again."""
+    m, o, X, perm = make_pair(sem, **MESHES["twolevel-N4"])
+    q_o = vortex_state(o.XG, o.Lz)
+    q_ref = ork.rk_step(o, PRM, q_o, 1.0)
+    p = sem.sem_params_default(precision=sem.SEM_PREC_MIXED)
+    q = dev(q_o[:, perm])
+    q32 = torch.empty(q.shape, dtype=torch.float32, device="cuda")
+    work = torch.empty((10, m.NG), dtype=torch.float32, device="cuda")
+    sem.sem_mirror(m, q, q32)
+    rows, chosen = sem.sem_autotune(m, p, q32, 2)
+    assert len(rows) >= 2 and 0 <= chosen < len(rows)
+    assert all(r[2] > 0 for r in rows)
+    sem.sem_step_mixed(m, p, q, q32, work, 1.0)
+    z = X[:, 2]
+    err = group_rel_l2(full_fields(host(q), z), full_fields(q_ref[:, perm], z))
+    assert np.all(err <= 1e-4), err
