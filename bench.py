@@ -281,8 +281,19 @@ def main():
     # ratio of measured DRAM traffic (ncu, same kernel and workload) to the
     # algorithmic bytes, kept under profiles/; null until a capture of the
     # current kernel exists
+    traffic = None
+    try:
+        import hashlib
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tr = json.load(f)
+        with open(os.path.join(ROOT, "paper_2410_21607_gb300", "csrc", "k_stage.cu"), "rb") as f:
+            cur = hashlib.sha1(f.read()).hexdigest()
+        if tr.get("k_stage_sha1") == cur and dom in tr:
+            traffic = tr[dom]["bytes"]
+    except Exception:
+        traffic = None
     roof = {"kernel": dom, "bound": "hbm", "achieved": kernels[dom]["gbs"], "peak": hbm,
-            "unit": "GB/s", "frac": kernels[dom]["gbs"] / hbm, "traffic": None,
+            "unit": "GB/s", "frac": kernels[dom]["gbs"] / hbm, "traffic": traffic,
             "peak_source": peak_kind}
 
     # FP64 form beside it, and the max-wind gate after gate_steps steps
