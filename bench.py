@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--gate-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
 
@@ -122,6 +123,61 @@ def cpu_oracle_sample(steps=1, n=32):
     desc = (f"{steps} SSP-RK3 step(s) of the oracle on a {n}x{n}x16 block of the same "
             f"elements ({o.Ne} of 65,536; N=4), float64 numpy/scipy")
     return dofs / dt, threads, desc, dt
+
+
+def batched_measure(sem, torch, steps=10, warmup=3):
+    """The 16-instance batched workload: one CUDA-graph launch per step over
+    all instances (persistent element kernel + gather/increment kernel per
+    stage) against stepping the instances one after another."""
+    from synth.vortex import VortexSpec, vortex_state
+    from synth.workloads import batched_instances, geometric_flags
+    insts = batched_instances()
+    meshes, qs, q32, work, dts, dof = [], [], [], [], [], 0
+    p = sem.sem_params_default(precision=sem.SEM_PREC_MIXED)
+    for k, it in enumerate(insts):
+        m = sem.sem_mesh_create(it.L, it.L, it.Lz, it.nx, it.nx, it.nz, it.N, lvl_max=max(it.levels, 1))
+        for _ in range(it.levels):
+            lv = [tuple(x) for x in sem.sem_mesh_leaves_host(m)]
+            m = sem.sem_transfer_plan(m, geometric_flags(lv, it.nx, it.nz, it.L, 3 * it.rmw, it.levels))
+        spec = VortexSpec(vmax=it.vmax, rmw=it.rmw, seed=1000 + k)
+        q = torch.from_numpy(vortex_state(sem.sem_mesh_coords_host(m).T, it.Lz, spec)).cuda()
+        meshes.append(m)
+        qs.append(q)
+        q32.append(torch.empty(q.shape, dtype=torch.float32, device="cuda"))
+        work.append(torch.empty((10, q.shape[1]), dtype=torch.float32, device="cuda"))
+        sem.sem_mirror(m, q, q32[-1])
+        dts.append(it.dt)
+        dof += 5 * m.Ne * (it.N + 1) ** 3
+    batch = sem.sem_batch_create(meshes)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def seq():
+        for k, m in enumerate(meshes):
+            sem.sem_step_mixed(m, p, qs[k], q32[k], work[k], dts[k], stream)
+
+    ms_seq = timed(seq)
+    ms_graph = timed(lambda: sem.sem_batch_step_mixed(batch, p, qs, q32, work, dts, True, stream))
+    ms_nograph = timed(lambda: sem.sem_batch_step_mixed(batch, p, qs, q32, work, dts, False, stream))
+    status = sem.sem_batch_status(batch)
+    return {"workload": "16 seeded instances, bases 8..48, N 3..6, 0..3 levels",
+            "instances": len(insts), "elements": int(sum(m.Ne for m in meshes)),
+            "dof_per_stage": dof, "ms_per_step_graph": ms_graph, "ms_per_step_batched_no_graph": ms_nograph,
+            "ms_per_step_sequential": ms_seq,
+            "value_graph": dof * 3 / (ms_graph * 1e-3), "value_sequential": dof * 3 / (ms_seq * 1e-3),
+            "speedup": ms_seq / ms_graph, "status": status,
+            "launches_per_step_graph": 1, "launches_per_step_sequential": 6 * len(insts)}
 
 
 def run_reference(a):
@@ -344,6 +400,10 @@ def main():
     e2e_ms = e0.elapsed_time(e1) / ke
     nbytes = 5 * NG * 8
 
+    batched = None
+    if not a.no_batched and a.form == "mixed":
+        batched = batched_measure(sem, torch)
+
     line = None
     if rank == 0:
         cpu = None
@@ -364,7 +424,7 @@ def main():
                 "ms_per_step": fp64_ms, "value": dof_stage * 3 * world / (fp64_ms * 1e-3),
                 "speedup_mixed_over_fp64": fp64_ms / ms},
             "gate": gate,
-            "roofline": roof, "kernels": kernels, "autotune": tune,
+            "roofline": roof, "kernels": kernels, "autotune": tune, "batched": batched,
             "cpu_baseline": cpu,
             "e2e": {"value": dof_stage * 3 * world / (e2e_ms * 1e-3), "unit": "DOF-updates/s",
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,

@@ -201,6 +201,25 @@ int sem_rk_stage_mixed(sem_mesh* m, const sem_params* p, int stage, const double
 int sem_step_mixed(sem_mesh* m, const sem_params* p, double* q_dev, float* q32_dev,
                    float* work32_dev, double dt, cudaStream_t stream);
 
+/* Batched mixed-form steps over many independent meshes (uneven sizes,
+ * orders N = 2..6, any refinement levels).  Per stage, one persistent element
+ * kernel walks all columns of all meshes from a work queue (costliest columns
+ * first) and one gather/increment kernel covers the concatenated global nodes;
+ * a step is the increment form of sem_step_mixed for every instance.  The
+ * meshes must outlive the batch.  sem_batch_step_mixed takes per-instance
+ * arrays (q[k] float64 [5][NG_k], q32[k] its float32 mirror, work32[k] float32
+ * 2 x [5][NG_k]) and time steps dt[k]; with use_graph != 0 the step's launches
+ * are captured once into a CUDA graph and replayed (re-captured when an array
+ * pointer, a dt or a physical parameter changes).  sem_batch_status reads and
+ * clears the batch's non-finite flag (synchronises). */
+typedef struct sem_batch sem_batch;
+int sem_batch_create(sem_mesh* const* meshes, int n, sem_batch** out);
+void sem_batch_destroy(sem_batch* b);
+int sem_batch_step_mixed(sem_batch* b, const sem_params* p, double* const* q_dev,
+                         float* const* q32_dev, float* const* work32_dev, const double* dt,
+                         int use_graph, cudaStream_t stream);
+int sem_batch_status(sem_batch* b, int* status_host, cudaStream_t stream);
+
 /* q32 = float32 mirror of q ([5][NG]; significand truncated to 24 bits). */
 int sem_mirror(sem_mesh* m, const double* q_dev, float* q32_dev, cudaStream_t stream);
 

@@ -353,6 +353,50 @@ int sem_autotune(sem_mesh* mh, const sem_params* p, const float* q32, int reps, 
   return autotune_pencil(mh->m, *p, q32, reps, out, st);
 }
 
+int sem_batch_create(sem_mesh* const* meshes, int n, sem_batch** out) {
+  if (!meshes || !out || n <= 0) return fail(SEM_ERR_ARG, "bad argument");
+  *out = nullptr;
+  std::vector<Mesh*> ms(n);
+  for (int k = 0; k < n; ++k) {
+    if (!meshes[k]) return fail(SEM_ERR_ARG, "NULL mesh");
+    ms[k] = &meshes[k]->m;
+  }
+  sem_batch* b = new (std::nothrow) sem_batch();
+  if (!b) return fail(SEM_ERR_ARG, "out of host memory");
+  int rc = batch_create(ms.data(), n, &b->impl);
+  if (rc) {
+    delete b;
+    return rc;
+  }
+  b->n = n;
+  cudaGetDevice(&b->dev);
+  *out = b;
+  return SEM_OK;
+}
+
+void sem_batch_destroy(sem_batch* b) {
+  if (!b) return;
+  batch_destroy(b->impl);
+  delete b;
+}
+
+int sem_batch_step_mixed(sem_batch* b, const sem_params* p, double* const* q, float* const* q32,
+                         float* const* work32, const double* dt, int use_graph, cudaStream_t st) {
+  if (!b || !p || !q || !q32 || !work32 || !dt) return fail(SEM_ERR_ARG, "NULL argument");
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (p->precision != SEM_PREC_MIXED || p->eqset != SEM_EQ_CONSERVATIVE)
+    return fail(SEM_ERR_ARG, "batched steps need SEM_PREC_MIXED and the conservative set");
+  for (int k = 0; k < b->n; ++k)
+    if (!q[k] || !q32[k] || !work32[k]) return fail(SEM_ERR_ARG, "NULL array");
+  return batch_step_mixed(b->impl, *p, q, q32, work32, dt, use_graph, st);
+}
+
+int sem_batch_status(sem_batch* b, int* status, cudaStream_t st) {
+  if (!b || !status) return fail(SEM_ERR_ARG, "NULL argument");
+  return batch_status(b->impl, status, st);
+}
+
 int sem_mirror(sem_mesh* mh, const double* q, float* q32, cudaStream_t st) {
   if (!mh || !q || !q32) return fail(SEM_ERR_ARG, "NULL argument");
   int rc = ensure_device(mh->m);

@@ -15,7 +15,9 @@
 // R is the arithmetic type of the element work: double for the FP64 form,
 // float for the mixed form (perturbation arithmetic in float32; reference
 // state and metric terms from float64 tables; stage accumulation in float64).
+#include <algorithm>
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 
 #include "sem_internal.h"
@@ -475,24 +477,24 @@ static void launch_volume_n(const VolArgs& A, int eq, bool mixed, cudaStream_t s
 // shared by consecutive layers is summed inside the CTA (vertical DSS), as in
 // volume_column.  Arithmetic: float32; geometry and reference state come from
 // tables computed in float64.
-template <int N, int KL, int MB>
-__global__ void __launch_bounds__(KL * (N + 1) * (N + 1), MB)
-volume_pencil_mixed(const VolArgs A) {
+// Body shared by the single-mesh kernel (one CTA per column) and the batched
+// persistent kernel (CTAs pull columns of many meshes from a queue).  Threads
+// t >= KL (N+1)^2 of a larger CTA take part in the barriers only.
+template <int N, int KL>
+__device__ __forceinline__ void pencil_body(const VolArgs& A, const int col, float* smem, const int t) {
   constexpr int n1 = N + 1, Nq = n1 * n1, CP = (n1 + 1) / 2, CW = 2 * CP;
   constexpr int SXY = kFields * KL * Nq * CW;  // floats per flux direction
-  extern __shared__ __align__(16) float smem[];
+  const bool part = t < KL * Nq;
   float* sX = smem;                    // [f][kk][j][m][c]
   float* sY = sX + SXY;                // [f][kk][i][m][c]
   float* sT = sY + SXY;                // [f][kk][ab]: top-face residual
   float* sP = sT + kFields * KL * Nq;  // [f][ab]: carry between chunks
-  const int t = threadIdx.x;
-  const int kk = t % KL, ab = t / KL;
+  const int kk = t % KL, ab = part ? t / KL : 0;
   const int i = ab % n1, j = ab / n1;
-  const int col = blockIdx.x;
   const int lev = A.col_level[col];
   const float* geo = A.geof[lev];
   const float sx = geo[4], sy = geo[5], sz = geo[6], J = geo[3];
-  const int hm = A.hmap[(long long)col * Nq + ab];
+  const int hm = part ? A.hmap[(long long)col * Nq + ab] : 0;
   const float* q = (const float*)A.q;
   const float* hw = (const float*)A.hang_w;
   float Dwi[n1], Dwj[n1];
@@ -507,7 +509,7 @@ volume_pencil_mixed(const VolArgs A) {
   const int nchunk = (A.nz + KL - 1) / KL;
   for (int ch = 0; ch < nchunk; ++ch) {
     const int k = ch * KL + kk;
-    const bool act = k < A.nz;
+    const bool act = part && k < A.nz;
     const int kz0 = k * N;
     float2 r[kFields][CP];
 #pragma unroll
@@ -584,7 +586,7 @@ volume_pencil_mixed(const VolArgs A) {
           myY[f * FS + n1] = 0.f;
         }
       }
-    } else {
+    } else if (part) {
 #pragma unroll
       for (int f = 0; f < kFields; ++f)
 #pragma unroll
@@ -613,18 +615,20 @@ volume_pencil_mixed(const VolArgs A) {
       }
     // vertical DSS: the top node of layer k and the bottom node of layer k+1
     float* rr = reinterpret_cast<float*>(&r[0][0]);
+    if (part) {
 #pragma unroll
-    for (int f = 0; f < kFields; ++f) sT[(f * KL + kk) * Nq + ab] = rr[f * CP * 2 + N];
-    if (kk == 0 && ch > 0) {
+      for (int f = 0; f < kFields; ++f) sT[(f * KL + kk) * Nq + ab] = rr[f * CP * 2 + N];
+    }
+    if (part && kk == 0 && ch > 0) {
 #pragma unroll
       for (int f = 0; f < kFields; ++f) rr[f * CP * 2] += sP[f * Nq + ab];
     }
     __syncthreads();
-    if (kk > 0) {
+    if (part && kk > 0) {
 #pragma unroll
       for (int f = 0; f < kFields; ++f) rr[f * CP * 2] += sT[(f * KL + kk - 1) * Nq + ab];
     }
-    if (kk == KL - 1) {
+    if (part && kk == KL - 1) {
 #pragma unroll
       for (int f = 0; f < kFields; ++f) sP[f * Nq + ab] = rr[f * CP * 2 + N];
     }
@@ -646,6 +650,13 @@ volume_pencil_mixed(const VolArgs A) {
     }
     __syncthreads();
   }
+}
+
+template <int N, int KL, int MB>
+__global__ void __launch_bounds__(KL * (N + 1) * (N + 1), MB)
+volume_pencil_mixed(const VolArgs A) {
+  extern __shared__ __align__(16) float smem[];
+  pencil_body<N, KL>(A, blockIdx.x, smem, threadIdx.x);
 }
 
 template <int N, int KL>
@@ -783,37 +794,41 @@ struct IncArgs {
 };
 
 template <int STAGE>
-__global__ void __launch_bounds__(256) dss_inc(const IncArgs A) {
-  int bad = 0;
-  for (int gidx = blockIdx.x * blockDim.x + threadIdx.x; gidx < A.NG; gidx += gridDim.x * blockDim.x) {
-    const int h = (int)((unsigned)gidx / (unsigned)A.NZ);
-    const int kz = gidx - h * A.NZ;
-    const int beg = __ldg(A.qt_ptr + h), end = __ldg(A.qt_ptr + h + 1);
-    const float s = A.cdt * (__ldg(A.Minv_h + h) * __ldg(A.Minv_z + kz));
-    const bool lid = (kz == 0) || (kz == A.NZ - 1);
-    float acc[kFields] = {0, 0, 0, 0, 0};
-    for (int e = beg; e < end; ++e) {
-      const float w = __ldg(A.qt_w + e);
-      const float* p = A.rc + (long long)__ldg(A.qt_src + e) * kFields * A.NZr + kz;
+__device__ __forceinline__ void inc_body(const IncArgs& A, const int gidx, int& bad) {
+  const int h = (int)((unsigned)gidx / (unsigned)A.NZ);
+  const int kz = gidx - h * A.NZ;
+  const int beg = __ldg(A.qt_ptr + h), end = __ldg(A.qt_ptr + h + 1);
+  const float s = A.cdt * (__ldg(A.Minv_h + h) * __ldg(A.Minv_z + kz));
+  const bool lid = (kz == 0) || (kz == A.NZ - 1);
+  float acc[kFields] = {0, 0, 0, 0, 0};
+  for (int e = beg; e < end; ++e) {
+    const float w = __ldg(A.qt_w + e);
+    const float* p = A.rc + (long long)__ldg(A.qt_src + e) * kFields * A.NZr + kz;
 #pragma unroll
-      for (int fl = 0; fl < kFields; ++fl) acc[fl] = fmaf(w, __ldg(p + fl * A.NZr), acc[fl]);
-    }
+    for (int fl = 0; fl < kFields; ++fl) acc[fl] = fmaf(w, __ldg(p + fl * A.NZr), acc[fl]);
+  }
 #pragma unroll
-    for (int fl = 0; fl < kFields; ++fl) {
-      const long long o = (long long)fl * A.NG + gidx;
-      const float inc = (fl == 3 && lid) ? 0.f : acc[fl] * s;
-      const float dn = (STAGE == 0) ? inc : fmaf(A.bcoef, A.d[o], inc);
-      if (STAGE < 2) {
-        A.d[o] = dn;
-        A.qs32[o] = __ldg(A.q32 + o) + dn;
-      } else {
-        const double qv = A.q[o] + f2d_bits(dn);
-        A.q[o] = qv;
-        A.q32_out[o] = d2f_bits(qv);
-        bad |= nonfinite_bits(qv);
-      }
+  for (int fl = 0; fl < kFields; ++fl) {
+    const long long o = (long long)fl * A.NG + gidx;
+    const float inc = (fl == 3 && lid) ? 0.f : acc[fl] * s;
+    const float dn = (STAGE == 0) ? inc : fmaf(A.bcoef, A.d[o], inc);
+    if (STAGE < 2) {
+      A.d[o] = dn;
+      A.qs32[o] = __ldg(A.q32 + o) + dn;
+    } else {
+      const double qv = A.q[o] + f2d_bits(dn);
+      A.q[o] = qv;
+      A.q32_out[o] = d2f_bits(qv);
+      bad |= nonfinite_bits(qv);
     }
   }
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(256) dss_inc(const IncArgs A) {
+  int bad = 0;
+  for (int gidx = blockIdx.x * blockDim.x + threadIdx.x; gidx < A.NG; gidx += gridDim.x * blockDim.x)
+    inc_body<STAGE>(A, gidx, bad);
   if (STAGE == 2 && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(A.status, 1);
 }
 
@@ -900,6 +915,260 @@ int autotune_pencil(Mesh& m, const sem_params& p, const float* q32, int reps, se
   cudaEventDestroy(e1);
   if (best < 0) return fail(SEM_ERR_UNSUPPORTED, "no variant for this order");
   m.pencil_variant = best;
+  return SEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched mixed-form steps over many independent meshes (sem_batch_*).
+//
+// One persistent element kernel per stage: CTAs of kBatchThreads threads pull
+// (instance, column) tiles, costliest first, from an atomic counter and run
+// the pencil body for the tile's order N (layers per CTA fixed per N so that
+// KL (N+1)^2 <= kBatchThreads).  One gather/increment kernel per stage runs
+// over the concatenated global nodes of all instances.  With graphs enabled
+// the nine launches of a step (3 x counter reset, element, increment) are
+// captured once and replayed with one cudaGraphLaunch per step.
+constexpr int kBatchThreads = 400;
+template <int N> struct BatchKL { static constexpr int value = (N <= 4) ? 16 : 8; };
+
+__global__ void __launch_bounds__(kBatchThreads, 1)
+volume_batch_mixed(const VolArgs* __restrict__ insts, const int* __restrict__ inst_N,
+                   const int2* __restrict__ tiles, int ntiles, int* counter) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ int s_tile;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= ntiles) break;
+    const int2 tl = tiles[tile];
+    const VolArgs& A = insts[tl.x];
+    switch (inst_N[tl.x]) {
+      case 2: pencil_body<2, BatchKL<2>::value>(A, tl.y, smem, threadIdx.x); break;
+      case 3: pencil_body<3, BatchKL<3>::value>(A, tl.y, smem, threadIdx.x); break;
+      case 4: pencil_body<4, BatchKL<4>::value>(A, tl.y, smem, threadIdx.x); break;
+      case 5: pencil_body<5, BatchKL<5>::value>(A, tl.y, smem, threadIdx.x); break;
+      case 6: pencil_body<6, BatchKL<6>::value>(A, tl.y, smem, threadIdx.x); break;
+      default: break;
+    }
+  }
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(256)
+dss_inc_batch(const IncArgs* __restrict__ insts, const int* __restrict__ off, int ninst, int total,
+              int* status) {
+  int bad = 0;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+    int lo = 0, hi = ninst - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(off + mid) <= g) lo = mid; else hi = mid - 1;
+    }
+    inc_body<STAGE>(insts[lo], g - __ldg(off + lo), bad);
+  }
+  if (STAGE == 2 && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, 1);
+}
+
+static size_t batch_smem_max() {
+  size_t m = pencil_smem<2, BatchKL<2>::value>();
+  m = std::max(m, pencil_smem<3, BatchKL<3>::value>());
+  m = std::max(m, pencil_smem<4, BatchKL<4>::value>());
+  m = std::max(m, pencil_smem<5, BatchKL<5>::value>());
+  m = std::max(m, pencil_smem<6, BatchKL<6>::value>());
+  return m;
+}
+
+struct BatchImpl {
+  std::vector<Mesh*> meshes;
+  int total_nodes = 0;
+  VolArgs* d_vol = nullptr;   // [2][n]: stage 0 (reads q32), stages 1-2 (read the stage mirror)
+  IncArgs* d_inc = nullptr;   // [3][n]
+  int* d_N = nullptr;
+  int2* d_tiles = nullptr;
+  int ntiles = 0;
+  int* d_off = nullptr;
+  int* d_counter = nullptr;   // [3]
+  int* d_status = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  std::vector<const void*> key;  // arrays and dt the device tables were built for
+  std::vector<double> key_dt;
+  double key_par[7] = {0};
+  int nsm = 152;
+};
+
+static void batch_free(BatchImpl* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  void* ptrs[] = {b->d_vol, b->d_inc, b->d_N, b->d_tiles, b->d_off, b->d_counter, b->d_status};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+int batch_create(Mesh* const* meshes, int n, void** out) {
+  int rc = upload_basis_constants();
+  if (rc) return rc;
+  BatchImpl* b = new BatchImpl();
+  b->meshes.assign(meshes, meshes + n);
+  long long tot = 0;
+  std::vector<int> Ns(n), off(n);
+  std::vector<std::pair<long long, int2>> tiles;
+  for (int k = 0; k < n; ++k) {
+    Mesh& m = *meshes[k];
+    if ((rc = ensure_device(m))) { batch_free(b); delete b; return rc; }
+    Ns[k] = m.N;
+    off[k] = (int)tot;
+    tot += m.NG;
+    const long long cost = (long long)(m.N + 1) * (m.N + 1) * (m.N + 1) * m.nz;
+    for (int c = 0; c < (int)m.Ncol(); ++c) tiles.push_back({cost, make_int2(k, c)});
+  }
+  if (tot * kFields >= (1ll << 31)) { delete b; return fail(SEM_ERR_ARG, "batch too large for 32-bit indexing"); }
+  b->total_nodes = (int)tot;
+  std::stable_sort(tiles.begin(), tiles.end(),
+                   [](const std::pair<long long, int2>& x, const std::pair<long long, int2>& y) { return x.first > y.first; });
+  std::vector<int2> tl(tiles.size());
+  for (size_t t = 0; t < tiles.size(); ++t) tl[t] = tiles[t].second;
+  b->ntiles = (int)tl.size();
+  cudaError_t e = cudaMalloc((void**)&b->d_vol, sizeof(VolArgs) * 2 * n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_inc, sizeof(IncArgs) * 3 * n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_N, sizeof(int) * n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tiles, sizeof(int2) * tl.size());
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_off, sizeof(int) * n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counter, sizeof(int) * 3);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_N, Ns.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_off, off.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(volume_batch_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)batch_smem_max());
+  if (e != cudaSuccess) {
+    batch_free(b);
+    delete b;
+    return fail(SEM_ERR_CUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+  *out = b;
+  return SEM_OK;
+}
+
+void batch_destroy(void* h) {
+  BatchImpl* b = (BatchImpl*)h;
+  if (!b) return;
+  batch_free(b);
+  delete b;
+}
+
+static void batch_enqueue(BatchImpl* b, cudaStream_t st) {
+  const int n = (int)b->meshes.size();
+  const size_t smem = batch_smem_max();
+  const int vgrid = std::min(b->ntiles, b->nsm);
+  const int igrid = std::max(1, std::min((b->total_nodes + 255) / 256, b->nsm * 8));
+  for (int stage = 0; stage < 3; ++stage) {
+    cudaMemsetAsync(b->d_counter + stage, 0, sizeof(int), st);
+    volume_batch_mixed<<<vgrid, kBatchThreads, smem, st>>>(b->d_vol + (stage == 0 ? 0 : n), b->d_N,
+                                                           b->d_tiles, b->ntiles, b->d_counter + stage);
+    if (stage == 0) dss_inc_batch<0><<<igrid, 256, 0, st>>>(b->d_inc, b->d_off, n, b->total_nodes, b->d_status);
+    else if (stage == 1) dss_inc_batch<1><<<igrid, 256, 0, st>>>(b->d_inc + n, b->d_off, n, b->total_nodes, b->d_status);
+    else dss_inc_batch<2><<<igrid, 256, 0, st>>>(b->d_inc + 2 * n, b->d_off, n, b->total_nodes, b->d_status);
+  }
+}
+
+int batch_step_mixed(void* h, const sem_params& p, double* const* q, float* const* q32,
+                     float* const* work32, const double* dt, int use_graph, cudaStream_t st) {
+  BatchImpl* b = (BatchImpl*)h;
+  const int n = (int)b->meshes.size();
+  std::vector<const void*> key;
+  for (int k = 0; k < n; ++k) {
+    key.push_back(q[k]);
+    key.push_back(q32[k]);
+    key.push_back(work32[k]);
+  }
+  std::vector<double> kdt(dt, dt + n);
+  const double par[7] = {p.g, p.f, p.R_d, p.c_p, p.p00, p.theta_s, p.N_bv};
+  const bool same = key == b->key && kdt == b->key_dt && std::memcmp(par, b->key_par, sizeof(par)) == 0;
+  if (!same) {
+    std::vector<VolArgs> vol(2 * n);
+    std::vector<IncArgs> inc(3 * n);
+    for (int k = 0; k < n; ++k) {
+      Mesh& m = *b->meshes[k];
+      int rc = ensure_reference(m, p);
+      if (rc) return rc;
+      float* qs32 = work32[k] + (size_t)kFields * m.NG;
+      vol[k] = make_vol_args(m, p, q32[k], true, nullptr);
+      vol[n + k] = make_vol_args(m, p, qs32, true, nullptr);
+      DeviceTables& D = *m.dev;
+      const double cs[3] = {1.0, 0.25, 2.0 / 3.0};
+      for (int s = 0; s < 3; ++s) {
+        IncArgs& B = inc[s * n + k];
+        B.rc = (const float*)D.scratch;
+        B.qt_ptr = D.qt_ptr;
+        B.qt_src = D.qt_src;
+        B.qt_w = D.qt_w32;
+        B.Minv_h = D.Minv_h32;
+        B.Minv_z = D.Minv_z32;
+        B.q32 = q32[k];
+        B.d = work32[k];
+        B.qs32 = qs32;
+        B.q = q[k];
+        B.q32_out = q32[k];
+        B.cdt = (float)(cs[s] * dt[k]);
+        B.bcoef = (float)cs[s];
+        B.NG = (int)m.NG;
+        B.NZ = m.NZ;
+        B.NZr = m.NZr();
+        B.status = b->d_status;
+      }
+    }
+    // the previous graph may still read the old tables
+    SEM_CUDA_TRY(cudaStreamSynchronize(st));
+    SEM_CUDA_TRY(cudaMemcpy(b->d_vol, vol.data(), sizeof(VolArgs) * vol.size(), cudaMemcpyHostToDevice));
+    SEM_CUDA_TRY(cudaMemcpy(b->d_inc, inc.data(), sizeof(IncArgs) * inc.size(), cudaMemcpyHostToDevice));
+    b->key = key;
+    b->key_dt = kdt;
+    std::memcpy(b->key_par, par, sizeof(par));
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    if (b->graph) {
+      cudaGraphDestroy(b->graph);
+      b->graph = nullptr;
+    }
+  }
+  if (!use_graph) {
+    ProfScope ps("batch_step_mixed", st);
+    batch_enqueue(b, st);
+    SEM_CUDA_TRY(cudaGetLastError());
+    return SEM_OK;
+  }
+  if (!b->exec) {
+    SEM_CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    batch_enqueue(b, b->cap);
+    cudaError_t e = cudaStreamEndCapture(b->cap, &b->graph);
+    if (e != cudaSuccess) return fail(SEM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    SEM_CUDA_TRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  }
+  ProfScope ps("batch_step_mixed_graph", st);
+  SEM_CUDA_TRY(cudaGraphLaunch(b->exec, st));
+  return SEM_OK;
+}
+
+int batch_status(void* h, int* status, cudaStream_t st) {
+  BatchImpl* b = (BatchImpl*)h;
+  int v = 0;
+  SEM_CUDA_TRY(cudaMemcpyAsync(&v, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SEM_CUDA_TRY(cudaMemsetAsync(b->d_status, 0, sizeof(int), st));
+  SEM_CUDA_TRY(cudaStreamSynchronize(st));
+  *status = v ? SEM_ERR_NUMERIC : SEM_OK;
   return SEM_OK;
 }
 

@@ -167,6 +167,11 @@ int launch_diag(Mesh& m, const sem_params& p, const double* q, double half_width
 int launch_transfer(Mesh& oldm, Mesh& newm, const double* qold, double* qnew, cudaStream_t st);
 int launch_coords(Mesh& m, double* xyz, cudaStream_t st);
 int launch_mirror(const double* q, float* q32, long long n, cudaStream_t st);
+int batch_create(Mesh* const* meshes, int n, void** out);
+void batch_destroy(void* b);
+int batch_step_mixed(void* b, const sem_params& p, double* const* q, float* const* q32,
+                     float* const* work32, const double* dt, int use_graph, cudaStream_t st);
+int batch_status(void* b, int* status, cudaStream_t st);
 int autotune_pencil(Mesh& m, const sem_params& p, const float* q32, int reps, sem_tune_out* out,
                     cudaStream_t st);
 int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float* work32, double dt,
@@ -186,4 +191,10 @@ struct ProfScope {
 
 struct sem_mesh {
   sem::Mesh m;
+};
+
+struct sem_batch {
+  void* impl = nullptr;
+  int n = 0;
+  int dev = -1;
 };

@@ -29,6 +29,7 @@ EXPORTS = (
     "sem_mirror", "sem_step", "sem_step_mixed",
     "sem_adapt_flags", "sem_adapt_flags_host", "sem_transfer_plan", "sem_transfer", "sem_diag",
     "sem_status", "sem_profile_begin", "sem_profile_end", "sem_autotune",
+    "sem_batch_create", "sem_batch_destroy", "sem_batch_step_mixed", "sem_batch_status",
 )
 
 
@@ -104,6 +105,11 @@ def _load():
         "sem_diag": (i, [vp, C.POINTER(Params), vp, d, C.POINTER(DiagOut), vp]),
         "sem_status": (i, [vp, C.POINTER(C.c_int), vp]),
         "sem_profile_begin": (i, []),
+        "sem_batch_create": (i, [C.POINTER(vp), i, C.POINTER(vp)]),
+        "sem_batch_destroy": (None, [vp]),
+        "sem_batch_step_mixed": (i, [vp, C.POINTER(Params), C.POINTER(vp), C.POINTER(vp),
+                                     C.POINTER(vp), C.POINTER(d), i, vp]),
+        "sem_batch_status": (i, [vp, C.POINTER(C.c_int), vp]),
         "sem_autotune": (i, [vp, C.POINTER(Params), vp, i, C.POINTER(TuneOut), vp]),
         "sem_profile_end": (i, [C.POINTER(ProfileOut)]),
     }
@@ -364,3 +370,46 @@ def sem_autotune(mesh, params, q32, reps=5, stream=None):
                             _stream(stream)))
     rows = [(out.layers_per_cta[k], out.min_ctas_per_sm[k], out.ms[k]) for k in range(out.n_variants)]
     return rows, out.chosen
+
+
+class Batch:
+    """Owning handle of a sem_batch; keeps its meshes alive."""
+
+    def __init__(self, handle, meshes):
+        self.h = C.c_void_p(handle)
+        self.meshes = list(meshes)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            LIB.sem_batch_destroy(h)
+            self.h = None
+
+
+def sem_batch_create(meshes):
+    arr = (C.c_void_p * len(meshes))(*[m.h.value for m in meshes])
+    h = C.c_void_p()
+    _check(LIB.sem_batch_create(arr, len(meshes), C.byref(h)))
+    return Batch(h.value, meshes)
+
+
+def sem_batch_step_mixed(batch, params, qs, q32s, works, dts, use_graph=True, stream=None):
+    n = len(batch.meshes)
+    if not (len(qs) == len(q32s) == len(works) == len(dts) == n):
+        raise ValueError("one array set and dt per instance")
+    for m, q, q32, w in zip(batch.meshes, qs, q32s, works):
+        _f64(q, m.field_shape)
+        _f32(q32, m.field_shape)
+        _f32(w, (10, m.NG))
+    aq = (C.c_void_p * n)(*[q.data_ptr() for q in qs])
+    a32 = (C.c_void_p * n)(*[q.data_ptr() for q in q32s])
+    aw = (C.c_void_p * n)(*[w.data_ptr() for w in works])
+    adt = (C.c_double * n)(*[float(x) for x in dts])
+    _check(LIB.sem_batch_step_mixed(batch.h, C.byref(params), aq, a32, aw, adt, int(bool(use_graph)),
+                                    _stream(stream)))
+
+
+def sem_batch_status(batch, stream=None):
+    v = C.c_int(0)
+    _check(LIB.sem_batch_status(batch.h, C.byref(v), _stream(stream)))
+    return v.value

@@ -56,3 +56,71 @@ WORKLOADS = {
         refine_radius=150e3, refine_levels=2,
         notes="reduced-size adaptive case for oracle comparison"),
 }
+
+
+@dataclass(frozen=True)
+class Instance:
+    """One member of the batched workload."""
+    nx: int
+    nz: int
+    N: int
+    L: float
+    Lz: float
+    vmax: float
+    rmw: float
+    levels: int
+    dt: float
+
+
+def lgl_min_gap(N):
+    """Smallest LGL node spacing on [-1, 1] as a fraction of the element width."""
+    import numpy as np
+    x = -np.cos(np.pi * np.arange(N + 1) / N)
+    for _ in range(60):            # Newton on (1 - x^2) P_N'(x) = 0, interior nodes
+        P = np.polynomial.legendre.Legendre.basis(N)
+        dP, d2P = P.deriv(), P.deriv(2)
+        f = (1 - x * x) * dP(x)
+        df = -2 * x * dP(x) + (1 - x * x) * d2P(x)
+        step = np.zeros_like(x)
+        step[1:-1] = f[1:-1] / df[1:-1]
+        x = x - step
+    return float(np.min(np.diff(np.sort(x)))) / 2.0
+
+
+def batched_instances(seed=4, count=16):
+    """The 16-instance batched workload: seeded base sizes 8..48 (nz = nx/4),
+    orders 3..6, v_max 15..40 m/s, radius of maximum wind 30..80 km and 0..3
+    levels of geometric refinement inside r < 3 RMW; 600 km boxes for nx >= 16,
+    300 km below.  dt keeps the acoustic Courant number at 0.35 on the finest
+    LGL spacing (vertical or horizontal)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        nx = int(rng.integers(2, 13)) * 4          # 8 .. 48
+        nz = max(nx // 4, 2)
+        N = int(rng.integers(3, 7))
+        vmax = float(rng.uniform(15.0, 40.0))
+        rmw = float(rng.uniform(30e3, 80e3))
+        levels = int(rng.integers(0, 4))
+        L = 600e3 if nx >= 16 else 300e3
+        Lz = 24e3
+        g = lgl_min_gap(N)
+        h = min(L / (nx << levels), Lz / nz)
+        dt = 0.35 * g * h / 347.0
+        out.append(Instance(nx, nz, N, L, Lz, vmax, rmw, levels, dt))
+    return out
+
+
+def geometric_flags(leaves, nx, nz, L, radius, lvl_max):
+    """Refinement flags (+1) for every element of a column whose centre lies
+    within `radius` of the domain centre, below lvl_max; 0 elsewhere."""
+    import numpy as np
+    fl = np.zeros(len(leaves) * nz, dtype=np.int8)
+    for c, (l, i, j) in enumerate(leaves):
+        h = L / (nx << l)
+        xc = -0.5 * L + (i + 0.5) * h
+        yc = -0.5 * L + (j + 0.5) * h
+        if l < lvl_max and np.hypot(xc, yc) < radius:
+            fl[c * nz:(c + 1) * nz] = 1
+    return fl
