@@ -125,13 +125,16 @@ def cpu_oracle_sample(steps=1, n=32):
     return dofs / dt, threads, desc, dt
 
 
-def batched_measure(sem, torch, steps=10, warmup=3):
+def batched_measure(sem, torch, steps=10, warmup=3, refine=True):
     """The 16-instance batched workload: one CUDA-graph launch per step over
     all instances (persistent element kernel + gather/increment kernel per
     stage) against stepping the instances one after another."""
     from synth.vortex import VortexSpec, vortex_state
     from synth.workloads import batched_instances, geometric_flags
     insts = batched_instances()
+    if not refine:
+        import dataclasses
+        insts = [dataclasses.replace(it, levels=0) for it in insts]
     meshes, qs, q32, work, dts, dof = [], [], [], [], [], 0
     p = sem.sem_params_default(precision=sem.SEM_PREC_MIXED)
     for k, it in enumerate(insts):
@@ -167,11 +170,15 @@ def batched_measure(sem, torch, steps=10, warmup=3):
         for k, m in enumerate(meshes):
             sem.sem_step_mixed(m, p, qs[k], q32[k], work[k], dts[k], stream)
 
+    # sequential reference: every instance with its own autotuned element kernel
+    for k, m in enumerate(meshes):
+        sem.sem_autotune(m, p, q32[k], 3, stream)
     ms_seq = timed(seq)
     ms_graph = timed(lambda: sem.sem_batch_step_mixed(batch, p, qs, q32, work, dts, True, stream))
     ms_nograph = timed(lambda: sem.sem_batch_step_mixed(batch, p, qs, q32, work, dts, False, stream))
     status = sem.sem_batch_status(batch)
-    return {"workload": "16 seeded instances, bases 8..48, N 3..6, 0..3 levels",
+    return {"workload": "16 seeded instances, bases 8..48, N 3..6, "
+                        + ("0..3 levels" if refine else "unrefined"),
             "instances": len(insts), "elements": int(sum(m.Ne for m in meshes)),
             "dof_per_stage": dof, "ms_per_step_graph": ms_graph, "ms_per_step_batched_no_graph": ms_nograph,
             "ms_per_step_sequential": ms_seq,
@@ -402,7 +409,7 @@ def main():
 
     batched = None
     if not a.no_batched and a.form == "mixed":
-        batched = batched_measure(sem, torch)
+        batched = [batched_measure(sem, torch), batched_measure(sem, torch, refine=False)]
 
     line = None
     if rank == 0:

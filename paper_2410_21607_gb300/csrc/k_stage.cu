@@ -928,10 +928,13 @@ int autotune_pencil(Mesh& m, const sem_params& p, const float* q32, int reps, se
 // over the concatenated global nodes of all instances.  With graphs enabled
 // the nine launches of a step (3 x counter reset, element, increment) are
 // captured once and replayed with one cudaGraphLaunch per step.
-constexpr int kBatchThreads = 400;
-template <int N> struct BatchKL { static constexpr int value = (N <= 4) ? 16 : 8; };
+// Layers per CTA for order N in a CTA of BT threads: as many as fit, at most 16.
+__host__ __device__ constexpr int batch_kl(int N, int BT) {
+  return (BT / ((N + 1) * (N + 1))) < 16 ? (BT / ((N + 1) * (N + 1))) : 16;
+}
 
-__global__ void __launch_bounds__(kBatchThreads, 1)
+template <int BT, int MB>
+__global__ void __launch_bounds__(BT, MB)
 volume_batch_mixed(const VolArgs* __restrict__ insts, const int* __restrict__ inst_N,
                    const int2* __restrict__ tiles, int ntiles, int* counter) {
   extern __shared__ __align__(16) float smem[];
@@ -945,15 +948,40 @@ volume_batch_mixed(const VolArgs* __restrict__ insts, const int* __restrict__ in
     const int2 tl = tiles[tile];
     const VolArgs& A = insts[tl.x];
     switch (inst_N[tl.x]) {
-      case 2: pencil_body<2, BatchKL<2>::value>(A, tl.y, smem, threadIdx.x); break;
-      case 3: pencil_body<3, BatchKL<3>::value>(A, tl.y, smem, threadIdx.x); break;
-      case 4: pencil_body<4, BatchKL<4>::value>(A, tl.y, smem, threadIdx.x); break;
-      case 5: pencil_body<5, BatchKL<5>::value>(A, tl.y, smem, threadIdx.x); break;
-      case 6: pencil_body<6, BatchKL<6>::value>(A, tl.y, smem, threadIdx.x); break;
+      case 2: pencil_body<2, batch_kl(2, BT)>(A, tl.y, smem, threadIdx.x); break;
+      case 3: pencil_body<3, batch_kl(3, BT)>(A, tl.y, smem, threadIdx.x); break;
+      case 4: pencil_body<4, batch_kl(4, BT)>(A, tl.y, smem, threadIdx.x); break;
+      case 5: pencil_body<5, batch_kl(5, BT)>(A, tl.y, smem, threadIdx.x); break;
+      case 6: pencil_body<6, batch_kl(6, BT)>(A, tl.y, smem, threadIdx.x); break;
       default: break;
     }
   }
 }
+
+template <int BT>
+static size_t batch_smem() {
+  size_t m = pencil_smem<2, batch_kl(2, BT)>();
+  m = std::max(m, pencil_smem<3, batch_kl(3, BT)>());
+  m = std::max(m, pencil_smem<4, batch_kl(4, BT)>());
+  m = std::max(m, pencil_smem<5, batch_kl(5, BT)>());
+  m = std::max(m, pencil_smem<6, batch_kl(6, BT)>());
+  return m;
+}
+
+// Launch configurations of the batched element kernel (threads per CTA and
+// the CTAs per SM its registers are sized for); chosen by timing at set-up.
+struct BatchVariant {
+  int BT, MB;
+  void (*kernel)(const VolArgs*, const int*, const int2*, int, int*);
+  size_t (*smem)();
+};
+static const BatchVariant kBatch[] = {
+    {400, 1, volume_batch_mixed<400, 1>, batch_smem<400>},
+    {200, 2, volume_batch_mixed<200, 2>, batch_smem<200>},
+    {200, 3, volume_batch_mixed<200, 3>, batch_smem<200>},
+    {256, 2, volume_batch_mixed<256, 2>, batch_smem<256>},
+};
+constexpr int kNumBatch = sizeof(kBatch) / sizeof(kBatch[0]);
 
 template <int STAGE>
 __global__ void __launch_bounds__(256)
@@ -971,14 +999,6 @@ dss_inc_batch(const IncArgs* __restrict__ insts, const int* __restrict__ off, in
   if (STAGE == 2 && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, 1);
 }
 
-static size_t batch_smem_max() {
-  size_t m = pencil_smem<2, BatchKL<2>::value>();
-  m = std::max(m, pencil_smem<3, BatchKL<3>::value>());
-  m = std::max(m, pencil_smem<4, BatchKL<4>::value>());
-  m = std::max(m, pencil_smem<5, BatchKL<5>::value>());
-  m = std::max(m, pencil_smem<6, BatchKL<6>::value>());
-  return m;
-}
 
 struct BatchImpl {
   std::vector<Mesh*> meshes;
@@ -998,6 +1018,12 @@ struct BatchImpl {
   std::vector<double> key_dt;
   double key_par[7] = {0};
   int nsm = 152;
+  std::vector<IncArgs> h_inc;  // host copy of the increment-kernel arguments [3][n]
+  int nsmall = 0;
+  int variant = -1;          // batched element-kernel configuration (kBatch)
+  std::vector<char> big;     // instances launched with their own tuned kernel
+  std::vector<VolArgs> h_vol;  // host copy of the element-kernel arguments [2][n]
+  float variant_ms[kNumBatch] = {0};
 };
 
 static void batch_free(BatchImpl* b) {
@@ -1017,16 +1043,32 @@ int batch_create(Mesh* const* meshes, int n, void** out) {
   long long tot = 0;
   std::vector<int> Ns(n), off(n);
   std::vector<std::pair<long long, int2>> tiles;
+  int dev0 = 0, nsm0 = 152;
+  cudaGetDevice(&dev0);
+  cudaDeviceGetAttribute(&nsm0, cudaDevAttrMultiProcessorCount, dev0);
+  b->big.assign(n, 0);
   for (int k = 0; k < n; ++k) {
     Mesh& m = *meshes[k];
     if ((rc = ensure_device(m))) { batch_free(b); delete b; return rc; }
     Ns[k] = m.N;
+    // meshes with enough columns to fill the GPU keep their own tuned
+    // launches; the rest share the persistent column queue and one
+    // concatenated gather/increment launch
+    if (m.Ncol() >= 2LL * nsm0) {
+      b->big[k] = 1;
+      off[k] = (int)tot;
+      continue;
+    }
     off[k] = (int)tot;
     tot += m.NG;
     const long long cost = (long long)(m.N + 1) * (m.N + 1) * (m.N + 1) * m.nz;
     for (int c = 0; c < (int)m.Ncol(); ++c) tiles.push_back({cost, make_int2(k, c)});
   }
-  if (tot * kFields >= (1ll << 31)) { delete b; return fail(SEM_ERR_ARG, "batch too large for 32-bit indexing"); }
+  for (int k = 0; k < n; ++k)
+    if (meshes[k]->NG * kFields >= (1ll << 31)) {
+      delete b;
+      return fail(SEM_ERR_ARG, "mesh too large for 32-bit indexing");
+    }
   b->total_nodes = (int)tot;
   std::stable_sort(tiles.begin(), tiles.end(),
                    [](const std::pair<long long, int2>& x, const std::pair<long long, int2>& y) { return x.first > y.first; });
@@ -1036,18 +1078,24 @@ int batch_create(Mesh* const* meshes, int n, void** out) {
   cudaError_t e = cudaMalloc((void**)&b->d_vol, sizeof(VolArgs) * 2 * n);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_inc, sizeof(IncArgs) * 3 * n);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_N, sizeof(int) * n);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tiles, sizeof(int2) * tl.size());
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tiles, sizeof(int2) * (tl.size() ? tl.size() : 1));
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_off, sizeof(int) * n);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counter, sizeof(int) * 3);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(b->d_N, Ns.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(b->d_tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(b->d_off, off.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !tl.empty())
+    e = cudaMemcpy(b->d_tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice);
+  std::vector<int> soff;
+  for (int k = 0; k < n; ++k)
+    if (!b->big[k]) soff.push_back(off[k]);
+  b->nsmall = (int)soff.size();
+  if (e == cudaSuccess && !soff.empty())
+    e = cudaMemcpy(b->d_off, soff.data(), sizeof(int) * soff.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(volume_batch_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)batch_smem_max());
+  for (int v = 0; v < kNumBatch && e == cudaSuccess; ++v)
+    e = cudaFuncSetAttribute(kBatch[v].kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kBatch[v].smem());
   if (e != cudaSuccess) {
     batch_free(b);
     delete b;
@@ -1067,18 +1115,74 @@ void batch_destroy(void* h) {
   delete b;
 }
 
+static void batch_volume(BatchImpl* b, int v, const VolArgs* vol, int* counter, cudaStream_t st) {
+  const BatchVariant& V = kBatch[v];
+  const int vgrid = std::min(b->ntiles, b->nsm * V.MB);
+  V.kernel<<<vgrid, V.BT, V.smem(), st>>>(vol, b->d_N, b->d_tiles, b->ntiles, counter);
+}
+
+// time every configuration of the element kernel on stage-0 inputs (side
+// effect: the meshes' residual scratch) and keep the fastest
+static int batch_tune(BatchImpl* b, cudaStream_t st) {
+  cudaEvent_t e0, e1;
+  SEM_CUDA_TRY(cudaEventCreate(&e0));
+  SEM_CUDA_TRY(cudaEventCreate(&e1));
+  float best = 0.f;
+  for (int v = 0; v < kNumBatch; ++v) {
+    cudaMemsetAsync(b->d_counter, 0, sizeof(int), st);
+    batch_volume(b, v, b->d_vol, b->d_counter, st);
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3; ++r) {
+      cudaMemsetAsync(b->d_counter, 0, sizeof(int), st);
+      batch_volume(b, v, b->d_vol, b->d_counter, st);
+    }
+    cudaEventRecord(e1, st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return fail(SEM_ERR_CUDA, std::string("batch tuning: ") + cudaGetErrorString(e));
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    b->variant_ms[v] = ms / 3.f;
+    if (b->variant < 0 || b->variant_ms[v] < best) {
+      best = b->variant_ms[v];
+      b->variant = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return SEM_OK;
+}
+
 static void batch_enqueue(BatchImpl* b, cudaStream_t st) {
   const int n = (int)b->meshes.size();
-  const size_t smem = batch_smem_max();
-  const int vgrid = std::min(b->ntiles, b->nsm);
   const int igrid = std::max(1, std::min((b->total_nodes + 255) / 256, b->nsm * 8));
   for (int stage = 0; stage < 3; ++stage) {
-    cudaMemsetAsync(b->d_counter + stage, 0, sizeof(int), st);
-    volume_batch_mixed<<<vgrid, kBatchThreads, smem, st>>>(b->d_vol + (stage == 0 ? 0 : n), b->d_N,
-                                                           b->d_tiles, b->ntiles, b->d_counter + stage);
-    if (stage == 0) dss_inc_batch<0><<<igrid, 256, 0, st>>>(b->d_inc, b->d_off, n, b->total_nodes, b->d_status);
-    else if (stage == 1) dss_inc_batch<1><<<igrid, 256, 0, st>>>(b->d_inc + n, b->d_off, n, b->total_nodes, b->d_status);
-    else dss_inc_batch<2><<<igrid, 256, 0, st>>>(b->d_inc + 2 * n, b->d_off, n, b->total_nodes, b->d_status);
+    if (b->ntiles > 0) {
+      cudaMemsetAsync(b->d_counter + stage, 0, sizeof(int), st);
+      batch_volume(b, b->variant, b->d_vol + (stage == 0 ? 0 : n), b->d_counter + stage, st);
+    }
+    for (int k = 0; k < n; ++k)
+      if (b->big[k]) {
+        Mesh& m = *b->meshes[k];
+        launch_pencil_n(b->h_vol[(stage == 0 ? 0 : n) + k], m.N, m.nz, st, m.pencil_variant);
+      }
+    const int ns = b->nsmall;
+    if (ns > 0 && b->total_nodes > 0) {
+      if (stage == 0) dss_inc_batch<0><<<igrid, 256, 0, st>>>(b->d_inc, b->d_off, ns, b->total_nodes, b->d_status);
+      else if (stage == 1) dss_inc_batch<1><<<igrid, 256, 0, st>>>(b->d_inc + ns, b->d_off, ns, b->total_nodes, b->d_status);
+      else dss_inc_batch<2><<<igrid, 256, 0, st>>>(b->d_inc + 2 * ns, b->d_off, ns, b->total_nodes, b->d_status);
+    }
+    for (int k = 0; k < n; ++k) {
+      if (!b->big[k]) continue;
+      const IncArgs& B = b->h_inc[stage * n + k];
+      const int blocks = grid_cap(B.NG);
+      if (stage == 0) dss_inc<0><<<blocks, 256, 0, st>>>(B);
+      else if (stage == 1) dss_inc<1><<<blocks, 256, 0, st>>>(B);
+      else dss_inc<2><<<blocks, 256, 0, st>>>(B);
+    }
   }
 }
 
@@ -1131,7 +1235,22 @@ int batch_step_mixed(void* h, const sem_params& p, double* const* q, float* cons
     // the previous graph may still read the old tables
     SEM_CUDA_TRY(cudaStreamSynchronize(st));
     SEM_CUDA_TRY(cudaMemcpy(b->d_vol, vol.data(), sizeof(VolArgs) * vol.size(), cudaMemcpyHostToDevice));
-    SEM_CUDA_TRY(cudaMemcpy(b->d_inc, inc.data(), sizeof(IncArgs) * inc.size(), cudaMemcpyHostToDevice));
+    // device copy: small instances only, [3][nsmall]
+    std::vector<IncArgs> sinc;
+    for (int s2 = 0; s2 < 3; ++s2)
+      for (int k = 0; k < n; ++k)
+        if (!b->big[k]) sinc.push_back(inc[s2 * n + k]);
+    if (!sinc.empty())
+      SEM_CUDA_TRY(cudaMemcpy(b->d_inc, sinc.data(), sizeof(IncArgs) * sinc.size(), cudaMemcpyHostToDevice));
+    b->h_inc = inc;
+    b->h_vol = vol;
+    for (int k = 0; k < n; ++k)
+      if (b->big[k] && b->meshes[k]->pencil_variant < 0) {
+        sem_tune_out tout;
+        std::memset(&tout, 0, sizeof(tout));
+        int rc = autotune_pencil(*b->meshes[k], p, q32[k], 3, &tout, st);
+        if (rc) return rc;
+      }
     b->key = key;
     b->key_dt = kdt;
     std::memcpy(b->key_par, par, sizeof(par));
@@ -1142,6 +1261,10 @@ int batch_step_mixed(void* h, const sem_params& p, double* const* q, float* cons
     if (b->graph) {
       cudaGraphDestroy(b->graph);
       b->graph = nullptr;
+    }
+    if (b->variant < 0 && b->ntiles > 0) {
+      int rc = batch_tune(b, st);
+      if (rc) return rc;
     }
   }
   if (!use_graph) {
@@ -1160,6 +1283,17 @@ int batch_step_mixed(void* h, const sem_params& p, double* const* q, float* cons
   ProfScope ps("batch_step_mixed_graph", st);
   SEM_CUDA_TRY(cudaGraphLaunch(b->exec, st));
   return SEM_OK;
+}
+
+int batch_tuning(void* h, int* variant, int* bt, int* mb, float* ms, int max) {
+  BatchImpl* b = (BatchImpl*)h;
+  *variant = b->variant;
+  for (int v = 0; v < kNumBatch && v < max; ++v) {
+    bt[v] = kBatch[v].BT;
+    mb[v] = kBatch[v].MB;
+    ms[v] = b->variant_ms[v];
+  }
+  return kNumBatch < max ? kNumBatch : max;
 }
 
 int batch_status(void* h, int* status, cudaStream_t st) {
