@@ -220,6 +220,46 @@ int sem_batch_step_mixed(sem_batch* b, const sem_params* p, double* const* q_dev
                          int use_graph, cudaStream_t stream);
 int sem_batch_status(sem_batch* b, int* status_host, cudaStream_t stream);
 
+/* Learned refinement flags.  The paper notes (Sec. 5) that its velocity
+ * criterion only fires once intensification has begun; this per-element
+ * network predicts the criterion's flags (Sec. 3.1) some steps ahead so that
+ * adaptation can run less often, with the criterion kept as fallback.
+ *
+ * Features (sem_mlp_features): for element e (order of sem_mesh_leaves_host,
+ * column * nz + layer), the five state fields at the 27 points {-1, 0, 1}^3 of
+ * the element (its polynomial evaluated there, hanging nodes interpolated),
+ * field f divided by scales[f], stored at feats[e * 136 + f * 27 + a + 3 b +
+ * 9 c], and the element's level at feats[e * 136 + 135]; float32, device.
+ * Network: Linear(136,128)-ReLU-Linear(128,128)-ReLU-Linear(128,3), softmax
+ * over (coarsen, keep, refine) = flags (-1, 0, +1).  Products run on bfloat16
+ * tensor cores with float32 accumulation (inputs, weights and hidden
+ * activations rounded to bfloat16); the backward pass is float32 on the same
+ * rounded values; master weights and Adam moments are float32.  Parameters
+ * (sem_mlp_param_count() floats): W1 [136][128] (input-major), b1 [128],
+ * W2 [128][128], b2 [128], W3 [128][3], b3 [3].  sem_mlp_create draws the
+ * initial weights uniform in +-1/sqrt(fan_in) from splitmix64(seed, index),
+ * zero biases; max_rows bounds n for sem_mlp_backward (work arrays).
+ * sem_mlp_backward: labels are classes 0..2 (= flag + 1), the loss is the
+ * class-weighted mean cross-entropy sum w_y (-log p_y) / sum w_y; it leaves
+ * the gradient in the handle (sem_mlp_get_grads) and, if loss_host is not
+ * NULL, synchronises and returns the loss.  sem_mlp_adam applies one Adam
+ * step (beta 0.9, 0.999, eps 1e-8, bias-corrected) with those gradients. */
+typedef struct sem_mlp sem_mlp;
+int sem_mlp_create(unsigned long long seed, int max_rows, sem_mlp** out);
+void sem_mlp_destroy(sem_mlp* m);
+int sem_mlp_param_count(void);
+int sem_mlp_get_params(sem_mlp* m, float* params_host);
+int sem_mlp_set_params(sem_mlp* m, const float* params_host);
+int sem_mlp_get_grads(sem_mlp* m, float* grads_host);
+int sem_mlp_features(sem_mesh* mesh, const double* q_dev, const float* scales_host,
+                     float* feats_dev, cudaStream_t stream);
+int sem_mlp_forward(sem_mlp* m, const float* feats_dev, int n, float* prob_dev, cudaStream_t stream);
+int sem_mlp_predict_flags(sem_mlp* m, const float* feats_dev, int n, int8_t* flags_dev,
+                          cudaStream_t stream);
+int sem_mlp_backward(sem_mlp* m, const float* feats_dev, const int8_t* labels_dev,
+                     const float* class_w_host, int n, double* loss_host, cudaStream_t stream);
+int sem_mlp_adam(sem_mlp* m, float lr, cudaStream_t stream);
+
 /* q32 = float32 mirror of q ([5][NG]; significand truncated to 24 bits). */
 int sem_mirror(sem_mesh* m, const double* q_dev, float* q32_dev, cudaStream_t stream);
 

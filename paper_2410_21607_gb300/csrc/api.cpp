@@ -397,6 +397,75 @@ int sem_batch_status(sem_batch* b, int* status, cudaStream_t st) {
   return batch_status(b->impl, status, st);
 }
 
+int sem_mlp_create(unsigned long long seed, int max_rows, sem_mlp** out) {
+  if (!out || max_rows <= 0) return fail(SEM_ERR_ARG, "bad argument");
+  *out = nullptr;
+  sem_mlp* m = new (std::nothrow) sem_mlp();
+  if (!m) return fail(SEM_ERR_ARG, "out of host memory");
+  int rc = mlp_create(seed, max_rows, &m->impl);
+  if (rc) {
+    delete m;
+    return rc;
+  }
+  m->max_rows = max_rows;
+  *out = m;
+  return SEM_OK;
+}
+
+void sem_mlp_destroy(sem_mlp* m) {
+  if (!m) return;
+  mlp_destroy(m->impl);
+  delete m;
+}
+
+int sem_mlp_param_count(void) { return mlp_param_count(); }
+
+int sem_mlp_get_params(sem_mlp* m, float* host) {
+  if (!m || !host) return fail(SEM_ERR_ARG, "NULL argument");
+  return mlp_params(m->impl, host, 0, 0);
+}
+
+int sem_mlp_set_params(sem_mlp* m, const float* host) {
+  if (!m || !host) return fail(SEM_ERR_ARG, "NULL argument");
+  return mlp_params(m->impl, const_cast<float*>(host), 1, 0);
+}
+
+int sem_mlp_get_grads(sem_mlp* m, float* host) {
+  if (!m || !host) return fail(SEM_ERR_ARG, "NULL argument");
+  return mlp_params(m->impl, host, 0, 1);
+}
+
+int sem_mlp_features(sem_mesh* mh, const double* q, const float* scales, float* feats,
+                     cudaStream_t st) {
+  if (!mh || !q || !scales || !feats) return fail(SEM_ERR_ARG, "NULL argument");
+  for (int f = 0; f < kFields; ++f)
+    if (!(scales[f] != 0.0f)) return fail(SEM_ERR_ARG, "feature scales must be non-zero");
+  int rc = ensure_device(mh->m);
+  if (rc) return rc;
+  return mlp_features_api(mh->m, q, scales, feats, st);
+}
+
+int sem_mlp_forward(sem_mlp* m, const float* feats, int n, float* prob, cudaStream_t st) {
+  if (!m || !feats || !prob || n < 0) return fail(SEM_ERR_ARG, "bad argument");
+  return mlp_forward_api(m->impl, feats, n, prob, nullptr, st);
+}
+
+int sem_mlp_predict_flags(sem_mlp* m, const float* feats, int n, int8_t* flags, cudaStream_t st) {
+  if (!m || !feats || !flags || n < 0) return fail(SEM_ERR_ARG, "bad argument");
+  return mlp_forward_api(m->impl, feats, n, nullptr, flags, st);
+}
+
+int sem_mlp_backward(sem_mlp* m, const float* feats, const int8_t* labels, const float* class_w,
+                     int n, double* loss_host, cudaStream_t st) {
+  if (!m || !feats || !labels || !class_w) return fail(SEM_ERR_ARG, "NULL argument");
+  return mlp_backward_api(m->impl, feats, labels, class_w, n, loss_host, st);
+}
+
+int sem_mlp_adam(sem_mlp* m, float lr, cudaStream_t st) {
+  if (!m || !(lr > 0)) return fail(SEM_ERR_ARG, "bad argument");
+  return mlp_adam_api(m->impl, lr, st);
+}
+
 int sem_mirror(sem_mesh* mh, const double* q, float* q32, cudaStream_t st) {
   if (!mh || !q || !q32) return fail(SEM_ERR_ARG, "NULL argument");
   int rc = ensure_device(mh->m);

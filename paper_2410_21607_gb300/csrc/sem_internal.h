@@ -172,6 +172,15 @@ void batch_destroy(void* b);
 int batch_step_mixed(void* b, const sem_params& p, double* const* q, float* const* q32,
                      float* const* work32, const double* dt, int use_graph, cudaStream_t st);
 int batch_status(void* b, int* status, cudaStream_t st);
+int mlp_create(unsigned long long seed, int max_rows, void** out);
+void mlp_destroy(void* m);
+int mlp_params(void* m, float* host, int set, int which);
+int mlp_param_count();
+int mlp_forward_api(void* m, const float* X, int n, float* prob, int8_t* flags, cudaStream_t st);
+int mlp_backward_api(void* m, const float* X, const int8_t* y, const float* cw, int n, double* loss_host,
+                     cudaStream_t st);
+int mlp_adam_api(void* m, float lr, cudaStream_t st);
+int mlp_features_api(Mesh& mesh, const double* q, const float* scales, float* F, cudaStream_t st);
 int autotune_pencil(Mesh& m, const sem_params& p, const float* q32, int reps, sem_tune_out* out,
                     cudaStream_t st);
 int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float* work32, double dt,
@@ -191,6 +200,11 @@ struct ProfScope {
 
 struct sem_mesh {
   sem::Mesh m;
+};
+
+struct sem_mlp {
+  void* impl = nullptr;
+  int max_rows = 0;
 };
 
 struct sem_batch {

@@ -30,6 +30,9 @@ EXPORTS = (
     "sem_adapt_flags", "sem_adapt_flags_host", "sem_transfer_plan", "sem_transfer", "sem_diag",
     "sem_status", "sem_profile_begin", "sem_profile_end", "sem_autotune",
     "sem_batch_create", "sem_batch_destroy", "sem_batch_step_mixed", "sem_batch_status",
+    "sem_mlp_create", "sem_mlp_destroy", "sem_mlp_param_count", "sem_mlp_get_params",
+    "sem_mlp_set_params", "sem_mlp_get_grads", "sem_mlp_features", "sem_mlp_forward",
+    "sem_mlp_predict_flags", "sem_mlp_backward", "sem_mlp_adam",
 )
 
 
@@ -110,6 +113,17 @@ def _load():
         "sem_batch_step_mixed": (i, [vp, C.POINTER(Params), C.POINTER(vp), C.POINTER(vp),
                                      C.POINTER(vp), C.POINTER(d), i, vp]),
         "sem_batch_status": (i, [vp, C.POINTER(C.c_int), vp]),
+        "sem_mlp_create": (i, [C.c_ulonglong, i, C.POINTER(vp)]),
+        "sem_mlp_destroy": (None, [vp]),
+        "sem_mlp_param_count": (i, []),
+        "sem_mlp_get_params": (i, [vp, vp]),
+        "sem_mlp_set_params": (i, [vp, vp]),
+        "sem_mlp_get_grads": (i, [vp, vp]),
+        "sem_mlp_features": (i, [vp, vp, vp, vp, vp]),
+        "sem_mlp_forward": (i, [vp, vp, i, vp, vp]),
+        "sem_mlp_predict_flags": (i, [vp, vp, i, vp, vp]),
+        "sem_mlp_backward": (i, [vp, vp, vp, vp, i, C.POINTER(d), vp]),
+        "sem_mlp_adam": (i, [vp, C.c_float, vp]),
         "sem_autotune": (i, [vp, C.POINTER(Params), vp, i, C.POINTER(TuneOut), vp]),
         "sem_profile_end": (i, [C.POINTER(ProfileOut)]),
     }
@@ -413,3 +427,80 @@ def sem_batch_status(batch, stream=None):
     v = C.c_int(0)
     _check(LIB.sem_batch_status(batch.h, C.byref(v), _stream(stream)))
     return v.value
+
+
+class Mlp:
+    """Owning handle of a sem_mlp."""
+
+    def __init__(self, handle, max_rows):
+        self.h = C.c_void_p(handle)
+        self.max_rows = max_rows
+        self.nparam = LIB.sem_mlp_param_count()
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            LIB.sem_mlp_destroy(h)
+            self.h = None
+
+
+def sem_mlp_create(seed, max_rows):
+    h = C.c_void_p()
+    _check(LIB.sem_mlp_create(int(seed), int(max_rows), C.byref(h)))
+    return Mlp(h.value, max_rows)
+
+
+def sem_mlp_get_params(mlp):
+    out = np.zeros(mlp.nparam, dtype=np.float32)
+    _check(LIB.sem_mlp_get_params(mlp.h, _ptr(out)))
+    return out
+
+
+def sem_mlp_set_params(mlp, params):
+    a = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+    if a.size != mlp.nparam:
+        raise ValueError("wrong parameter count")
+    _check(LIB.sem_mlp_set_params(mlp.h, _ptr(a)))
+
+
+def sem_mlp_get_grads(mlp):
+    out = np.zeros(mlp.nparam, dtype=np.float32)
+    _check(LIB.sem_mlp_get_grads(mlp.h, _ptr(out)))
+    return out
+
+
+def sem_mlp_features(mesh, q, scales, feats, stream=None):
+    _f64(q, mesh.field_shape)
+    _f32(feats, (mesh.Ne, 136))
+    sc = np.ascontiguousarray(np.asarray(scales, dtype=np.float32))
+    _check(LIB.sem_mlp_features(mesh.h, _ptr(q), _ptr(sc), _ptr(feats), _stream(stream)))
+    return feats
+
+
+def sem_mlp_forward(mlp, feats, prob, stream=None):
+    n = feats.shape[0]
+    _f32(feats, (n, 136))
+    _f32(prob, (n, 3))
+    _check(LIB.sem_mlp_forward(mlp.h, _ptr(feats), n, _ptr(prob), _stream(stream)))
+    return prob
+
+
+def sem_mlp_predict_flags(mlp, feats, flags, stream=None):
+    n = feats.shape[0]
+    _f32(feats, (n, 136))
+    _check(LIB.sem_mlp_predict_flags(mlp.h, _ptr(feats), n, _ptr(flags), _stream(stream)))
+    return flags
+
+
+def sem_mlp_backward(mlp, feats, labels, class_w, want_loss=True, stream=None):
+    n = feats.shape[0]
+    _f32(feats, (n, 136))
+    cw = np.ascontiguousarray(np.asarray(class_w, dtype=np.float32))
+    loss = C.c_double(0.0)
+    _check(LIB.sem_mlp_backward(mlp.h, _ptr(feats), _ptr(labels), _ptr(cw), n,
+                                C.byref(loss) if want_loss else None, _stream(stream)))
+    return loss.value if want_loss else None
+
+
+def sem_mlp_adam(mlp, lr, stream=None):
+    _check(LIB.sem_mlp_adam(mlp.h, float(lr), _stream(stream)))
