@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--gate-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     return ap.parse_args()
 
 
@@ -185,6 +186,26 @@ def batched_measure(sem, torch, steps=10, warmup=3, refine=True):
             "value_graph": dof * 3 / (ms_graph * 1e-3), "value_sequential": dof * 3 / (ms_seq * 1e-3),
             "speedup": ms_seq / ms_graph, "status": status,
             "launches_per_step_graph": 1, "launches_per_step_sequential": 6 * len(insts)}
+
+
+def learned_measure(sem, torch):
+    """The learned adaptation schedule against the criterion alone (same
+    remesh count): ten seeded translating vortices, train on eight."""
+    from paper_2410_21607_gb300 import learned
+    from synth.vortex import vortex_state
+    from synth.workloads import translating_vortices
+    L, Lz = 150e3, 24e3
+    m = sem.sem_mesh_create(L, L, Lz, 24, 24, 2, 4, lvl_max=2)
+    X = sem.sem_mesh_coords_host(m).T
+    states = [torch.from_numpy(vortex_state(X, Lz, s)).cuda() for s in translating_vortices()]
+    t0 = time.perf_counter()
+    res = learned.gain_experiment(sem, torch, m, states, dt=1.0, n_train=8)
+    keep = ("rows", "loss_first", "loss_last", "remeshes", "missed_criterion", "missed_learned",
+            "level_criterion", "level_learned", "status")
+    out = {k: res[k] for k in keep}
+    out["workload"] = "24x24x2 N=4, 150 km box, 10 translating vortices x 400 steps, flags 50 steps ahead"
+    out["seconds"] = time.perf_counter() - t0
+    return out
 
 
 def run_reference(a):
@@ -411,6 +432,10 @@ def main():
     if not a.no_batched and a.form == "mixed":
         batched = [batched_measure(sem, torch), batched_measure(sem, torch, refine=False)]
 
+    learned_res = None
+    if not a.no_learned and a.form == "mixed":
+        learned_res = learned_measure(sem, torch)
+
     line = None
     if rank == 0:
         cpu = None
@@ -432,6 +457,7 @@ def main():
                 "speedup_mixed_over_fp64": fp64_ms / ms},
             "gate": gate,
             "roofline": roof, "kernels": kernels, "autotune": tune, "batched": batched,
+            "learned": learned_res,
             "cpu_baseline": cpu,
             "e2e": {"value": dof_stage * 3 * world / (e2e_ms * 1e-3), "unit": "DOF-updates/s",
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,

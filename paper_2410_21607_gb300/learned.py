@@ -1,0 +1,147 @@
+"""Learned adaptation schedule: training data from solver trajectories, training
+and the missed-refinement comparison against the paper's criterion.
+
+Every field operation runs in libsem.so (steps, criterion, features, network
+forward/backward/Adam); this module only sequences the calls and does the
+integer bookkeeping of element levels with torch tensor ops.
+
+Protocol.  The solver runs trajectories; every `every` steps it records each
+element's features (sem_mlp_features) and the criterion's per-element maximum
+speed (sem_adapt_flags).  A training row pairs the features at step t, with
+the element's level set to L, with the criterion's flag for level L at step
+t + ahead (Sec. 3.1 rule: +1 above threshold(L+1), -1 at or below
+threshold(L), else 0), for every L in 0..lvl_max.
+
+Scheduling (element levels kept as a virtual level per element on the fixed
+solver mesh, so that the comparison isolates the scheduling): every `ahead`
+steps the levels move by the flags (one level at most, Remark 3.1); at the
+checks in between, an element is a missed refinement when the criterion wants
+a higher level than it has.  Schedules compared at the same remesh count:
+the criterion alone, and the criterion with the network, where an element is
+refined when either the current criterion or the network's prediction for
+`ahead` steps later asks for it, and coarsened only when both do (the
+criterion stays the fallback).
+"""
+import numpy as np
+
+
+def target_level(cmax, thresholds):
+    """Number of thresholds the element maximum speed exceeds (Sec. 3.1)."""
+    t = (cmax > thresholds[0]).long()
+    for thr in thresholds[1:]:
+        t = t + (cmax > thr).long()
+    return t
+
+
+def trajectory(sem, torch, mesh, p_step, p_crit, q0, dt, steps, every, scales):
+    """[(features, cmax)] every `every` steps of a mixed-form run from q0."""
+    q = q0.clone()
+    q32 = torch.empty(q.shape, dtype=torch.float32, device=q.device)
+    work = torch.empty((10, mesh.NG), dtype=torch.float32, device=q.device)
+    sem.sem_mirror(mesh, q, q32)
+    flags = torch.empty(mesh.Ne, dtype=torch.int8, device=q.device)
+    out = []
+    for s in range(steps + 1):
+        if s % every == 0:
+            cmax = torch.empty(mesh.Ne, dtype=torch.float64, device=q.device)
+            sem.sem_adapt_flags(mesh, p_crit, q, flags, cmax)
+            F = torch.empty((mesh.Ne, 136), dtype=torch.float32, device=q.device)
+            sem.sem_mlp_features(mesh, q, scales, F)
+            out.append((F, cmax))
+        if s < steps:
+            sem.sem_step_mixed(mesh, p_step, q, q32, work, dt)
+    return out
+
+
+def training_rows(torch, snaps, ahead, every, thresholds, lvl_max):
+    k = ahead // every
+    Fs, Ys = [], []
+    for i in range(len(snaps) - k):
+        F = snaps[i][0]
+        T = target_level(snaps[i + k][1], thresholds)
+        for L in range(lvl_max + 1):
+            G = F.clone()
+            G[:, 135] = float(L)
+            y = torch.where(T > L, 2, torch.where(T < L, 0, 1)).to(torch.int8)
+            Fs.append(G)
+            Ys.append(y)
+    return torch.cat(Fs), torch.cat(Ys)
+
+
+def train(sem, torch, F, Y, iters=1500, batch=65536, seed=1, lr=1e-3):
+    counts = torch.bincount(Y.long(), minlength=3).cpu().numpy()
+    cw = (counts.sum() / np.maximum(counts, 1) / 3.0).astype(np.float32)
+    batch = min(batch, F.shape[0])
+    net = sem.sem_mlp_create(seed, batch)
+    g = torch.Generator(device=F.device).manual_seed(seed)
+    first = last = None
+    for it in range(iters):
+        idx = torch.randint(0, F.shape[0], (batch,), device=F.device, generator=g)
+        want = it == 0 or it == iters - 1
+        loss = sem.sem_mlp_backward(net, F[idx].contiguous(), Y[idx].contiguous(), cw, want_loss=want)
+        if it == 0:
+            first = loss
+        if it == iters - 1:
+            last = loss
+        sem.sem_mlp_adam(net, lr if it < 2 * iters // 3 else lr / 3)
+    return net, first, last
+
+
+def schedule(sem, torch, snaps, ahead, every, thresholds, lvl_max, net=None):
+    """Missed-refinement rate, mean refined levels and remesh count."""
+    Ne = snaps[0][0].shape[0]
+    dev = snaps[0][0].device
+    L = torch.zeros(Ne, dtype=torch.long, device=dev)
+    k = ahead // every
+    missed = want = 0
+    refined = 0.0
+    remesh = 0
+    for i, (F, cmax) in enumerate(snaps):
+        T = target_level(cmax, thresholds)
+        if i % k == 0:
+            remesh += 1
+            now = (T > L).long() - ((T < L) & (L > 0)).long()
+            if net is None:
+                fl = now
+            else:
+                G = F.clone()
+                G[:, 135] = L.float()
+                pred = torch.empty(Ne, dtype=torch.int8, device=dev)
+                sem.sem_mlp_predict_flags(net, G, pred)
+                pred = pred.long()
+                fl = torch.where((now > 0) | (pred > 0), 1,
+                                 torch.where((now < 0) & (pred < 0), -1, 0))
+            L = torch.clamp(L + fl, 0, lvl_max)
+        else:
+            missed += int((T > L).sum())
+            want += int((T > 0).sum())
+        refined += float(L.float().mean())
+    return {"missed_rate": missed / max(want, 1), "mean_level": refined / len(snaps),
+            "remeshes": remesh}
+
+
+def gain_experiment(sem, torch, mesh, states, dt, n_train, steps=400, every=10, ahead=50,
+                    thresholds=(15.0, 25.0), scales=(1e-3, 10.0, 10.0, 1.0, 1.0), iters=1500, seed=1):
+    """Train on the first n_train initial states' trajectories, compare the
+    two schedules on the others.  Returns a dict of the measured numbers."""
+    lvl_max = len(thresholds)
+    p_step = sem.sem_params_default(precision=sem.SEM_PREC_MIXED)
+    p_crit = sem.sem_params_default(thresholds=list(thresholds), lvl_max=lvl_max)
+    sc = np.asarray(scales, dtype=np.float32)
+    trajs = [trajectory(sem, torch, mesh, p_step, p_crit, q0, dt, steps, every, sc) for q0 in states]
+    status = sem.sem_status(mesh)
+    parts = [training_rows(torch, t, ahead, every, thresholds, lvl_max) for t in trajs[:n_train]]
+    F = torch.cat([a for a, _ in parts])
+    Y = torch.cat([b for _, b in parts])
+    net, loss0, loss1 = train(sem, torch, F, Y, iters=iters, seed=seed)
+    res = {"status": status, "rows": int(F.shape[0]), "loss_first": loss0, "loss_last": loss1,
+           "criterion": [], "learned": []}
+    for t in trajs[n_train:]:
+        res["criterion"].append(schedule(sem, torch, t, ahead, every, thresholds, lvl_max))
+        res["learned"].append(schedule(sem, torch, t, ahead, every, thresholds, lvl_max, net))
+    res["missed_criterion"] = float(np.mean([r["missed_rate"] for r in res["criterion"]]))
+    res["missed_learned"] = float(np.mean([r["missed_rate"] for r in res["learned"]]))
+    res["level_criterion"] = float(np.mean([r["mean_level"] for r in res["criterion"]]))
+    res["level_learned"] = float(np.mean([r["mean_level"] for r in res["learned"]]))
+    res["remeshes"] = res["criterion"][0]["remeshes"]
+    return res

@@ -66,6 +66,8 @@ class VortexSpec:
     seed: int = 20241028
     xc: float = 0.0
     yc: float = 0.0
+    u0: float = 0.0             # uniform background wind added to the vortex (m/s)
+    v0: float = 0.0
 
 
 def gaussian_vortex_scale(vmax, rmw):
@@ -155,7 +157,7 @@ def vortex_state(xyz, Lz, spec=VortexSpec(), eqset="C", Rmax=None):
     with np.errstate(invalid="ignore", divide="ignore"):
         s_ = np.where(r > 0, y / r, 0.0)
         c_ = np.where(r > 0, x / r, 0.0)
-    u, v, w = -vb * s_, vb * c_, np.zeros_like(vb)
+    u, v, w = -vb * s_ + spec.u0, vb * c_ + spec.v0, np.zeros_like(vb)
     dth = spec.noise_K * (2.0 * splitmix64_uniform(spec.seed, xyz) - 1.0)
     Tp = drt + rho * dth
     if eqset == "C":

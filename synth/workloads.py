@@ -124,3 +124,24 @@ def geometric_flags(leaves, nx, nz, L, radius, lvl_max):
         if l < lvl_max and np.hypot(xc, yc) < radius:
             fl[c * nz:(c + 1) * nz] = 1
     return fl
+
+
+def translating_vortices(count=10, seed=7):
+    """Seeded vortices for the learned-schedule experiment on a 150 km box:
+    v_max 20..32 m/s, radius of maximum wind 14..22 km, outer taper 45 km so
+    the vortex fits the periodic box, centre within 40 km of the middle, and a
+    uniform background wind of 6..14 m/s in a random direction that carries
+    it across element boundaries.  No theta noise (the inviscid
+    discretisation amplifies grid-scale noise over a few hundred steps)."""
+    import numpy as np
+    from .vortex import VortexSpec
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        ang = rng.uniform(0, 2 * np.pi)
+        sp = rng.uniform(6, 14)
+        out.append(VortexSpec(vmax=float(rng.uniform(20, 32)), rmw=float(rng.uniform(14e3, 22e3)),
+                              D2=45e3, u0=float(sp * np.cos(ang)), v0=float(sp * np.sin(ang)),
+                              noise_K=0.0, xc=float(rng.uniform(-40e3, 40e3)),
+                              yc=float(rng.uniform(-40e3, 40e3)), seed=10 + k))
+    return out
