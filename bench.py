@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-amr", action="store_true")
     return ap.parse_args()
 
 
@@ -186,6 +187,57 @@ def batched_measure(sem, torch, steps=10, warmup=3, refine=True):
             "value_graph": dof * 3 / (ms_graph * 1e-3), "value_sequential": dof * 3 / (ms_seq * 1e-3),
             "speedup": ms_seq / ms_graph, "status": status,
             "launches_per_step_graph": 1, "launches_per_step_sequential": 6 * len(insts)}
+
+
+def amr_measure(sem, torch, steps=500, t_amr=50):
+    """The adaptive workload: 32x32x8 base, N=4, 600 km box, geometric level-3
+    refinement inside r < 150 km (2:1 balanced), criterion thresholds
+    [5, 10, 15] m/s, remesh with solution transfer every 50 steps, mixed form,
+    dt = 0.4 s.  Reports throughput including the remeshes."""
+    from synth.vortex import vortex_state
+    from synth.workloads import geometric_flags
+    L, Lz, n, nz, N, dt = 600e3, 24e3, 32, 8, 4, 0.4
+    thr = [5.0, 10.0, 15.0]
+    m = sem.sem_mesh_create(L, L, Lz, n, n, nz, N, lvl_max=3)
+    for _ in range(3):
+        lv = [tuple(x) for x in sem.sem_mesh_leaves_host(m)]
+        m = sem.sem_transfer_plan(m, geometric_flags(lv, n, nz, L, 150e3, 3))
+    q = torch.from_numpy(vortex_state(sem.sem_mesh_coords_host(m).T, Lz)).cuda()
+    p = sem.sem_params_default(precision=sem.SEM_PREC_MIXED)
+    pc = sem.sem_params_default(thresholds=thr, lvl_max=3)
+    stream = torch.cuda.current_stream()
+    history = []
+    dof = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    remesh_s = 0.0
+    s = 0
+    while s < steps:
+        q32 = torch.empty(q.shape, dtype=torch.float32, device="cuda")
+        work = torch.empty((10, m.NG), dtype=torch.float32, device="cuda")
+        sem.sem_mirror(m, q, q32, stream)
+        for _ in range(min(t_amr, steps - s)):
+            sem.sem_step_mixed(m, p, q, q32, work, dt, stream)
+            dof += 3 * 5 * m.Ne * (N + 1) ** 3
+            s += 1
+        history.append({"step": s, "elements": int(m.Ne),
+                        "levels": [int(m.info.level_hist[k]) for k in range(4)]})
+        if s < steps:
+            torch.cuda.synchronize()
+            r0 = time.perf_counter()
+            flags = sem.sem_adapt_flags_host(m, pc, q, stream)
+            new = sem.sem_transfer_plan(m, flags)
+            qn = torch.empty((5, new.NG), dtype=torch.float64, device="cuda")
+            sem.sem_transfer(m, new, q, qn, stream)
+            torch.cuda.synchronize()
+            remesh_s += time.perf_counter() - r0
+            m, q = new, qn
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    d = sem.sem_diag(m, pc, q)
+    return {"workload": "32x32x8 base N=4, level 3 inside 150 km, thresholds [5,10,15], remesh every 50",
+            "steps": steps, "wall_s": wall, "remesh_s": remesh_s, "dof_updates_per_s": dof / wall,
+            "history": history, "status": sem.sem_status(m), "max_wind": d["max_wind"]}
 
 
 def learned_measure(sem, torch):
@@ -432,6 +484,9 @@ def main():
     if not a.no_batched and a.form == "mixed":
         batched = [batched_measure(sem, torch), batched_measure(sem, torch, refine=False)]
 
+    amr_res = None
+    if not a.no_amr and a.form == "mixed":
+        amr_res = amr_measure(sem, torch)
     learned_res = None
     if not a.no_learned and a.form == "mixed":
         learned_res = learned_measure(sem, torch)
@@ -457,7 +512,7 @@ def main():
                 "speedup_mixed_over_fp64": fp64_ms / ms},
             "gate": gate,
             "roofline": roof, "kernels": kernels, "autotune": tune, "batched": batched,
-            "learned": learned_res,
+            "learned": learned_res, "amr": amr_res,
             "cpu_baseline": cpu,
             "e2e": {"value": dof_stage * 3 * world / (e2e_ms * 1e-3), "unit": "DOF-updates/s",
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
