@@ -315,6 +315,7 @@ typedef struct {
   int chosen;                          /* index into the arrays below */
   int layers_per_cta[SEM_TUNE_MAX];
   int min_ctas_per_sm[SEM_TUNE_MAX];
+  int persistent[SEM_TUNE_MAX];        /* 1: persistent CTAs prefetching the next column */
   double ms[SEM_TUNE_MAX];             /* mean event time per launch */
 } sem_tune_out;
 int sem_autotune(sem_mesh* m, const sem_params* p, const float* q32_dev, int reps,

@@ -99,6 +99,7 @@ struct VolArgs {
   int nx, ny;
   double g, f, gamma;
   float gf, ff, gammaf;
+  float bin[8];         // binomial-series coefficients C(gamma, k), k = 1..7
   double geo[kLev][8];
   float geof[kLev][8];
   const float* ref32;
@@ -477,13 +478,36 @@ static void launch_volume_n(const VolArgs& A, int eq, bool mixed, cudaStream_t s
 // shared by consecutive layers is summed inside the CTA (vertical DSS), as in
 // volume_column.  Arithmetic: float32; geometry and reference state come from
 // tables computed in float64.
+__host__ __device__ constexpr int pencil_sk(int N) {
+  // n1 * n1 * CW words rounded up to the next value = 2 (mod 32)
+  return ((N + 1) * (N + 1) * (2 * ((N + 2) / 2)) + 29) / 32 * 32 + 2;
+}
+
+// (1 + x)^gamma - 1 in float32.  For |x| <= 1/8 the binomial series
+// sum_{k=1..7} C(gamma, k) x^k (Horner form, no cancellation); its first
+// dropped term is below 3e-9 of the result there, under float32 rounding.
+// Larger |x| take expm1(gamma log1p(x)).
+__device__ __forceinline__ float pow1p_m1(float x, const float* bin, float gam) {
+  if (fabsf(x) <= 0.125f) {
+    float s = bin[6];
+#pragma unroll
+    for (int k = 5; k >= 0; --k) s = fmaf(s, x, bin[k]);
+    return s * x;
+  }
+  return expm1f(gam * log1pf(x));
+}
+
 // Body shared by the single-mesh kernel (one CTA per column) and the batched
 // persistent kernel (CTAs pull columns of many meshes from a queue).  Threads
 // t >= KL (N+1)^2 of a larger CTA take part in the barriers only.
 template <int N, int KL>
 __device__ __forceinline__ void pencil_body(const VolArgs& A, const int col, float* smem, const int t) {
   constexpr int n1 = N + 1, Nq = n1 * n1, CP = (n1 + 1) / 2, CW = 2 * CP;
-  constexpr int SXY = kFields * KL * Nq * CW;  // floats per flux direction
+  // words per layer block, padded to 2 (mod 32) so that the 16 layers a
+  // half-warp reads (64-bit loads of one z-line's rows) fall on 16 distinct
+  // bank pairs
+  constexpr int SK = pencil_sk(N);
+  constexpr int SXY = kFields * KL * SK;  // floats per flux direction
   const bool part = t < KL * Nq;
   float* sX = smem;                    // [f][kk][j][m][c]
   float* sY = sX + SXY;                // [f][kk][i][m][c]
@@ -516,9 +540,9 @@ __device__ __forceinline__ void pencil_body(const VolArgs& A, const int col, flo
     for (int f = 0; f < kFields; ++f)
 #pragma unroll
       for (int p = 0; p < CP; ++p) r[f][p] = make_float2(0.f, 0.f);
-    float* myX = sX + ((0 * KL + kk) * n1 + j) * n1 * CW + i * CW;  // + f * KL*Nq*CW + c
-    float* myY = sY + ((0 * KL + kk) * n1 + i) * n1 * CW + j * CW;
-    constexpr int FS = KL * Nq * CW;                               // field stride
+    float* myX = sX + kk * SK + j * n1 * CW + i * CW;  // + f * FS + c
+    float* myY = sY + kk * SK + i * n1 * CW + j * CW;
+    constexpr int FS = KL * SK;                         // field stride
     if (act) {
 #pragma unroll
       for (int c = 0; c < n1; ++c) {
@@ -545,7 +569,7 @@ __device__ __forceinline__ void pencil_body(const VolArgs& A, const int col, flo
         const float rp = v[0], U = v[1], V = v[2], W = v[3], Tp = v[4];
         const float inv = __frcp_rn(rho0 + rp);
         const float u = U * inv, vv = V * inv, w = W * inv;
-        const float pp = p0 * expm1f(gam * log1pf(Tp * inv_rt0));
+        const float pp = p0 * pow1p_m1(Tp * inv_rt0, A.bin, gam);
         const float rt = rt0 + Tp;
         const float wc = c_wf[N][c];
         const float ax = wj * wc * sx, ay = wi * wc * sy, az = wi * wj * sz;
@@ -597,8 +621,8 @@ __device__ __forceinline__ void pencil_body(const VolArgs& A, const int col, flo
     }
     __syncthreads();
     // x and y contractions from shared memory, two nodes per packed FMA
-    const float* rowX = sX + ((0 * KL + kk) * n1 + j) * n1 * CW;  // + f*FS + m*CW + c
-    const float* rowY = sY + ((0 * KL + kk) * n1 + i) * n1 * CW;
+    const float* rowX = sX + kk * SK + j * n1 * CW;  // + f*FS + m*CW + c
+    const float* rowY = sY + kk * SK + i * n1 * CW;
 #pragma unroll
     for (int f = 0; f < kFields; ++f)
 #pragma unroll
@@ -659,10 +683,259 @@ volume_pencil_mixed(const VolArgs A) {
   pencil_body<N, KL>(A, blockIdx.x, smem, threadIdx.x);
 }
 
+// Persistent, software-pipelined variant of the pencil kernel: each CTA walks
+// columns blockIdx.x, blockIdx.x + gridDim.x, ... and, while it computes one
+// (column, layer chunk), the state values of the next one stream into a second
+// shared-memory stage with per-thread cp.async copies (each thread copies and
+// later reads only its own z-line values, so the stage needs no barrier).
+// Flux rows are written as 64-bit node pairs.  Arithmetic identical to
+// pencil_body.
+__device__ __forceinline__ void cp_async4(float* smem_dst, const float* gsrc) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(a), "l"(gsrc));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+template <int N, int KL>
+__host__ __device__ constexpr int pipe_stage_floats() {
+  return 2 * kFields * (N + 1) * KL * (N + 1) * (N + 1);
+}
+
+template <int N, int KL, int MB>
+__global__ void __launch_bounds__(KL * (N + 1) * (N + 1), MB)
+volume_pencil_pipe(const VolArgs A) {
+  constexpr int n1 = N + 1, Nq = n1 * n1, CP = (n1 + 1) / 2, CW = 2 * CP;
+  constexpr int NT = KL * Nq;
+  constexpr int SK = pencil_sk(N);
+  constexpr int SXY = kFields * KL * SK;
+  constexpr int FS = KL * SK;
+  extern __shared__ __align__(16) float smem[];
+  float* sX = smem;
+  float* sY = sX + SXY;
+  float* sT = sY + SXY;
+  float* sP = sT + kFields * KL * Nq;
+  float* stage = sP + kFields * Nq;      // [2][f][c][NT]
+  const int t = threadIdx.x;
+  const int kk = t % KL, ab = t / KL;
+  const int i = ab % n1, j = ab / n1;
+  const float* q = (const float*)A.q;
+  const float* hw = (const float*)A.hang_w;
+  float Dwi[n1], Dwj[n1];
+#pragma unroll
+  for (int m = 0; m < n1; ++m) {
+    Dwi[m] = c_Dwf[N][i * n1 + m];
+    Dwj[m] = c_Dwf[N][j * n1 + m];
+  }
+  const float wi = c_wf[N][i], wj = c_wf[N][j];
+  const float g = A.gf, fc = A.ff, gam = A.gammaf;
+  float* rc = (float*)A.rc;
+  const int nchunk = (A.nz + KL - 1) / KL;
+
+  auto issue = [&](int col, int ch, int buf) {
+    const int k = ch * KL + kk;
+    if (k < A.nz) {
+      const int hm = A.hmap[(long long)col * Nq + ab];
+      if (hm >= 0) {
+        const float* pq = q + (long long)hm * A.NZ + k * N;
+        float* st = stage + (long long)buf * kFields * n1 * NT + t;
+#pragma unroll
+        for (int f = 0; f < kFields; ++f)
+#pragma unroll
+          for (int c = 0; c < n1; ++c) cp_async4(st + (f * n1 + c) * NT, pq + (long long)f * A.NG + c);
+      }
+    }
+    cp_async_commit();
+  };
+
+  int col = blockIdx.x, ch = 0, buf = 0;
+  if (col < A.Ncol) issue(col, 0, 0);
+  while (col < A.Ncol) {
+    int ncol = col, nch = ch + 1;
+    if (nch == nchunk) {
+      ncol = col + gridDim.x;
+      nch = 0;
+    }
+    if (ncol < A.Ncol) issue(ncol, nch, buf ^ 1);
+    else cp_async_commit();
+    cp_async_wait1();
+
+    const int lev = A.col_level[col];
+    const float* geo = A.geof[lev];
+    const float sx = geo[4], sy = geo[5], sz = geo[6], J = geo[3];
+    const int hm = A.hmap[(long long)col * Nq + ab];
+    const int k = ch * KL + kk;
+    const bool act = k < A.nz;
+    const int kz0 = k * N;
+    const float* st = stage + (long long)buf * kFields * n1 * NT + t;
+    float2 r[kFields][CP];
+#pragma unroll
+    for (int f = 0; f < kFields; ++f)
+#pragma unroll
+      for (int p = 0; p < CP; ++p) r[f][p] = make_float2(0.f, 0.f);
+    float* myX = sX + kk * SK + j * n1 * CW + i * CW;
+    float* myY = sY + kk * SK + i * n1 * CW + j * CW;
+    if (act) {
+#pragma unroll
+      for (int p = 0; p < CP; ++p) {
+        float fx[2][kFields], fy[2][kFields];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = 2 * p + h;
+          if (c >= n1) {
+#pragma unroll
+            for (int f = 0; f < kFields; ++f) fx[h][f] = fy[h][f] = 0.f;
+            continue;
+          }
+          float v[kFields];
+          const int kz = kz0 + c;
+          if (hm >= 0) {
+#pragma unroll
+            for (int f = 0; f < kFields; ++f) v[f] = st[(f * n1 + c) * NT];
+          } else {
+            const int hk = -1 - hm;
+#pragma unroll
+            for (int f = 0; f < kFields; ++f) v[f] = 0.f;
+#pragma unroll
+            for (int m = 0; m < n1; ++m) {
+              const float wm = __ldg(hw + hk * n1 + m);
+              const float* pq = q + (long long)__ldg(A.hang_h + hk * n1 + m) * A.NZ + kz;
+#pragma unroll
+              for (int f = 0; f < kFields; ++f) v[f] = fmaf(wm, __ldg(pq + (long long)f * A.NG), v[f]);
+            }
+          }
+          const float* rf = A.ref32 + (long long)kz * kRef;
+          const float p0 = __ldg(rf + 2), rho0 = __ldg(rf + 3), rt0 = __ldg(rf + 4), inv_rt0 = __ldg(rf + 6);
+          const float rp = v[0], U = v[1], V = v[2], W = v[3], Tp = v[4];
+          const float inv = __frcp_rn(rho0 + rp);
+          const float u = U * inv, vv = V * inv, w = W * inv;
+          const float pp = p0 * pow1p_m1(Tp * inv_rt0, A.bin, gam);
+          const float rt = rt0 + Tp;
+          const float wc = c_wf[N][c];
+          const float ax = wj * wc * sx, ay = wi * wc * sy, az = wi * wj * sz;
+          fx[h][0] = U * ax;
+          fx[h][1] = (U * u + pp) * ax;
+          fx[h][2] = V * u * ax;
+          fx[h][3] = W * u * ax;
+          fx[h][4] = rt * u * ax;
+          fy[h][0] = V * ay;
+          fy[h][1] = U * vv * ay;
+          fy[h][2] = (V * vv + pp) * ay;
+          fy[h][3] = W * vv * ay;
+          fy[h][4] = rt * vv * ay;
+          const float fzv[kFields] = {W * az, U * w * az, V * w * az, (W * w + pp) * az, rt * w * az};
+#pragma unroll
+          for (int f = 0; f < kFields; ++f) {
+            const float2 fm = make_float2(fzv[f], fzv[f]);
+#pragma unroll
+            for (int pp2 = 0; pp2 < CP; ++pp2) {
+              const float d0 = c_Dwf[N][(2 * pp2) * n1 + c];
+              const float d1 = (2 * pp2 + 1 < n1) ? c_Dwf[N][(2 * pp2 + 1) * n1 + c] : 0.f;
+              r[f][pp2] = __ffma2_rn(make_float2(d0, d1), fm, r[f][pp2]);
+            }
+          }
+          const float wJ = wi * wj * wc * J;
+          float* rr = reinterpret_cast<float*>(&r[0][0]);
+          rr[(1 * CP * 2) + c] += wJ * (fc * V);
+          rr[(2 * CP * 2) + c] += wJ * (-fc * U);
+          rr[(3 * CP * 2) + c] += wJ * (-rp * g);
+        }
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) {
+          *reinterpret_cast<float2*>(myX + f * FS + 2 * p) = make_float2(fx[0][f], fx[1][f]);
+          *reinterpret_cast<float2*>(myY + f * FS + 2 * p) = make_float2(fy[0][f], fy[1][f]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int f = 0; f < kFields; ++f)
+#pragma unroll
+        for (int p = 0; p < CP; ++p) {
+          *reinterpret_cast<float2*>(myX + f * FS + 2 * p) = make_float2(0.f, 0.f);
+          *reinterpret_cast<float2*>(myY + f * FS + 2 * p) = make_float2(0.f, 0.f);
+        }
+    }
+    __syncthreads();
+    const float* rowX = sX + kk * SK + j * n1 * CW;
+    const float* rowY = sY + kk * SK + i * n1 * CW;
+#pragma unroll
+    for (int f = 0; f < kFields; ++f)
+#pragma unroll
+      for (int m = 0; m < n1; ++m) {
+        const float2 dx = make_float2(Dwi[m], Dwi[m]);
+        const float2 dy = make_float2(Dwj[m], Dwj[m]);
+#pragma unroll
+        for (int p = 0; p < CP; ++p) {
+          const float2 vx = *reinterpret_cast<const float2*>(rowX + f * FS + m * CW + 2 * p);
+          const float2 vy = *reinterpret_cast<const float2*>(rowY + f * FS + m * CW + 2 * p);
+          r[f][p] = __ffma2_rn(dx, vx, r[f][p]);
+          r[f][p] = __ffma2_rn(dy, vy, r[f][p]);
+        }
+      }
+    float* rr = reinterpret_cast<float*>(&r[0][0]);
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) sT[(f * KL + kk) * Nq + ab] = rr[f * CP * 2 + N];
+    if (kk == 0 && ch > 0) {
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) rr[f * CP * 2] += sP[f * Nq + ab];
+    }
+    __syncthreads();
+    if (kk > 0) {
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) rr[f * CP * 2] += sT[(f * KL + kk - 1) * Nq + ab];
+    }
+    if (kk == KL - 1) {
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) sP[f * Nq + ab] = rr[f * CP * 2 + N];
+    }
+    if (act) {
+      float* dst = rc + ((long long)((long long)col * Nq + ab) * kFields) * A.NZr + kz0;
+      const bool top = (k == A.nz - 1);
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) {
+        float* df = dst + (long long)f * A.NZr;
+        if (N == 4) {
+          *reinterpret_cast<float4*>(df) = make_float4(rr[f * CP * 2 + 0], rr[f * CP * 2 + 1],
+                                                       rr[f * CP * 2 + 2], rr[f * CP * 2 + 3]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < N; ++c) df[c] = rr[f * CP * 2 + c];
+        }
+        if (top) df[N] = rr[f * CP * 2 + N];
+      }
+    }
+    __syncthreads();
+    buf ^= 1;
+    col = ncol;
+    ch = nch;
+  }
+}
+
+template <int N, int KL, int MB>
+static int launch_pipe(const VolArgs& A, cudaStream_t st) {
+  constexpr int n1 = N + 1, Nq = n1 * n1;
+  const size_t sm = sizeof(float) * (2 * kFields * KL * pencil_sk(N) + kFields * KL * Nq + kFields * Nq +
+                                     pipe_stage_floats<N, KL>());
+  static bool attr = false;
+  static int nsm = 0;
+  if (!attr) {
+    SEM_CUDA_TRY(cudaFuncSetAttribute(volume_pencil_pipe<N, KL, MB>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    attr = true;
+  }
+  const int grid = std::min(A.Ncol, nsm * MB);
+  ProfScope ps("volume_mixed", st);
+  volume_pencil_pipe<N, KL, MB><<<grid, KL * Nq, sm, st>>>(A);
+  return SEM_OK;
+}
+
 template <int N, int KL>
 static size_t pencil_smem() {
-  constexpr int n1 = N + 1, Nq = n1 * n1, CW = 2 * ((n1 + 1) / 2);
-  return sizeof(float) * (2 * kFields * KL * Nq * CW + kFields * KL * Nq + kFields * Nq);
+  constexpr int n1 = N + 1, Nq = n1 * n1;
+  return sizeof(float) * (2 * kFields * KL * pencil_sk(N) + kFields * KL * Nq + kFields * Nq);
 }
 
 template <int N, int KL, int MB>
@@ -685,13 +958,16 @@ static int launch_pencil(const VolArgs& A, cudaStream_t st) {
 struct PencilVariant {
   int N, KL, MB;
   int (*launch)(const VolArgs&, cudaStream_t);
+  int persistent;   // 1: pipelined persistent kernel (volume_pencil_pipe)
 };
 static const PencilVariant kPencil[] = {
     {2, 8, 4, launch_pencil<2, 8, 4>},   {2, 16, 2, launch_pencil<2, 16, 2>},
     {3, 8, 3, launch_pencil<3, 8, 3>},   {3, 16, 2, launch_pencil<3, 16, 2>},
     {4, 4, 8, launch_pencil<4, 4, 8>},   {4, 8, 2, launch_pencil<4, 8, 2>},
     {4, 8, 4, launch_pencil<4, 8, 4>},   {4, 16, 1, launch_pencil<4, 16, 1>},
-    {4, 16, 2, launch_pencil<4, 16, 2>}, {5, 8, 1, launch_pencil<5, 8, 1>},
+    {4, 16, 2, launch_pencil<4, 16, 2>}, {4, 8, 2, launch_pipe<4, 8, 2>, 1},
+    {4, 16, 1, launch_pipe<4, 16, 1>, 1}, {4, 4, 4, launch_pipe<4, 4, 4>, 1},
+    {5, 8, 1, launch_pencil<5, 8, 1>},
     {5, 8, 2, launch_pencil<5, 8, 2>},   {6, 4, 2, launch_pencil<6, 4, 2>},
     {6, 8, 1, launch_pencil<6, 8, 1>},
 };
@@ -701,7 +977,7 @@ constexpr int kNumPencil = sizeof(kPencil) / sizeof(kPencil[0]);
 static int pencil_default(int N, int nz) {
   int best = -1;
   for (int v = 0; v < kNumPencil; ++v) {
-    if (kPencil[v].N != N) continue;
+    if (kPencil[v].N != N || kPencil[v].persistent) continue;
     if (best < 0) { best = v; continue; }
     const PencilVariant& a = kPencil[v];
     const PencilVariant& b = kPencil[best];
@@ -745,6 +1021,14 @@ static VolArgs make_vol_args(Mesh& m, const sem_params& p, const void* q, bool m
   A.gf = (float)A.g;
   A.ff = (float)A.f;
   A.gammaf = (float)A.gamma;
+  {
+    double cb = 1.0;
+    for (int k = 1; k <= 7; ++k) {
+      cb *= (A.gamma - (k - 1)) / k;
+      A.bin[k - 1] = (float)cb;
+    }
+    A.bin[7] = 0.f;
+  }
   for (int l = 0; l < kLev; ++l) {
     const double hx = m.hx(l), hy = m.hy(l), hz = m.hz();
     const double g[8] = {hx, hy, hz, hx * hy * hz * 0.125, hy * hz * 0.25, hx * hz * 0.25,
@@ -757,12 +1041,12 @@ static VolArgs make_vol_args(Mesh& m, const sem_params& p, const void* q, bool m
   return A;
 }
 
-static int grid_cap(long long work) {
+static int grid_cap(long long work, int per_sm = 8) {
   int dev = 0, nsm = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   long long blocks = (work + 255) / 256;
-  long long cap = (long long)nsm * 8;
+  long long cap = (long long)nsm * per_sm;
   return (int)(blocks < cap ? (blocks > 0 ? blocks : 1) : cap);
 }
 
@@ -864,7 +1148,7 @@ int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float
     B.NZr = m.NZr();
     B.status = D.status;
     ProfScope ps("dss_inc_mixed", st);
-    const int blocks = grid_cap(m.NG);
+    const int blocks = grid_cap(m.NG, 64);
     if (stage == 0) dss_inc<0><<<blocks, 256, 0, st>>>(B);
     else if (stage == 1) dss_inc<1><<<blocks, 256, 0, st>>>(B);
     else dss_inc<2><<<blocks, 256, 0, st>>>(B);
@@ -904,6 +1188,7 @@ int autotune_pencil(Mesh& m, const sem_params& p, const float* q32, int reps, se
     const int k = out->n_variants++;
     out->layers_per_cta[k] = kPencil[v].KL;
     out->min_ctas_per_sm[k] = kPencil[v].MB;
+    out->persistent[k] = kPencil[v].persistent;
     out->ms[k] = ms;
     if (best < 0 || ms < best_ms) {
       best = v;

@@ -71,7 +71,8 @@ class ProfileOut(C.Structure):
 
 class TuneOut(C.Structure):
     _fields_ = [("n_variants", C.c_int), ("chosen", C.c_int), ("layers_per_cta", C.c_int * 16),
-                ("min_ctas_per_sm", C.c_int * 16), ("ms", C.c_double * 16)]
+                ("min_ctas_per_sm", C.c_int * 16), ("persistent", C.c_int * 16),
+                ("ms", C.c_double * 16)]
 
 
 class DiagOut(C.Structure):
@@ -382,7 +383,8 @@ def sem_autotune(mesh, params, q32, reps=5, stream=None):
     out = TuneOut()
     _check(LIB.sem_autotune(mesh.h, C.byref(params), _ptr(q32), int(reps), C.byref(out),
                             _stream(stream)))
-    rows = [(out.layers_per_cta[k], out.min_ctas_per_sm[k], out.ms[k]) for k in range(out.n_variants)]
+    rows = [(out.layers_per_cta[k], out.min_ctas_per_sm[k], out.ms[k], out.persistent[k])
+            for k in range(out.n_variants)]
     return rows, out.chosen
 
 

@@ -389,3 +389,22 @@ def test_batched_steps_equal_single_mesh_steps(sem, use_graph):
         assert d <= 1e-13 * scale, (k, d)
         assert torch.equal(a32[k], b32[k]) or (a32[k] - b32[k]).abs().max().item() <= 1e-6
     assert sem.sem_batch_status(batch) == 0
+
+
+def test_mixed_pressure_both_branches(sem):
+    """The mixed form evaluates (1 + x)^gamma - 1, x = (rho theta)'/(rho theta)0,
+    by its binomial series for |x| <= 1/8 and by expm1/log1p beyond: a state
+    with |x| up to about 0.3 exercises both against the oracle."""
+    m, o, X, perm = make_pair(sem, **MESHES["uniform-6x6x4-N4"])
+    q_o = random_state(o.XG, o.Lz, 13)
+    rng = np.random.default_rng(0)
+    ref = refstate.reference_state(o.XG[:, 2], PRM)
+    q_o[4] = ref["rhotheta0"] * rng.uniform(-0.3, 0.3, size=o.NG)
+    q_o[3, o.z_bottom | o.z_top] = 0.0
+    T_o = orhs.rhs(o, q_o, PRM, "C")
+    p = sem.sem_params_default(precision=sem.SEM_PREC_MIXED)
+    q = dev(q_o[:, perm])
+    out = torch.empty_like(q)
+    sem.sem_rhs(m, p, q, out)
+    err = group_rel_l2(host(out), T_o[:, perm])
+    assert np.all(err <= 1e-4), err
