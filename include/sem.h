@@ -321,6 +321,20 @@ typedef struct {
 int sem_autotune(sem_mesh* m, const sem_params* p, const float* q32_dev, int reps,
                  sem_tune_out* out_host, cudaStream_t stream);
 
+/* Checkpoint / resume.  sem_checkpoint_write copies the float64 state to the
+ * host (synchronises the stream) and writes the mesh description, its leaf
+ * columns, the state, `time` and `step`, and a checksum, through a temporary
+ * file renamed into place.  sem_checkpoint_read_mesh rebuilds the mesh (host
+ * only; same leaves, hence the same node numbering) and returns time and step;
+ * sem_checkpoint_read_state copies the state into q_dev ([5][NG]) after
+ * checking that the file was written for that mesh.  A missing, truncated or
+ * corrupted file gives SEM_ERR_IO before any device work. */
+int sem_checkpoint_write(sem_mesh* m, const double* q_dev, double time, long long step,
+                         const char* path, cudaStream_t stream);
+int sem_checkpoint_read_mesh(const char* path, sem_mesh** mesh_out, double* time_out,
+                             long long* step_out);
+int sem_checkpoint_read_state(const char* path, sem_mesh* m, double* q_dev, cudaStream_t stream);
+
 /* Kernel timing.  Between sem_profile_begin and sem_profile_end every kernel
  * the library launches is bracketed by CUDA events recorded on the stream it
  * is launched on.  sem_profile_end synchronises those streams and returns, per

@@ -1,6 +1,7 @@
 // C ABI entry points (include/sem.h), device tables and the reference state.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
@@ -464,6 +465,130 @@ int sem_mlp_backward(sem_mlp* m, const float* feats, const int8_t* labels, const
 int sem_mlp_adam(sem_mlp* m, float lr, cudaStream_t st) {
   if (!m || !(lr > 0)) return fail(SEM_ERR_ARG, "bad argument");
   return mlp_adam_api(m->impl, lr, st);
+}
+
+// ---------------------------------------------------------------------------
+// checkpoints: header, leaves, float64 state, FNV-1a checksum of everything
+namespace {
+const char kMagic[8] = {'S', 'E', 'M', 'C', 'K', 'P', 'T', '1'};
+struct CkptHead {
+  char magic[8];
+  double Lx, Ly, Lz, time;
+  int nx, ny, nz, N, px, py, lvl_max, pad;
+  long long ncol, NG, step;
+};
+uint64_t fnv1a(const void* p, size_t n, uint64_t h = 1469598103934665603ull) {
+  const unsigned char* c = (const unsigned char*)p;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= c[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+int read_ckpt(const char* path, CkptHead& H, std::vector<int>& leaves, std::vector<double>* state) {
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(SEM_ERR_IO, std::string("cannot open ") + path);
+  auto bad = [&](const char* why) {
+    std::fclose(f);
+    return fail(SEM_ERR_IO, std::string("checkpoint ") + path + ": " + why);
+  };
+  if (std::fread(&H, sizeof(H), 1, f) != 1) return bad("truncated header");
+  if (std::memcmp(H.magic, kMagic, 8) != 0) return bad("not a checkpoint");
+  if (H.ncol <= 0 || H.ncol > (1ll << 30) || H.NG <= 0 || H.NG > (1ll << 36)) return bad("bad sizes");
+  leaves.resize((size_t)H.ncol * 3);
+  if (std::fread(leaves.data(), sizeof(int), leaves.size(), f) != leaves.size()) return bad("truncated leaves");
+  uint64_t h = fnv1a(&H, sizeof(H));
+  h = fnv1a(leaves.data(), leaves.size() * sizeof(int), h);
+  std::vector<double> tmp;
+  std::vector<double>& q = state ? *state : tmp;
+  q.resize((size_t)H.NG * kFields);
+  if (std::fread(q.data(), sizeof(double), q.size(), f) != q.size()) return bad("truncated state");
+  h = fnv1a(q.data(), q.size() * sizeof(double), h);
+  uint64_t stored = 0;
+  if (std::fread(&stored, sizeof(stored), 1, f) != 1) return bad("missing checksum");
+  std::fclose(f);
+  if (stored != h) return fail(SEM_ERR_IO, std::string("checkpoint ") + path + ": checksum mismatch");
+  return SEM_OK;
+}
+}  // namespace
+
+int sem_checkpoint_write(sem_mesh* mh, const double* q, double time, long long step, const char* path,
+                         cudaStream_t st) {
+  if (!mh || !q || !path) return fail(SEM_ERR_ARG, "NULL argument");
+  const Mesh& m = mh->m;
+  CkptHead H;
+  std::memset(&H, 0, sizeof(H));
+  std::memcpy(H.magic, kMagic, 8);
+  H.Lx = m.Lx; H.Ly = m.Ly; H.Lz = m.Lz; H.time = time;
+  H.nx = m.nx; H.ny = m.ny; H.nz = m.nz; H.N = m.N; H.px = m.px; H.py = m.py; H.lvl_max = m.lvl_max;
+  H.ncol = m.Ncol(); H.NG = m.NG; H.step = step;
+  std::vector<int> leaves((size_t)m.Ncol() * 3);
+  for (long long c = 0; c < m.Ncol(); ++c) {
+    leaves[3 * c] = m.leaves[c].l;
+    leaves[3 * c + 1] = m.leaves[c].i;
+    leaves[3 * c + 2] = m.leaves[c].j;
+  }
+  std::vector<double> host((size_t)m.NG * kFields);
+  SEM_CUDA_TRY(cudaMemcpyAsync(host.data(), q, host.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SEM_CUDA_TRY(cudaStreamSynchronize(st));
+  uint64_t h = fnv1a(&H, sizeof(H));
+  h = fnv1a(leaves.data(), leaves.size() * sizeof(int), h);
+  h = fnv1a(host.data(), host.size() * sizeof(double), h);
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "wb");
+  if (!f) return fail(SEM_ERR_IO, "cannot create " + tmp);
+  bool ok = std::fwrite(&H, sizeof(H), 1, f) == 1 &&
+            std::fwrite(leaves.data(), sizeof(int), leaves.size(), f) == leaves.size() &&
+            std::fwrite(host.data(), sizeof(double), host.size(), f) == host.size() &&
+            std::fwrite(&h, sizeof(h), 1, f) == 1;
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok || std::rename(tmp.c_str(), path) != 0) {
+    std::remove(tmp.c_str());
+    return fail(SEM_ERR_IO, std::string("cannot write ") + path);
+  }
+  return SEM_OK;
+}
+
+int sem_checkpoint_read_mesh(const char* path, sem_mesh** out, double* time, long long* step) {
+  if (!path || !out) return fail(SEM_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  CkptHead H;
+  std::vector<int> leaves;
+  int rc = read_ckpt(path, H, leaves, nullptr);
+  if (rc) return rc;
+  sem_mesh_desc d;
+  std::memset(&d, 0, sizeof(d));
+  d.Lx = H.Lx; d.Ly = H.Ly; d.Lz = H.Lz; d.nx = H.nx; d.ny = H.ny; d.nz = H.nz; d.N = H.N;
+  d.periodic_x = H.px; d.periodic_y = H.py; d.lvl_max = H.lvl_max;
+  d.n_leaves = (int)H.ncol;
+  d.leaves = leaves.data();
+  if ((rc = sem_mesh_create(&d, out))) return rc;
+  if ((*out)->m.NG != H.NG) {
+    sem_mesh_destroy(*out);
+    *out = nullptr;
+    return fail(SEM_ERR_IO, "checkpoint node count does not match its mesh");
+  }
+  if (time) *time = H.time;
+  if (step) *step = H.step;
+  return SEM_OK;
+}
+
+int sem_checkpoint_read_state(const char* path, sem_mesh* mh, double* q, cudaStream_t st) {
+  if (!path || !mh || !q) return fail(SEM_ERR_ARG, "NULL argument");
+  CkptHead H;
+  std::vector<int> leaves;
+  std::vector<double> host;
+  int rc = read_ckpt(path, H, leaves, &host);
+  if (rc) return rc;
+  const Mesh& m = mh->m;
+  bool same = H.NG == m.NG && H.ncol == m.Ncol();
+  for (long long c = 0; same && c < m.Ncol(); ++c)
+    same = leaves[3 * c] == m.leaves[c].l && leaves[3 * c + 1] == m.leaves[c].i &&
+           leaves[3 * c + 2] == m.leaves[c].j;
+  if (!same) return fail(SEM_ERR_ARG, "checkpoint was written for another mesh");
+  SEM_CUDA_TRY(cudaMemcpyAsync(q, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  SEM_CUDA_TRY(cudaStreamSynchronize(st));
+  return SEM_OK;
 }
 
 int sem_mirror(sem_mesh* mh, const double* q, float* q32, cudaStream_t st) {

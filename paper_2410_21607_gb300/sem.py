@@ -33,6 +33,7 @@ EXPORTS = (
     "sem_mlp_create", "sem_mlp_destroy", "sem_mlp_param_count", "sem_mlp_get_params",
     "sem_mlp_set_params", "sem_mlp_get_grads", "sem_mlp_features", "sem_mlp_forward",
     "sem_mlp_predict_flags", "sem_mlp_backward", "sem_mlp_adam",
+    "sem_checkpoint_write", "sem_checkpoint_read_mesh", "sem_checkpoint_read_state",
 )
 
 
@@ -125,6 +126,9 @@ def _load():
         "sem_mlp_predict_flags": (i, [vp, vp, i, vp, vp]),
         "sem_mlp_backward": (i, [vp, vp, vp, vp, i, C.POINTER(d), vp]),
         "sem_mlp_adam": (i, [vp, C.c_float, vp]),
+        "sem_checkpoint_write": (i, [vp, vp, d, C.c_longlong, C.c_char_p, vp]),
+        "sem_checkpoint_read_mesh": (i, [C.c_char_p, C.POINTER(vp), C.POINTER(d), C.POINTER(C.c_longlong)]),
+        "sem_checkpoint_read_state": (i, [C.c_char_p, vp, vp, vp]),
         "sem_autotune": (i, [vp, C.POINTER(Params), vp, i, C.POINTER(TuneOut), vp]),
         "sem_profile_end": (i, [C.POINTER(ProfileOut)]),
     }
@@ -506,3 +510,24 @@ def sem_mlp_backward(mlp, feats, labels, class_w, want_loss=True, stream=None):
 
 def sem_mlp_adam(mlp, lr, stream=None):
     _check(LIB.sem_mlp_adam(mlp.h, float(lr), _stream(stream)))
+
+
+def sem_checkpoint_write(mesh, q, path, time=0.0, step=0, stream=None):
+    _f64(q, mesh.field_shape)
+    _check(LIB.sem_checkpoint_write(mesh.h, _ptr(q), float(time), int(step), str(path).encode(),
+                                    _stream(stream)))
+
+
+def sem_checkpoint_read_mesh(path):
+    """(mesh, time, step) from a checkpoint file (host only)."""
+    h = C.c_void_p()
+    t = C.c_double(0.0)
+    s = C.c_longlong(0)
+    _check(LIB.sem_checkpoint_read_mesh(str(path).encode(), C.byref(h), C.byref(t), C.byref(s)))
+    return Mesh(h.value), t.value, s.value
+
+
+def sem_checkpoint_read_state(path, mesh, q, stream=None):
+    _f64(q, mesh.field_shape)
+    _check(LIB.sem_checkpoint_read_state(str(path).encode(), mesh.h, _ptr(q), _stream(stream)))
+    return q

@@ -132,3 +132,46 @@ def test_uniform_counts_and_info(sem):
     assert (m.Ne, m.NG, m.NH, m.NZ) == (65536, 4259840, 65536, 65)
     assert m.info.NL == 8192000
     assert m.info.n_hanging_h == 0
+
+
+def _fake_checkpoint(path, ncol_leaves, NG, corrupt=None):
+    """A checkpoint file in the library's layout (header, leaves, state, FNV-1a)."""
+    import struct
+    head = struct.pack("<8s4d8i3q", b"SEMCKPT1", 80e3, 80e3, 10e3, 1.5, 2, 2, 1, 4, 1, 1, 0, 0,
+                       len(ncol_leaves), NG, 7)
+    leaves = np.asarray(ncol_leaves, dtype=np.int32).tobytes()
+    state = np.arange(5 * NG, dtype=np.float64).tobytes()
+    h = 1469598103934665603
+    for b in head + leaves + state:
+        h ^= b
+        h = (h * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    data = head + leaves + state + struct.pack("<Q", h)
+    if corrupt == "truncate":
+        data = data[:-100]
+    elif corrupt == "flip":
+        data = data[:200] + bytes([data[200] ^ 1]) + data[201:]
+    with open(path, "wb") as f:
+        f.write(data)
+
+
+def test_checkpoint_reading_rejects_bad_files(sem, tmp_path):
+    leaves = [(0, i, j) for j in range(2) for i in range(2)]
+    m = sem.sem_mesh_create(80e3, 80e3, 10e3, 2, 2, 1, 4)
+    good = tmp_path / "good.ckpt"
+    _fake_checkpoint(good, leaves, m.NG)
+    m2, t, s = sem.sem_checkpoint_read_mesh(good)
+    assert (m2.NG, t, s) == (m.NG, 1.5, 7)
+    for mode in ("truncate", "flip"):
+        bad = tmp_path / f"{mode}.ckpt"
+        _fake_checkpoint(bad, leaves, m.NG, corrupt=mode)
+        with pytest.raises(sem.SemError) as e:
+            sem.sem_checkpoint_read_mesh(bad)
+        assert e.value.code == sem.SEM_ERR_IO
+    with pytest.raises(sem.SemError) as e:
+        sem.sem_checkpoint_read_mesh(tmp_path / "missing.ckpt")
+    assert e.value.code == sem.SEM_ERR_IO
+    garbage = tmp_path / "garbage.ckpt"
+    garbage.write_bytes(b"\x00" * 300)
+    with pytest.raises(sem.SemError) as e:
+        sem.sem_checkpoint_read_mesh(garbage)
+    assert e.value.code == sem.SEM_ERR_IO

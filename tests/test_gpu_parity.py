@@ -408,3 +408,37 @@ def test_mixed_pressure_both_branches(sem):
     sem.sem_rhs(m, p, q, out)
     err = group_rel_l2(host(out), T_o[:, perm])
     assert np.all(err <= 1e-4), err
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_checkpoint_resume_is_bitwise(sem, prec, tmp_path):
+    """Six steps straight through equal three steps, checkpoint, a fresh mesh
+    and state read back from the file, and three more steps, bit for bit."""
+    m, o, X, perm = make_pair(sem, **MESHES["twolevel-N4"])
+    q0 = dev(vortex_state(o.XG, o.Lz)[:, perm])
+    p = sem.sem_params_default(precision=prec)
+
+    def steps(mesh, q, n):
+        if prec == 0:
+            w1, w2 = torch.empty_like(q), torch.empty_like(q)
+            for _ in range(n):
+                sem.sem_step(mesh, p, q, w1, w2, 1.0)
+        else:
+            q32 = torch.empty(q.shape, dtype=torch.float32, device="cuda")
+            work = torch.empty((10, mesh.NG), dtype=torch.float32, device="cuda")
+            sem.sem_mirror(mesh, q, q32)
+            for _ in range(n):
+                sem.sem_step_mixed(mesh, p, q, q32, work, 1.0)
+        return q
+
+    a = steps(m, q0.clone(), 6)
+    b = steps(m, q0.clone(), 3)
+    path = tmp_path / "state.ckpt"
+    sem.sem_checkpoint_write(m, b, path, time=3.0, step=3)
+    m2, t, s = sem.sem_checkpoint_read_mesh(path)
+    assert (t, s) == (3.0, 3)
+    c = torch.empty((5, m2.NG), dtype=torch.float64, device="cuda")
+    sem.sem_checkpoint_read_state(path, m2, c)
+    c = steps(m2, c, 3)
+    torch.cuda.synchronize()
+    assert torch.equal(a, c)
