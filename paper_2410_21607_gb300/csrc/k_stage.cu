@@ -586,15 +586,14 @@ __device__ __forceinline__ void pencil_body(const VolArgs& A, const int col, flo
         // z contraction on registers as a rank-1 update per node:
         // r[c'] += Dw[c'][c] Fz[c] for every node c' of the z-line
         const float fzv[kFields] = {W * az, U * w * az, V * w * az, (W * w + pp) * az, rt * w * az};
+        {
+          // scalar FMAs: the coefficients are compile-time constant-bank operands
+          float* rz = reinterpret_cast<float*>(&r[0][0]);
 #pragma unroll
-        for (int f = 0; f < kFields; ++f) {
-          const float2 fm = make_float2(fzv[f], fzv[f]);
+          for (int f = 0; f < kFields; ++f)
 #pragma unroll
-          for (int p = 0; p < CP; ++p) {
-            const float d0 = c_Dwf[N][(2 * p) * n1 + c];
-            const float d1 = (2 * p + 1 < n1) ? c_Dwf[N][(2 * p + 1) * n1 + c] : 0.f;
-            r[f][p] = __ffma2_rn(make_float2(d0, d1), fm, r[f][p]);
-          }
+            for (int c2 = 0; c2 < n1; ++c2)
+              rz[f * CP * 2 + c2] = fmaf(c_Dwf[N][c2 * n1 + c], fzv[f], rz[f * CP * 2 + c2]);
         }
         // sources: Coriolis on rho u, rho v; buoyancy on rho w
         const float wJ = wi * wj * wc * J;
@@ -824,15 +823,13 @@ volume_pencil_pipe(const VolArgs A) {
           fy[h][3] = W * vv * ay;
           fy[h][4] = rt * vv * ay;
           const float fzv[kFields] = {W * az, U * w * az, V * w * az, (W * w + pp) * az, rt * w * az};
+          {
+            float* rz = reinterpret_cast<float*>(&r[0][0]);
 #pragma unroll
-          for (int f = 0; f < kFields; ++f) {
-            const float2 fm = make_float2(fzv[f], fzv[f]);
+            for (int f = 0; f < kFields; ++f)
 #pragma unroll
-            for (int pp2 = 0; pp2 < CP; ++pp2) {
-              const float d0 = c_Dwf[N][(2 * pp2) * n1 + c];
-              const float d1 = (2 * pp2 + 1 < n1) ? c_Dwf[N][(2 * pp2 + 1) * n1 + c] : 0.f;
-              r[f][pp2] = __ffma2_rn(make_float2(d0, d1), fm, r[f][pp2]);
-            }
+              for (int c2 = 0; c2 < n1; ++c2)
+                rz[f * CP * 2 + c2] = fmaf(c_Dwf[N][c2 * n1 + c], fzv[f], rz[f * CP * 2 + c2]);
           }
           const float wJ = wi * wj * wc * J;
           float* rr = reinterpret_cast<float*>(&r[0][0]);
