@@ -353,7 +353,7 @@ def main():
     if a.form == "mixed":
         rows, chosen = sem.sem_autotune(m, p, bufs[3], 5, stream)
         tune = {"variants": [{"layers_per_cta": r[0], "min_ctas_per_sm": r[1], "ms": r[2],
-                              "persistent": r[3]} for r in rows], "chosen": chosen}
+                              "kind": r[3], "approx_rcp": r[4]} for r in rows], "chosen": chosen}
     dof_stage = 5 * m.Ne * (N + 1) ** 3
     for _ in range(max(a.warmup, 3)):
         bufs = step(bufs, p)

@@ -315,11 +315,21 @@ typedef struct {
   int chosen;                          /* index into the arrays below */
   int layers_per_cta[SEM_TUNE_MAX];
   int min_ctas_per_sm[SEM_TUNE_MAX];
-  int persistent[SEM_TUNE_MAX];        /* 1: persistent CTAs prefetching the next column */
+  int kind[SEM_TUNE_MAX];              /* 0: z-pencil kernel, one CTA per column;
+                                          1: persistent z-pencil CTAs prefetching the next column;
+                                          2: line-exchange kernel, one CTA per column */
+  int approx_rcp[SEM_TUNE_MAX];        /* 1: 1/rho from the hardware reciprocal approximation */
   double ms[SEM_TUNE_MAX];             /* mean event time per launch */
 } sem_tune_out;
 int sem_autotune(sem_mesh* m, const sem_params* p, const float* q32_dev, int reps,
                  sem_tune_out* out_host, cudaStream_t stream);
+/* Selects row `row` of the table sem_autotune reports for this mesh's order
+ * (same order, 0 <= row < n_variants) as the mesh's element-kernel variant,
+ * or the untuned default for row = -1; no timing and no device work.  For
+ * tests that run every variant, and for callers that cache a tuning result.
+ * The paper has no counterpart (launch configuration only).  SEM_ERR_ARG for
+ * a row outside the table. */
+int sem_autotune_select(sem_mesh* m, int row);
 
 /* Checkpoint / resume.  sem_checkpoint_write copies the float64 state to the
  * host (synchronises the stream) and writes the mesh description, its leaf

@@ -84,7 +84,7 @@ int ensure_device(Mesh& m) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&D.status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(D.status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void**)&D.ref, (size_t)m.NZ * kRef * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&D.ref32, (size_t)m.NZ * kRef * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&D.ref32, (size_t)m.NZ * (kRef + 4) * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc((void**)&D.elem_cmax, (size_t)m.Ne() * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void**)&D.elem_flags, (size_t)m.Ne());
   if (e == cudaSuccess) e = cudaMalloc((void**)&D.diag_buf, (size_t)m.NZ * 4 * sizeof(double));
@@ -123,7 +123,7 @@ int ensure_reference(Mesh& m, const sem_params& p) {
     return fail(SEM_ERR_ARG, "reference state needs g > 0, N_bv > 0, c_p > R_d > 0");
   const double c_v = p.c_p - p.R_d, N2 = p.N_bv * p.N_bv;
   std::vector<double> ref((size_t)m.NZ * kRef);
-  std::vector<float> ref32((size_t)m.NZ * kRef);
+  std::vector<float> ref32((size_t)m.NZ * (kRef + 4));
   for (int k = 0; k < m.NZ; ++k) {
     const double z = m.zk[k];
     const double th0 = p.theta_s * std::exp(N2 * z / p.g);
@@ -136,6 +136,12 @@ int ensure_reference(Mesh& m, const sem_params& p) {
       ref[(size_t)k * kRef + q] = r[q];
       ref32[(size_t)k * kRef + q] = (float)r[q];
     }
+    // packed rows after the table: p0, rho0, (rho theta)0, 1/(rho theta)0
+    float* r4 = ref32.data() + (size_t)m.NZ * kRef + (size_t)k * 4;
+    r4[0] = (float)p0;
+    r4[1] = (float)rho0;
+    r4[2] = (float)(rho0 * th0);
+    r4[3] = (float)(1.0 / (rho0 * th0));
   }
   SEM_CUDA_TRY(cudaMemcpy(D.ref, ref.data(), ref.size() * sizeof(double), cudaMemcpyHostToDevice));
   SEM_CUDA_TRY(cudaMemcpy(D.ref32, ref32.data(), ref32.size() * sizeof(float), cudaMemcpyHostToDevice));
@@ -352,6 +358,11 @@ int sem_autotune(sem_mesh* mh, const sem_params* p, const float* q32, int reps, 
   if (!q32 || !out || reps < 1) return fail(SEM_ERR_ARG, "bad argument");
   std::memset(out, 0, sizeof(*out));
   return autotune_pencil(mh->m, *p, q32, reps, out, st);
+}
+
+int sem_autotune_select(sem_mesh* mh, int row) {
+  if (!mh) return fail(SEM_ERR_ARG, "bad argument");
+  return select_pencil(mh->m, row);
 }
 
 int sem_batch_create(sem_mesh* const* meshes, int n, sem_batch** out) {

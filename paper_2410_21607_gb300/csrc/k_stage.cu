@@ -103,6 +103,7 @@ struct VolArgs {
   double geo[kLev][8];
   float geof[kLev][8];
   const float* ref32;
+  const float4* ref4;   // [NZ] packed p0, rho0, (rho theta)0, 1/(rho theta)0 (float32)
 };
 
 template <typename R> __device__ __forceinline__ const R* geo_of(const VolArgs& A, int l);
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(256) dss_stage_fp64(const DssArgs A) {
       const double w = __ldg(qtw + e);
       const double* p = rc + (long long)__ldg(A.qt_src + e) * kFields * A.NZr + kz;
 #pragma unroll
-      for (int fl = 0; fl < kFields; ++fl) acc[fl] = fma(w, p[(long long)fl * A.NZr], acc[fl]);
+      for (int fl = 0; fl < kFields; ++fl) acc[fl] = fma(w, __ldg(p + (long long)fl * A.NZr), acc[fl]);
     }
 #pragma unroll
     for (int fl = 0; fl < kFields; ++fl) {
@@ -420,7 +421,7 @@ __global__ void __launch_bounds__(256) dss_stage_mixed(const DssArgs A) {
       const float w = __ldg(qtw + e);
       const float* p = rc + (long long)__ldg(A.qt_src + e) * kFields * A.NZr + kz;
 #pragma unroll
-      for (int fl = 0; fl < kFields; ++fl) acc[fl] = fmaf(w, p[(long long)fl * A.NZr], acc[fl]);
+      for (int fl = 0; fl < kFields; ++fl) acc[fl] = fmaf(w, __ldg(p + (long long)fl * A.NZr), acc[fl]);
     }
 #pragma unroll
     for (int fl = 0; fl < kFields; ++fl) {
@@ -497,10 +498,86 @@ __device__ __forceinline__ float pow1p_m1(float x, const float* bin, float gam) 
   return expm1f(gam * log1pf(x));
 }
 
+// 1/x from the hardware reciprocal approximation (rcp.approx.ftz.f32, relative
+// error within 2^-22), in place of the correctly rounded reciprocal.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// State perturbation v = (rho', rho u, rho v, rho w, (rho theta)') of one node
+// of column line `hm` at level kz: a direct load, or for a hanging line the
+// interpolation from the coarse neighbour's lines (Sec. 3.1).
+template <int N>
+__device__ __forceinline__ void load_node(const VolArgs& A, const int hm, const int kz, float (&v)[kFields]) {
+  const float* q = (const float*)A.q;
+  if (hm >= 0) {
+    const float* pq = q + (long long)hm * A.NZ + kz;
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) v[f] = __ldg(pq + (long long)f * A.NG);
+  } else {
+    const int hk = -1 - hm;
+    const float* hw = (const float*)A.hang_w;
+#pragma unroll
+    for (int f = 0; f < kFields; ++f) v[f] = 0.f;
+#pragma unroll
+    for (int m = 0; m < N + 1; ++m) {
+      const float wm = __ldg(hw + hk * (N + 1) + m);
+      const float* pq = q + (long long)__ldg(A.hang_h + hk * (N + 1) + m) * A.NZ + kz;
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) v[f] = fmaf(wm, __ldg(pq + (long long)f * A.NG), v[f]);
+    }
+  }
+}
+
+// Pointwise part of the conservative set at one node (Sec. 2, eqs.
+// mass_split..ent_split, plus the f-plane Coriolis term): the weighted flux
+// components ax F^x, ay F^y, az F^z of the five equations and the weighted
+// momentum sources wJ S (Coriolis on rho u and rho v, buoyancy on rho w).
+// The reference state of the level is one packed 16-byte row.
+// RA selects the hardware reciprocal approximation for 1/rho instead of the
+// correctly rounded reciprocal (whose rarely taken slow path also limits how
+// far the compiler hoists the next nodes' loads, and so register pressure).
+struct NodeTerms {
+  float fx[kFields], fy[kFields], fz[kFields];
+  float su, sv, sw;
+};
+template <bool RA>
+__device__ __forceinline__ void node_terms(const VolArgs& A, const float (&v)[kFields], const int kz,
+                                           const float ax, const float ay, const float az, const float wJ,
+                                           NodeTerms& o) {
+  const float4 ra = __ldg(A.ref4 + kz);
+  const float p0 = ra.x, rho0 = ra.y, rt0 = ra.z, inv_rt0 = ra.w;
+  const float rp = v[0], U = v[1], V = v[2], W = v[3], Tp = v[4];
+  const float inv = RA ? rcp_approx(rho0 + rp) : __frcp_rn(rho0 + rp);
+  const float u = U * inv, vv = V * inv, w = W * inv;
+  const float pp = p0 * pow1p_m1(Tp * inv_rt0, A.bin, A.gammaf);
+  const float rt = rt0 + Tp;
+  o.fx[0] = U * ax;
+  o.fx[1] = (U * u + pp) * ax;
+  o.fx[2] = V * u * ax;
+  o.fx[3] = W * u * ax;
+  o.fx[4] = rt * u * ax;
+  o.fy[0] = V * ay;
+  o.fy[1] = U * vv * ay;
+  o.fy[2] = (V * vv + pp) * ay;
+  o.fy[3] = W * vv * ay;
+  o.fy[4] = rt * vv * ay;
+  o.fz[0] = W * az;
+  o.fz[1] = U * w * az;
+  o.fz[2] = V * w * az;
+  o.fz[3] = (W * w + pp) * az;
+  o.fz[4] = rt * w * az;
+  o.su = wJ * (A.ff * V);
+  o.sv = wJ * (-A.ff * U);
+  o.sw = wJ * (-rp * A.gf);
+}
+
 // Body shared by the single-mesh kernel (one CTA per column) and the batched
 // persistent kernel (CTAs pull columns of many meshes from a queue).  Threads
 // t >= KL (N+1)^2 of a larger CTA take part in the barriers only.
-template <int N, int KL>
+template <int N, int KL, bool RA = false>
 __device__ __forceinline__ void pencil_body(const VolArgs& A, const int col, float* smem, const int t) {
   constexpr int n1 = N + 1, Nq = n1 * n1, CP = (n1 + 1) / 2, CW = 2 * CP;
   // words per layer block, padded to 2 (mod 32) so that the 16 layers a
@@ -519,8 +596,6 @@ __device__ __forceinline__ void pencil_body(const VolArgs& A, const int col, flo
   const float* geo = A.geof[lev];
   const float sx = geo[4], sy = geo[5], sz = geo[6], J = geo[3];
   const int hm = part ? A.hmap[(long long)col * Nq + ab] : 0;
-  const float* q = (const float*)A.q;
-  const float* hw = (const float*)A.hang_w;
   float Dwi[n1], Dwj[n1];
 #pragma unroll
   for (int m = 0; m < n1; ++m) {
@@ -528,7 +603,6 @@ __device__ __forceinline__ void pencil_body(const VolArgs& A, const int col, flo
     Dwj[m] = c_Dwf[N][j * n1 + m];
   }
   const float wi = c_wf[N][i], wj = c_wf[N][j];
-  const float g = A.gf, fc = A.ff, gam = A.gammaf;
   float* rc = (float*)A.rc;
   const int nchunk = (A.nz + KL - 1) / KL;
   for (int ch = 0; ch < nchunk; ++ch) {
@@ -548,59 +622,27 @@ __device__ __forceinline__ void pencil_body(const VolArgs& A, const int col, flo
       for (int c = 0; c < n1; ++c) {
         float v[kFields];
         const int kz = kz0 + c;
-        if (hm >= 0) {
-          const float* pq = q + (long long)hm * A.NZ + kz;
-#pragma unroll
-          for (int f = 0; f < kFields; ++f) v[f] = __ldg(pq + (long long)f * A.NG);
-        } else {
-          const int hk = -1 - hm;
-#pragma unroll
-          for (int f = 0; f < kFields; ++f) v[f] = 0.f;
-#pragma unroll
-          for (int m = 0; m < n1; ++m) {
-            const float wm = __ldg(hw + hk * n1 + m);
-            const float* pq = q + (long long)__ldg(A.hang_h + hk * n1 + m) * A.NZ + kz;
-#pragma unroll
-            for (int f = 0; f < kFields; ++f) v[f] = fmaf(wm, __ldg(pq + (long long)f * A.NG), v[f]);
-          }
-        }
-        const float* rf = A.ref32 + (long long)kz * kRef;
-        const float p0 = __ldg(rf + 2), rho0 = __ldg(rf + 3), rt0 = __ldg(rf + 4), inv_rt0 = __ldg(rf + 6);
-        const float rp = v[0], U = v[1], V = v[2], W = v[3], Tp = v[4];
-        const float inv = __frcp_rn(rho0 + rp);
-        const float u = U * inv, vv = V * inv, w = W * inv;
-        const float pp = p0 * pow1p_m1(Tp * inv_rt0, A.bin, gam);
-        const float rt = rt0 + Tp;
+        load_node<N>(A, hm, kz, v);
         const float wc = c_wf[N][c];
-        const float ax = wj * wc * sx, ay = wi * wc * sy, az = wi * wj * sz;
-        myX[0 * FS + c] = U * ax;
-        myX[1 * FS + c] = (U * u + pp) * ax;
-        myX[2 * FS + c] = V * u * ax;
-        myX[3 * FS + c] = W * u * ax;
-        myX[4 * FS + c] = rt * u * ax;
-        myY[0 * FS + c] = V * ay;
-        myY[1 * FS + c] = U * vv * ay;
-        myY[2 * FS + c] = (V * vv + pp) * ay;
-        myY[3 * FS + c] = W * vv * ay;
-        myY[4 * FS + c] = rt * vv * ay;
-        // z contraction on registers as a rank-1 update per node:
-        // r[c'] += Dw[c'][c] Fz[c] for every node c' of the z-line
-        const float fzv[kFields] = {W * az, U * w * az, V * w * az, (W * w + pp) * az, rt * w * az};
-        {
-          // scalar FMAs: the coefficients are compile-time constant-bank operands
-          float* rz = reinterpret_cast<float*>(&r[0][0]);
+        NodeTerms T;
+        node_terms<RA>(A, v, kz, wj * wc * sx, wi * wc * sy, wi * wj * sz, wi * wj * wc * J, T);
 #pragma unroll
-          for (int f = 0; f < kFields; ++f)
-#pragma unroll
-            for (int c2 = 0; c2 < n1; ++c2)
-              rz[f * CP * 2 + c2] = fmaf(c_Dwf[N][c2 * n1 + c], fzv[f], rz[f * CP * 2 + c2]);
+        for (int f = 0; f < kFields; ++f) {
+          myX[f * FS + c] = T.fx[f];
+          myY[f * FS + c] = T.fy[f];
         }
-        // sources: Coriolis on rho u, rho v; buoyancy on rho w
-        const float wJ = wi * wj * wc * J;
-        float* rr = reinterpret_cast<float*>(&r[0][0]);
-        rr[(1 * CP * 2) + c] += wJ * (fc * V);
-        rr[(2 * CP * 2) + c] += wJ * (-fc * U);
-        rr[(3 * CP * 2) + c] += wJ * (-rp * g);
+        // z contraction on registers as a rank-1 update per node:
+        // r[c'] += Dw[c'][c] Fz[c] for every node c' of the z-line (scalar
+        // FMAs: the coefficients are compile-time constant-bank operands)
+        float* rz = reinterpret_cast<float*>(&r[0][0]);
+#pragma unroll
+        for (int f = 0; f < kFields; ++f)
+#pragma unroll
+          for (int c2 = 0; c2 < n1; ++c2)
+            rz[f * CP * 2 + c2] = fmaf(c_Dwf[N][c2 * n1 + c], T.fz[f], rz[f * CP * 2 + c2]);
+        rz[(1 * CP * 2) + c] += T.su;
+        rz[(2 * CP * 2) + c] += T.sv;
+        rz[(3 * CP * 2) + c] += T.sw;
       }
       if (n1 < CW) {
 #pragma unroll
@@ -675,11 +717,11 @@ __device__ __forceinline__ void pencil_body(const VolArgs& A, const int col, flo
   }
 }
 
-template <int N, int KL, int MB>
+template <int N, int KL, int MB, bool RA = false>
 __global__ void __launch_bounds__(KL * (N + 1) * (N + 1), MB)
 volume_pencil_mixed(const VolArgs A) {
   extern __shared__ __align__(16) float smem[];
-  pencil_body<N, KL>(A, blockIdx.x, smem, threadIdx.x);
+  pencil_body<N, KL, RA>(A, blockIdx.x, smem, threadIdx.x);
 }
 
 // Persistent, software-pipelined variant of the pencil kernel: each CTA walks
@@ -701,7 +743,7 @@ __host__ __device__ constexpr int pipe_stage_floats() {
   return 2 * kFields * (N + 1) * KL * (N + 1) * (N + 1);
 }
 
-template <int N, int KL, int MB>
+template <int N, int KL, int MB, bool RA = false>
 __global__ void __launch_bounds__(KL * (N + 1) * (N + 1), MB)
 volume_pencil_pipe(const VolArgs A) {
   constexpr int n1 = N + 1, Nq = n1 * n1, CP = (n1 + 1) / 2, CW = 2 * CP;
@@ -719,7 +761,6 @@ volume_pencil_pipe(const VolArgs A) {
   const int kk = t % KL, ab = t / KL;
   const int i = ab % n1, j = ab / n1;
   const float* q = (const float*)A.q;
-  const float* hw = (const float*)A.hang_w;
   float Dwi[n1], Dwj[n1];
 #pragma unroll
   for (int m = 0; m < n1; ++m) {
@@ -727,7 +768,6 @@ volume_pencil_pipe(const VolArgs A) {
     Dwj[m] = c_Dwf[N][j * n1 + m];
   }
   const float wi = c_wf[N][i], wj = c_wf[N][j];
-  const float g = A.gf, fc = A.ff, gam = A.gammaf;
   float* rc = (float*)A.rc;
   const int nchunk = (A.nz + KL - 1) / KL;
 
@@ -792,50 +832,25 @@ volume_pencil_pipe(const VolArgs A) {
 #pragma unroll
             for (int f = 0; f < kFields; ++f) v[f] = st[(f * n1 + c) * NT];
           } else {
-            const int hk = -1 - hm;
-#pragma unroll
-            for (int f = 0; f < kFields; ++f) v[f] = 0.f;
-#pragma unroll
-            for (int m = 0; m < n1; ++m) {
-              const float wm = __ldg(hw + hk * n1 + m);
-              const float* pq = q + (long long)__ldg(A.hang_h + hk * n1 + m) * A.NZ + kz;
-#pragma unroll
-              for (int f = 0; f < kFields; ++f) v[f] = fmaf(wm, __ldg(pq + (long long)f * A.NG), v[f]);
-            }
+            load_node<N>(A, hm, kz, v);
           }
-          const float* rf = A.ref32 + (long long)kz * kRef;
-          const float p0 = __ldg(rf + 2), rho0 = __ldg(rf + 3), rt0 = __ldg(rf + 4), inv_rt0 = __ldg(rf + 6);
-          const float rp = v[0], U = v[1], V = v[2], W = v[3], Tp = v[4];
-          const float inv = __frcp_rn(rho0 + rp);
-          const float u = U * inv, vv = V * inv, w = W * inv;
-          const float pp = p0 * pow1p_m1(Tp * inv_rt0, A.bin, gam);
-          const float rt = rt0 + Tp;
           const float wc = c_wf[N][c];
-          const float ax = wj * wc * sx, ay = wi * wc * sy, az = wi * wj * sz;
-          fx[h][0] = U * ax;
-          fx[h][1] = (U * u + pp) * ax;
-          fx[h][2] = V * u * ax;
-          fx[h][3] = W * u * ax;
-          fx[h][4] = rt * u * ax;
-          fy[h][0] = V * ay;
-          fy[h][1] = U * vv * ay;
-          fy[h][2] = (V * vv + pp) * ay;
-          fy[h][3] = W * vv * ay;
-          fy[h][4] = rt * vv * ay;
-          const float fzv[kFields] = {W * az, U * w * az, V * w * az, (W * w + pp) * az, rt * w * az};
-          {
-            float* rz = reinterpret_cast<float*>(&r[0][0]);
+          NodeTerms T;
+          node_terms<RA>(A, v, kz, wj * wc * sx, wi * wc * sy, wi * wj * sz, wi * wj * wc * J, T);
 #pragma unroll
-            for (int f = 0; f < kFields; ++f)
-#pragma unroll
-              for (int c2 = 0; c2 < n1; ++c2)
-                rz[f * CP * 2 + c2] = fmaf(c_Dwf[N][c2 * n1 + c], fzv[f], rz[f * CP * 2 + c2]);
+          for (int f = 0; f < kFields; ++f) {
+            fx[h][f] = T.fx[f];
+            fy[h][f] = T.fy[f];
           }
-          const float wJ = wi * wj * wc * J;
-          float* rr = reinterpret_cast<float*>(&r[0][0]);
-          rr[(1 * CP * 2) + c] += wJ * (fc * V);
-          rr[(2 * CP * 2) + c] += wJ * (-fc * U);
-          rr[(3 * CP * 2) + c] += wJ * (-rp * g);
+          float* rz = reinterpret_cast<float*>(&r[0][0]);
+#pragma unroll
+          for (int f = 0; f < kFields; ++f)
+#pragma unroll
+            for (int c2 = 0; c2 < n1; ++c2)
+              rz[f * CP * 2 + c2] = fmaf(c_Dwf[N][c2 * n1 + c], T.fz[f], rz[f * CP * 2 + c2]);
+          rz[(1 * CP * 2) + c] += T.su;
+          rz[(2 * CP * 2) + c] += T.sv;
+          rz[(3 * CP * 2) + c] += T.sw;
         }
 #pragma unroll
         for (int f = 0; f < kFields; ++f) {
@@ -935,17 +950,185 @@ static size_t pencil_smem() {
   return sizeof(float) * (2 * kFields * KL * pencil_sk(N) + kFields * KL * Nq + kFields * Nq);
 }
 
-template <int N, int KL, int MB>
+template <int N, int KL, int MB, bool RA = false>
 static int launch_pencil(const VolArgs& A, cudaStream_t st) {
   const size_t sm = pencil_smem<N, KL>();
   static bool attr = false;
   if (!attr) {
-    SEM_CUDA_TRY(cudaFuncSetAttribute(volume_pencil_mixed<N, KL, MB>,
+    SEM_CUDA_TRY(cudaFuncSetAttribute(volume_pencil_mixed<N, KL, MB, RA>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr = true;
   }
   ProfScope ps("volume_mixed", st);
-  volume_pencil_mixed<N, KL, MB><<<A.Ncol, KL * (N + 1) * (N + 1), sm, st>>>(A);
+  volume_pencil_mixed<N, KL, MB, RA><<<A.Ncol, KL * (N + 1) * (N + 1), sm, st>>>(A);
+  return SEM_OK;
+}
+
+// Line-exchange variant of the mixed-form element kernel (same thread
+// mapping, z-line ownership, z contraction and vertical DSS as pencil_body;
+// the same sums, added in another order).  The x and y contractions are done
+// by line owners: once the x and y flux components of every node of the chunk
+// are in shared memory, thread (kk, L) contracts the whole x-line (j, c) = L
+// and the whole y-line (i, c) = L of layer kk with the weak-derivative matrix
+// and writes the results back onto the nodes it read (no other thread touches
+// them in that phase); the z-line owner then adds both to its register-held z
+// contraction.  Node (i, j, c), field f of layer kk sits at
+// kk LS + (i + n1 j) LW + f n1 + c.  With LW odd and LS = 32 / KL (mod 32),
+// every access of the three phases is a 32-bit access free of bank conflicts
+// for N = 4 (consecutive threads: consecutive layers, then lines).
+template <int N>
+__host__ __device__ constexpr int lines_lw() { return (kFields * (N + 1)) | 1; }
+template <int N, int KL>
+__host__ __device__ constexpr int lines_ls() {
+  return (N + 1) * (N + 1) * lines_lw<N>() +
+         ((32 / KL - ((N + 1) * (N + 1) * lines_lw<N>()) % 32) % 32 + 32) % 32;
+}
+template <int N, int KL>
+__host__ __device__ constexpr int lines_smem_floats() {
+  return 2 * KL * lines_ls<N, KL>() + kFields * KL * (N + 1) * (N + 1) + 2 * kFields * (N + 1) * (N + 1);
+}
+
+template <int N, int KL, int MB, bool RA>
+__global__ void __launch_bounds__(KL * (N + 1) * (N + 1), MB)
+volume_lines_mixed(const VolArgs A) {
+  constexpr int n1 = N + 1, Nq = n1 * n1;
+  constexpr int LW = lines_lw<N>(), LS = lines_ls<N, KL>();
+  extern __shared__ __align__(16) float smem[];
+  float* sX = smem;                       // [kk][LS]: x fluxes, then x contractions
+  float* sY = sX + KL * LS;               // [kk][LS]: the same for y
+  float* sT = sY + KL * LS;               // [f][kk][ab]: z part of the top-node residual
+  float* sP = sT + kFields * KL * Nq;     // [2][f][ab]: top-node carry between chunks
+  const int col = blockIdx.x, t = threadIdx.x;
+  const int kk = t % KL, ab = t / KL;
+  const int i = ab % n1, j = ab / n1;
+  const int lc = ab % n1, lo = ab / n1;   // exchange phase: x-line (j, c) = (lo, lc), y-line (i, c) = (lo, lc)
+  const int lev = A.col_level[col];
+  const float* geo = A.geof[lev];
+  const float sx = geo[4], sy = geo[5], sz = geo[6], J = geo[3];
+  const int hm = A.hmap[(long long)col * Nq + ab];
+  const float wi = c_wf[N][i], wj = c_wf[N][j];
+  float* rc = (float*)A.rc;
+  const int nchunk = (A.nz + KL - 1) / KL;
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const int k = ch * KL + kk;
+    const bool act = k < A.nz;
+    const int kz0 = k * N;
+    float rz[kFields][n1];
+#pragma unroll
+    for (int f = 0; f < kFields; ++f)
+#pragma unroll
+      for (int c = 0; c < n1; ++c) rz[f][c] = 0.f;
+    float* zX = sX + kk * LS + ab * LW;   // this thread's z-line, + f n1 + c
+    float* zY = sY + kk * LS + ab * LW;
+    if (act) {
+#pragma unroll
+      for (int c = 0; c < n1; ++c) {
+        float v[kFields];
+        const int kz = kz0 + c;
+        load_node<N>(A, hm, kz, v);
+        const float wc = c_wf[N][c];
+        NodeTerms T;
+        node_terms<RA>(A, v, kz, wj * wc * sx, wi * wc * sy, wi * wj * sz, wi * wj * wc * J, T);
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) {
+          zX[f * n1 + c] = T.fx[f];
+          zY[f * n1 + c] = T.fy[f];
+        }
+#pragma unroll
+        for (int f = 0; f < kFields; ++f)
+#pragma unroll
+          for (int c2 = 0; c2 < n1; ++c2) rz[f][c2] = fmaf(c_Dwf[N][c2 * n1 + c], T.fz[f], rz[f][c2]);
+        rz[1][c] += T.su;
+        rz[2][c] += T.sv;
+        rz[3][c] += T.sw;
+      }
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) sT[(f * KL + kk) * Nq + ab] = rz[f][N];
+    }
+    __syncthreads();
+    if (act) {
+      // x-line (lo, lc): nodes (m, lo, lc), m = 0..N
+      float* bx = sX + kk * LS + lo * n1 * LW + lc;
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) {
+        float F[n1];
+#pragma unroll
+        for (int m = 0; m < n1; ++m) F[m] = bx[m * LW + f * n1];
+#pragma unroll
+        for (int i2 = 0; i2 < n1; ++i2) {
+          float acc = 0.f;
+#pragma unroll
+          for (int m = 0; m < n1; ++m) acc = fmaf(c_Dwf[N][i2 * n1 + m], F[m], acc);
+          bx[i2 * LW + f * n1] = acc;
+        }
+      }
+      // y-line (lo, lc): nodes (lo, m, lc)
+      float* by = sY + kk * LS + lo * LW + lc;
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) {
+        float F[n1];
+#pragma unroll
+        for (int m = 0; m < n1; ++m) F[m] = by[m * n1 * LW + f * n1];
+#pragma unroll
+        for (int j2 = 0; j2 < n1; ++j2) {
+          float acc = 0.f;
+#pragma unroll
+          for (int m = 0; m < n1; ++m) acc = fmaf(c_Dwf[N][j2 * n1 + m], F[m], acc);
+          by[j2 * n1 * LW + f * n1] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+      for (int f = 0; f < kFields; ++f)
+#pragma unroll
+        for (int c = 0; c < n1; ++c) rz[f][c] += zX[f * n1 + c] + zY[f * n1 + c];
+      // vertical DSS: the bottom node takes the full top-node value of the
+      // layer below (its z part from sT, its x and y parts still in sX, sY)
+      if (kk > 0) {
+        const float* pX = sX + (kk - 1) * LS + ab * LW;
+        const float* pY = sY + (kk - 1) * LS + ab * LW;
+#pragma unroll
+        for (int f = 0; f < kFields; ++f)
+          rz[f][0] += sT[(f * KL + kk - 1) * Nq + ab] + pX[f * n1 + N] + pY[f * n1 + N];
+      } else if (ch > 0) {
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) rz[f][0] += sP[((ch - 1) & 1) * kFields * Nq + f * Nq + ab];
+      }
+      if (kk == KL - 1) {
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) sP[(ch & 1) * kFields * Nq + f * Nq + ab] = rz[f][N];
+      }
+      float* dst = rc + ((long long)((long long)col * Nq + ab) * kFields) * A.NZr + kz0;
+      const bool top = (k == A.nz - 1);
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) {
+        float* df = dst + (long long)f * A.NZr;
+        if (N == 4) {
+          *reinterpret_cast<float4*>(df) = make_float4(rz[f][0], rz[f][1], rz[f][2], rz[f][3]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < N; ++c) df[c] = rz[f][c];
+        }
+        if (top) df[N] = rz[f][N];
+      }
+    }
+    if (ch + 1 < nchunk) __syncthreads();
+  }
+}
+
+template <int N, int KL, int MB, bool RA>
+static int launch_lines(const VolArgs& A, cudaStream_t st) {
+  const size_t sm = sizeof(float) * lines_smem_floats<N, KL>();
+  static bool attr = false;
+  if (!attr) {
+    SEM_CUDA_TRY(cudaFuncSetAttribute(volume_lines_mixed<N, KL, MB, RA>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr = true;
+  }
+  ProfScope ps("volume_mixed", st);
+  volume_lines_mixed<N, KL, MB, RA><<<A.Ncol, KL * (N + 1) * (N + 1), sm, st>>>(A);
   return SEM_OK;
 }
 
@@ -955,7 +1138,9 @@ static int launch_pencil(const VolArgs& A, cudaStream_t st) {
 struct PencilVariant {
   int N, KL, MB;
   int (*launch)(const VolArgs&, cudaStream_t);
-  int persistent;   // 1: pipelined persistent kernel (volume_pencil_pipe)
+  int kind;         // 0: volume_pencil_mixed; 1: pipelined persistent volume_pencil_pipe;
+                    // 2: line-exchange volume_lines_mixed
+  int approx_rcp;   // 1: hardware reciprocal approximation for 1/rho
 };
 static const PencilVariant kPencil[] = {
     {2, 8, 4, launch_pencil<2, 8, 4>},   {2, 16, 2, launch_pencil<2, 16, 2>},
@@ -964,6 +1149,9 @@ static const PencilVariant kPencil[] = {
     {4, 8, 4, launch_pencil<4, 8, 4>},   {4, 16, 1, launch_pencil<4, 16, 1>},
     {4, 16, 2, launch_pencil<4, 16, 2>}, {4, 8, 2, launch_pipe<4, 8, 2>, 1},
     {4, 16, 1, launch_pipe<4, 16, 1>, 1}, {4, 4, 4, launch_pipe<4, 4, 4>, 1},
+    {4, 16, 2, launch_pencil<4, 16, 2, true>, 0, 1}, {4, 8, 2, launch_pencil<4, 8, 2, true>, 0, 1},
+    {4, 16, 2, launch_lines<4, 16, 2, false>, 2}, {4, 16, 2, launch_lines<4, 16, 2, true>, 2, 1},
+    {4, 8, 4, launch_lines<4, 8, 4, false>, 2}, {4, 16, 1, launch_lines<4, 16, 1, true>, 2, 1},
     {5, 8, 1, launch_pencil<5, 8, 1>},
     {5, 8, 2, launch_pencil<5, 8, 2>},   {6, 4, 2, launch_pencil<6, 4, 2>},
     {6, 8, 1, launch_pencil<6, 8, 1>},
@@ -974,7 +1162,7 @@ constexpr int kNumPencil = sizeof(kPencil) / sizeof(kPencil[0]);
 static int pencil_default(int N, int nz) {
   int best = -1;
   for (int v = 0; v < kNumPencil; ++v) {
-    if (kPencil[v].N != N || kPencil[v].persistent) continue;
+    if (kPencil[v].N != N || kPencil[v].kind || kPencil[v].approx_rcp) continue;
     if (best < 0) { best = v; continue; }
     const PencilVariant& a = kPencil[v];
     const PencilVariant& b = kPencil[best];
@@ -1001,6 +1189,7 @@ static VolArgs make_vol_args(Mesh& m, const sem_params& p, const void* q, bool m
   A.col_level = D.col_level;
   A.ref = D.ref;
   A.ref32 = D.ref32;
+  A.ref4 = reinterpret_cast<const float4*>(D.ref32 + (size_t)m.NZ * kRef);
   A.Ncol = (int)m.Ncol();
   A.nz = m.nz;
   A.NZ = m.NZ;
@@ -1078,6 +1267,17 @@ template <int STAGE>
 __device__ __forceinline__ void inc_body(const IncArgs& A, const int gidx, int& bad) {
   const int h = (int)((unsigned)gidx / (unsigned)A.NZ);
   const int kz = gidx - h * A.NZ;
+  // The values this node updates are loaded before the gather and before any
+  // store, so that their memory latency overlaps the gather's.
+  float dprev[kFields], q32v[kFields];
+  double qv[kFields];
+#pragma unroll
+  for (int fl = 0; fl < kFields; ++fl) {
+    const long long o = (long long)fl * A.NG + gidx;
+    if (STAGE > 0) dprev[fl] = A.d[o];
+    if (STAGE < 2) q32v[fl] = __ldg(A.q32 + o);
+    else qv[fl] = A.q[o];
+  }
   const int beg = __ldg(A.qt_ptr + h), end = __ldg(A.qt_ptr + h + 1);
   const float s = A.cdt * (__ldg(A.Minv_h + h) * __ldg(A.Minv_z + kz));
   const bool lid = (kz == 0) || (kz == A.NZ - 1);
@@ -1092,15 +1292,15 @@ __device__ __forceinline__ void inc_body(const IncArgs& A, const int gidx, int& 
   for (int fl = 0; fl < kFields; ++fl) {
     const long long o = (long long)fl * A.NG + gidx;
     const float inc = (fl == 3 && lid) ? 0.f : acc[fl] * s;
-    const float dn = (STAGE == 0) ? inc : fmaf(A.bcoef, A.d[o], inc);
+    const float dn = (STAGE == 0) ? inc : fmaf(A.bcoef, dprev[fl], inc);
     if (STAGE < 2) {
       A.d[o] = dn;
-      A.qs32[o] = __ldg(A.q32 + o) + dn;
+      A.qs32[o] = q32v[fl] + dn;
     } else {
-      const double qv = A.q[o] + f2d_bits(dn);
-      A.q[o] = qv;
-      A.q32_out[o] = d2f_bits(qv);
-      bad |= nonfinite_bits(qv);
+      const double qn = qv[fl] + f2d_bits(dn);
+      A.q[o] = qn;
+      A.q32_out[o] = d2f_bits(qn);
+      bad |= nonfinite_bits(qn);
     }
   }
 }
@@ -1185,7 +1385,8 @@ int autotune_pencil(Mesh& m, const sem_params& p, const float* q32, int reps, se
     const int k = out->n_variants++;
     out->layers_per_cta[k] = kPencil[v].KL;
     out->min_ctas_per_sm[k] = kPencil[v].MB;
-    out->persistent[k] = kPencil[v].persistent;
+    out->kind[k] = kPencil[v].kind;
+    out->approx_rcp[k] = kPencil[v].approx_rcp;
     out->ms[k] = ms;
     if (best < 0 || ms < best_ms) {
       best = v;
@@ -1198,6 +1399,24 @@ int autotune_pencil(Mesh& m, const sem_params& p, const float* q32, int reps, se
   if (best < 0) return fail(SEM_ERR_UNSUPPORTED, "no variant for this order");
   m.pencil_variant = best;
   return SEM_OK;
+}
+
+// Row `row` of the autotuner's table for the mesh's order (-1: default).
+int select_pencil(Mesh& m, int row) {
+  if (row == -1) {
+    m.pencil_variant = -1;
+    return SEM_OK;
+  }
+  int k = 0;
+  for (int v = 0; v < kNumPencil && k < SEM_TUNE_MAX; ++v) {
+    if (kPencil[v].N != m.N) continue;
+    if (k == row) {
+      m.pencil_variant = v;
+      return SEM_OK;
+    }
+    ++k;
+  }
+  return fail(SEM_ERR_ARG, "autotune_select: row outside the variant table of this order");
 }
 
 // ---------------------------------------------------------------------------

@@ -116,7 +116,7 @@ struct DeviceTables {
   double* Mh = nullptr;
   double* Mz = nullptr;
   double* ref = nullptr;        // [NZ][kRef] float64 reference state
-  float* ref32 = nullptr;       // [NZ][kRef] float32 copy
+  float* ref32 = nullptr;       // [NZ][kRef] float32 copy, then [NZ][4] packed rows (p0, rho0, (rho theta)0, 1/(rho theta)0)
   int* col_level = nullptr;     // [Ncol]
   double* xh = nullptr;         // [NH]
   double* yh = nullptr;
@@ -183,6 +183,7 @@ int mlp_adam_api(void* m, float lr, cudaStream_t st);
 int mlp_features_api(Mesh& mesh, const double* q, const float* scales, float* F, cudaStream_t st);
 int autotune_pencil(Mesh& m, const sem_params& p, const float* q32, int reps, sem_tune_out* out,
                     cudaStream_t st);
+int select_pencil(Mesh& m, int row);
 int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float* work32, double dt,
                       cudaStream_t st);
 

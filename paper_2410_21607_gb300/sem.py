@@ -28,7 +28,7 @@ EXPORTS = (
     "sem_rk_stage_mixed",
     "sem_mirror", "sem_step", "sem_step_mixed",
     "sem_adapt_flags", "sem_adapt_flags_host", "sem_transfer_plan", "sem_transfer", "sem_diag",
-    "sem_status", "sem_profile_begin", "sem_profile_end", "sem_autotune",
+    "sem_status", "sem_profile_begin", "sem_profile_end", "sem_autotune", "sem_autotune_select",
     "sem_batch_create", "sem_batch_destroy", "sem_batch_step_mixed", "sem_batch_status",
     "sem_mlp_create", "sem_mlp_destroy", "sem_mlp_param_count", "sem_mlp_get_params",
     "sem_mlp_set_params", "sem_mlp_get_grads", "sem_mlp_features", "sem_mlp_forward",
@@ -72,7 +72,7 @@ class ProfileOut(C.Structure):
 
 class TuneOut(C.Structure):
     _fields_ = [("n_variants", C.c_int), ("chosen", C.c_int), ("layers_per_cta", C.c_int * 16),
-                ("min_ctas_per_sm", C.c_int * 16), ("persistent", C.c_int * 16),
+                ("min_ctas_per_sm", C.c_int * 16), ("kind", C.c_int * 16), ("approx_rcp", C.c_int * 16),
                 ("ms", C.c_double * 16)]
 
 
@@ -130,6 +130,7 @@ def _load():
         "sem_checkpoint_read_mesh": (i, [C.c_char_p, C.POINTER(vp), C.POINTER(d), C.POINTER(C.c_longlong)]),
         "sem_checkpoint_read_state": (i, [C.c_char_p, vp, vp, vp]),
         "sem_autotune": (i, [vp, C.POINTER(Params), vp, i, C.POINTER(TuneOut), vp]),
+        "sem_autotune_select": (i, [vp, i]),
         "sem_profile_end": (i, [C.POINTER(ProfileOut)]),
     }
     for name, (res, args) in sig.items():
@@ -382,14 +383,21 @@ def sem_profile_end():
 
 def sem_autotune(mesh, params, q32, reps=5, stream=None):
     """Time the element-kernel variants on this mesh and keep the fastest.
-    Returns [(layers_per_cta, min_ctas_per_sm, ms)] and the chosen index."""
+    Returns [(layers_per_cta, min_ctas_per_sm, ms, kind, approx_rcp)] and the
+    chosen index (kind 0: z-pencil, 1: persistent z-pencil, 2: line exchange)."""
     _f32(q32, mesh.field_shape)
     out = TuneOut()
     _check(LIB.sem_autotune(mesh.h, C.byref(params), _ptr(q32), int(reps), C.byref(out),
                             _stream(stream)))
-    rows = [(out.layers_per_cta[k], out.min_ctas_per_sm[k], out.ms[k], out.persistent[k])
+    rows = [(out.layers_per_cta[k], out.min_ctas_per_sm[k], out.ms[k], out.kind[k],
+             out.approx_rcp[k])
             for k in range(out.n_variants)]
     return rows, out.chosen
+
+
+def sem_autotune_select(mesh, row):
+    """Use row `row` of sem_autotune's table (-1: the untuned default)."""
+    _check(LIB.sem_autotune_select(mesh.h, int(row)))
 
 
 class Batch:

@@ -127,6 +127,16 @@ def test_rejects_bad_meshes(sem):
     assert e.value.code == sem.SEM_ERR_ARG
 
 
+def test_autotune_select_rejects_rows_outside_the_table(sem):
+    m = sem.sem_mesh_create(80e3, 80e3, 10e3, 2, 2, 1, 4)
+    sem.sem_autotune_select(m, -1)
+    sem.sem_autotune_select(m, 0)
+    for bad in (-2, 16, 1000):
+        with pytest.raises(sem.SemError) as e:
+            sem.sem_autotune_select(m, bad)
+        assert e.value.code == sem.SEM_ERR_ARG
+
+
 def test_uniform_counts_and_info(sem):
     m = sem.sem_mesh_create(2048e3, 2048e3, 24e3, 64, 64, 16, 4)
     assert (m.Ne, m.NG, m.NH, m.NZ) == (65536, 4259840, 65536, 65)

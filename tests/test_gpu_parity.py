@@ -102,6 +102,39 @@ def test_rhs_mixed_matches_oracle(sem, name, eqset):
     assert np.all(err <= 1e-4), err
 
 
+@pytest.mark.parametrize("name", ["twolevel-N4", "twolevel-17-layers-N4", "uniform-5x4x3-N6"])
+def test_every_element_kernel_variant_matches_oracle(sem, name):
+    """Each launch variant of the mixed element kernel (z-pencil, persistent
+    pipelined z-pencil, line exchange; every layers-per-CTA count) gives the
+    mixed tendency within 1e-4 of the oracle.  17 layers make several layer
+    chunks per column for every variant, so the carry of the top-face residual
+    between chunks is exercised."""
+    spec = dict(MESHES.get(name, {}))
+    if name == "twolevel-17-layers-N4":
+        spec = dict(L=300e3, Lz=24e3, nx=4, nz=17, N=4, leaves=two_level_leaves())
+    m, o, X, perm = make_pair(sem, **spec)
+    q_o = random_state(o.XG, o.Lz, 13)
+    T_o = orhs.rhs(o, q_o, PRM)
+    p = sem.sem_params_default(precision=sem.SEM_PREC_MIXED)
+    q = dev(q_o[:, perm])
+    q32 = torch.empty(q.shape, dtype=torch.float32, device="cuda")
+    sem.sem_mirror(m, q, q32)
+    rows, _ = sem.sem_autotune(m, p, q32, 1)
+    assert len(rows) >= 2
+    kinds = set()
+    for row in list(range(len(rows))) + [-1]:
+        sem.sem_autotune_select(m, row)
+        out = torch.full_like(q, float("nan"))
+        sem.sem_rhs(m, p, q, out)
+        err = group_rel_l2(host(out), T_o[:, perm])
+        assert np.all(err <= 1e-4), (row, rows[row] if row >= 0 else "default", err)
+        if row >= 0:
+            kinds.add(rows[row][3])
+    if spec["N"] == 4:
+        assert kinds == {0, 1, 2}
+    assert sem.sem_status(m) == 0
+
+
 def test_rest_state_exactly_steady_on_gpu(sem):
     m, o, X, perm = make_pair(sem, **MESHES["twolevel-N4"])
     for prec in (0, 1):
