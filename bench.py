@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-amr", action="store_true")
+    ap.add_argument("--kernel-row", type=int, default=None,
+                    help="use this row of the element-kernel variant table instead of autotuning "
+                         "(for profiler runs, whose per-launch overhead distorts the timings)")
     return ap.parse_args()
 
 
@@ -350,10 +353,13 @@ def main():
 
     bufs = new_bufs()
     tune = None
-    if a.form == "mixed":
+    if a.form == "mixed" and a.kernel_row is not None:
+        sem.sem_autotune_select(m, a.kernel_row)
+        tune = {"variants": None, "chosen": a.kernel_row}
+    elif a.form == "mixed":
         rows, chosen = sem.sem_autotune(m, p, bufs[3], 5, stream)
         tune = {"variants": [{"layers_per_cta": r[0], "min_ctas_per_sm": r[1], "ms": r[2],
-                              "kind": r[3], "approx_rcp": r[4]} for r in rows], "chosen": chosen}
+                              "kind": r[3]} for r in rows], "chosen": chosen}
     dof_stage = 5 * m.Ne * (N + 1) ** 3
     for _ in range(max(a.warmup, 3)):
         bufs = step(bufs, p)

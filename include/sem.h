@@ -315,10 +315,7 @@ typedef struct {
   int chosen;                          /* index into the arrays below */
   int layers_per_cta[SEM_TUNE_MAX];
   int min_ctas_per_sm[SEM_TUNE_MAX];
-  int kind[SEM_TUNE_MAX];              /* 0: z-pencil kernel, one CTA per column;
-                                          1: persistent z-pencil CTAs prefetching the next column;
-                                          2: line-exchange kernel, one CTA per column */
-  int approx_rcp[SEM_TUNE_MAX];        /* 1: 1/rho from the hardware reciprocal approximation */
+  int kind[SEM_TUNE_MAX];              /* 0: z-pencil kernel, 1: line-exchange kernel */
   double ms[SEM_TUNE_MAX];             /* mean event time per launch */
 } sem_tune_out;
 int sem_autotune(sem_mesh* m, const sem_params* p, const float* q32_dev, int reps,

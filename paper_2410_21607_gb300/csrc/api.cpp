@@ -34,7 +34,7 @@ void free_device(Mesh& m) {
   if (m.dev_id >= 0 && cur != m.dev_id) cudaSetDevice(m.dev_id);
   DeviceTables& D = *m.dev;
   void* ptrs[] = {D.hmap, D.hang_h, D.hang_w, D.qt_ptr, D.qt_src, D.qt_w, D.Minv_h, D.Minv_z,
-                  D.Mh, D.Mz, D.Minv_h32, D.Minv_z32, D.qt_w32, D.hang_w32, D.mirror, D.ref, D.ref32, D.col_level, D.xh, D.yh, D.zk, D.scratch,
+                  D.Mh, D.Mz, D.Minv_h32, D.Minv_z32, D.qt_w32, D.qt_rec_src, D.qt_rec_w, D.hang_w32, D.mirror, D.ref, D.ref32, D.col_level, D.xh, D.yh, D.zk, D.scratch,
                   D.status, D.org, D.elem_cmax, D.elem_flags, D.diag_buf,
                   D.tr_comp_ptr, D.tr_nodes, D.tr_A_ptr, D.tr_A_col, D.tr_A_val, D.tr_coupled};
   for (void* p : ptrs)
@@ -65,6 +65,21 @@ int ensure_device(Mesh& m) {
   for (int k = 0; k < m.NZ; ++k) minvz32[k] = (float)minvz[k];
   for (size_t k = 0; k < qtw32.size(); ++k) qtw32[k] = (float)m.qt_w[k];
   for (size_t k = 0; k < hw32.size(); ++k) hw32[k] = (float)m.hang_w[k];
+  // compact Q_h^T records: the up to 4 sources of a horizontal node and their
+  // weights side by side (one 16-byte load each), in the CSR order
+  std::vector<int> rsrc((size_t)m.NH * 4, -1);
+  std::vector<float> rw((size_t)m.NH * 4, 0.f);
+  for (long long h = 0; h < m.NH; ++h) {
+    const int beg = m.qt_ptr[h], cnt = m.qt_ptr[h + 1] - beg;
+    if (cnt > 4) {
+      rsrc[(size_t)h * 4] = -2;
+      continue;
+    }
+    for (int e = 0; e < cnt; ++e) {
+      rsrc[(size_t)h * 4 + e] = m.qt_src[beg + e];
+      rw[(size_t)h * 4 + e] = qtw32[beg + e];
+    }
+  }
   std::vector<int> lev(m.Ncol());
   for (long long c = 0; c < m.Ncol(); ++c) lev[c] = m.leaves[c].l;
   if ((rc = upload(D.hmap, m.hmap)) || (rc = upload(D.hang_h, m.hang_h)) ||
@@ -74,7 +89,8 @@ int ensure_device(Mesh& m) {
       (rc = upload(D.Mh, m.Mh)) || (rc = upload(D.Mz, m.Mz)) || (rc = upload(D.col_level, lev)) ||
       (rc = upload(D.xh, m.xh)) || (rc = upload(D.yh, m.yh)) || (rc = upload(D.zk, m.zk)) ||
       (rc = upload(D.Minv_h32, minvh32)) || (rc = upload(D.Minv_z32, minvz32)) ||
-      (rc = upload(D.qt_w32, qtw32)) || (rc = upload(D.hang_w32, hw32))) {
+      (rc = upload(D.qt_w32, qtw32)) || (rc = upload(D.hang_w32, hw32)) ||
+      (rc = upload(D.qt_rec_src, rsrc)) || (rc = upload(D.qt_rec_w, rw))) {
     free_device(m);
     return rc;
   }

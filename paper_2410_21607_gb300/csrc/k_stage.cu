@@ -498,14 +498,6 @@ __device__ __forceinline__ float pow1p_m1(float x, const float* bin, float gam) 
   return expm1f(gam * log1pf(x));
 }
 
-// 1/x from the hardware reciprocal approximation (rcp.approx.ftz.f32, relative
-// error within 2^-22), in place of the correctly rounded reciprocal.
-__device__ __forceinline__ float rcp_approx(float x) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-
 // State perturbation v = (rho', rho u, rho v, rho w, (rho theta)') of one node
 // of column line `hm` at level kz: a direct load, or for a hanging line the
 // interpolation from the coarse neighbour's lines (Sec. 3.1).
@@ -536,21 +528,17 @@ __device__ __forceinline__ void load_node(const VolArgs& A, const int hm, const 
 // components ax F^x, ay F^y, az F^z of the five equations and the weighted
 // momentum sources wJ S (Coriolis on rho u and rho v, buoyancy on rho w).
 // The reference state of the level is one packed 16-byte row.
-// RA selects the hardware reciprocal approximation for 1/rho instead of the
-// correctly rounded reciprocal (whose rarely taken slow path also limits how
-// far the compiler hoists the next nodes' loads, and so register pressure).
 struct NodeTerms {
   float fx[kFields], fy[kFields], fz[kFields];
   float su, sv, sw;
 };
-template <bool RA>
 __device__ __forceinline__ void node_terms(const VolArgs& A, const float (&v)[kFields], const int kz,
                                            const float ax, const float ay, const float az, const float wJ,
                                            NodeTerms& o) {
   const float4 ra = __ldg(A.ref4 + kz);
   const float p0 = ra.x, rho0 = ra.y, rt0 = ra.z, inv_rt0 = ra.w;
   const float rp = v[0], U = v[1], V = v[2], W = v[3], Tp = v[4];
-  const float inv = RA ? rcp_approx(rho0 + rp) : __frcp_rn(rho0 + rp);
+  const float inv = __frcp_rn(rho0 + rp);
   const float u = U * inv, vv = V * inv, w = W * inv;
   const float pp = p0 * pow1p_m1(Tp * inv_rt0, A.bin, A.gammaf);
   const float rt = rt0 + Tp;
@@ -577,7 +565,7 @@ __device__ __forceinline__ void node_terms(const VolArgs& A, const float (&v)[kF
 // Body shared by the single-mesh kernel (one CTA per column) and the batched
 // persistent kernel (CTAs pull columns of many meshes from a queue).  Threads
 // t >= KL (N+1)^2 of a larger CTA take part in the barriers only.
-template <int N, int KL, bool RA = false>
+template <int N, int KL>
 __device__ __forceinline__ void pencil_body(const VolArgs& A, const int col, float* smem, const int t) {
   constexpr int n1 = N + 1, Nq = n1 * n1, CP = (n1 + 1) / 2, CW = 2 * CP;
   // words per layer block, padded to 2 (mod 32) so that the 16 layers a
@@ -625,7 +613,7 @@ __device__ __forceinline__ void pencil_body(const VolArgs& A, const int col, flo
         load_node<N>(A, hm, kz, v);
         const float wc = c_wf[N][c];
         NodeTerms T;
-        node_terms<RA>(A, v, kz, wj * wc * sx, wi * wc * sy, wi * wj * sz, wi * wj * wc * J, T);
+        node_terms(A, v, kz, wj * wc * sx, wi * wc * sy, wi * wj * sz, wi * wj * wc * J, T);
 #pragma unroll
         for (int f = 0; f < kFields; ++f) {
           myX[f * FS + c] = T.fx[f];
@@ -717,231 +705,11 @@ __device__ __forceinline__ void pencil_body(const VolArgs& A, const int col, flo
   }
 }
 
-template <int N, int KL, int MB, bool RA = false>
+template <int N, int KL, int MB>
 __global__ void __launch_bounds__(KL * (N + 1) * (N + 1), MB)
 volume_pencil_mixed(const VolArgs A) {
   extern __shared__ __align__(16) float smem[];
-  pencil_body<N, KL, RA>(A, blockIdx.x, smem, threadIdx.x);
-}
-
-// Persistent, software-pipelined variant of the pencil kernel: each CTA walks
-// columns blockIdx.x, blockIdx.x + gridDim.x, ... and, while it computes one
-// (column, layer chunk), the state values of the next one stream into a second
-// shared-memory stage with per-thread cp.async copies (each thread copies and
-// later reads only its own z-line values, so the stage needs no barrier).
-// Flux rows are written as 64-bit node pairs.  Arithmetic identical to
-// pencil_body.
-__device__ __forceinline__ void cp_async4(float* smem_dst, const float* gsrc) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(a), "l"(gsrc));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
-
-template <int N, int KL>
-__host__ __device__ constexpr int pipe_stage_floats() {
-  return 2 * kFields * (N + 1) * KL * (N + 1) * (N + 1);
-}
-
-template <int N, int KL, int MB, bool RA = false>
-__global__ void __launch_bounds__(KL * (N + 1) * (N + 1), MB)
-volume_pencil_pipe(const VolArgs A) {
-  constexpr int n1 = N + 1, Nq = n1 * n1, CP = (n1 + 1) / 2, CW = 2 * CP;
-  constexpr int NT = KL * Nq;
-  constexpr int SK = pencil_sk(N);
-  constexpr int SXY = kFields * KL * SK;
-  constexpr int FS = KL * SK;
-  extern __shared__ __align__(16) float smem[];
-  float* sX = smem;
-  float* sY = sX + SXY;
-  float* sT = sY + SXY;
-  float* sP = sT + kFields * KL * Nq;
-  float* stage = sP + kFields * Nq;      // [2][f][c][NT]
-  const int t = threadIdx.x;
-  const int kk = t % KL, ab = t / KL;
-  const int i = ab % n1, j = ab / n1;
-  const float* q = (const float*)A.q;
-  float Dwi[n1], Dwj[n1];
-#pragma unroll
-  for (int m = 0; m < n1; ++m) {
-    Dwi[m] = c_Dwf[N][i * n1 + m];
-    Dwj[m] = c_Dwf[N][j * n1 + m];
-  }
-  const float wi = c_wf[N][i], wj = c_wf[N][j];
-  float* rc = (float*)A.rc;
-  const int nchunk = (A.nz + KL - 1) / KL;
-
-  auto issue = [&](int col, int ch, int buf) {
-    const int k = ch * KL + kk;
-    if (k < A.nz) {
-      const int hm = A.hmap[(long long)col * Nq + ab];
-      if (hm >= 0) {
-        const float* pq = q + (long long)hm * A.NZ + k * N;
-        float* st = stage + (long long)buf * kFields * n1 * NT + t;
-#pragma unroll
-        for (int f = 0; f < kFields; ++f)
-#pragma unroll
-          for (int c = 0; c < n1; ++c) cp_async4(st + (f * n1 + c) * NT, pq + (long long)f * A.NG + c);
-      }
-    }
-    cp_async_commit();
-  };
-
-  int col = blockIdx.x, ch = 0, buf = 0;
-  if (col < A.Ncol) issue(col, 0, 0);
-  while (col < A.Ncol) {
-    int ncol = col, nch = ch + 1;
-    if (nch == nchunk) {
-      ncol = col + gridDim.x;
-      nch = 0;
-    }
-    if (ncol < A.Ncol) issue(ncol, nch, buf ^ 1);
-    else cp_async_commit();
-    cp_async_wait1();
-
-    const int lev = A.col_level[col];
-    const float* geo = A.geof[lev];
-    const float sx = geo[4], sy = geo[5], sz = geo[6], J = geo[3];
-    const int hm = A.hmap[(long long)col * Nq + ab];
-    const int k = ch * KL + kk;
-    const bool act = k < A.nz;
-    const int kz0 = k * N;
-    const float* st = stage + (long long)buf * kFields * n1 * NT + t;
-    float2 r[kFields][CP];
-#pragma unroll
-    for (int f = 0; f < kFields; ++f)
-#pragma unroll
-      for (int p = 0; p < CP; ++p) r[f][p] = make_float2(0.f, 0.f);
-    float* myX = sX + kk * SK + j * n1 * CW + i * CW;
-    float* myY = sY + kk * SK + i * n1 * CW + j * CW;
-    if (act) {
-#pragma unroll
-      for (int p = 0; p < CP; ++p) {
-        float fx[2][kFields], fy[2][kFields];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int c = 2 * p + h;
-          if (c >= n1) {
-#pragma unroll
-            for (int f = 0; f < kFields; ++f) fx[h][f] = fy[h][f] = 0.f;
-            continue;
-          }
-          float v[kFields];
-          const int kz = kz0 + c;
-          if (hm >= 0) {
-#pragma unroll
-            for (int f = 0; f < kFields; ++f) v[f] = st[(f * n1 + c) * NT];
-          } else {
-            load_node<N>(A, hm, kz, v);
-          }
-          const float wc = c_wf[N][c];
-          NodeTerms T;
-          node_terms<RA>(A, v, kz, wj * wc * sx, wi * wc * sy, wi * wj * sz, wi * wj * wc * J, T);
-#pragma unroll
-          for (int f = 0; f < kFields; ++f) {
-            fx[h][f] = T.fx[f];
-            fy[h][f] = T.fy[f];
-          }
-          float* rz = reinterpret_cast<float*>(&r[0][0]);
-#pragma unroll
-          for (int f = 0; f < kFields; ++f)
-#pragma unroll
-            for (int c2 = 0; c2 < n1; ++c2)
-              rz[f * CP * 2 + c2] = fmaf(c_Dwf[N][c2 * n1 + c], T.fz[f], rz[f * CP * 2 + c2]);
-          rz[(1 * CP * 2) + c] += T.su;
-          rz[(2 * CP * 2) + c] += T.sv;
-          rz[(3 * CP * 2) + c] += T.sw;
-        }
-#pragma unroll
-        for (int f = 0; f < kFields; ++f) {
-          *reinterpret_cast<float2*>(myX + f * FS + 2 * p) = make_float2(fx[0][f], fx[1][f]);
-          *reinterpret_cast<float2*>(myY + f * FS + 2 * p) = make_float2(fy[0][f], fy[1][f]);
-        }
-      }
-    } else {
-#pragma unroll
-      for (int f = 0; f < kFields; ++f)
-#pragma unroll
-        for (int p = 0; p < CP; ++p) {
-          *reinterpret_cast<float2*>(myX + f * FS + 2 * p) = make_float2(0.f, 0.f);
-          *reinterpret_cast<float2*>(myY + f * FS + 2 * p) = make_float2(0.f, 0.f);
-        }
-    }
-    __syncthreads();
-    const float* rowX = sX + kk * SK + j * n1 * CW;
-    const float* rowY = sY + kk * SK + i * n1 * CW;
-#pragma unroll
-    for (int f = 0; f < kFields; ++f)
-#pragma unroll
-      for (int m = 0; m < n1; ++m) {
-        const float2 dx = make_float2(Dwi[m], Dwi[m]);
-        const float2 dy = make_float2(Dwj[m], Dwj[m]);
-#pragma unroll
-        for (int p = 0; p < CP; ++p) {
-          const float2 vx = *reinterpret_cast<const float2*>(rowX + f * FS + m * CW + 2 * p);
-          const float2 vy = *reinterpret_cast<const float2*>(rowY + f * FS + m * CW + 2 * p);
-          r[f][p] = __ffma2_rn(dx, vx, r[f][p]);
-          r[f][p] = __ffma2_rn(dy, vy, r[f][p]);
-        }
-      }
-    float* rr = reinterpret_cast<float*>(&r[0][0]);
-#pragma unroll
-    for (int f = 0; f < kFields; ++f) sT[(f * KL + kk) * Nq + ab] = rr[f * CP * 2 + N];
-    if (kk == 0 && ch > 0) {
-#pragma unroll
-      for (int f = 0; f < kFields; ++f) rr[f * CP * 2] += sP[f * Nq + ab];
-    }
-    __syncthreads();
-    if (kk > 0) {
-#pragma unroll
-      for (int f = 0; f < kFields; ++f) rr[f * CP * 2] += sT[(f * KL + kk - 1) * Nq + ab];
-    }
-    if (kk == KL - 1) {
-#pragma unroll
-      for (int f = 0; f < kFields; ++f) sP[f * Nq + ab] = rr[f * CP * 2 + N];
-    }
-    if (act) {
-      float* dst = rc + ((long long)((long long)col * Nq + ab) * kFields) * A.NZr + kz0;
-      const bool top = (k == A.nz - 1);
-#pragma unroll
-      for (int f = 0; f < kFields; ++f) {
-        float* df = dst + (long long)f * A.NZr;
-        if (N == 4) {
-          *reinterpret_cast<float4*>(df) = make_float4(rr[f * CP * 2 + 0], rr[f * CP * 2 + 1],
-                                                       rr[f * CP * 2 + 2], rr[f * CP * 2 + 3]);
-        } else {
-#pragma unroll
-          for (int c = 0; c < N; ++c) df[c] = rr[f * CP * 2 + c];
-        }
-        if (top) df[N] = rr[f * CP * 2 + N];
-      }
-    }
-    __syncthreads();
-    buf ^= 1;
-    col = ncol;
-    ch = nch;
-  }
-}
-
-template <int N, int KL, int MB>
-static int launch_pipe(const VolArgs& A, cudaStream_t st) {
-  constexpr int n1 = N + 1, Nq = n1 * n1;
-  const size_t sm = sizeof(float) * (2 * kFields * KL * pencil_sk(N) + kFields * KL * Nq + kFields * Nq +
-                                     pipe_stage_floats<N, KL>());
-  static bool attr = false;
-  static int nsm = 0;
-  if (!attr) {
-    SEM_CUDA_TRY(cudaFuncSetAttribute(volume_pencil_pipe<N, KL, MB>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    attr = true;
-  }
-  const int grid = std::min(A.Ncol, nsm * MB);
-  ProfScope ps("volume_mixed", st);
-  volume_pencil_pipe<N, KL, MB><<<grid, KL * Nq, sm, st>>>(A);
-  return SEM_OK;
+  pencil_body<N, KL>(A, blockIdx.x, smem, threadIdx.x);
 }
 
 template <int N, int KL>
@@ -950,17 +718,17 @@ static size_t pencil_smem() {
   return sizeof(float) * (2 * kFields * KL * pencil_sk(N) + kFields * KL * Nq + kFields * Nq);
 }
 
-template <int N, int KL, int MB, bool RA = false>
+template <int N, int KL, int MB>
 static int launch_pencil(const VolArgs& A, cudaStream_t st) {
   const size_t sm = pencil_smem<N, KL>();
   static bool attr = false;
   if (!attr) {
-    SEM_CUDA_TRY(cudaFuncSetAttribute(volume_pencil_mixed<N, KL, MB, RA>,
+    SEM_CUDA_TRY(cudaFuncSetAttribute(volume_pencil_mixed<N, KL, MB>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr = true;
   }
   ProfScope ps("volume_mixed", st);
-  volume_pencil_mixed<N, KL, MB, RA><<<A.Ncol, KL * (N + 1) * (N + 1), sm, st>>>(A);
+  volume_pencil_mixed<N, KL, MB><<<A.Ncol, KL * (N + 1) * (N + 1), sm, st>>>(A);
   return SEM_OK;
 }
 
@@ -988,30 +756,31 @@ __host__ __device__ constexpr int lines_smem_floats() {
   return 2 * KL * lines_ls<N, KL>() + kFields * KL * (N + 1) * (N + 1) + 2 * kFields * (N + 1) * (N + 1);
 }
 
-template <int N, int KL, int MB, bool RA>
-__global__ void __launch_bounds__(KL * (N + 1) * (N + 1), MB)
-volume_lines_mixed(const VolArgs A) {
+// Body shared by the single-mesh kernel (one CTA per column) and the batched
+// persistent kernel.  Threads t >= KL (N+1)^2 of a larger CTA take part in
+// the barriers only.
+template <int N, int KL>
+__device__ __forceinline__ void lines_body(const VolArgs& A, const int col, float* smem, const int t) {
   constexpr int n1 = N + 1, Nq = n1 * n1;
   constexpr int LW = lines_lw<N>(), LS = lines_ls<N, KL>();
-  extern __shared__ __align__(16) float smem[];
   float* sX = smem;                       // [kk][LS]: x fluxes, then x contractions
   float* sY = sX + KL * LS;               // [kk][LS]: the same for y
   float* sT = sY + KL * LS;               // [f][kk][ab]: z part of the top-node residual
   float* sP = sT + kFields * KL * Nq;     // [2][f][ab]: top-node carry between chunks
-  const int col = blockIdx.x, t = threadIdx.x;
-  const int kk = t % KL, ab = t / KL;
+  const bool part = t < KL * Nq;
+  const int kk = t % KL, ab = part ? t / KL : 0;
   const int i = ab % n1, j = ab / n1;
   const int lc = ab % n1, lo = ab / n1;   // exchange phase: x-line (j, c) = (lo, lc), y-line (i, c) = (lo, lc)
   const int lev = A.col_level[col];
   const float* geo = A.geof[lev];
   const float sx = geo[4], sy = geo[5], sz = geo[6], J = geo[3];
-  const int hm = A.hmap[(long long)col * Nq + ab];
+  const int hm = part ? A.hmap[(long long)col * Nq + ab] : 0;
   const float wi = c_wf[N][i], wj = c_wf[N][j];
   float* rc = (float*)A.rc;
   const int nchunk = (A.nz + KL - 1) / KL;
   for (int ch = 0; ch < nchunk; ++ch) {
     const int k = ch * KL + kk;
-    const bool act = k < A.nz;
+    const bool act = part && k < A.nz;
     const int kz0 = k * N;
     float rz[kFields][n1];
 #pragma unroll
@@ -1028,7 +797,7 @@ volume_lines_mixed(const VolArgs A) {
         load_node<N>(A, hm, kz, v);
         const float wc = c_wf[N][c];
         NodeTerms T;
-        node_terms<RA>(A, v, kz, wj * wc * sx, wi * wc * sy, wi * wj * sz, wi * wj * wc * J, T);
+        node_terms(A, v, kz, wj * wc * sx, wi * wc * sy, wi * wj * sz, wi * wj * wc * J, T);
 #pragma unroll
         for (int f = 0; f < kFields; ++f) {
           zX[f * n1 + c] = T.fx[f];
@@ -1118,17 +887,24 @@ volume_lines_mixed(const VolArgs A) {
   }
 }
 
-template <int N, int KL, int MB, bool RA>
+template <int N, int KL, int MB>
+__global__ void __launch_bounds__(KL * (N + 1) * (N + 1), MB)
+volume_lines_mixed(const VolArgs A) {
+  extern __shared__ __align__(16) float smem[];
+  lines_body<N, KL>(A, blockIdx.x, smem, threadIdx.x);
+}
+
+template <int N, int KL, int MB>
 static int launch_lines(const VolArgs& A, cudaStream_t st) {
   const size_t sm = sizeof(float) * lines_smem_floats<N, KL>();
   static bool attr = false;
   if (!attr) {
-    SEM_CUDA_TRY(cudaFuncSetAttribute(volume_lines_mixed<N, KL, MB, RA>,
+    SEM_CUDA_TRY(cudaFuncSetAttribute(volume_lines_mixed<N, KL, MB>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr = true;
   }
   ProfScope ps("volume_mixed", st);
-  volume_lines_mixed<N, KL, MB, RA><<<A.Ncol, KL * (N + 1) * (N + 1), sm, st>>>(A);
+  volume_lines_mixed<N, KL, MB><<<A.Ncol, KL * (N + 1) * (N + 1), sm, st>>>(A);
   return SEM_OK;
 }
 
@@ -1138,31 +914,29 @@ static int launch_lines(const VolArgs& A, cudaStream_t st) {
 struct PencilVariant {
   int N, KL, MB;
   int (*launch)(const VolArgs&, cudaStream_t);
-  int kind;         // 0: volume_pencil_mixed; 1: pipelined persistent volume_pencil_pipe;
-                    // 2: line-exchange volume_lines_mixed
-  int approx_rcp;   // 1: hardware reciprocal approximation for 1/rho
+  int kind;         // 0: z-pencil volume_pencil_mixed; 1: line-exchange volume_lines_mixed
 };
 static const PencilVariant kPencil[] = {
-    {2, 8, 4, launch_pencil<2, 8, 4>},   {2, 16, 2, launch_pencil<2, 16, 2>},
-    {3, 8, 3, launch_pencil<3, 8, 3>},   {3, 16, 2, launch_pencil<3, 16, 2>},
-    {4, 4, 8, launch_pencil<4, 4, 8>},   {4, 8, 2, launch_pencil<4, 8, 2>},
-    {4, 8, 4, launch_pencil<4, 8, 4>},   {4, 16, 1, launch_pencil<4, 16, 1>},
-    {4, 16, 2, launch_pencil<4, 16, 2>}, {4, 8, 2, launch_pipe<4, 8, 2>, 1},
-    {4, 16, 1, launch_pipe<4, 16, 1>, 1}, {4, 4, 4, launch_pipe<4, 4, 4>, 1},
-    {4, 16, 2, launch_pencil<4, 16, 2, true>, 0, 1}, {4, 8, 2, launch_pencil<4, 8, 2, true>, 0, 1},
-    {4, 16, 2, launch_lines<4, 16, 2, false>, 2}, {4, 16, 2, launch_lines<4, 16, 2, true>, 2, 1},
-    {4, 8, 4, launch_lines<4, 8, 4, false>, 2}, {4, 16, 1, launch_lines<4, 16, 1, true>, 2, 1},
-    {5, 8, 1, launch_pencil<5, 8, 1>},
-    {5, 8, 2, launch_pencil<5, 8, 2>},   {6, 4, 2, launch_pencil<6, 4, 2>},
-    {6, 8, 1, launch_pencil<6, 8, 1>},
+    {2, 16, 2, launch_pencil<2, 16, 2>},    {2, 16, 4, launch_lines<2, 16, 4>, 1},
+    {2, 32, 2, launch_lines<2, 32, 2>, 1},
+    {3, 16, 2, launch_pencil<3, 16, 2>},    {3, 16, 2, launch_lines<3, 16, 2>, 1},
+    {3, 8, 4, launch_lines<3, 8, 4>, 1},
+    {4, 8, 2, launch_pencil<4, 8, 2>},      {4, 16, 2, launch_pencil<4, 16, 2>},
+    {4, 16, 2, launch_lines<4, 16, 2>, 1},  {4, 8, 4, launch_lines<4, 8, 4>, 1},
+    {4, 8, 2, launch_lines<4, 8, 2>, 1},    {4, 4, 8, launch_lines<4, 4, 8>, 1},
+    {5, 8, 2, launch_pencil<5, 8, 2>},      {5, 8, 2, launch_lines<5, 8, 2>, 1},
+    {5, 4, 4, launch_lines<5, 4, 4>, 1},
+    {6, 4, 2, launch_pencil<6, 4, 2>},      {6, 8, 1, launch_lines<6, 8, 1>, 1},
+    {6, 4, 2, launch_lines<6, 4, 2>, 1},
 };
 constexpr int kNumPencil = sizeof(kPencil) / sizeof(kPencil[0]);
 
-// default choice before tuning: the most layers per CTA that fit nz
+// default choice before tuning: the line-exchange variant with the most
+// layers per CTA that fit nz (ties: more CTAs per SM), else the fewest layers
 static int pencil_default(int N, int nz) {
   int best = -1;
   for (int v = 0; v < kNumPencil; ++v) {
-    if (kPencil[v].N != N || kPencil[v].kind || kPencil[v].approx_rcp) continue;
+    if (kPencil[v].N != N || kPencil[v].kind != 1) continue;
     if (best < 0) { best = v; continue; }
     const PencilVariant& a = kPencil[v];
     const PencilVariant& b = kPencil[best];
@@ -1251,6 +1025,8 @@ struct IncArgs {
   const int* qt_ptr;
   const int* qt_src;
   const float* qt_w;
+  const int4* qt_rec_src;
+  const float4* qt_rec_w;
   const float* Minv_h;
   const float* Minv_z;
   const float* q32;   // mirror of q_n
@@ -1267,26 +1043,43 @@ template <int STAGE>
 __device__ __forceinline__ void inc_body(const IncArgs& A, const int gidx, int& bad) {
   const int h = (int)((unsigned)gidx / (unsigned)A.NZ);
   const int kz = gidx - h * A.NZ;
-  // The values this node updates are loaded before the gather and before any
-  // store, so that their memory latency overlaps the gather's.
+  // Stages 1 and 2 update d or q in place: their values are loaded before
+  // the gather and before any store, so that the loads are not ordered after
+  // the stores of the other fields and their latency overlaps the gather's.
   float dprev[kFields], q32v[kFields];
   double qv[kFields];
 #pragma unroll
   for (int fl = 0; fl < kFields; ++fl) {
     const long long o = (long long)fl * A.NG + gidx;
     if (STAGE > 0) dprev[fl] = A.d[o];
-    if (STAGE < 2) q32v[fl] = __ldg(A.q32 + o);
-    else qv[fl] = A.q[o];
+    if (STAGE == 1) q32v[fl] = __ldg(A.q32 + o);
+    if (STAGE == 2) qv[fl] = A.q[o];
   }
-  const int beg = __ldg(A.qt_ptr + h), end = __ldg(A.qt_ptr + h + 1);
   const float s = A.cdt * (__ldg(A.Minv_h + h) * __ldg(A.Minv_z + kz));
   const bool lid = (kz == 0) || (kz == A.NZ - 1);
   float acc[kFields] = {0, 0, 0, 0, 0};
-  for (int e = beg; e < end; ++e) {
-    const float w = __ldg(A.qt_w + e);
-    const float* p = A.rc + (long long)__ldg(A.qt_src + e) * kFields * A.NZr + kz;
+  // Q_h^T gather, in the order of the CSR lists: from the compact record
+  // (sources and weights known after one load each), else from the lists
+  const int4 s4 = __ldg(A.qt_rec_src + h);
+  if (s4.x >= 0) {
+    const float4 w4 = __ldg(A.qt_rec_w + h);
+    const int src[4] = {s4.x, s4.y, s4.z, s4.w};
+    const float ww[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-    for (int fl = 0; fl < kFields; ++fl) acc[fl] = fmaf(w, __ldg(p + fl * A.NZr), acc[fl]);
+    for (int e = 0; e < 4; ++e) {
+      if (src[e] < 0) break;
+      const float* p = A.rc + (long long)src[e] * kFields * A.NZr + kz;
+#pragma unroll
+      for (int fl = 0; fl < kFields; ++fl) acc[fl] = fmaf(ww[e], __ldg(p + fl * A.NZr), acc[fl]);
+    }
+  } else {
+    const int beg = __ldg(A.qt_ptr + h), end = __ldg(A.qt_ptr + h + 1);
+    for (int e = beg; e < end; ++e) {
+      const float w = __ldg(A.qt_w + e);
+      const float* p = A.rc + (long long)__ldg(A.qt_src + e) * kFields * A.NZr + kz;
+#pragma unroll
+      for (int fl = 0; fl < kFields; ++fl) acc[fl] = fmaf(w, __ldg(p + fl * A.NZr), acc[fl]);
+    }
   }
 #pragma unroll
   for (int fl = 0; fl < kFields; ++fl) {
@@ -1295,7 +1088,7 @@ __device__ __forceinline__ void inc_body(const IncArgs& A, const int gidx, int& 
     const float dn = (STAGE == 0) ? inc : fmaf(A.bcoef, dprev[fl], inc);
     if (STAGE < 2) {
       A.d[o] = dn;
-      A.qs32[o] = q32v[fl] + dn;
+      A.qs32[o] = (STAGE == 0 ? __ldg(A.q32 + o) : q32v[fl]) + dn;
     } else {
       const double qn = qv[fl] + f2d_bits(dn);
       A.q[o] = qn;
@@ -1330,6 +1123,8 @@ int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float
     B.qt_ptr = D.qt_ptr;
     B.qt_src = D.qt_src;
     B.qt_w = D.qt_w32;
+    B.qt_rec_src = reinterpret_cast<const int4*>(D.qt_rec_src);
+    B.qt_rec_w = reinterpret_cast<const float4*>(D.qt_rec_w);
     B.Minv_h = D.Minv_h32;
     B.Minv_z = D.Minv_z32;
     B.q32 = q32;
@@ -1386,7 +1181,6 @@ int autotune_pencil(Mesh& m, const sem_params& p, const float* q32, int reps, se
     out->layers_per_cta[k] = kPencil[v].KL;
     out->min_ctas_per_sm[k] = kPencil[v].MB;
     out->kind[k] = kPencil[v].kind;
-    out->approx_rcp[k] = kPencil[v].approx_rcp;
     out->ms[k] = ms;
     if (best < 0 || ms < best_ms) {
       best = v;
@@ -1449,11 +1243,11 @@ volume_batch_mixed(const VolArgs* __restrict__ insts, const int* __restrict__ in
     const int2 tl = tiles[tile];
     const VolArgs& A = insts[tl.x];
     switch (inst_N[tl.x]) {
-      case 2: pencil_body<2, batch_kl(2, BT)>(A, tl.y, smem, threadIdx.x); break;
-      case 3: pencil_body<3, batch_kl(3, BT)>(A, tl.y, smem, threadIdx.x); break;
-      case 4: pencil_body<4, batch_kl(4, BT)>(A, tl.y, smem, threadIdx.x); break;
-      case 5: pencil_body<5, batch_kl(5, BT)>(A, tl.y, smem, threadIdx.x); break;
-      case 6: pencil_body<6, batch_kl(6, BT)>(A, tl.y, smem, threadIdx.x); break;
+      case 2: lines_body<2, batch_kl(2, BT)>(A, tl.y, smem, threadIdx.x); break;
+      case 3: lines_body<3, batch_kl(3, BT)>(A, tl.y, smem, threadIdx.x); break;
+      case 4: lines_body<4, batch_kl(4, BT)>(A, tl.y, smem, threadIdx.x); break;
+      case 5: lines_body<5, batch_kl(5, BT)>(A, tl.y, smem, threadIdx.x); break;
+      case 6: lines_body<6, batch_kl(6, BT)>(A, tl.y, smem, threadIdx.x); break;
       default: break;
     }
   }
@@ -1461,12 +1255,12 @@ volume_batch_mixed(const VolArgs* __restrict__ insts, const int* __restrict__ in
 
 template <int BT>
 static size_t batch_smem() {
-  size_t m = pencil_smem<2, batch_kl(2, BT)>();
-  m = std::max(m, pencil_smem<3, batch_kl(3, BT)>());
-  m = std::max(m, pencil_smem<4, batch_kl(4, BT)>());
-  m = std::max(m, pencil_smem<5, batch_kl(5, BT)>());
-  m = std::max(m, pencil_smem<6, batch_kl(6, BT)>());
-  return m;
+  size_t m = lines_smem_floats<2, batch_kl(2, BT)>();
+  m = std::max(m, (size_t)lines_smem_floats<3, batch_kl(3, BT)>());
+  m = std::max(m, (size_t)lines_smem_floats<4, batch_kl(4, BT)>());
+  m = std::max(m, (size_t)lines_smem_floats<5, batch_kl(5, BT)>());
+  m = std::max(m, (size_t)lines_smem_floats<6, batch_kl(6, BT)>());
+  return m * sizeof(float);
 }
 
 // Launch configurations of the batched element kernel (threads per CTA and
@@ -1718,6 +1512,8 @@ int batch_step_mixed(void* h, const sem_params& p, double* const* q, float* cons
         B.qt_ptr = D.qt_ptr;
         B.qt_src = D.qt_src;
         B.qt_w = D.qt_w32;
+        B.qt_rec_src = reinterpret_cast<const int4*>(D.qt_rec_src);
+        B.qt_rec_w = reinterpret_cast<const float4*>(D.qt_rec_w);
         B.Minv_h = D.Minv_h32;
         B.Minv_z = D.Minv_z32;
         B.q32 = q32[k];

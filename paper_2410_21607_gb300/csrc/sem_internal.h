@@ -111,6 +111,8 @@ struct DeviceTables {
   float* Minv_h32 = nullptr;    // float32 copies for the mixed form
   float* Minv_z32 = nullptr;
   float* qt_w32 = nullptr;
+  int* qt_rec_src = nullptr;    // [NH][4]: Q_h^T sources of h when it has at most 4 (-1: unused), else -2 (use the CSR lists)
+  float* qt_rec_w = nullptr;    // [NH][4]: their float32 weights
   float* hang_w32 = nullptr;
   float* mirror = nullptr;      // float32 state mirror scratch [5][NG]
   double* Mh = nullptr;

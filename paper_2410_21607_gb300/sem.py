@@ -72,7 +72,7 @@ class ProfileOut(C.Structure):
 
 class TuneOut(C.Structure):
     _fields_ = [("n_variants", C.c_int), ("chosen", C.c_int), ("layers_per_cta", C.c_int * 16),
-                ("min_ctas_per_sm", C.c_int * 16), ("kind", C.c_int * 16), ("approx_rcp", C.c_int * 16),
+                ("min_ctas_per_sm", C.c_int * 16), ("kind", C.c_int * 16),
                 ("ms", C.c_double * 16)]
 
 
@@ -383,14 +383,13 @@ def sem_profile_end():
 
 def sem_autotune(mesh, params, q32, reps=5, stream=None):
     """Time the element-kernel variants on this mesh and keep the fastest.
-    Returns [(layers_per_cta, min_ctas_per_sm, ms, kind, approx_rcp)] and the
-    chosen index (kind 0: z-pencil, 1: persistent z-pencil, 2: line exchange)."""
+    Returns [(layers_per_cta, min_ctas_per_sm, ms, kind)] and the chosen index
+    (kind 0: z-pencil kernel, 1: line-exchange kernel)."""
     _f32(q32, mesh.field_shape)
     out = TuneOut()
     _check(LIB.sem_autotune(mesh.h, C.byref(params), _ptr(q32), int(reps), C.byref(out),
                             _stream(stream)))
-    rows = [(out.layers_per_cta[k], out.min_ctas_per_sm[k], out.ms[k], out.kind[k],
-             out.approx_rcp[k])
+    rows = [(out.layers_per_cta[k], out.min_ctas_per_sm[k], out.ms[k], out.kind[k])
             for k in range(out.n_variants)]
     return rows, out.chosen
 
