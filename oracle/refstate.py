@@ -23,14 +23,19 @@ import numpy as np
 
 class Params:
     """Physical constants (Sec. 2: g = 9.81; the gas constants are unstated
-    in the paper, the values below are the ones used throughout)."""
+    in the paper, the values below are the ones used throughout), and the
+    sub-grid and absorbing-layer terms of the paper's runs (Sec. 4), off by
+    default: smag_cs is the Smagorinsky coefficient C_s (the paper's 0.21),
+    sponge_gamma and sponge_depth the Rayleigh layer's gamma and z_d (the
+    paper's 1.0 and 4 km)."""
 
     def __init__(self, g=9.81, R_d=287.0, c_p=1004.0, p00=1.0e5, f=5.0e-5,
-                 theta_s=300.0, N_bv=0.01):
+                 theta_s=300.0, N_bv=0.01, smag_cs=0.0, sponge_gamma=0.0, sponge_depth=4000.0):
         self.g, self.R_d, self.c_p, self.p00 = g, R_d, c_p, p00
         self.c_v = c_p - R_d
         self.gamma = c_p / self.c_v
         self.f, self.theta_s, self.N_bv = f, theta_s, N_bv
+        self.smag_cs, self.sponge_gamma, self.sponge_depth = smag_cs, sponge_gamma, sponge_depth
 
 
 def reference_state(z, prm):

@@ -18,6 +18,26 @@ Two equation sets share one discretisation (Sec. 3):
 
 In both, p' = p0 expm1(gamma log1p((rho theta)'/(rho theta)0)).
 
+Optional terms of the paper's runs (Sec. 4), off unless the parameters set them:
+
+* Rayleigh absorbing layer ("Boundary conditions"): every equation gets
+  -R(z) q' with q' its own perturbation variable (for "C" the conservative
+  perturbations, for "NC" rho', u, v, w, theta') and
+      R(z) = min(1, max(0, gamma sin^2(pi/2 (1 - (z_top - z)/z_d))))
+  for z >= z_top - z_d and R = 0 below (reading of the garbled formula: the
+  layer is the top z_d of the domain, z_top = Lz; the term damps, so it
+  enters with a minus sign; gamma is a rate in 1/s).  It is a collocated
+  source, r_l += w_l J (-R q'_l), like the other sources.
+* Horizontal Smagorinsky-Lilly stress ("Sub-grid models"): with the
+  element-local velocity gradients, S_h the horizontal strain of (u, v)
+  (S_xx = du/dx, S_yy = dv/dy, S_xy = (du/dy + dv/dx)/2),
+      nu_t = (C_s Delta)^2 sqrt(2 (S_xx^2 + S_yy^2 + 2 S_xy^2)),
+  Delta = (hx + hy) / (2N) the mean horizontal node spacing of the element,
+  the momentum equations get -div(tau) with the horizontal stress
+  tau_{i,d} = -2 nu_t S_{i,d} for i, d in {x, y} and tau_{z,d} = -nu_t dw/dx_d,
+  d in {x, y} (reading: the vertical part is the PBL scheme's, out of
+  scope), in weak form with the flux rho tau ("C") or tau ("NC").
+
 Discretisation: the divergence terms are taken in weak form,
     r_l = sum_k w_k J grad psi_l(x_k) . F(x_k)   (+ boundary terms, see below),
 the remaining (source, advective and pressure-gradient) terms in collocated
@@ -36,6 +56,15 @@ from .refstate import reference_state, pressure_perturbation
 
 FIELDS_C = ("rho'", "rho u", "rho v", "rho w", "(rho theta)'")
 FIELDS_NC = ("rho'", "u", "v", "w", "theta'")
+
+
+def sponge_rate(z, Lz, prm):
+    """R(z) of the Rayleigh absorbing layer (Sec. 4), zero below Lz - z_d."""
+    z = np.asarray(z, dtype=np.float64)
+    zd = prm.sponge_depth
+    a = np.pi / 2.0 * (1.0 - (Lz - z) / zd)
+    R = np.minimum(1.0, np.maximum(0.0, prm.sponge_gamma * np.sin(a) ** 2))
+    return np.where(z >= Lz - zd, R, 0.0)
 
 
 def element_residual(mesh, qL, prm, eqset="C"):
@@ -89,6 +118,27 @@ def element_residual(mesh, qL, prm, eqset="C"):
             r[2, es] = W_ * sv
             r[3, es] = W_ * sw
             r[4, es] = W_ * st
+        if getattr(prm, "smag_cs", 0.0) > 0.0:
+            if eqset == "C":
+                uu, vv, ww, rfac = q[1] / rho, q[2] / rho, q[3] / rho, rho
+            else:
+                uu, vv, ww, rfac = q[1], q[2], q[3], 1.0
+            gu, gv, gw = grad(uu), grad(vv), grad(ww)
+            Sxx, Syy, Sxy = gu[0], gv[1], 0.5 * (gu[1] + gv[0])
+            hx = mesh.Lx / (mesh.nx << int(lev))
+            hy = mesh.Ly / (mesh.ny << int(lev))
+            delta = (hx + hy) / (2.0 * mesh.N)
+            nut = (prm.smag_cs * delta) ** 2 * np.sqrt(2.0 * (Sxx ** 2 + Syy ** 2 + 2.0 * Sxy ** 2))
+            k = rfac * nut
+            zero = np.zeros_like(k)
+            # -div(tau) in weak form: flux rho tau (C) or tau (NC)
+            r[1, es] += weak((-2.0 * k * Sxx, -2.0 * k * Sxy, zero))
+            r[2, es] += weak((-2.0 * k * Sxy, -2.0 * k * Syy, zero))
+            r[3, es] += weak((-k * gw[0], -k * gw[1], zero))
+        if getattr(prm, "sponge_gamma", 0.0) > 0.0:
+            Rz = sponge_rate(z[es], mesh.Lz, prm)
+            for fl in range(5):
+                r[fl, es] += W_ * (-Rz * q[fl])
     return r
 
 

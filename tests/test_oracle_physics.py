@@ -1,0 +1,169 @@
+"""Pins of the oracle's optional terms of the paper's runs (Sec. 4): the
+Rayleigh absorbing layer and the horizontal Smagorinsky-Lilly stress.
+
+Each pin is a property the discretisation must have, not a retyping of the
+formula: closed-form tendencies of fields the element polynomials hold
+exactly (they fix the factors 2 and sqrt(2), the gradient scale, the filter
+width and the sign), the kinetic-energy identity of the weak stress
+divergence (it fixes the pairing of fluxes with test-function gradients) and
+the pointwise action of the lumped collocated sponge.
+"""
+import numpy as np
+import pytest
+
+from oracle import mesh, refstate, rhs
+from synth.vortex import random_state
+from tests.test_oracle_mesh import two_level_leaves
+
+L, LZ = 300e3, 12e3
+
+
+def visc_tendency(m, q, prm, eqset="C"):
+    """Tendency of the added terms alone (rhs with them minus rhs without)."""
+    off = refstate.Params(f=prm.f)
+    return rhs.rhs(m, q, prm, eqset) - rhs.rhs(m, q, off, eqset)
+
+
+def test_sponge_rate_profile():
+    prm = refstate.Params(sponge_gamma=0.8, sponge_depth=4000.0)
+    z = np.array([LZ, LZ - 2000.0, LZ - 4000.0, LZ - 6000.0, 0.0])
+    R = rhs.sponge_rate(z, LZ, prm)
+    # gamma sin^2(pi/2) at the lid, gamma sin^2(pi/4) half-way, zero at and
+    # below the bottom of the layer (where the literal formula would rise again)
+    np.testing.assert_allclose(R, [0.8, 0.4, 0.0, 0.0, 0.0], atol=1e-15)
+    strong = refstate.Params(sponge_gamma=3.0)
+    assert rhs.sponge_rate(np.array([LZ]), LZ, strong)[0] == 1.0     # clipped to 1
+
+
+@pytest.mark.parametrize("eqset", ["C", "NC"])
+def test_lumped_sponge_acts_pointwise_on_a_conforming_mesh(eqset):
+    """A collocated source assembled with the lumped mass is the pointwise
+    value at every global node: -R(z) q' for every field."""
+    m = mesh.OracleMesh(L, L, LZ, 3, 3, 3, 4)
+    prm = refstate.Params(sponge_gamma=0.01, sponge_depth=6000.0)
+    q = random_state(m.XG, LZ, 3, eqset)
+    T = visc_tendency(m, q, prm, eqset)
+    expect = -rhs.sponge_rate(m.XG[:, 2], LZ, prm)[None, :] * q
+    expect[3, m.z_bottom | m.z_top] = 0.0
+    np.testing.assert_allclose(T, expect, rtol=1e-10, atol=1e-12 * np.abs(expect).max())
+    assert np.count_nonzero(expect[0]) > 0 and np.all(expect[:, m.XG[:, 2] < LZ - 6000.0] == 0.0)
+
+
+def _interior(m, Ly=L):
+    x, y = m.XG[:, 0], m.XG[:, 1]
+    return (np.abs(np.abs(x) - L / 2) > 1.0) & (np.abs(np.abs(y) - Ly / 2) > 1.0)
+
+
+def _polynomial_state(m, u, v, w):
+    """Conservative state with rho' = 0, momentum rho0(z) times the velocity."""
+    rho0 = refstate.reference_state(m.XG[:, 2], refstate.Params())["rho0"]
+    q = np.zeros((5, m.NG))
+    q[1], q[2], q[3] = rho0 * u, rho0 * v, rho0 * w
+    return q, rho0
+
+
+@pytest.mark.parametrize("nx", [3, 4])
+def test_smagorinsky_closed_form_tendencies(nx):
+    """Velocities of degree <= 2 in x, y: the stress flux is a polynomial the
+    quadrature integrates exactly, so at interior nodes the tendency equals
+    the analytic -div(rho tau) to round-off.  C_s is chosen so that
+    C_s Delta = L0 with Delta = (hx + hy) / (2N)."""
+    N, Ly = 4, 0.8 * L                   # hx != hy: Delta is their mean over N
+    m = mesh.OracleMesh(L, Ly, LZ, nx, nx, 2, N, periodic=(False, False))
+    L0 = 500.0
+    prm = refstate.Params(f=0.0, smag_cs=L0 / ((L / nx + Ly / nx) / (2 * N)))
+    x, y = m.XG[:, 0], m.XG[:, 1]
+    inner = _interior(m, Ly) & ~(m.z_bottom | m.z_top)
+    a, b = 2e-5, 1e-11                   # u_x = a + 2 b x > 0 on the box
+    # 1. u = a x + b x^2: nu_t = sqrt(2) L0^2 u_x, d(rho u)/dt = 4 sqrt(2) rho0 L0^2 u_x u_xx
+    q, rho0 = _polynomial_state(m, a * x + b * x ** 2, 0 * x, 0 * x)
+    T = visc_tendency(m, q, prm)
+    ux = a + 2 * b * x
+    exp1 = 4 * np.sqrt(2) * rho0 * L0 ** 2 * ux * (2 * b)
+    np.testing.assert_allclose(T[1, inner], exp1[inner], rtol=1e-9)
+    assert np.abs(T[2:4, inner]).max() <= 1e-9 * np.abs(exp1).max()
+    # 2. the same along y for v
+    q, rho0 = _polynomial_state(m, 0 * y, a * y + b * y ** 2, 0 * y)
+    T = visc_tendency(m, q, prm)
+    exp2 = 4 * np.sqrt(2) * rho0 * L0 ** 2 * (a + 2 * b * y) * (2 * b)
+    np.testing.assert_allclose(T[2, inner], exp2[inner], rtol=1e-9)
+    # 3. shear u = c (y + L)^2: S_xy = c (y + L), nu_t = 2 L0^2 S_xy,
+    #    d(rho u)/dt = d/dy (4 rho0 L0^2 S_xy^2) = 8 rho0 L0^2 c^2 (y + L)
+    c = 1e-10
+    q, rho0 = _polynomial_state(m, c * (y + L) ** 2, 0 * y, 0 * y)
+    T = visc_tendency(m, q, prm)
+    exp3 = 8 * rho0 * L0 ** 2 * c ** 2 * (y + L)
+    np.testing.assert_allclose(T[1, inner], exp3[inner], rtol=1e-9)
+    # the v equation sees d/dx of the same stress, which is zero
+    assert np.abs(T[2, inner]).max() <= 1e-9 * np.abs(exp3).max()
+    # 4. vertical velocity diffused by the horizontal viscosity of u = a x:
+    #    w = d x^2, d(rho w)/dt = d/dx (rho0 nu_t 2 d x) = 2 sqrt(2) rho0 L0^2 a d
+    d = 1e-10
+    q, rho0 = _polynomial_state(m, a * x, 0 * x, d * x ** 2)
+    T = visc_tendency(m, q, prm)
+    exp4 = 2 * np.sqrt(2) * rho0 * L0 ** 2 * a * d
+    np.testing.assert_allclose(T[3, inner], exp4[inner], rtol=1e-9)
+
+
+def _energy_identity(m, q, prm, eqset):
+    """Sum over global nodes of u . R_visc (assembled, before the lid rule)
+    and the quadrature of -rho nu_t (2 S_h:S_h + |grad_h w|^2)."""
+    off = refstate.Params(f=prm.f)
+    qL = m.to_local(q)
+    dr = rhs.element_residual(m, qL, prm, eqset) - rhs.element_residual(m, qL, off, eqset)
+    R = m.assemble(dr)
+    ref = refstate.reference_state(m.XG[:, 2], prm)
+    if eqset == "C":
+        rho = ref["rho0"] + q[0]
+        vel = q[1:4] / rho
+    else:
+        vel = q[1:4]
+    lhs = np.sum(vel * R[1:4])
+    # right-hand side from element-local gradients
+    refl = refstate.reference_state(m.X[:, :, 2], prm)
+    rhsum = 0.0
+    for lev in np.unique(m.level):
+        es = np.nonzero(m.level == lev)[0]
+        G = m.element_ops(int(lev))
+        if eqset == "C":
+            rl = refl["rho0"][es] + qL[0, es]
+            ul, vl, wl = qL[1, es] / rl, qL[2, es] / rl, qL[3, es] / rl
+        else:
+            rl = 1.0
+            ul, vl, wl = qL[1, es], qL[2, es], qL[3, es]
+        du = [ul @ G[dd].T for dd in range(2)]
+        dv = [vl @ G[dd].T for dd in range(2)]
+        dw = [wl @ G[dd].T for dd in range(2)]
+        sxx, syy, sxy = du[0], dv[1], 0.5 * (du[1] + dv[0])
+        ss = sxx ** 2 + syy ** 2 + 2 * sxy ** 2
+        delta = (L / (m.nx << int(lev)) + L / (m.ny << int(lev))) / (2 * m.N)
+        nut = (prm.smag_cs * delta) ** 2 * np.sqrt(2 * ss)
+        rhsum += np.sum(m.wJ[es] * rl * nut * (2 * ss + dw[0] ** 2 + dw[1] ** 2))
+    return lhs, -rhsum
+
+
+@pytest.mark.parametrize("eqset,nc", [("C", False), ("NC", False), ("NC", True)])
+def test_smagorinsky_energy_identity_and_dissipation(eqset, nc):
+    """The weak stress divergence paired with the (continuous) velocity is
+    minus the quadrature of rho nu_t (2 S_h:S_h + |grad_h w|^2) <= 0.  Holds
+    on non-conforming meshes for the velocity set, where the velocity is the
+    interpolated field itself."""
+    m = (mesh.OracleMesh(L, L, LZ, 4, 4, 2, 4, leaves=two_level_leaves()) if nc
+         else mesh.OracleMesh(L, L, LZ, 3, 3, 2, 4))
+    prm = refstate.Params(smag_cs=0.21)
+    q = random_state(m.XG, LZ, 8, eqset)
+    lhs, rhs_ = _energy_identity(m, q, prm, eqset)
+    assert rhs_ < 0.0
+    assert abs(lhs - rhs_) <= 1e-10 * abs(rhs_)
+
+
+@pytest.mark.parametrize("eqset", ["C", "NC"])
+def test_physics_keep_mass_conservation_and_rest_state(eqset):
+    m = mesh.OracleMesh(L, L, LZ, 4, 4, 2, 4, leaves=two_level_leaves())
+    prm = refstate.Params(smag_cs=0.21, sponge_gamma=0.01)
+    T = rhs.rhs(m, np.zeros((5, m.NG)), prm, eqset)
+    assert np.all(T == 0.0)
+    q = random_state(m.XG, LZ, 4, eqset)
+    Tv = visc_tendency(m, q, refstate.Params(smag_cs=0.21), eqset)
+    # the stress acts on momentum only
+    assert np.all(Tv[0] == 0.0) and np.all(Tv[4] == 0.0)
