@@ -103,6 +103,18 @@ typedef struct {
   int n_thresholds;   /* criterion thresholds, one per level (Sec. 3.1) */
   int lvl_max;
   double thresholds[SEM_MAX_THRESHOLDS];
+  /* Terms of the paper's runs (Sec. 4), off at 0.  smag_cs: Smagorinsky
+   * coefficient C_s of the horizontal Smagorinsky-Lilly stress (the paper's
+   * 0.21), filter width (hx + hy) / (2N) of each element.  sponge_gamma,
+   * sponge_depth: rate gamma (1/s) and depth z_d (m) of the Rayleigh layer
+   * at the top of the domain, R(z) = min(1, gamma sin^2(pi/2 (1 - (Lz - z)/z_d)))
+   * for z >= Lz - z_d, 0 below, acting as -R(z) q' on every equation (the
+   * paper's gamma 1.0, z_d 4 km).  Both enter the element residual (the
+   * stress in weak form, the layer as a collocated source).  Not in the
+   * batched step. */
+  double smag_cs;
+  double sponge_gamma;
+  double sponge_depth;
 } sem_params;
 
 typedef struct {
@@ -113,7 +125,8 @@ typedef struct {
 const char* sem_last_error(void);
 
 /* Defaults: g 9.81, f 5e-5, R_d 287, c_p 1004, p00 1e5, theta_s 300,
- * N_bv 0.01, conservative set, FP64, thresholds [7.5, 15, 22.5] (Sec. 4.1). */
+ * N_bv 0.01, conservative set, FP64, thresholds [7.5, 15, 22.5] (Sec. 4.1),
+ * no Smagorinsky stress, no absorbing layer (sponge_depth 4000). */
 int sem_params_default(sem_params* p);
 
 /* Host only.  Builds the leaf columns (Morton order), the global node

@@ -34,7 +34,7 @@ void free_device(Mesh& m) {
   if (m.dev_id >= 0 && cur != m.dev_id) cudaSetDevice(m.dev_id);
   DeviceTables& D = *m.dev;
   void* ptrs[] = {D.hmap, D.hang_h, D.hang_w, D.qt_ptr, D.qt_src, D.qt_w, D.Minv_h, D.Minv_z,
-                  D.Mh, D.Mz, D.Minv_h32, D.Minv_z32, D.qt_w32, D.qt_rec_src, D.qt_rec_w, D.hang_w32, D.mirror, D.ref, D.ref32, D.col_level, D.xh, D.yh, D.zk, D.scratch,
+                  D.Mh, D.Mz, D.Minv_h32, D.Minv_z32, D.qt_w32, D.qt_rec_src, D.qt_rec_w, D.hang_w32, D.mirror, D.spg, D.spg32, D.ref, D.ref32, D.col_level, D.xh, D.yh, D.zk, D.scratch,
                   D.status, D.org, D.elem_cmax, D.elem_flags, D.diag_buf,
                   D.tr_comp_ptr, D.tr_nodes, D.tr_A_ptr, D.tr_A_col, D.tr_A_val, D.tr_coupled};
   for (void* p : ptrs)
@@ -174,6 +174,8 @@ static int check_params(const sem_params* p) {
     return fail(SEM_ERR_ARG, "unknown precision");
   if (p->n_thresholds < 0 || p->n_thresholds > SEM_MAX_THRESHOLDS)
     return fail(SEM_ERR_ARG, "n_thresholds out of range");
+  if (!(p->smag_cs >= 0.0) || !(p->sponge_gamma >= 0.0) || (p->sponge_gamma > 0.0 && !(p->sponge_depth > 0.0)))
+    return fail(SEM_ERR_ARG, "smag_cs and sponge_gamma must be >= 0, sponge_depth > 0");
   return SEM_OK;
 }
 
@@ -210,6 +212,9 @@ int sem_params_default(sem_params* p) {
   p->thresholds[0] = 7.5;
   p->thresholds[1] = 15.0;
   p->thresholds[2] = 22.5;
+  p->smag_cs = 0.0;
+  p->sponge_gamma = 0.0;
+  p->sponge_depth = 4000.0;
   return SEM_OK;
 }
 

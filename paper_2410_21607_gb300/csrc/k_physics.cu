@@ -1,0 +1,304 @@
+// Terms of the paper's runs (Sec. 4): the horizontal Smagorinsky-Lilly
+// stress ("Sub-grid models") and the Rayleigh absorbing layer ("Boundary
+// conditions"), as an element pass that adds to the column residuals the
+// element kernel has written, before the gather.
+//
+//   physics_column<N, EQ, R>: one CTA per leaf column marches up its layers.
+//     Per element node it gathers the state, forms the velocity, and
+//     - stress: the element-local horizontal velocity gradients, the strain
+//       S_xx = du/dx, S_yy = dv/dy, S_xy = (du/dy + dv/dx)/2, the eddy
+//       viscosity nu_t = (C_s Delta)^2 sqrt(2 (S_xx^2 + S_yy^2 + 2 S_xy^2))
+//       with Delta = (hx + hy)/(2N), and the weak divergence of the fluxes
+//       rho tau (EQ 0, conservative set) or tau (EQ 1), tau_{i,d} = -2 nu_t
+//       S_{i,d} for the horizontal momentum and tau_{z,d} = -nu_t dw/dx_d,
+//       d in {x, y};
+//     - absorbing layer: the collocated source w J (-R(z) q') on every field;
+//     then sums the face shared with the layer below (vertical DSS) and adds
+//     the result into r_C[column][ab][field][kz].
+//
+// R is the arithmetic type: double for the float64 form, float for the mixed
+// form (float32 mirror of the state, float32 residuals).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "sem_internal.h"
+
+namespace sem {
+namespace {
+
+__constant__ double p_w[kMaxN + 1][kMaxN + 1];
+__constant__ double p_D[kMaxN + 1][(kMaxN + 1) * (kMaxN + 1)];   // [i][m] = h_m'(xi_i)
+__constant__ double p_Dw[kMaxN + 1][(kMaxN + 1) * (kMaxN + 1)];  // [i][m] = w_m h_i'(xi_m)
+__constant__ float p_wf[kMaxN + 1][kMaxN + 1];
+__constant__ float p_Df[kMaxN + 1][(kMaxN + 1) * (kMaxN + 1)];
+__constant__ float p_Dwf[kMaxN + 1][(kMaxN + 1) * (kMaxN + 1)];
+
+template <typename R> struct PTab;
+template <> struct PTab<double> {
+  __device__ static double w(int N, int i) { return p_w[N][i]; }
+  __device__ static double D(int N, int k) { return p_D[N][k]; }
+  __device__ static double Dw(int N, int k) { return p_Dw[N][k]; }
+};
+template <> struct PTab<float> {
+  __device__ static float w(int N, int i) { return p_wf[N][i]; }
+  __device__ static float D(int N, int k) { return p_Df[N][k]; }
+  __device__ static float Dw(int N, int k) { return p_Dwf[N][k]; }
+};
+
+int upload_constants() {
+  static bool done = false;
+  if (done) return SEM_OK;
+  constexpr int K = (kMaxN + 1) * (kMaxN + 1);
+  double w[kMaxN + 1][kMaxN + 1] = {}, D[kMaxN + 1][K] = {}, Dw[kMaxN + 1][K] = {};
+  float wf[kMaxN + 1][kMaxN + 1] = {}, Df[kMaxN + 1][K] = {}, Dwf[kMaxN + 1][K] = {};
+  for (int N = 2; N <= kMaxN; ++N) {
+    const Basis1D& B = basis(N);
+    const int n = N + 1;
+    for (int i = 0; i < n; ++i) {
+      w[N][i] = B.w[i];
+      wf[N][i] = (float)B.w[i];
+      for (int m = 0; m < n; ++m) {
+        D[N][i * n + m] = B.D[i * n + m];
+        Dw[N][i * n + m] = B.w[m] * B.D[m * n + i];
+        Df[N][i * n + m] = (float)D[N][i * n + m];
+        Dwf[N][i * n + m] = (float)Dw[N][i * n + m];
+      }
+    }
+  }
+  SEM_CUDA_TRY(cudaMemcpyToSymbol(p_w, w, sizeof(w)));
+  SEM_CUDA_TRY(cudaMemcpyToSymbol(p_D, D, sizeof(D)));
+  SEM_CUDA_TRY(cudaMemcpyToSymbol(p_Dw, Dw, sizeof(Dw)));
+  SEM_CUDA_TRY(cudaMemcpyToSymbol(p_wf, wf, sizeof(wf)));
+  SEM_CUDA_TRY(cudaMemcpyToSymbol(p_Df, Df, sizeof(Df)));
+  SEM_CUDA_TRY(cudaMemcpyToSymbol(p_Dwf, Dwf, sizeof(Dwf)));
+  done = true;
+  return SEM_OK;
+}
+
+struct PhysArgs {
+  const void* q;        // state [5][NG]: float64, or the float32 mirror (mixed form)
+  void* rc;             // column residuals (same type)
+  const int* hmap;
+  const int* hang_h;
+  const void* hang_w;   // hanging-row weights (same type)
+  const int* col_level;
+  const void* ref;      // reference state [NZ][kRef] (same type)
+  const void* spg;      // absorbing-layer rate [NZ] (same type), null when off
+  int nz, NZ, NZr, smag;
+  long long NG;
+  double cs;
+  double geo[16][4];    // hx, hy, hz, J per level
+};
+
+template <typename R>
+__device__ __forceinline__ R geo_at(const PhysArgs& A, int l, int k) { return (R)A.geo[l][k]; }
+
+template <int N, int EQ, typename R>
+__global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
+physics_column(const PhysArgs A) {
+  constexpr int n1 = N + 1, Nq = n1 * n1, P = n1 * n1 * n1;
+  __shared__ R sU[3][P];
+  __shared__ R sF[6][P];
+  __shared__ R sC[2][kFields][Nq];
+  const int col = blockIdx.x, t = threadIdx.x;
+  const bool act = t < P;
+  const int i = t % n1, j = (t / n1) % n1, c = t / Nq;
+  const int ab = i + n1 * j;
+  const int lev = A.col_level[col];
+  const R hx = geo_at<R>(A, lev, 0), hy = geo_at<R>(A, lev, 1), hz = geo_at<R>(A, lev, 2);
+  const R J = geo_at<R>(A, lev, 3);
+  const R gx = (R)2 / hx, gy = (R)2 / hy;
+  const R sx = hy * hz * (R)0.25, sy = hx * hz * (R)0.25;   // J dxi/dx, J deta/dy
+  const R delta = (hx + hy) / (R)(2 * N);
+  const R csd = (R)A.cs * delta;
+  const R cs2 = csd * csd;
+  const int hm = act ? A.hmap[(long long)col * Nq + ab] : 0;
+  const R wi = act ? PTab<R>::w(N, i) : (R)0, wj = act ? PTab<R>::w(N, j) : (R)0;
+  const R wc = act ? PTab<R>::w(N, c) : (R)0;
+  const R wJ = wi * wj * wc * J;
+  const R* q = (const R*)A.q;
+  const R* hw = (const R*)A.hang_w;
+  const R* ref = (const R*)A.ref;
+  const R* spg = (const R*)A.spg;
+  R* rc = (R*)A.rc;
+  for (int k = 0; k < A.nz; ++k) {
+    const int kz = k * N + c;
+    R r[kFields] = {0, 0, 0, 0, 0};
+    R rfac = (R)1;
+    if (act) {
+      R v[kFields];
+      if (hm >= 0) {
+        const R* p = q + (long long)hm * A.NZ + kz;
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) v[f] = p[(long long)f * A.NG];
+      } else {
+        const int hk = -1 - hm;
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) v[f] = (R)0;
+#pragma unroll
+        for (int m = 0; m < n1; ++m) {
+          const R wm = hw[hk * n1 + m];
+          const R* p = q + (long long)A.hang_h[hk * n1 + m] * A.NZ + kz;
+#pragma unroll
+          for (int f = 0; f < kFields; ++f) v[f] += wm * p[(long long)f * A.NG];
+        }
+      }
+      R u = v[1], vv = v[2], w = v[3];
+      if (EQ == 0) {
+        const R rho = ref[(long long)kz * kRef + 3] + v[0];
+        const R inv = (R)1 / rho;
+        u *= inv;
+        vv *= inv;
+        w *= inv;
+        rfac = rho;
+      }
+      if (spg) {
+        const R Rz = spg[kz];
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) r[f] = wJ * (-Rz * v[f]);
+      }
+      if (A.smag) {
+        sU[0][t] = u;
+        sU[1][t] = vv;
+        sU[2][t] = w;
+      }
+    }
+    if (A.smag) {
+      __syncthreads();
+      if (act) {
+        R ux = 0, uy = 0, vx = 0, vy = 0, wx = 0, wy = 0;
+#pragma unroll
+        for (int m = 0; m < n1; ++m) {
+          const R Di = PTab<R>::D(N, i * n1 + m), Dj = PTab<R>::D(N, j * n1 + m);
+          const int lx = m + n1 * j + Nq * c, ly = i + n1 * m + Nq * c;
+          ux += Di * sU[0][lx];
+          uy += Dj * sU[0][ly];
+          vx += Di * sU[1][lx];
+          vy += Dj * sU[1][ly];
+          wx += Di * sU[2][lx];
+          wy += Dj * sU[2][ly];
+        }
+        ux *= gx; vx *= gx; wx *= gx;
+        uy *= gy; vy *= gy; wy *= gy;
+        const R sxx = ux, syy = vy, sxy = (R)0.5 * (uy + vx);
+        const R nut = cs2 * sqrt((R)2 * (sxx * sxx + syy * syy + (R)2 * sxy * sxy));
+        const R kv = rfac * nut;
+        const R ax = wj * wc * sx, ay = wi * wc * sy;
+        sF[0][t] = ax * ((R)-2 * kv * sxx);
+        sF[1][t] = ay * ((R)-2 * kv * sxy);
+        sF[2][t] = ax * ((R)-2 * kv * sxy);
+        sF[3][t] = ay * ((R)-2 * kv * syy);
+        sF[4][t] = ax * (-kv * wx);
+        sF[5][t] = ay * (-kv * wy);
+      }
+      __syncthreads();
+      if (act) {
+#pragma unroll
+        for (int m = 0; m < n1; ++m) {
+          const R Dwi = PTab<R>::Dw(N, i * n1 + m), Dwj = PTab<R>::Dw(N, j * n1 + m);
+          const int lx = m + n1 * j + Nq * c, ly = i + n1 * m + Nq * c;
+          r[1] += Dwi * sF[0][lx] + Dwj * sF[1][ly];
+          r[2] += Dwi * sF[2][lx] + Dwj * sF[3][ly];
+          r[3] += Dwi * sF[4][lx] + Dwj * sF[5][ly];
+        }
+      }
+    }
+    if (act) {
+      // vertical direct stiffness summation inside the column, then add
+      if (c == 0 && k > 0) {
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) r[f] += sC[(k - 1) & 1][f][ab];
+      }
+      if (c == N && k < A.nz - 1) {
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) sC[k & 1][f][ab] = r[f];
+      } else {
+        R* dst = rc + ((long long)((long long)col * Nq + ab) * kFields) * A.NZr + kz;
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) dst[(long long)f * A.NZr] += r[f];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int N, typename R>
+void launch_n(const PhysArgs& A, int eq, int ncol, cudaStream_t st) {
+  constexpr int threads = ((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32;
+  if (eq == SEM_EQ_CONSERVATIVE) physics_column<N, 0, R><<<ncol, threads, 0, st>>>(A);
+  else physics_column<N, 1, R><<<ncol, threads, 0, st>>>(A);
+}
+
+// R(z) of the absorbing layer per level, rebuilt when gamma or z_d change
+int ensure_sponge(Mesh& m, const sem_params& p) {
+  DeviceTables& D = *m.dev;
+  if (D.spg && D.spg_key[0] == p.sponge_gamma && D.spg_key[1] == p.sponge_depth) return SEM_OK;
+  std::vector<double> R(m.NZ);
+  std::vector<float> R32(m.NZ);
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < m.NZ; ++k) {
+    const double z = m.zk[k];
+    const double a = 0.5 * pi * (1.0 - (m.Lz - z) / p.sponge_depth);
+    const double s = std::sin(a);
+    double r = std::min(1.0, std::max(0.0, p.sponge_gamma * s * s));
+    if (!(z >= m.Lz - p.sponge_depth)) r = 0.0;
+    R[k] = r;
+    R32[k] = (float)r;
+  }
+  if (!D.spg) {
+    SEM_CUDA_TRY(cudaMalloc((void**)&D.spg, (size_t)m.NZ * sizeof(double)));
+    SEM_CUDA_TRY(cudaMalloc((void**)&D.spg32, (size_t)m.NZ * sizeof(float)));
+  }
+  SEM_CUDA_TRY(cudaMemcpy(D.spg, R.data(), R.size() * sizeof(double), cudaMemcpyHostToDevice));
+  SEM_CUDA_TRY(cudaMemcpy(D.spg32, R32.data(), R32.size() * sizeof(float), cudaMemcpyHostToDevice));
+  D.spg_key[0] = p.sponge_gamma;
+  D.spg_key[1] = p.sponge_depth;
+  return SEM_OK;
+}
+
+}  // namespace
+
+int launch_physics(Mesh& m, const sem_params& p, const void* q, bool mixed, void* scratch,
+                   cudaStream_t st) {
+  int rc = upload_constants();
+  if (rc) return rc;
+  DeviceTables& D = *m.dev;
+  const bool sponge = p.sponge_gamma > 0.0;
+  if (sponge && (rc = ensure_sponge(m, p))) return rc;
+  PhysArgs A;
+  A.q = q;
+  A.rc = scratch ? scratch : D.scratch;
+  A.hmap = D.hmap;
+  A.hang_h = D.hang_h;
+  A.hang_w = mixed ? (const void*)D.hang_w32 : (const void*)D.hang_w;
+  A.col_level = D.col_level;
+  A.ref = mixed ? (const void*)D.ref32 : (const void*)D.ref;
+  A.spg = sponge ? (mixed ? (const void*)D.spg32 : (const void*)D.spg) : nullptr;
+  A.nz = m.nz;
+  A.NZ = m.NZ;
+  A.NZr = m.NZr();
+  A.smag = p.smag_cs > 0.0;
+  A.NG = m.NG;
+  A.cs = p.smag_cs;
+  for (int l = 0; l < 16; ++l) {
+    A.geo[l][0] = m.hx(l);
+    A.geo[l][1] = m.hy(l);
+    A.geo[l][2] = m.hz();
+    A.geo[l][3] = m.hx(l) * m.hy(l) * m.hz() * 0.125;
+  }
+  ProfScope ps("physics", st);
+  const int ncol = (int)m.Ncol();
+  switch (m.N) {
+    case 2: mixed ? launch_n<2, float>(A, p.eqset, ncol, st) : launch_n<2, double>(A, p.eqset, ncol, st); break;
+    case 3: mixed ? launch_n<3, float>(A, p.eqset, ncol, st) : launch_n<3, double>(A, p.eqset, ncol, st); break;
+    case 4: mixed ? launch_n<4, float>(A, p.eqset, ncol, st) : launch_n<4, double>(A, p.eqset, ncol, st); break;
+    case 5: mixed ? launch_n<5, float>(A, p.eqset, ncol, st) : launch_n<5, double>(A, p.eqset, ncol, st); break;
+    case 6: mixed ? launch_n<6, float>(A, p.eqset, ncol, st) : launch_n<6, double>(A, p.eqset, ncol, st); break;
+    default: return fail(SEM_ERR_UNSUPPORTED, "order N not compiled");
+  }
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
+
+}  // namespace sem

@@ -1118,6 +1118,7 @@ int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float
     VolArgs A = make_vol_args(m, p, stage == 0 ? (const void*)q32 : (const void*)qs32, true, nullptr);
     if ((rc = launch_pencil_n(A, m.N, m.nz, st, m.pencil_variant))) return rc;
     SEM_CUDA_TRY(cudaGetLastError());
+    if (physics_on(p) && (rc = launch_physics(m, p, A.q, true, nullptr, st))) return rc;
     IncArgs B;
     B.rc = (const float*)D.scratch;
     B.qt_ptr = D.qt_ptr;
@@ -1484,6 +1485,8 @@ static void batch_enqueue(BatchImpl* b, cudaStream_t st) {
 int batch_step_mixed(void* h, const sem_params& p, double* const* q, float* const* q32,
                      float* const* work32, const double* dt, int use_graph, cudaStream_t st) {
   BatchImpl* b = (BatchImpl*)h;
+  if (physics_on(p))
+    return fail(SEM_ERR_UNSUPPORTED, "batched step: no Smagorinsky stress or absorbing layer (smag_cs, sponge_gamma)");
   const int n = (int)b->meshes.size();
   std::vector<const void*> key;
   for (int k = 0; k < n; ++k) {
@@ -1634,6 +1637,9 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
     default: return fail(SEM_ERR_UNSUPPORTED, "order N not compiled");
   }
   SEM_CUDA_TRY(cudaGetLastError());
+  if (physics_on(p) &&
+      (rc = launch_physics(m, p, mixed ? (const void*)qs32 : (const void*)s.qs, mixed, s.scratch, st)))
+    return rc;
   DssArgs B;
   B.rc = s.scratch ? s.scratch : D.scratch;
   B.qt_ptr = D.qt_ptr;

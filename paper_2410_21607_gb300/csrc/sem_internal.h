@@ -143,6 +143,10 @@ struct DeviceTables {
   // the params the ref tables were built with
   double ref_key[8] = {0};
   bool ref_valid = false;
+  // absorbing-layer rate R(z) per level (float64 and float32) and its key
+  double* spg = nullptr;
+  float* spg32 = nullptr;
+  double spg_key[2] = {-1.0, -1.0};
 };
 constexpr int kRef = 8;  // theta0, pi0, p0, rho0, rhotheta0, dtheta0/dz, 1/(rho theta)0, z
 
@@ -188,6 +192,11 @@ int autotune_pencil(Mesh& m, const sem_params& p, const float* q32, int reps, se
 int select_pencil(Mesh& m, int row);
 int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float* work32, double dt,
                       cudaStream_t st);
+// terms of the paper's runs (k_physics.cu): adds the Smagorinsky stress and the
+// absorbing layer to the column residuals in `scratch` (null: the mesh's own)
+inline bool physics_on(const sem_params& p) { return p.smag_cs > 0.0 || p.sponge_gamma > 0.0; }
+int launch_physics(Mesh& m, const sem_params& p, const void* q, bool mixed, void* scratch,
+                   cudaStream_t st);
 
 // per-kernel event timing (profile.cpp); -1 when profiling is off
 int prof_begin_kernel(const char* name, cudaStream_t st);

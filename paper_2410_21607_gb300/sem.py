@@ -62,7 +62,8 @@ class Params(C.Structure):
     _fields_ = [("g", C.c_double), ("f", C.c_double), ("R_d", C.c_double), ("c_p", C.c_double),
                 ("p00", C.c_double), ("theta_s", C.c_double), ("N_bv", C.c_double),
                 ("eqset", C.c_int), ("precision", C.c_int), ("n_thresholds", C.c_int),
-                ("lvl_max", C.c_int), ("thresholds", C.c_double * SEM_MAX_THRESHOLDS)]
+                ("lvl_max", C.c_int), ("thresholds", C.c_double * SEM_MAX_THRESHOLDS),
+                ("smag_cs", C.c_double), ("sponge_gamma", C.c_double), ("sponge_depth", C.c_double)]
 
 
 class ProfileOut(C.Structure):

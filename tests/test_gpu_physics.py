@@ -1,0 +1,123 @@
+"""GPU parity of the terms of the paper's runs (Sec. 4): the horizontal
+Smagorinsky stress and the Rayleigh absorbing layer, through the C ABI,
+against the oracle (oracle/rhs.py).
+
+The added terms are checked on their own (tendency with them minus tendency
+without, on both sides) as well as in the total, so that a small term cannot
+hide under the tolerance of the inviscid part.  Float64: total 1e-12, added
+terms 1e-9 (the difference of two float64 tendencies).  Mixed: total 1e-4,
+added terms 1e-4 times the ratio of the total to the added norm (float32
+rounding of the total carries into the difference).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import mesh as om, refstate, rhs as orhs, rk as ork  # noqa: E402
+from synth.vortex import random_state, vortex_state  # noqa: E402
+from tests.helpers import group_rel_l2, node_perm  # noqa: E402
+from tests.test_gpu_parity import MESHES, dev, full_fields, host, make_pair  # noqa: E402
+
+PHYS = dict(smag_cs=0.21, sponge_gamma=0.02, sponge_depth=6000.0)
+
+
+@pytest.fixture(scope="module")
+def sem():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_21607_gb300 import build
+    build.build()
+    from paper_2410_21607_gb300 import sem as s
+    return s
+
+
+def _gpu_rhs(sem, m, q, eqset, prec, **phys):
+    p = sem.sem_params_default(eqset=0 if eqset == "C" else 1, precision=prec, **phys)
+    out = torch.empty_like(q)
+    sem.sem_rhs(m, p, q, out)
+    return host(out)
+
+
+@pytest.mark.parametrize("name", list(MESHES))
+@pytest.mark.parametrize("eqset", ["C", "NC"])
+def test_physics_rhs_fp64_matches_oracle(sem, name, eqset):
+    m, o, X, perm = make_pair(sem, **MESHES[name])
+    q_o = random_state(o.XG, o.Lz, 21, eqset)
+    prm = refstate.Params(**PHYS)
+    T_o = orhs.rhs(o, q_o, prm, eqset)
+    dT_o = T_o - orhs.rhs(o, q_o, refstate.Params(), eqset)
+    q = dev(q_o[:, perm])
+    T = _gpu_rhs(sem, m, q, eqset, 0, **PHYS)
+    dT = T - _gpu_rhs(sem, m, q, eqset, 0)
+    assert np.all(group_rel_l2(T, T_o[:, perm]) <= 1e-12)
+    err = group_rel_l2(dT, dT_o[:, perm])
+    assert np.all(err <= 1e-9), err
+    assert np.linalg.norm(dT_o[1]) > 0 and np.linalg.norm(dT_o[0]) > 0
+
+
+@pytest.mark.parametrize("name", ["uniform-6x6x4-N4", "twolevel-N4"])
+@pytest.mark.parametrize("eqset", ["C", "NC"])
+def test_physics_rhs_mixed_matches_oracle(sem, name, eqset):
+    m, o, X, perm = make_pair(sem, **MESHES[name])
+    q_o = random_state(o.XG, o.Lz, 22, eqset)
+    prm = refstate.Params(**PHYS)
+    T_o = orhs.rhs(o, q_o, prm, eqset)
+    dT_o = T_o - orhs.rhs(o, q_o, refstate.Params(), eqset)
+    q = dev(q_o[:, perm])
+    T = _gpu_rhs(sem, m, q, eqset, 1, **PHYS)
+    dT = T - _gpu_rhs(sem, m, q, eqset, 1)
+    assert np.all(group_rel_l2(T, T_o[:, perm]) <= 1e-4)
+    ratio = group_rel_l2(T_o, 0 * T_o) / np.maximum(group_rel_l2(dT_o, 0 * dT_o), 1e-300)
+    err = group_rel_l2(dT, dT_o[:, perm])
+    assert np.all(err <= 1e-4 * np.maximum(ratio, 1.0)), (err, ratio)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_physics_steps_match_oracle(sem, prec):
+    """Ten SSP-RK3 steps of 1 s with both terms on the two-level mesh, in the
+    float64 form (sem_step) and the mixed increment form (sem_step_mixed)."""
+    m, o, X, perm = make_pair(sem, **MESHES["twolevel-N4"])
+    q_o = vortex_state(o.XG, o.Lz)
+    prm = refstate.Params(**PHYS)
+    p = sem.sem_params_default(precision=prec, **PHYS)
+    q = dev(q_o[:, perm])
+    if prec == 0:
+        w1, w2 = torch.empty_like(q), torch.empty_like(q)
+        for _ in range(10):
+            sem.sem_step(m, p, q, w1, w2, 1.0)
+    else:
+        q32 = torch.empty(q.shape, dtype=torch.float32, device="cuda")
+        work = torch.empty((10, m.NG), dtype=torch.float32, device="cuda")
+        sem.sem_mirror(m, q, q32)
+        for _ in range(10):
+            sem.sem_step_mixed(m, p, q, q32, work, 1.0)
+    for _ in range(10):
+        q_o = ork.rk_step(o, prm, q_o, 1.0)
+    z = X[:, 2]
+    err = group_rel_l2(full_fields(host(q), z), full_fields(q_o[:, perm], z))
+    assert np.all(err <= (1e-12 if prec == 0 else 1e-4)), err
+    assert sem.sem_status(m) == 0
+
+
+def test_physics_rejected_by_the_batched_step(sem):
+    m = sem.sem_mesh_create(300e3, 300e3, 12e3, 3, 3, 2, 4)
+    b = sem.sem_batch_create([m])
+    q = torch.zeros(5, m.NG, dtype=torch.float64, device="cuda")
+    q32 = torch.zeros(5, m.NG, dtype=torch.float32, device="cuda")
+    work = torch.zeros(10, m.NG, dtype=torch.float32, device="cuda")
+    p = sem.sem_params_default(precision=sem.SEM_PREC_MIXED, smag_cs=0.21)
+    with pytest.raises(sem.SemError) as e:
+        sem.sem_batch_step_mixed(b, p, [q], [q32], [work], [1.0])
+    assert e.value.code == sem.SEM_ERR_UNSUPPORTED
+
+
+def test_bad_physics_params_rejected(sem):
+    m = sem.sem_mesh_create(300e3, 300e3, 12e3, 3, 3, 2, 4)
+    q = torch.zeros(5, m.NG, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(q)
+    for bad in (dict(smag_cs=-0.1), dict(sponge_gamma=-1.0), dict(sponge_gamma=1.0, sponge_depth=0.0)):
+        with pytest.raises(sem.SemError) as e:
+            sem.sem_rhs(m, sem.sem_params_default(**bad), q, out)
+        assert e.value.code == sem.SEM_ERR_ARG
