@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-amr", action="store_true")
+    ap.add_argument("--no-physics", action="store_true")
     ap.add_argument("--kernel-row", type=int, default=None,
                     help="use this row of the element-kernel variant table instead of autotuning "
                          "(for profiler runs, whose per-launch overhead distorts the timings)")
@@ -467,6 +468,31 @@ def main():
                 "max_mean_wind_rel_err": abs(dm["max_mean_wind"] - dd["max_mean_wind"])
                 / dd["max_mean_wind"]}
 
+    # the same step with the terms of the paper's runs (Sec. 4): horizontal
+    # Smagorinsky stress C_s = 0.21, absorbing layer gamma = 1/s, z_d = 4 km
+    physics_res = None
+    if not a.no_physics and a.form == "mixed":
+        pphys = dict(smag_cs=0.21, sponge_gamma=1.0, sponge_depth=4000.0)
+        pp = sem.sem_params_default(precision=sem.SEM_PREC_MIXED, **pphys)
+        bp = new_bufs()
+        for _ in range(3):
+            bp = step(bp, pp)
+        torch.cuda.synchronize()
+        kp = max(3, min(a.steps, 10))
+        sem.sem_profile_begin()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(kp):
+            bp = step(bp, pp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pr = sem.sem_profile_end()
+        ms_p = e0.elapsed_time(e1) / kp
+        physics_res = {"params": pphys, "ms_per_step": ms_p, "value": dof_stage * 3 / (ms_p * 1e-3),
+                       "step_time_ratio": ms_p / ms,
+                       "kernels_ms_avg": {k: v[1] / max(v[0], 1) for k, v in pr.items()},
+                       "status": sem.sem_status(m)}
+
     # end to end through the C ABI with host buffers (pinned), copies timed
     hq = torch.from_numpy(q0_host).pin_memory()
     hout = torch.empty_like(hq).pin_memory()
@@ -518,7 +544,7 @@ def main():
                 "speedup_mixed_over_fp64": fp64_ms / ms},
             "gate": gate,
             "roofline": roof, "kernels": kernels, "autotune": tune, "batched": batched,
-            "learned": learned_res, "amr": amr_res,
+            "learned": learned_res, "amr": amr_res, "physics": physics_res,
             "cpu_baseline": cpu,
             "e2e": {"value": dof_stage * 3 * world / (e2e_ms * 1e-3), "unit": "DOF-updates/s",
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
