@@ -17,7 +17,8 @@
 //     the result into r_C[column][ab][field][kz].
 //
 // R is the arithmetic type: double for the float64 form, float for the mixed
-// form (float32 mirror of the state, float32 residuals).
+// form (float32 mirror of the state, float32 residuals).  The mixed form of
+// the conservative set uses physics_lines (below) instead.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -257,6 +258,242 @@ int ensure_sponge(Mesh& m, const sem_params& p) {
   return SEM_OK;
 }
 
+// Mixed form, conservative set: the same terms with the thread layout of the
+// line-exchange element kernel (coalesced z-line loads and residual updates).
+// Thread (layer kk, line ab) owns the vertical line of N+1 nodes of its
+// element; node (i, j, c) keeps 9 float32 components (u, v, w, then the x and
+// y derivatives, later the weighted x and y stress fluxes) at
+// kk LS + (i + (N+1) j) LW + comp (N+1) + c.  Phases, separated by barriers:
+//  A  z-line owner: state -> rho, u, v, w (and the layer source in registers);
+//  B  x-line / y-line owners: du/dx, dv/dx, dw/dx (comps 3-5), du/dy, dv/dy,
+//     dw/dy (comps 6-8) of their line, written onto its nodes;
+//  C  z-line owner: nu_t and the weighted fluxes of rho tau, in place;
+//  D  x-line / y-line owners: weak contraction of their line's fluxes, in place;
+//  E  z-line owner: sums, vertical DSS, residual update.
+template <int N>
+__host__ __device__ constexpr int plines_lw() { return (9 * (N + 1)) | 1; }
+template <int N, int KL>
+__host__ __device__ constexpr int plines_ls() {
+  return (N + 1) * (N + 1) * plines_lw<N>() +
+         ((32 / KL - ((N + 1) * (N + 1) * plines_lw<N>()) % 32) % 32 + 32) % 32;
+}
+template <int N, int KL>
+__host__ __device__ constexpr int plines_smem_floats() {
+  return KL * plines_ls<N, KL>() + kFields * KL * (N + 1) * (N + 1) + 2 * kFields * (N + 1) * (N + 1);
+}
+
+template <int N, int KL, int MB>
+__global__ void __launch_bounds__(KL * (N + 1) * (N + 1), MB)
+physics_lines(const PhysArgs A) {
+  constexpr int n1 = N + 1, Nq = n1 * n1;
+  constexpr int LW = plines_lw<N>(), LS = plines_ls<N, KL>();
+  extern __shared__ __align__(16) float smem[];
+  float* sV = smem;                       // [kk][LS]: node components
+  float* sT = sV + KL * LS;               // [f][kk][ab]: layer source of the top node
+  float* sP = sT + kFields * KL * Nq;     // [2][f][ab]: top-node carry between chunks
+  const int col = blockIdx.x, t = threadIdx.x;
+  const int kk = t % KL, ab = t / KL;
+  const int i = ab % n1, j = ab / n1;
+  const int lc = ab % n1, lo = ab / n1;   // x-line (j, c) = (lo, lc), y-line (i, c) = (lo, lc)
+  const int lev = A.col_level[col];
+  const float hx = (float)A.geo[lev][0], hy = (float)A.geo[lev][1], hz = (float)A.geo[lev][2];
+  const float J = (float)A.geo[lev][3];
+  const float gx = 2.f / hx, gy = 2.f / hy;
+  const float sx = hy * hz * 0.25f, sy = hx * hz * 0.25f;
+  const float csd = (float)A.cs * ((hx + hy) / (float)(2 * N));
+  const float cs2 = csd * csd;
+  const int hm = A.hmap[(long long)col * Nq + ab];
+  const float wi = p_wf[N][i], wj = p_wf[N][j];
+  const float* q = (const float*)A.q;
+  const float* hw = (const float*)A.hang_w;
+  const float* ref = (const float*)A.ref;
+  const float* spg = (const float*)A.spg;
+  float* rc = (float*)A.rc;
+  const int nchunk = (A.nz + KL - 1) / KL;
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const int k = ch * KL + kk;
+    const bool act = k < A.nz;
+    const int kz0 = k * N;
+    float r[kFields][n1];
+#pragma unroll
+    for (int f = 0; f < kFields; ++f)
+#pragma unroll
+      for (int c = 0; c < n1; ++c) r[f][c] = 0.f;
+    float rho[n1];
+    float* zV = sV + kk * LS + ab * LW;   // this thread's z-line, + comp n1 + c
+    if (act) {
+#pragma unroll
+      for (int c = 0; c < n1; ++c) {
+        const int kz = kz0 + c;
+        float v[kFields];
+        if (hm >= 0) {
+          const float* pq = q + (long long)hm * A.NZ + kz;
+#pragma unroll
+          for (int f = 0; f < kFields; ++f) v[f] = __ldg(pq + (long long)f * A.NG);
+        } else {
+          const int hk = -1 - hm;
+#pragma unroll
+          for (int f = 0; f < kFields; ++f) v[f] = 0.f;
+#pragma unroll
+          for (int m = 0; m < n1; ++m) {
+            const float wm = __ldg(hw + hk * n1 + m);
+            const float* pq = q + (long long)__ldg(A.hang_h + hk * n1 + m) * A.NZ + kz;
+#pragma unroll
+            for (int f = 0; f < kFields; ++f) v[f] = fmaf(wm, __ldg(pq + (long long)f * A.NG), v[f]);
+          }
+        }
+        rho[c] = __ldg(ref + (long long)kz * kRef + 3) + v[0];
+        const float inv = 1.f / rho[c];
+        zV[0 * n1 + c] = v[1] * inv;
+        zV[1 * n1 + c] = v[2] * inv;
+        zV[2 * n1 + c] = v[3] * inv;
+        if (spg) {
+          const float wJ = wi * wj * p_wf[N][c] * J;
+          const float Rz = __ldg(spg + kz);
+#pragma unroll
+          for (int f = 0; f < kFields; ++f) r[f][c] = wJ * (-Rz * v[f]);
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) sT[(f * KL + kk) * Nq + ab] = r[f][N];
+    }
+    if (A.smag) {
+      __syncthreads();
+      if (act) {
+        // B: derivatives along the thread's x-line (nodes (m, lo, lc)) and y-line (nodes (lo, m, lc))
+        float* bx = sV + kk * LS + lo * n1 * LW + lc;
+        float* by = sV + kk * LS + lo * LW + lc;
+#pragma unroll
+        for (int cp = 0; cp < 3; ++cp) {
+          float F[n1], G[n1];
+#pragma unroll
+          for (int m = 0; m < n1; ++m) {
+            F[m] = bx[m * LW + cp * n1];
+            G[m] = by[m * n1 * LW + cp * n1];
+          }
+#pragma unroll
+          for (int o = 0; o < n1; ++o) {
+            float ax_ = 0.f, ay_ = 0.f;
+#pragma unroll
+            for (int m = 0; m < n1; ++m) {
+              ax_ = fmaf(p_Df[N][o * n1 + m], F[m], ax_);
+              ay_ = fmaf(p_Df[N][o * n1 + m], G[m], ay_);
+            }
+            bx[o * LW + (3 + cp) * n1] = ax_ * gx;
+            by[o * n1 * LW + (6 + cp) * n1] = ay_ * gy;
+          }
+        }
+      }
+      __syncthreads();
+      if (act) {
+        // C: eddy viscosity and weighted fluxes of rho tau at the thread's nodes
+#pragma unroll
+        for (int c = 0; c < n1; ++c) {
+          const float ux = zV[3 * n1 + c], vx = zV[4 * n1 + c], wx = zV[5 * n1 + c];
+          const float uy = zV[6 * n1 + c], vy = zV[7 * n1 + c], wy = zV[8 * n1 + c];
+          const float sxy = 0.5f * (uy + vx);
+          const float nut = cs2 * sqrtf(2.f * (ux * ux + vy * vy + 2.f * sxy * sxy));
+          const float kv = rho[c] * nut;
+          const float wc = p_wf[N][c];
+          const float ax = wj * wc * sx, ay = wi * wc * sy;
+          zV[3 * n1 + c] = ax * (-2.f * kv * ux);
+          zV[4 * n1 + c] = ax * (-2.f * kv * sxy);
+          zV[5 * n1 + c] = ax * (-kv * wx);
+          zV[6 * n1 + c] = ay * (-2.f * kv * sxy);
+          zV[7 * n1 + c] = ay * (-2.f * kv * vy);
+          zV[8 * n1 + c] = ay * (-kv * wy);
+        }
+      }
+      __syncthreads();
+      if (act) {
+        // D: weak contraction of the line's fluxes, written back onto its nodes
+        float* bx = sV + kk * LS + lo * n1 * LW + lc;
+        float* by = sV + kk * LS + lo * LW + lc;
+#pragma unroll
+        for (int cp = 0; cp < 3; ++cp) {
+          float F[n1], G[n1];
+#pragma unroll
+          for (int m = 0; m < n1; ++m) {
+            F[m] = bx[m * LW + (3 + cp) * n1];
+            G[m] = by[m * n1 * LW + (6 + cp) * n1];
+          }
+#pragma unroll
+          for (int o = 0; o < n1; ++o) {
+            float ax_ = 0.f, ay_ = 0.f;
+#pragma unroll
+            for (int m = 0; m < n1; ++m) {
+              ax_ = fmaf(p_Dwf[N][o * n1 + m], F[m], ax_);
+              ay_ = fmaf(p_Dwf[N][o * n1 + m], G[m], ay_);
+            }
+            bx[o * LW + (3 + cp) * n1] = ax_;
+            by[o * n1 * LW + (6 + cp) * n1] = ay_;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (act) {
+      // E: sums at the thread's nodes, vertical DSS, residual update
+      if (A.smag) {
+#pragma unroll
+        for (int cp = 0; cp < 3; ++cp)
+#pragma unroll
+          for (int c = 0; c < n1; ++c) r[1 + cp][c] += zV[(3 + cp) * n1 + c] + zV[(6 + cp) * n1 + c];
+      }
+      if (kk > 0) {
+        const float* pV = sV + (kk - 1) * LS + ab * LW;
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) {
+          float add = sT[(f * KL + kk - 1) * Nq + ab];
+          if (A.smag && f >= 1 && f <= 3) add += pV[(2 + f) * n1 + N] + pV[(5 + f) * n1 + N];
+          r[f][0] += add;
+        }
+      } else if (ch > 0) {
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) r[f][0] += sP[((ch - 1) & 1) * kFields * Nq + f * Nq + ab];
+      }
+      if (kk == KL - 1) {
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) sP[(ch & 1) * kFields * Nq + f * Nq + ab] = r[f][N];
+      }
+      float* dst = rc + ((long long)((long long)col * Nq + ab) * kFields) * A.NZr + kz0;
+      const bool top = (k == A.nz - 1);
+      const bool all = spg != nullptr;   // the stress alone touches the momentum only
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) {
+        if (!all && (f == 0 || f == 4)) continue;
+        float* df = dst + (long long)f * A.NZr;
+        if (N == 4) {
+          float4 o = *reinterpret_cast<float4*>(df);
+          o.x += r[f][0];
+          o.y += r[f][1];
+          o.z += r[f][2];
+          o.w += r[f][3];
+          *reinterpret_cast<float4*>(df) = o;
+        } else {
+#pragma unroll
+          for (int c = 0; c < N; ++c) df[c] += r[f][c];
+        }
+        if (top) df[N] += r[f][N];
+      }
+    }
+    if (ch + 1 < nchunk) __syncthreads();
+  }
+}
+
+template <int N, int KL, int MB>
+int launch_lines(const PhysArgs& A, int ncol, cudaStream_t st) {
+  const size_t sm = sizeof(float) * plines_smem_floats<N, KL>();
+  static bool attr = false;
+  if (!attr) {
+    SEM_CUDA_TRY(cudaFuncSetAttribute(physics_lines<N, KL, MB>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr = true;
+  }
+  physics_lines<N, KL, MB><<<ncol, KL * (N + 1) * (N + 1), sm, st>>>(A);
+  return SEM_OK;
+}
+
 }  // namespace
 
 int launch_physics(Mesh& m, const sem_params& p, const void* q, bool mixed, void* scratch,
@@ -289,6 +526,19 @@ int launch_physics(Mesh& m, const sem_params& p, const void* q, bool mixed, void
   }
   ProfScope ps("physics", st);
   const int ncol = (int)m.Ncol();
+  if (mixed && p.eqset == SEM_EQ_CONSERVATIVE) {
+    switch (m.N) {
+      case 2: rc = launch_lines<2, 16, 4>(A, ncol, st); break;
+      case 3: rc = launch_lines<3, 16, 2>(A, ncol, st); break;
+      case 4: rc = launch_lines<4, 8, 4>(A, ncol, st); break;
+      case 5: rc = launch_lines<5, 4, 4>(A, ncol, st); break;
+      case 6: rc = launch_lines<6, 4, 2>(A, ncol, st); break;
+      default: return fail(SEM_ERR_UNSUPPORTED, "order N not compiled");
+    }
+    if (rc) return rc;
+    SEM_CUDA_TRY(cudaGetLastError());
+    return SEM_OK;
+  }
   switch (m.N) {
     case 2: mixed ? launch_n<2, float>(A, p.eqset, ncol, st) : launch_n<2, double>(A, p.eqset, ncol, st); break;
     case 3: mixed ? launch_n<3, float>(A, p.eqset, ncol, st) : launch_n<3, double>(A, p.eqset, ncol, st); break;
