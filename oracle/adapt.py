@@ -6,7 +6,17 @@ per refinement level,
     refine  (adapt = +1) if some k has C_{k,e} > threshold(lvl(e)+1) and lvl(e) < lvl_max,
     coarsen (adapt = -1) if every k has C_{k,e} <= threshold(lvl(e)) and lvl(e) > 0,
     otherwise adapt = 0.
-The criterion variable is the velocity magnitude (Sec. 4.1).  Algorithm 3's
+The criterion variable of the paper's runs is the velocity magnitude
+(Sec. 4.1).  Sec. 3.1 lets the variable depend on the level (C^l), and the
+paper names vorticity and potential vorticity, alone or combined, as the
+candidates for further criteria (Sec. 1, Sec. 5); `variables[l]` picks the
+variable whose element maximum is compared with threshold(l+1):
+  "speed"      |u| (3-D velocity magnitude),
+  "vorticity"  |dv/dx - du/dy| (vertical relative vorticity),
+  "pv"         |(curl u + f e_z) . grad theta| / rho (dry Ertel potential
+               vorticity, theta the full potential temperature),
+with element-local derivatives of the element polynomials (hanging nodes
+take the interpolated values, as everywhere).  Algorithm 3's
 loop writes adapt(e) once per (node, level) pair, so a later pair can
 overwrite an earlier refine decision with 0; the rule above is the statement
 in the text, which the loop is meant to implement, and it does not depend on
@@ -41,16 +51,69 @@ def criterion_speed(mesh, qG, prm, eqset="C"):
     return s
 
 
-def criterion_flags(mesh, qG, prm, thresholds, lvl_max, eqset="C"):
-    """adapt(e) in {-1, 0, 1} for every element; also returns max_k C_{k,e}."""
+def _velocity_theta(mesh, qL, prm, eqset):
+    """u, v, w, full theta and rho at every local node, each (Ne, P)."""
+    ref = reference_state(mesh.X[:, :, 2], prm)
+    if eqset == "C":
+        rho = ref["rho0"] + qL[0]
+        u, v, w = qL[1] / rho, qL[2] / rho, qL[3] / rho
+        theta = (ref["rhotheta0"] + qL[4]) / rho
+    else:
+        rho = ref["rho0"] + qL[0]
+        u, v, w = qL[1], qL[2], qL[3]
+        theta = ref["theta0"] + qL[4]
+    return u, v, w, theta, rho
+
+
+def _element_gradient(mesh, phi):
+    """Element-local x, y, z derivatives of nodal values phi (Ne, P)."""
+    out = [np.zeros_like(phi) for _ in range(3)]
+    for lev in np.unique(mesh.level):
+        es = np.nonzero(mesh.level == lev)[0]
+        G = mesh.element_ops(int(lev))
+        for d in range(3):
+            out[d][es] = phi[es] @ G[d].T
+    return out
+
+
+def criterion_vorticity(mesh, qG, prm, eqset="C"):
+    """C_{k,e} = |dv/dx - du/dy| at every local node, shape (Ne, P)."""
+    u, v, w, _, _ = _velocity_theta(mesh, mesh.to_local(qG), prm, eqset)
+    gu, gv = _element_gradient(mesh, u), _element_gradient(mesh, v)
+    return np.abs(gv[0] - gu[1])
+
+
+def criterion_pv(mesh, qG, prm, eqset="C"):
+    """C_{k,e} = |(curl u + f e_z) . grad theta| / rho, shape (Ne, P)."""
+    u, v, w, th, rho = _velocity_theta(mesh, mesh.to_local(qG), prm, eqset)
+    gu, gv, gw, gt = (_element_gradient(mesh, a) for a in (u, v, w, th))
+    wx = gw[1] - gv[2]
+    wy = gu[2] - gw[0]
+    wz = gv[0] - gu[1] + prm.f
+    return np.abs(wx * gt[0] + wy * gt[1] + wz * gt[2]) / rho
+
+
+CRITERIA = {"speed": criterion_speed, "vorticity": criterion_vorticity, "pv": criterion_pv}
+
+
+def criterion_flags(mesh, qG, prm, thresholds, lvl_max, eqset="C", variables=None):
+    """adapt(e) in {-1, 0, 1} for every element; also returns max_k C_{k,e}
+    of the variable of the element's refinement test (threshold(lvl+1), or
+    threshold(lvl) at lvl_max).  variables[l] names the variable compared
+    with threshold(l+1) (default: speed at every level)."""
     thr = np.asarray(thresholds, dtype=np.float64)
-    cmax = criterion_speed(mesh, qG, prm, eqset).max(axis=1)
+    if variables is None:
+        variables = ["speed"] * len(thr)
+    cm = {name: CRITERIA[name](mesh, qG, prm, eqset).max(axis=1) for name in set(variables)}
     flags = np.zeros(mesh.Ne, dtype=np.int8)
+    cmax = np.zeros(mesh.Ne)
     for e in range(mesh.Ne):
         lv = int(mesh.level[e])
-        refine = lv < lvl_max and cmax[e] > thr[lv]
-        coarsen = lv > 0 and cmax[e] <= thr[lv - 1]
+        refine = lv < lvl_max and cm[variables[lv]][e] > thr[lv]
+        coarsen = lv > 0 and cm[variables[lv - 1]][e] <= thr[lv - 1]
         flags[e] = 1 if refine else (-1 if coarsen else 0)
+        test = lv if lv < lvl_max else lv - 1
+        cmax[e] = cm[variables[test]][e] if 0 <= test < len(variables) else cm[variables[0]][e]
     return flags, cmax
 
 
