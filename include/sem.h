@@ -57,6 +57,13 @@ extern "C" {
 
 #define SEM_MAX_THRESHOLDS 8
 
+/* Criterion variables (Sec. 3.1: the variable C^l may change with the level;
+ * the paper's runs use the speed at every level, and it names vorticity and
+ * potential vorticity as candidates).  Element maxima over the nodes. */
+#define SEM_CRIT_SPEED 0      /* |u|, 3-D velocity magnitude                       */
+#define SEM_CRIT_VORTICITY 1  /* |dv/dx - du/dy|, vertical relative vorticity      */
+#define SEM_CRIT_PV 2         /* |(curl u + f e_z) . grad theta| / rho, dry Ertel PV */
+
 /* Mesh description (host).  Domain [-Lx/2, Lx/2] x [-Ly/2, Ly/2] x [0, Lz],
  * base grid nx x ny columns of nz hexahedra of order N (Sec. 3).  Refinement
  * is horizontal and by whole columns (Sec. 3.1): a leaf column is
@@ -115,6 +122,10 @@ typedef struct {
   double smag_cs;
   double sponge_gamma;
   double sponge_depth;
+  /* criterion[l]: the SEM_CRIT_* variable compared with thresholds[l], i.e.
+   * threshold(l+1) of Sec. 3.1 (default SEM_CRIT_SPEED everywhere).  The
+   * derivatives are element-local derivatives of the element polynomials. */
+  int criterion[SEM_MAX_THRESHOLDS];
 } sem_params;
 
 typedef struct {

@@ -176,6 +176,9 @@ static int check_params(const sem_params* p) {
     return fail(SEM_ERR_ARG, "n_thresholds out of range");
   if (!(p->smag_cs >= 0.0) || !(p->sponge_gamma >= 0.0) || (p->sponge_gamma > 0.0 && !(p->sponge_depth > 0.0)))
     return fail(SEM_ERR_ARG, "smag_cs and sponge_gamma must be >= 0, sponge_depth > 0");
+  for (int k = 0; k < SEM_MAX_THRESHOLDS; ++k)
+    if (p->criterion[k] < SEM_CRIT_SPEED || p->criterion[k] > SEM_CRIT_PV)
+      return fail(SEM_ERR_ARG, "unknown criterion variable");
   return SEM_OK;
 }
 

@@ -1,19 +1,39 @@
 // Criterion, diagnostics and coordinate kernels.
 //
 //   adapt_column<N, EQ>: Sec. 3.1 threshold criterion.  One CTA per leaf
-//     column; per element the velocity magnitude at every local node (hanging
-//     nodes interpolated as in the modified DSS), its maximum, and the flag
-//       +1 if max > threshold(lvl+1) and lvl < lvl_max,
-//       -1 if max <= threshold(lvl) and lvl > 0, else 0.
-//     The speed is evaluated with explicitly rounded float64 operations
-//     (sqrt(U U + V V + W W) / rho in that order, no contraction into FMA) so
-//     that the decision is taken in float64 exactly as written.
+//     column; per element the criterion variables at every local node
+//     (hanging nodes interpolated as in the modified DSS), their element
+//     maxima, and the flag
+//       +1 if max C^(lvl+1) > threshold(lvl+1) and lvl < lvl_max,
+//       -1 if max C^lvl <= threshold(lvl) and lvl > 0, else 0,
+//     with C^l the variable chosen for level l (speed by default; vertical
+//     vorticity or dry Ertel potential vorticity from element-local
+//     derivatives).  The speed is evaluated with explicitly rounded float64
+//     operations (sqrt(U U + V V + W W) / rho in that order, no contraction
+//     into FMA) so that the decision is taken in float64 exactly as written.
 //   diag_level: Sec. 4.2 diagnostics, one CTA per vertical level: maximum
 //     horizontal speed and the mass-weighted mean speed over the horizontal
 //     sub-domain |x|, |y| <= half_width, reduced in a fixed order.
+#include <algorithm>
+
 #include "sem_internal.h"
 
 namespace sem {
+
+__constant__ double a_D[kMaxN + 1][(kMaxN + 1) * (kMaxN + 1)];  // [i][m] = h_m'(xi_i)
+
+static int upload_aux_constants() {
+  static bool done = false;
+  if (done) return SEM_OK;
+  double D[kMaxN + 1][(kMaxN + 1) * (kMaxN + 1)] = {};
+  for (int N = 2; N <= kMaxN; ++N) {
+    const Basis1D& B = basis(N);
+    for (int k = 0; k < (N + 1) * (N + 1); ++k) D[N][k] = B.D[k];
+  }
+  SEM_CUDA_TRY(cudaMemcpyToSymbol(a_D, D, sizeof(D)));
+  done = true;
+  return SEM_OK;
+}
 
 struct AdaptArgs {
   const double* q;
@@ -27,7 +47,11 @@ struct AdaptArgs {
   int nz, NZ;
   long long NG;
   int lvl_max;
+  int need_grad;                  // 1: vorticity, 2: also potential vorticity
+  double f;
   double thr[SEM_MAX_THRESHOLDS];
+  int var[SEM_MAX_THRESHOLDS];    // SEM_CRIT_* per threshold
+  double gx[16], gy[16], gz;      // 2 / h per level, 2 / hz
 };
 
 template <int N, int EQ>
@@ -35,7 +59,8 @@ __global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
 adapt_column(const AdaptArgs A) {
   constexpr int n1 = N + 1, Nq = n1 * n1, P = n1 * n1 * n1;
   constexpr int NW = (P + 31) / 32;
-  __shared__ double red[NW];
+  __shared__ double red[3][NW];
+  __shared__ double sQ[4][P];     // u, v, w, theta at the element's nodes
   const int col = blockIdx.x, t = threadIdx.x;
   const bool act = t < P;
   const int i = t % n1, j = (t / n1) % n1, c = t / Nq;
@@ -43,38 +68,91 @@ adapt_column(const AdaptArgs A) {
   const int hm = act ? A.hmap[(long long)col * Nq + ab] : 0;
   const int lev = A.col_level[col];
   for (int k = 0; k < A.nz; ++k) {
-    double s = 0.0;
+    double s = 0.0, zeta = 0.0, pv = 0.0, rho = 1.0;
     if (act) {
       const int kz = k * N + c;
-      double v[4] = {0, 0, 0, 0};
+      double v[kFields] = {0, 0, 0, 0, 0};
       if (hm >= 0) {
         const double* p = A.q + (long long)hm * A.NZ + kz;
-        for (int f = 0; f < 4; ++f) v[f] = p[(long long)f * A.NG];
+        for (int f = 0; f < kFields; ++f) v[f] = p[(long long)f * A.NG];
       } else {
         const int h = -1 - hm;
         for (int m = 0; m <= N; ++m) {
           const double w = A.hang_w[h * n1 + m];
           const double* p = A.q + (long long)A.hang_h[h * n1 + m] * A.NZ + kz;
-          for (int f = 0; f < 4; ++f) v[f] = __dadd_rn(v[f], __dmul_rn(w, p[(long long)f * A.NG]));
+          for (int f = 0; f < kFields; ++f) v[f] = __dadd_rn(v[f], __dmul_rn(w, p[(long long)f * A.NG]));
         }
       }
       double ss = __dadd_rn(__dadd_rn(__dmul_rn(v[1], v[1]), __dmul_rn(v[2], v[2])), __dmul_rn(v[3], v[3]));
       s = __dsqrt_rn(ss);
-      if (EQ == 0) s = __ddiv_rn(s, __dadd_rn(A.ref[(long long)kz * kRef + 3], v[0]));
+      const double* rf = A.ref + (long long)kz * kRef;
+      rho = rf[3] + v[0];
+      if (EQ == 0) s = __ddiv_rn(s, __dadd_rn(rf[3], v[0]));
+      if (A.need_grad) {
+        if (EQ == 0) {
+          sQ[0][t] = v[1] / rho;
+          sQ[1][t] = v[2] / rho;
+          sQ[2][t] = v[3] / rho;
+          sQ[3][t] = (rf[4] + v[4]) / rho;
+        } else {
+          sQ[0][t] = v[1];
+          sQ[1][t] = v[2];
+          sQ[2][t] = v[3];
+          sQ[3][t] = rf[0] + v[4];
+        }
+      }
     }
-    // block maximum over the element's nodes
-    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
-    if ((t & 31) == 0) red[t >> 5] = s;
+    if (A.need_grad) {
+      __syncthreads();
+      if (act) {
+        // element-local derivatives d/dx (along i), d/dy (along j), d/dz (along c)
+        double d[4][3] = {};
+        for (int m = 0; m < n1; ++m) {
+          const double Di = a_D[N][i * n1 + m], Dj = a_D[N][j * n1 + m], Dc = a_D[N][c * n1 + m];
+          const int lx = m + n1 * j + Nq * c, ly = i + n1 * m + Nq * c, lz = i + n1 * j + Nq * m;
+          for (int qv = 0; qv < 4; ++qv) {
+            d[qv][0] += Di * sQ[qv][lx];
+            d[qv][1] += Dj * sQ[qv][ly];
+            d[qv][2] += Dc * sQ[qv][lz];
+          }
+        }
+        const double gx = A.gx[lev], gy = A.gy[lev], gz = A.gz;
+        for (int qv = 0; qv < 4; ++qv) {
+          d[qv][0] *= gx;
+          d[qv][1] *= gy;
+          d[qv][2] *= gz;
+        }
+        const double wz = d[1][0] - d[0][1];
+        zeta = fabs(wz);
+        if (A.need_grad > 1) {
+          const double wx = d[2][1] - d[1][2], wy = d[0][2] - d[2][0];
+          pv = fabs(wx * d[3][0] + wy * d[3][1] + (wz + A.f) * d[3][2]) / rho;
+        }
+      }
+    }
+    // block maxima over the element's nodes
+    double mv[3] = {s, zeta, pv};
+    for (int cv = 0; cv < 3; ++cv) {
+      double x = mv[cv];
+      for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+      if ((t & 31) == 0) red[cv][t >> 5] = x;
+    }
     __syncthreads();
     if (t == 0) {
-      double mx = red[0];
-      for (int w = 1; w < NW; ++w) mx = fmax(mx, red[w]);
+      double mx[3];
+      for (int cv = 0; cv < 3; ++cv) {
+        mx[cv] = red[cv][0];
+        for (int w = 1; w < NW; ++w) mx[cv] = fmax(mx[cv], red[cv][w]);
+      }
       const long long e = (long long)col * A.nz + k;
       int flag = 0;
-      if (lev < A.lvl_max && mx > A.thr[lev]) flag = 1;
-      else if (lev > 0 && mx <= A.thr[lev - 1]) flag = -1;
+      if (lev < A.lvl_max && mx[A.var[lev]] > A.thr[lev]) flag = 1;
+      else if (lev > 0 && mx[A.var[lev - 1]] <= A.thr[lev - 1]) flag = -1;
       A.flags[e] = (int8_t)flag;
-      if (A.cmax) A.cmax[e] = mx;
+      if (A.cmax) {
+        const int test = lev < A.lvl_max ? lev : lev - 1;
+        A.cmax[e] = mx[(test >= 0 && test < SEM_MAX_THRESHOLDS) ? A.var[test] : A.var[0]];
+      }
     }
     __syncthreads();
   }
@@ -106,7 +184,24 @@ int launch_adapt(Mesh& m, const sem_params& p, const double* q, int8_t* flags, d
   A.NZ = m.NZ;
   A.NG = m.NG;
   A.lvl_max = p.lvl_max;
-  for (int k = 0; k < SEM_MAX_THRESHOLDS; ++k) A.thr[k] = p.thresholds[k];
+  A.need_grad = 0;
+  for (int k = 0; k < SEM_MAX_THRESHOLDS; ++k) {
+    A.thr[k] = p.thresholds[k];
+    A.var[k] = p.criterion[k];
+    // only the thresholds the levels use decide whether derivatives are needed
+    if (k < p.n_thresholds && k < std::max(p.lvl_max, 1))
+      A.need_grad = std::max(A.need_grad, p.criterion[k] == SEM_CRIT_PV ? 2 : (p.criterion[k] == SEM_CRIT_VORTICITY ? 1 : 0));
+  }
+  A.f = p.f;
+  for (int l = 0; l < 16; ++l) {
+    A.gx[l] = 2.0 / m.hx(l);
+    A.gy[l] = 2.0 / m.hy(l);
+  }
+  A.gz = 2.0 / m.hz();
+  if (A.need_grad) {
+    int rc = upload_aux_constants();
+    if (rc) return rc;
+  }
   const int nc = (int)m.Ncol();
   switch (m.N) {
     case 2: launch_adapt_n<2>(A, nc, p.eqset, st); break;

@@ -19,6 +19,7 @@ SEM_ERR_NUMERIC, SEM_ERR_TIMEOUT, SEM_ERR_IO, SEM_ERR_UNSUPPORTED = 4, 5, 6, 7
 SEM_EQ_CONSERVATIVE, SEM_EQ_NONCONSERVATIVE = 0, 1
 SEM_PREC_FP64, SEM_PREC_MIXED = 0, 1
 SEM_MAX_THRESHOLDS = 8
+SEM_CRIT_SPEED, SEM_CRIT_VORTICITY, SEM_CRIT_PV = 0, 1, 2
 
 # every symbol include/sem.h declares
 EXPORTS = (
@@ -63,7 +64,8 @@ class Params(C.Structure):
                 ("p00", C.c_double), ("theta_s", C.c_double), ("N_bv", C.c_double),
                 ("eqset", C.c_int), ("precision", C.c_int), ("n_thresholds", C.c_int),
                 ("lvl_max", C.c_int), ("thresholds", C.c_double * SEM_MAX_THRESHOLDS),
-                ("smag_cs", C.c_double), ("sponge_gamma", C.c_double), ("sponge_depth", C.c_double)]
+                ("smag_cs", C.c_double), ("sponge_gamma", C.c_double), ("sponge_depth", C.c_double),
+                ("criterion", C.c_int * SEM_MAX_THRESHOLDS)]
 
 
 class ProfileOut(C.Structure):
@@ -181,8 +183,12 @@ def sem_params_default(**overrides):
     p = Params()
     _check(LIB.sem_params_default(C.byref(p)))
     thr = overrides.pop("thresholds", None)
+    crit = overrides.pop("criterion", None)
     for k, v in overrides.items():
         setattr(p, k, v)
+    if crit is not None:
+        for k, v in enumerate(crit):
+            p.criterion[k] = v
     if thr is not None:
         p.n_thresholds = len(thr)
         for k, v in enumerate(thr):

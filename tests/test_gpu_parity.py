@@ -216,6 +216,43 @@ def test_adapt_flags_match_oracle(sem, name):
         assert np.array_equal(sem.sem_adapt_flags_host(m, p, q), fl)
 
 
+CRIT = {"speed": 0, "vorticity": 1, "pv": 2}
+
+
+@pytest.mark.parametrize("name", ["uniform-6x6x4-N4", "twolevel-N4", "uniform-5x4x3-N6"])
+@pytest.mark.parametrize("eqset", ["C", "NC"])
+@pytest.mark.parametrize("variables", [("vorticity",) * 3, ("pv",) * 3, ("speed", "vorticity", "pv")])
+def test_adapt_flags_alternative_criteria_match_oracle(sem, name, eqset, variables):
+    """Vorticity, potential vorticity and a per-level combination (Sec. 3.1's
+    C^l): element maxima within 1e-10 and flags equal to the oracle's away
+    from ties (the derivative sums are rounded in different orders)."""
+    m, o, X, perm = make_pair(sem, **MESHES[name])
+    q_o = random_state(o.XG, o.Lz, 31, eqset, amp=0.2)
+    lv = sem.sem_mesh_leaves_host(m)
+    oleaf = {tuple(l): c for c, l in enumerate(o.leaves)}
+    emap = np.array([oleaf[tuple(l)] * o.nz + k for l in lv for k in range(o.nz)])
+    # thresholds at quantiles of each level's variable, so that every flag occurs
+    maxima = {v: adapt.CRITERIA[v](o, q_o, PRM, eqset).max(axis=1) for v in set(variables)}
+    thr = [float(np.quantile(maxima[v], qq)) * (1 + 1e-6) for v, qq in zip(variables, (0.3, 0.6, 0.9))]
+    fl_o, cmax_o = adapt.criterion_flags(o, q_o, PRM, thr, 3, eqset, variables=list(variables))
+    p = sem.sem_params_default(eqset=0 if eqset == "C" else 1, thresholds=thr, lvl_max=3,
+                               criterion=[CRIT[v] for v in variables])
+    flags = torch.empty(m.Ne, dtype=torch.int8, device="cuda")
+    cmax = torch.empty(m.Ne, dtype=torch.float64, device="cuda")
+    sem.sem_adapt_flags(m, p, dev(q_o[:, perm]), flags, cmax)
+    fl, cm = host(flags), host(cmax)
+    np.testing.assert_allclose(cm, cmax_o[emap], rtol=1e-10, atol=1e-12 * np.abs(cmax_o).max())
+    levels = o.level[emap]
+    near = np.zeros(m.Ne, dtype=bool)
+    for lvl in range(4):
+        for t_idx in (lvl - 1, lvl):          # the coarsening and the refinement test
+            if 0 <= t_idx < 3:
+                mx = maxima[variables[t_idx]][emap]
+                near |= (levels == lvl) & (np.abs(mx - thr[t_idx]) <= 1e-9 * abs(thr[t_idx]))
+    assert np.array_equal(fl[~near], fl_o[emap][~near])
+    assert len(set(fl.tolist())) >= 2
+
+
 def test_transfer_matches_oracle(sem):
     """Refine by the criterion, then coarsen everything back: both transfers
     against the oracle's (interpolation, L2 projection, continuous projection)."""
