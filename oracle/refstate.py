@@ -27,15 +27,30 @@ class Params:
     sub-grid and absorbing-layer terms of the paper's runs (Sec. 4), off by
     default: smag_cs is the Smagorinsky coefficient C_s (the paper's 0.21),
     sponge_gamma and sponge_depth the Rayleigh layer's gamma and z_d (the
-    paper's 1.0 and 4 km)."""
+    paper's 1.0 and 4 km), heat_* the synthetic heating source (off at
+    heat_q0 = 0) and time the time of the state."""
 
     def __init__(self, g=9.81, R_d=287.0, c_p=1004.0, p00=1.0e5, f=5.0e-5,
-                 theta_s=300.0, N_bv=0.01, smag_cs=0.0, sponge_gamma=0.0, sponge_depth=4000.0):
+                 theta_s=300.0, N_bv=0.01, smag_cs=0.0, sponge_gamma=0.0, sponge_depth=4000.0,
+                 heat_q0=0.0, heat_r0=27.5e3, heat_width=10.0e3, heat_rmax=60.0e3,
+                 heat_ztop=15.0e3, heat_ramp=600.0, time=0.0):
         self.g, self.R_d, self.c_p, self.p00 = g, R_d, c_p, p00
         self.c_v = c_p - R_d
         self.gamma = c_p / self.c_v
         self.f, self.theta_s, self.N_bv = f, theta_s, N_bv
         self.smag_cs, self.sponge_gamma, self.sponge_depth = smag_cs, sponge_gamma, sponge_depth
+        # synthetic latent-heating source (stand-in for the paper's observed
+        # heating, Sec. 4): peak rate heat_q0 (K/s) on the ring r = heat_r0
+        self.heat_q0, self.heat_r0, self.heat_width = heat_q0, heat_r0, heat_width
+        self.heat_rmax, self.heat_ztop, self.heat_ramp = heat_rmax, heat_ztop, heat_ramp
+        self.time = time
+
+    def at(self, time):
+        """A copy with the state's time set (the heating depends on it)."""
+        import copy
+        c = copy.copy(self)
+        c.time = time
+        return c
 
 
 def reference_state(z, prm):

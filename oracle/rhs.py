@@ -28,6 +28,14 @@ Optional terms of the paper's runs (Sec. 4), off unless the parameters set them:
   layer is the top z_d of the domain, z_top = Lz; the term damps, so it
   enters with a minus sign; gamma is a rate in 1/s).  It is a collocated
   source, r_l += w_l J (-R q'_l), like the other sources.
+* Synthetic latent heating (stand-in for the paper's observed heating,
+  Sec. 4 "Observational heating": radially confined to r <= 60 km, largest
+  at 25-30 km, introduced over the first 30 minutes by a tanh ramp):
+      Q(x, t) = q0 tanh(t / tau) exp(-((r - r0) / width)^2) sin(pi z / z_top)
+  for r <= r_max and z <= z_top (r from the domain centre), zero elsewhere,
+  a heating rate of theta in K/s: a collocated source w J rho Q on
+  (rho theta)' ("C") or w J Q on theta' ("NC"), evaluated at the time of
+  the state (prm.time).
 * Horizontal Smagorinsky-Lilly stress ("Sub-grid models"): with the
   element-local velocity gradients, S_h the horizontal strain of (u, v)
   (S_xx = du/dx, S_yy = dv/dy, S_xy = (du/dy + dv/dx)/2),
@@ -65,6 +73,14 @@ def sponge_rate(z, Lz, prm):
     a = np.pi / 2.0 * (1.0 - (Lz - z) / zd)
     R = np.minimum(1.0, np.maximum(0.0, prm.sponge_gamma * np.sin(a) ** 2))
     return np.where(z >= Lz - zd, R, 0.0)
+
+
+def heating_rate(x, y, z, prm):
+    """Q(x, t) of the synthetic heating, K/s, at points (x, y, z) and prm.time."""
+    r = np.hypot(x, y)
+    shape = np.exp(-((r - prm.heat_r0) / prm.heat_width) ** 2) * np.sin(np.pi * z / prm.heat_ztop)
+    inside = (r <= prm.heat_rmax) & (z <= prm.heat_ztop)
+    return np.where(inside, prm.heat_q0 * np.tanh(prm.time / prm.heat_ramp) * shape, 0.0)
 
 
 def element_residual(mesh, qL, prm, eqset="C"):
@@ -139,6 +155,9 @@ def element_residual(mesh, qL, prm, eqset="C"):
             Rz = sponge_rate(z[es], mesh.Lz, prm)
             for fl in range(5):
                 r[fl, es] += W_ * (-Rz * q[fl])
+        if getattr(prm, "heat_q0", 0.0) > 0.0:
+            Q = heating_rate(mesh.X[es, :, 0], mesh.X[es, :, 1], z[es], prm)
+            r[4, es] += W_ * (rho * Q if eqset == "C" else Q)
     return r
 
 

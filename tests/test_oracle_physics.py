@@ -167,3 +167,57 @@ def test_physics_keep_mass_conservation_and_rest_state(eqset):
     Tv = visc_tendency(m, q, refstate.Params(smag_cs=0.21), eqset)
     # the stress acts on momentum only
     assert np.all(Tv[0] == 0.0) and np.all(Tv[4] == 0.0)
+
+
+# ---------------------------------------------------------------------------
+# synthetic heating source and the stage times
+
+
+def test_heating_rate_profile():
+    prm = refstate.Params(heat_q0=0.005, time=1e6)
+    zt, r0, rmax = prm.heat_ztop, prm.heat_r0, prm.heat_rmax
+    Q = rhs.heating_rate(np.array([r0, 0.0, r0 + 1e3, rmax + 1.0, r0]),
+                         np.array([0.0, r0, 0.0, 0.0, 0.0]),
+                         np.array([zt / 2, zt / 2, zt / 2, zt / 2, zt + 1.0]), prm)
+    ring = np.exp(-(1e3 / prm.heat_width) ** 2)
+    np.testing.assert_allclose(Q, [0.005, 0.005, 0.005 * ring, 0.0, 0.0], rtol=1e-14, atol=1e-18)
+    # the tanh ramp: nothing at t = 0, tanh(1) of the peak at t = tau
+    assert rhs.heating_rate(np.array([r0]), np.array([0.0]), np.array([zt / 2]), prm.at(0.0))[0] == 0.0
+    np.testing.assert_allclose(
+        rhs.heating_rate(np.array([r0]), np.array([0.0]), np.array([zt / 2]), prm.at(prm.heat_ramp)),
+        0.005 * np.tanh(1.0), rtol=1e-14)
+
+
+@pytest.mark.parametrize("eqset", ["C", "NC"])
+def test_lumped_heating_acts_pointwise_on_a_conforming_mesh(eqset):
+    m = mesh.OracleMesh(200e3, 200e3, 18e3, 4, 4, 3, 4)
+    prm = refstate.Params(heat_q0=0.004, time=900.0)
+    T = rhs.rhs(m, np.zeros((5, m.NG)), prm, eqset)
+    Q = rhs.heating_rate(m.XG[:, 0], m.XG[:, 1], m.XG[:, 2], prm)
+    fac = refstate.reference_state(m.XG[:, 2], prm)["rho0"] if eqset == "C" else 1.0
+    np.testing.assert_allclose(T[4], fac * Q, rtol=1e-12, atol=1e-15 * np.abs(fac * Q).max())
+    assert np.all(T[:4] == 0.0) and np.count_nonzero(Q) > 0
+
+
+def test_rk3_stage_times_integrate_quadratic_forcing_exactly():
+    """SSP-RK3 with the stage times (t, t + dt, t + dt/2) is Simpson's rule on
+    a pure forcing dq/dt = g(t), exact for quadratics."""
+    from oracle.rk import step_generic
+    t0, dt = 3.0, 0.7
+    g = lambda q, t: 3.0 * t ** 2 - 2.0 * t + 1.0
+    exact = (t0 + dt) ** 3 - (t0 + dt) ** 2 + (t0 + dt) - (t0 ** 3 - t0 ** 2 + t0)
+    assert abs(step_generic(g, 0.0, dt, t0) - exact) <= 1e-13 * abs(exact)
+
+
+def test_heating_enters_the_step_at_the_stage_times():
+    """One short step from rest with the heating on: the theta change is the
+    stage-time quadrature of the forcing (the dynamics answer at O(dt^2))."""
+    from oracle.rk import rk_step
+    m = mesh.OracleMesh(200e3, 200e3, 18e3, 4, 4, 3, 4)
+    prm = refstate.Params(heat_q0=0.004, heat_ramp=0.05, time=0.01)
+    dt = 0.02
+    q1 = rk_step(m, prm, np.zeros((5, m.NG)), dt)
+    rho0 = refstate.reference_state(m.XG[:, 2], prm)["rho0"]
+    Qs = [rhs.heating_rate(m.XG[:, 0], m.XG[:, 1], m.XG[:, 2], prm.at(prm.time + c * dt)) for c in (0, 1, 0.5)]
+    simpson = dt * (Qs[0] + Qs[1] + 4 * Qs[2]) / 6
+    np.testing.assert_allclose(q1[4], rho0 * simpson, rtol=1e-5, atol=1e-5 * np.abs(rho0 * simpson).max())
