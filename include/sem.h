@@ -126,6 +126,16 @@ typedef struct {
    * threshold(l+1) of Sec. 3.1 (default SEM_CRIT_SPEED everywhere).  The
    * derivatives are element-local derivatives of the element polynomials. */
   int criterion[SEM_MAX_THRESHOLDS];
+  /* Synthetic latent heating (a stand-in for the paper's observed heating,
+   * Sec. 4), off at heat_q0 = 0: a theta source
+   *   Q = heat_q0 tanh(t / heat_ramp) exp(-((r - heat_r0) / heat_width)^2) sin(pi z / heat_ztop)
+   * (K/s) for r <= heat_rmax and z <= heat_ztop, r from the domain centre,
+   * entering (rho theta)' as rho Q (or theta' as Q) as a collocated source.
+   * time: the time of the state.  sem_rhs evaluates the source at `time`;
+   * the stage calls take `time` as the time of qn and evaluate stages 0, 1, 2
+   * at time, time + dt, time + dt/2 (SSP-RK3); they do not advance it. */
+  double heat_q0, heat_r0, heat_width, heat_rmax, heat_ztop, heat_ramp;
+  double time;
 } sem_params;
 
 typedef struct {
@@ -191,7 +201,9 @@ int sem_rhs(sem_mesh* m, const sem_params* p, const double* q_dev, double* rhs_d
  * the one array and every element of it that a call reads is first written
  * by the same call, so nothing needs clearing between calls; calls that
  * overlap on the GPU (on different streams, or from several threads) race on
- * the array and must be serialised by the caller. */
+ * the array and must be serialised by the caller.  The optional terms
+ * (smag_cs, sponge_gamma, heat_q0) keep tables allocated on first use and
+ * are refused here (SEM_ERR_UNSUPPORTED). */
 int sem_rhs_noalloc(sem_mesh* m, const sem_params* p, const double* q_dev, double* rhs_dev,
                     cudaStream_t stream);
 

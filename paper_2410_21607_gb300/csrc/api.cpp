@@ -34,7 +34,7 @@ void free_device(Mesh& m) {
   if (m.dev_id >= 0 && cur != m.dev_id) cudaSetDevice(m.dev_id);
   DeviceTables& D = *m.dev;
   void* ptrs[] = {D.hmap, D.hang_h, D.hang_w, D.qt_ptr, D.qt_src, D.qt_w, D.Minv_h, D.Minv_z,
-                  D.Mh, D.Mz, D.Minv_h32, D.Minv_z32, D.qt_w32, D.qt_rec_src, D.qt_rec_w, D.hang_w32, D.mirror, D.spg, D.spg32, D.ref, D.ref32, D.col_level, D.xh, D.yh, D.zk, D.scratch,
+                  D.Mh, D.Mz, D.Minv_h32, D.Minv_z32, D.qt_w32, D.qt_rec_src, D.qt_rec_w, D.hang_w32, D.mirror, D.spg, D.spg32, D.ref, D.ref32, D.col_level, D.col_x0, D.col_y0, D.xh, D.yh, D.zk, D.scratch,
                   D.status, D.org, D.elem_cmax, D.elem_flags, D.diag_buf,
                   D.tr_comp_ptr, D.tr_nodes, D.tr_A_ptr, D.tr_A_col, D.tr_A_val, D.tr_coupled};
   for (void* p : ptrs)
@@ -81,7 +81,13 @@ int ensure_device(Mesh& m) {
     }
   }
   std::vector<int> lev(m.Ncol());
-  for (long long c = 0; c < m.Ncol(); ++c) lev[c] = m.leaves[c].l;
+  std::vector<double> cx0(m.Ncol()), cy0(m.Ncol());
+  for (long long c = 0; c < m.Ncol(); ++c) {
+    const Leaf& L = m.leaves[c];
+    lev[c] = L.l;
+    cx0[c] = -0.5 * m.Lx + L.i * m.hx(L.l);
+    cy0[c] = -0.5 * m.Ly + L.j * m.hy(L.l);
+  }
   if ((rc = upload(D.hmap, m.hmap)) || (rc = upload(D.hang_h, m.hang_h)) ||
       (rc = upload(D.hang_w, m.hang_w)) || (rc = upload(D.qt_ptr, m.qt_ptr)) ||
       (rc = upload(D.qt_src, m.qt_src)) || (rc = upload(D.qt_w, m.qt_w)) ||
@@ -90,7 +96,8 @@ int ensure_device(Mesh& m) {
       (rc = upload(D.xh, m.xh)) || (rc = upload(D.yh, m.yh)) || (rc = upload(D.zk, m.zk)) ||
       (rc = upload(D.Minv_h32, minvh32)) || (rc = upload(D.Minv_z32, minvz32)) ||
       (rc = upload(D.qt_w32, qtw32)) || (rc = upload(D.hang_w32, hw32)) ||
-      (rc = upload(D.qt_rec_src, rsrc)) || (rc = upload(D.qt_rec_w, rw))) {
+      (rc = upload(D.qt_rec_src, rsrc)) || (rc = upload(D.qt_rec_w, rw)) ||
+      (rc = upload(D.col_x0, cx0)) || (rc = upload(D.col_y0, cy0))) {
     free_device(m);
     return rc;
   }
@@ -179,6 +186,10 @@ static int check_params(const sem_params* p) {
   for (int k = 0; k < SEM_MAX_THRESHOLDS; ++k)
     if (p->criterion[k] < SEM_CRIT_SPEED || p->criterion[k] > SEM_CRIT_PV)
       return fail(SEM_ERR_ARG, "unknown criterion variable");
+  if (!(p->heat_q0 >= 0.0) || (p->heat_q0 > 0.0 && !(p->heat_width > 0.0 && p->heat_ramp > 0.0 &&
+                                                       p->heat_ztop > 0.0 && p->heat_rmax >= 0.0)) ||
+      !std::isfinite(p->time))
+    return fail(SEM_ERR_ARG, "heating needs heat_q0 >= 0, heat_width, heat_ramp, heat_ztop > 0; finite time");
   return SEM_OK;
 }
 
@@ -218,6 +229,13 @@ int sem_params_default(sem_params* p) {
   p->smag_cs = 0.0;
   p->sponge_gamma = 0.0;
   p->sponge_depth = 4000.0;
+  p->heat_q0 = 0.0;
+  p->heat_r0 = 27.5e3;
+  p->heat_width = 10.0e3;
+  p->heat_rmax = 60.0e3;
+  p->heat_ztop = 15.0e3;
+  p->heat_ramp = 600.0;
+  p->time = 0.0;
   return SEM_OK;
 }
 
@@ -332,12 +350,14 @@ int sem_rhs(sem_mesh* mh, const sem_params* p, const double* q, double* rhs, cud
   if (rc) return rc;
   if (!q || !rhs || q == rhs) return fail(SEM_ERR_ARG, "q and rhs must be distinct device arrays");
   StageArgs s{nullptr, q, rhs, nullptr, nullptr, 0.0, 0.0, 1.0, 1};
+  s.time = p->time;
   return launch_rhs_stage(mh->m, *p, s, st);
 }
 
 static const double kA[3] = {0.0, 0.75, 1.0 / 3.0};
 static const double kB[3] = {1.0, 0.25, 2.0 / 3.0};
 static const double kC[3] = {1.0, 0.25, 2.0 / 3.0};
+static const double kT[3] = {0.0, 1.0, 0.5};   // stage times in units of dt
 
 int sem_rk_stage(sem_mesh* mh, const sem_params* p, int stage, const double* qn,
                  const double* qs, double* qout, double dt, cudaStream_t st) {
@@ -347,6 +367,7 @@ int sem_rk_stage(sem_mesh* mh, const sem_params* p, int stage, const double* qn,
   if (!qn || !qs || !qout || qout == qn || qout == qs)
     return fail(SEM_ERR_ARG, "qout must not alias qn or qs");
   StageArgs s{qn, qs, qout, nullptr, nullptr, kA[stage], kB[stage], kC[stage] * dt, 0};
+  s.time = p->time + kT[stage] * dt;
   return launch_rhs_stage(mh->m, *p, s, st);
 }
 
@@ -361,6 +382,7 @@ int sem_rk_stage_mixed(sem_mesh* mh, const sem_params* p, int stage, const doubl
       (const void*)qout32 == (const void*)qs32)
     return fail(SEM_ERR_ARG, "outputs must not alias inputs");
   StageArgs s{qn, qs, qout, qs32, qout32, kA[stage], kB[stage], kC[stage] * dt, 0};
+  s.time = p->time + kT[stage] * dt;
   return launch_rhs_stage(mh->m, *p, s, st);
 }
 

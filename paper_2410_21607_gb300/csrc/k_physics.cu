@@ -13,6 +13,10 @@
 //       S_{i,d} for the horizontal momentum and tau_{z,d} = -nu_t dw/dx_d,
 //       d in {x, y};
 //     - absorbing layer: the collocated source w J (-R(z) q') on every field;
+//     - synthetic heating: the collocated source w J rho Q (EQ 0) or w J Q
+//       on the theta equation, Q = q0 tanh(t / tau) exp(-((r - r0)/w)^2)
+//       sin(pi z / z_h) for r <= r_max, z <= z_h (a stand-in for the
+//       paper's observed heating);
 //     then sums the face shared with the layer below (vertical DSS) and adds
 //     the result into r_C[column][ab][field][kz].
 //
@@ -28,6 +32,7 @@
 namespace sem {
 namespace {
 
+__constant__ double p_xi[kMaxN + 1][kMaxN + 1];
 __constant__ double p_w[kMaxN + 1][kMaxN + 1];
 __constant__ double p_D[kMaxN + 1][(kMaxN + 1) * (kMaxN + 1)];   // [i][m] = h_m'(xi_i)
 __constant__ double p_Dw[kMaxN + 1][(kMaxN + 1) * (kMaxN + 1)];  // [i][m] = w_m h_i'(xi_m)
@@ -51,12 +56,13 @@ int upload_constants() {
   static bool done = false;
   if (done) return SEM_OK;
   constexpr int K = (kMaxN + 1) * (kMaxN + 1);
-  double w[kMaxN + 1][kMaxN + 1] = {}, D[kMaxN + 1][K] = {}, Dw[kMaxN + 1][K] = {};
+  double xi[kMaxN + 1][kMaxN + 1] = {}, w[kMaxN + 1][kMaxN + 1] = {}, D[kMaxN + 1][K] = {}, Dw[kMaxN + 1][K] = {};
   float wf[kMaxN + 1][kMaxN + 1] = {}, Df[kMaxN + 1][K] = {}, Dwf[kMaxN + 1][K] = {};
   for (int N = 2; N <= kMaxN; ++N) {
     const Basis1D& B = basis(N);
     const int n = N + 1;
     for (int i = 0; i < n; ++i) {
+      xi[N][i] = B.xi[i];
       w[N][i] = B.w[i];
       wf[N][i] = (float)B.w[i];
       for (int m = 0; m < n; ++m) {
@@ -67,6 +73,7 @@ int upload_constants() {
       }
     }
   }
+  SEM_CUDA_TRY(cudaMemcpyToSymbol(p_xi, xi, sizeof(xi)));
   SEM_CUDA_TRY(cudaMemcpyToSymbol(p_w, w, sizeof(w)));
   SEM_CUDA_TRY(cudaMemcpyToSymbol(p_D, D, sizeof(D)));
   SEM_CUDA_TRY(cudaMemcpyToSymbol(p_Dw, Dw, sizeof(Dw)));
@@ -90,7 +97,22 @@ struct PhysArgs {
   long long NG;
   double cs;
   double geo[16][4];    // hx, hy, hz, J per level
+  // synthetic heating: amplitude heat_q0 tanh(t / heat_ramp) at the time of
+  // the state (0: off), ring radius and width, cut-off radius, depth
+  double heat_amp, heat_r0, heat_width, heat_rmax, heat_ztop;
+  const double* col_x0;  // [Ncol] column corners
+  const double* col_y0;
+  const double* zk;      // [NZ] heights of the levels
 };
+
+// Q of the synthetic heating (K/s) at (x, y, z): ring in r, half sine in z,
+// zero beyond heat_rmax and above heat_ztop.
+__device__ __forceinline__ double heating_at(const PhysArgs& A, double x, double y, double z) {
+  const double r = hypot(x, y);
+  if (!(r <= A.heat_rmax && z <= A.heat_ztop)) return 0.0;
+  const double a = (r - A.heat_r0) / A.heat_width;
+  return A.heat_amp * exp(-a * a) * sin(3.14159265358979323846 * z / A.heat_ztop);
+}
 
 template <typename R>
 __device__ __forceinline__ R geo_at(const PhysArgs& A, int l, int k) { return (R)A.geo[l][k]; }
@@ -158,6 +180,13 @@ physics_column(const PhysArgs A) {
         const R Rz = spg[kz];
 #pragma unroll
         for (int f = 0; f < kFields; ++f) r[f] = wJ * (-Rz * v[f]);
+      }
+      if (A.heat_amp != 0.0) {
+        const double hxd = A.geo[lev][0], hyd = A.geo[lev][1];
+        const double x = A.col_x0[col] + 0.5 * (1.0 + p_xi[N][i]) * hxd;
+        const double y = A.col_y0[col] + 0.5 * (1.0 + p_xi[N][j]) * hyd;
+        const R Q = (R)heating_at(A, x, y, A.zk[kz]);
+        r[4] += wJ * (EQ == 0 ? rfac * Q : Q);
       }
       if (A.smag) {
         sU[0][t] = u;
@@ -353,6 +382,12 @@ physics_lines(const PhysArgs A) {
 #pragma unroll
           for (int f = 0; f < kFields; ++f) r[f][c] = wJ * (-Rz * v[f]);
         }
+        if (A.heat_amp != 0.0) {
+          const double x = A.col_x0[col] + 0.5 * (1.0 + p_xi[N][i]) * A.geo[lev][0];
+          const double y = A.col_y0[col] + 0.5 * (1.0 + p_xi[N][j]) * A.geo[lev][1];
+          const float Q = (float)heating_at(A, x, y, A.zk[kz]);
+          r[4][c] += wi * wj * p_wf[N][c] * J * (rho[c] * Q);
+        }
       }
 #pragma unroll
       for (int f = 0; f < kFields; ++f) sT[(f * KL + kk) * Nq + ab] = r[f][N];
@@ -458,10 +493,14 @@ physics_lines(const PhysArgs A) {
       }
       float* dst = rc + ((long long)((long long)col * Nq + ab) * kFields) * A.NZr + kz0;
       const bool top = (k == A.nz - 1);
-      const bool all = spg != nullptr;   // the stress alone touches the momentum only
+      // fields with a contribution: the layer touches all, the stress the
+      // momentum, the heating the theta equation
+      const bool lay = spg != nullptr, heat = A.heat_amp != 0.0;
 #pragma unroll
       for (int f = 0; f < kFields; ++f) {
-        if (!all && (f == 0 || f == 4)) continue;
+        if (f == 0 && !lay) continue;
+        if (f == 4 && !lay && !heat) continue;
+        if (f >= 1 && f <= 3 && !lay && !A.smag) continue;
         float* df = dst + (long long)f * A.NZr;
         if (N == 4) {
           float4 o = *reinterpret_cast<float4*>(df);
@@ -497,7 +536,7 @@ int launch_lines(const PhysArgs& A, int ncol, cudaStream_t st) {
 }  // namespace
 
 int launch_physics(Mesh& m, const sem_params& p, const void* q, bool mixed, void* scratch,
-                   cudaStream_t st) {
+                   double time, cudaStream_t st) {
   int rc = upload_constants();
   if (rc) return rc;
   DeviceTables& D = *m.dev;
@@ -518,6 +557,14 @@ int launch_physics(Mesh& m, const sem_params& p, const void* q, bool mixed, void
   A.smag = p.smag_cs > 0.0;
   A.NG = m.NG;
   A.cs = p.smag_cs;
+  A.heat_amp = p.heat_q0 > 0.0 ? p.heat_q0 * std::tanh(time / p.heat_ramp) : 0.0;
+  A.heat_r0 = p.heat_r0;
+  A.heat_width = p.heat_width;
+  A.heat_rmax = p.heat_rmax;
+  A.heat_ztop = p.heat_ztop;
+  A.col_x0 = D.col_x0;
+  A.col_y0 = D.col_y0;
+  A.zk = D.zk;
   for (int l = 0; l < 16; ++l) {
     A.geo[l][0] = m.hx(l);
     A.geo[l][1] = m.hy(l);

@@ -1118,7 +1118,9 @@ int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float
     VolArgs A = make_vol_args(m, p, stage == 0 ? (const void*)q32 : (const void*)qs32, true, nullptr);
     if ((rc = launch_pencil_n(A, m.N, m.nz, st, m.pencil_variant))) return rc;
     SEM_CUDA_TRY(cudaGetLastError());
-    if (physics_on(p) && (rc = launch_physics(m, p, A.q, true, nullptr, st))) return rc;
+    if (physics_on(p) &&
+        (rc = launch_physics(m, p, A.q, true, nullptr, p.time + (stage == 0 ? 0.0 : (stage == 1 ? dt : 0.5 * dt)), st)))
+      return rc;
     IncArgs B;
     B.rc = (const float*)D.scratch;
     B.qt_ptr = D.qt_ptr;
@@ -1638,7 +1640,7 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
   }
   SEM_CUDA_TRY(cudaGetLastError());
   if (physics_on(p) &&
-      (rc = launch_physics(m, p, mixed ? (const void*)qs32 : (const void*)s.qs, mixed, s.scratch, st)))
+      (rc = launch_physics(m, p, mixed ? (const void*)qs32 : (const void*)s.qs, mixed, s.scratch, s.time, st)))
     return rc;
   DssArgs B;
   B.rc = s.scratch ? s.scratch : D.scratch;
@@ -1723,10 +1725,13 @@ extern "C" int sem_rhs_noalloc(sem_mesh* mh, const sem_params* p, const double* 
     return fail(SEM_ERR_ARG, "the mesh has no device tables yet: make another device call on it "
                              "first (for example sem_mesh_coords)");
   if (m.dev_id != dev) return fail(SEM_ERR_ARG, "mesh tables live on another device");
+  // the terms of the paper's runs keep per-mesh tables that are allocated on first use
+  if (physics_on(*p)) return fail(SEM_ERR_UNSUPPORTED, "sem_rhs_noalloc: smag_cs, sponge_gamma and heat_q0 must be 0");
   int rc = ensure_reference(m, *p);
   if (rc) return rc;
   void* scratch = nullptr;
   if ((rc = noalloc_scratch_address(dev, &scratch))) return rc;
   StageArgs s{nullptr, q, rhs, nullptr, nullptr, 0.0, 0.0, 1.0, 1, scratch};
+  s.time = p->time;
   return launch_rhs_stage(m, *p, s, st);
 }

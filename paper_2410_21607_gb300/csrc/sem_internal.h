@@ -120,6 +120,8 @@ struct DeviceTables {
   double* ref = nullptr;        // [NZ][kRef] float64 reference state
   float* ref32 = nullptr;       // [NZ][kRef] float32 copy, then [NZ][4] packed rows (p0, rho0, (rho theta)0, 1/(rho theta)0)
   int* col_level = nullptr;     // [Ncol]
+  double* col_x0 = nullptr;     // [Ncol] lower-left corner of each column (x, y)
+  double* col_y0 = nullptr;
   double* xh = nullptr;         // [NH]
   double* yh = nullptr;
   double* zk = nullptr;         // [NZ]
@@ -164,6 +166,7 @@ struct StageArgs {
   double a, b, cdt;   // out = a qn + b qs + cdt * tendency; rhs mode: a=b=0, cdt=1
   int rhs_only;
   void* scratch;      // column-residual scratch; null: the mesh's own
+  double time = 0.0;  // time at which the tendency is evaluated (heating source)
 };
 int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStream_t st);
 int launch_adapt(Mesh& m, const sem_params& p, const double* q, int8_t* flags, double* cmax,
@@ -194,9 +197,11 @@ int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float
                       cudaStream_t st);
 // terms of the paper's runs (k_physics.cu): adds the Smagorinsky stress and the
 // absorbing layer to the column residuals in `scratch` (null: the mesh's own)
-inline bool physics_on(const sem_params& p) { return p.smag_cs > 0.0 || p.sponge_gamma > 0.0; }
+inline bool physics_on(const sem_params& p) {
+  return p.smag_cs > 0.0 || p.sponge_gamma > 0.0 || p.heat_q0 > 0.0;
+}
 int launch_physics(Mesh& m, const sem_params& p, const void* q, bool mixed, void* scratch,
-                   cudaStream_t st);
+                   double time, cudaStream_t st);
 
 // per-kernel event timing (profile.cpp); -1 when profiling is off
 int prof_begin_kernel(const char* name, cudaStream_t st);

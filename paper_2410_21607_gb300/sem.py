@@ -65,7 +65,10 @@ class Params(C.Structure):
                 ("eqset", C.c_int), ("precision", C.c_int), ("n_thresholds", C.c_int),
                 ("lvl_max", C.c_int), ("thresholds", C.c_double * SEM_MAX_THRESHOLDS),
                 ("smag_cs", C.c_double), ("sponge_gamma", C.c_double), ("sponge_depth", C.c_double),
-                ("criterion", C.c_int * SEM_MAX_THRESHOLDS)]
+                ("criterion", C.c_int * SEM_MAX_THRESHOLDS),
+                ("heat_q0", C.c_double), ("heat_r0", C.c_double), ("heat_width", C.c_double),
+                ("heat_rmax", C.c_double), ("heat_ztop", C.c_double), ("heat_ramp", C.c_double),
+                ("time", C.c_double)]
 
 
 class ProfileOut(C.Structure):

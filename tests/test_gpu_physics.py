@@ -1,6 +1,7 @@
 """GPU parity of the terms of the paper's runs (Sec. 4): the horizontal
-Smagorinsky stress and the Rayleigh absorbing layer, through the C ABI,
-against the oracle (oracle/rhs.py).
+Smagorinsky stress, the Rayleigh absorbing layer and the synthetic heating
+source (with the stage times of the steps), through the C ABI, against the
+oracle (oracle/rhs.py, oracle/rk.py).
 
 The added terms are checked on their own (tendency with them minus tendency
 without, on both sides) as well as in the total, so that a small term cannot
@@ -121,3 +122,70 @@ def test_bad_physics_params_rejected(sem):
         with pytest.raises(sem.SemError) as e:
             sem.sem_rhs(m, sem.sem_params_default(**bad), q, out)
         assert e.value.code == sem.SEM_ERR_ARG
+
+
+HEAT = dict(heat_q0=0.005, heat_r0=27.5e3, heat_width=10e3, heat_rmax=60e3, heat_ztop=10e3, heat_ramp=5.0)
+
+
+@pytest.mark.parametrize("name", ["uniform-6x6x4-N4", "twolevel-N4", "uniform-5x4x3-N6"])
+@pytest.mark.parametrize("eqset", ["C", "NC"])
+def test_heating_rhs_matches_oracle(sem, name, eqset):
+    """Heating source at t = 3 s: float64 total 1e-12 and the source alone
+    1e-10 (only the theta equation moves); mixed total 1e-4 and the source
+    alone 1e-4 times the ratio of the total to the source."""
+    m, o, X, perm = make_pair(sem, **MESHES[name])
+    q_o = random_state(o.XG, o.Lz, 23, eqset)
+    prm = refstate.Params(time=3.0, **HEAT)
+    T_o = orhs.rhs(o, q_o, prm, eqset)
+    dT_o = T_o - orhs.rhs(o, q_o, refstate.Params(), eqset)
+    q = dev(q_o[:, perm])
+    T = _gpu_rhs(sem, m, q, eqset, 0, time=3.0, **HEAT)
+    dT = T - _gpu_rhs(sem, m, q, eqset, 0)
+    assert np.all(group_rel_l2(T, T_o[:, perm]) <= 1e-12)
+    assert np.linalg.norm(dT_o[4]) > 0
+    assert np.linalg.norm(dT[4] - dT_o[4, perm]) <= 1e-10 * np.linalg.norm(dT_o[4])
+    assert np.all(dT[:4] == 0.0)
+    Tm = _gpu_rhs(sem, m, q, eqset, 1, time=3.0, **HEAT)
+    dTm = Tm - _gpu_rhs(sem, m, q, eqset, 1)
+    assert np.all(group_rel_l2(Tm, T_o[:, perm]) <= 1e-4)
+    ratio = max(np.linalg.norm(T_o[4]) / np.linalg.norm(dT_o[4]), 1.0)
+    assert np.linalg.norm(dTm[4] - dT_o[4, perm]) <= 1e-4 * ratio * np.linalg.norm(dT_o[4])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_heating_steps_use_the_stage_times(sem, prec):
+    """Ten steps of 1 s from t = 0 with a 5 s ramp: the source changes within
+    a step, so the stage times (t, t + dt, t + dt/2) matter.  The state's
+    increment over the run is compared (float64 1e-10, mixed 1e-4)."""
+    m, o, X, perm = make_pair(sem, **MESHES["uniform-6x6x4-N4"])
+    q0 = vortex_state(o.XG, o.Lz)
+    q_o = q0.copy()
+    p = sem.sem_params_default(precision=prec, **HEAT)
+    q = dev(q0[:, perm])
+    if prec == 1:
+        q32 = torch.empty(q.shape, dtype=torch.float32, device="cuda")
+        work = torch.empty((10, m.NG), dtype=torch.float32, device="cuda")
+        sem.sem_mirror(m, q, q32)
+    else:
+        w1, w2 = torch.empty_like(q), torch.empty_like(q)
+    for s in range(10):
+        p.time = float(s)
+        if prec == 1:
+            sem.sem_step_mixed(m, p, q, q32, work, 1.0)
+        else:
+            sem.sem_step(m, p, q, w1, w2, 1.0)
+        q_o = ork.rk_step(o, refstate.Params(time=float(s), **HEAT), q_o, 1.0)
+    inc = group_rel_l2(host(q) - q0[:, perm], q_o[:, perm] - q0[:, perm])
+    assert np.all(inc <= (1e-10 if prec == 0 else 1e-4)), inc
+    assert sem.sem_status(m) == 0
+
+
+def test_noalloc_refuses_the_optional_terms(sem):
+    m = sem.sem_mesh_create(300e3, 300e3, 12e3, 3, 3, 2, 4)
+    sem.sem_mesh_coords_host(m)
+    q = torch.zeros(5, m.NG, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(q)
+    sem.sem_rhs(m, sem.sem_params_default(), q, out)     # device tables exist now
+    with pytest.raises(sem.SemError) as e:
+        sem.sem_rhs_noalloc(m, sem.sem_params_default(heat_q0=0.01), q, out)
+    assert e.value.code == sem.SEM_ERR_UNSUPPORTED
