@@ -68,9 +68,7 @@ def _velocity_theta(mesh, qL, prm, eqset):
 def _element_gradient(mesh, phi):
     """Element-local x, y, z derivatives of nodal values phi (Ne, P)."""
     out = [np.zeros_like(phi) for _ in range(3)]
-    for lev in np.unique(mesh.level):
-        es = np.nonzero(mesh.level == lev)[0]
-        G = mesh.element_ops(int(lev))
+    for lev, es, G in mesh.op_groups():
         for d in range(3):
             out[d][es] = phi[es] @ G[d].T
     return out

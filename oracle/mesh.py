@@ -29,9 +29,19 @@ from . import basis
 
 class OracleMesh:
     def __init__(self, Lx, Ly, Lz, nx, ny, nz, N, leaves=None,
-                 periodic=(True, True)):
+                 periodic=(True, True), z_faces=None):
         self.Lx, self.Ly, self.Lz = float(Lx), float(Ly), float(Lz)
         self.nx, self.ny, self.nz, self.N = int(nx), int(ny), int(nz), int(N)
+        # layer faces 0 = z_0 < z_1 < ... < z_nz = Lz (uniform by default; a
+        # stretched grid gives its own): every element stays an axis-aligned box
+        if z_faces is None:
+            self.zf = np.array([k * (self.Lz / self.nz) for k in range(self.nz)] + [self.Lz])
+        else:
+            self.zf = np.asarray(z_faces, dtype=np.float64)
+            if (self.zf.shape != (self.nz + 1,) or self.zf[0] != 0.0 or self.zf[-1] != self.Lz
+                    or np.any(np.diff(self.zf) <= 0)):
+                raise ValueError("z_faces must rise strictly from 0 to Lz (nz + 1 values)")
+        self.hzk = np.diff(self.zf)
         self.periodic = tuple(bool(p) for p in periodic)
         if leaves is None:
             leaves = [(0, i, j) for j in range(ny) for i in range(nx)]
@@ -67,7 +77,6 @@ class OracleMesh:
         self.P = n1 ** 3
         self.Ncol = len(self.leaves)
         self.Ne = self.Ncol * nz
-        self.hz = self.Lz / nz
         ii, jj, kk = np.meshgrid(np.arange(n1), np.arange(n1), np.arange(n1),
                                  indexing="ij")
         # local index l = i + (N+1)(j + (N+1)k)  (Sec. 3)
@@ -89,11 +98,11 @@ class OracleMesh:
             x0, hx, y0, hy, l = self.column_box(c)
             for k in range(nz):
                 e = c * nz + k
-                z0 = k * self.hz
+                z0, hz = self.zf[k], self.hzk[k]
                 X[e, :, 0] = x0 + 0.5 * (1.0 + self.xi[li]) * hx
                 X[e, :, 1] = y0 + 0.5 * (1.0 + self.xi[lj]) * hy
-                X[e, :, 2] = z0 + 0.5 * (1.0 + self.xi[lk]) * self.hz
-                box[e] = (x0, hx, y0, hy, z0, self.hz)
+                X[e, :, 2] = z0 + 0.5 * (1.0 + self.xi[lk]) * hz
+                box[e] = (x0, hx, y0, hy, z0, hz)
                 level[e], col[e], layer[e] = l, c, k
         self.X, self.box, self.level, self.col, self.layer = X, box, level, col, layer
         w = self.w
@@ -196,7 +205,7 @@ class OracleMesh:
             c = hang_of[q]
             x0, hx, y0, hy, _ = self.column_box(c)
             pz = Xw[q, 2]
-            k = min(int(np.floor(pz / self.hz)), nz - 1)
+            k = min(max(int(np.searchsorted(self.zf, pz, side="right")) - 1, 0), nz - 1)
             e = c * nz + k
             pxy = Xw[q, :2].copy()
             for d, (a0, h, L) in enumerate(((x0, hx, self.Lx), (y0, hy, self.Ly))):
@@ -207,7 +216,7 @@ class OracleMesh:
                             break
             rx = self._ref_coord(np.array([pxy[0]]), x0, hx)
             ry = self._ref_coord(np.array([pxy[1]]), y0, hy)
-            rz = self._ref_coord(np.array([pz]), k * self.hz, self.hz)
+            rz = self._ref_coord(np.array([pz]), self.zf[k], self.hzk[k])
             hx_ = basis.lagrange_eval(self.xi, rx)[0]
             hy_ = basis.lagrange_eval(self.xi, ry)[0]
             hz_ = basis.lagrange_eval(self.xi, rz)[0]
@@ -248,22 +257,32 @@ class OracleMesh:
         """Gather: R_G = Q^T r_L.  rL: (F, Ne, P) -> (F, NG)."""
         return np.stack([self.QT @ f.reshape(-1) for f in rL])
 
-    def element_ops(self, e_or_level):
-        """Dense derivative operators G_d[k, l] = d psi_l / d x_d at node k.
+    def element_ops(self, level, layer=0):
+        """Dense derivative operators G_d[k, l] = d psi_l / d x_d at node k
+        for the elements of a refinement level and a layer.
 
         For an axis-aligned element the map is affine, d xi / dx = 2 / hx, so
         G_x = (2/hx) I (x) I (x) D with D[m, i] = h_i'(xi_m), in the ordering
-        l = i + (N+1)(j + (N+1)k) (i fastest).
+        l = i + (N+1)(j + (N+1)k) (i fastest); G_z has the layer's thickness.
         """
-        l = e_or_level
+        l = level
         hx = self.Lx / (self.nx << l)
         hy = self.Ly / (self.ny << l)
         D = basis.derivative_matrix(self.N)
         I = np.eye(self.N + 1)
         Gx = (2.0 / hx) * np.kron(I, np.kron(I, D))
         Gy = (2.0 / hy) * np.kron(I, np.kron(D, I))
-        Gz = (2.0 / self.hz) * np.kron(D, np.kron(I, I))
+        Gz = (2.0 / self.hzk[layer]) * np.kron(D, np.kron(I, I))
         return Gx, Gy, Gz
+
+    def op_groups(self):
+        """(level, element indices, (G_x, G_y, G_z)) for every group of
+        elements that share their derivative operators (level and layer)."""
+        for lev in np.unique(self.level):
+            for k in range(self.nz):
+                es = np.nonzero((self.level == lev) & (self.layer == k))[0]
+                if es.size:
+                    yield int(lev), es, self.element_ops(int(lev), k)
 
     def column_levels(self):
         return np.array([l for l, _, _ in self.leaves], dtype=np.int64)

@@ -94,9 +94,7 @@ def element_residual(mesh, qL, prm, eqset="C"):
     g, f, gamma = prm.g, prm.f, prm.gamma
     wJ = mesh.wJ
     r = np.zeros_like(qL)
-    for lev in np.unique(mesh.level):
-        es = np.nonzero(mesh.level == lev)[0]
-        G = mesh.element_ops(int(lev))
+    for lev, es, G in mesh.op_groups():
         q = qL[:, es, :]
         rp = q[0]
         rho = rho0[es] + rp

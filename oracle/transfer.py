@@ -45,7 +45,7 @@ def _tensor_eval(xi, rx, ry, rz):
 def transfer(old, new_leaves, origin, qG_old):
     """Move the global state qG_old (F, NG_old) of mesh `old` to the new leaves."""
     new = OracleMesh(old.Lx, old.Ly, old.Lz, old.nx, old.ny, old.nz, old.N,
-                     leaves=new_leaves, periodic=old.periodic)
+                     leaves=new_leaves, periodic=old.periodic, z_faces=old.zf)
     xi = old.xi
     nz, P = old.nz, old.P
     qL_old = old.to_local(qG_old)               # (F, Ne_old, P)

@@ -37,3 +37,13 @@ def lib_to_oracle(q_lib, perm, n_oracle):
     out = np.zeros((q_lib.shape[0], n_oracle))
     out[:, perm] = q_lib
     return out
+
+
+def stretched_faces(Lz, nz, a=1.0):
+    """Layer faces z_k = Lz g(k / nz) with g(s) = (s + a s^2) / (1 + a): a
+    smooth stretching, layers thickening upwards (top to bottom thickness
+    ratio (nz + a (2 nz - 1)) / (nz + a))."""
+    s = np.arange(nz + 1) / nz
+    z = Lz * (s + a * s * s) / (1.0 + a)
+    z[0], z[-1] = 0.0, Lz
+    return z

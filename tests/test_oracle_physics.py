@@ -122,9 +122,7 @@ def _energy_identity(m, q, prm, eqset):
     # right-hand side from element-local gradients
     refl = refstate.reference_state(m.X[:, :, 2], prm)
     rhsum = 0.0
-    for lev in np.unique(m.level):
-        es = np.nonzero(m.level == lev)[0]
-        G = m.element_ops(int(lev))
+    for lev, es, G in m.op_groups():
         if eqset == "C":
             rl = refl["rho0"][es] + qL[0, es]
             ul, vl, wl = qL[1, es] / rl, qL[2, es] / rl, qL[3, es] / rl
