@@ -79,6 +79,9 @@ typedef struct {
   int lvl_max;            /* largest level the criterion may request */
   int n_leaves;
   const int* leaves;      /* host, [n_leaves][3] = (level, i, j) */
+  const double* z_faces;  /* host, [nz + 1] layer faces 0 = z_0 < z_1 < ... < z_nz = Lz
+                             (a stretched vertical grid; every element stays an
+                             axis-aligned box), or NULL for nz equal layers */
 } sem_mesh_desc;
 
 typedef struct sem_mesh sem_mesh;
@@ -366,7 +369,8 @@ int sem_autotune_select(sem_mesh* m, int row);
 
 /* Checkpoint / resume.  sem_checkpoint_write copies the float64 state to the
  * host (synchronises the stream) and writes the mesh description, its leaf
- * columns, the state, `time` and `step`, and a checksum, through a temporary
+ * columns, its layer faces, the state, `time` and `step`, and a checksum
+ * (format SEMCKPT2), through a temporary
  * file renamed into place.  sem_checkpoint_read_mesh rebuilds the mesh (host
  * only; same leaves, hence the same node numbering) and returns time and step;
  * sem_checkpoint_read_state copies the state into q_dev ([5][NG]) after

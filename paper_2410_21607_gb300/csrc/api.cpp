@@ -34,7 +34,7 @@ void free_device(Mesh& m) {
   if (m.dev_id >= 0 && cur != m.dev_id) cudaSetDevice(m.dev_id);
   DeviceTables& D = *m.dev;
   void* ptrs[] = {D.hmap, D.hang_h, D.hang_w, D.qt_ptr, D.qt_src, D.qt_w, D.Minv_h, D.Minv_z,
-                  D.Mh, D.Mz, D.Minv_h32, D.Minv_z32, D.qt_w32, D.qt_rec_src, D.qt_rec_w, D.hang_w32, D.mirror, D.spg, D.spg32, D.ref, D.ref32, D.col_level, D.col_x0, D.col_y0, D.xh, D.yh, D.zk, D.scratch,
+                  D.Mh, D.Mz, D.Minv_h32, D.Minv_z32, D.qt_w32, D.qt_rec_src, D.qt_rec_w, D.hang_w32, D.mirror, D.spg, D.spg32, D.ref, D.ref32, D.col_level, D.col_x0, D.col_y0, D.xh, D.yh, D.zk, D.hzk, D.hzk32, D.scratch,
                   D.status, D.org, D.elem_cmax, D.elem_flags, D.diag_buf,
                   D.tr_comp_ptr, D.tr_nodes, D.tr_A_ptr, D.tr_A_col, D.tr_A_val, D.tr_coupled};
   for (void* p : ptrs)
@@ -80,6 +80,12 @@ int ensure_device(Mesh& m) {
       rw[(size_t)h * 4 + e] = qtw32[beg + e];
     }
   }
+  std::vector<double> hzk(m.nz);
+  std::vector<float> hzk32(m.nz);
+  for (int k = 0; k < m.nz; ++k) {
+    hzk[k] = m.hz(k);
+    hzk32[k] = (float)hzk[k];
+  }
   std::vector<int> lev(m.Ncol());
   std::vector<double> cx0(m.Ncol()), cy0(m.Ncol());
   for (long long c = 0; c < m.Ncol(); ++c) {
@@ -94,6 +100,7 @@ int ensure_device(Mesh& m) {
       (rc = upload(D.Minv_h, minvh)) || (rc = upload(D.Minv_z, minvz)) ||
       (rc = upload(D.Mh, m.Mh)) || (rc = upload(D.Mz, m.Mz)) || (rc = upload(D.col_level, lev)) ||
       (rc = upload(D.xh, m.xh)) || (rc = upload(D.yh, m.yh)) || (rc = upload(D.zk, m.zk)) ||
+      (rc = upload(D.hzk, hzk)) || (rc = upload(D.hzk32, hzk32)) ||
       (rc = upload(D.Minv_h32, minvh32)) || (rc = upload(D.Minv_z32, minvz32)) ||
       (rc = upload(D.qt_w32, qtw32)) || (rc = upload(D.hang_w32, hw32)) ||
       (rc = upload(D.qt_rec_src, rsrc)) || (rc = upload(D.qt_rec_w, rw)) ||
@@ -254,6 +261,19 @@ int sem_mesh_create(const sem_mesh_desc* d, sem_mesh** out) {
   m.nx = d->nx; m.ny = d->ny; m.nz = d->nz; m.N = d->N;
   m.px = d->periodic_x != 0; m.py = d->periodic_y != 0;
   m.lvl_max = d->lvl_max;
+  m.zf.resize(m.nz + 1);
+  if (d->z_faces) {
+    for (int k = 0; k <= m.nz; ++k) m.zf[k] = d->z_faces[k];
+    bool ok = m.zf[0] == 0.0 && m.zf[m.nz] == m.Lz;
+    for (int k = 0; k < m.nz; ++k) ok = ok && m.zf[k + 1] > m.zf[k];
+    if (!ok) {
+      delete mh;
+      return fail(SEM_ERR_ARG, "z_faces must rise strictly from 0 to Lz");
+    }
+  } else {
+    for (int k = 0; k < m.nz; ++k) m.zf[k] = k * (m.Lz / m.nz);
+    m.zf[m.nz] = m.Lz;
+  }
   if (d->n_leaves == 0) {
     for (int j = 0; j < d->ny; ++j)
       for (int i = 0; i < d->nx; ++i) m.leaves.push_back({0, i, j});
@@ -527,7 +547,7 @@ int sem_mlp_adam(sem_mlp* m, float lr, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // checkpoints: header, leaves, float64 state, FNV-1a checksum of everything
 namespace {
-const char kMagic[8] = {'S', 'E', 'M', 'C', 'K', 'P', 'T', '1'};
+const char kMagic[8] = {'S', 'E', 'M', 'C', 'K', 'P', 'T', '2'};
 struct CkptHead {
   char magic[8];
   double Lx, Ly, Lz, time;
@@ -542,7 +562,8 @@ uint64_t fnv1a(const void* p, size_t n, uint64_t h = 1469598103934665603ull) {
   }
   return h;
 }
-int read_ckpt(const char* path, CkptHead& H, std::vector<int>& leaves, std::vector<double>* state) {
+int read_ckpt(const char* path, CkptHead& H, std::vector<int>& leaves, std::vector<double>& zf,
+              std::vector<double>* state) {
   FILE* f = std::fopen(path, "rb");
   if (!f) return fail(SEM_ERR_IO, std::string("cannot open ") + path);
   auto bad = [&](const char* why) {
@@ -554,8 +575,12 @@ int read_ckpt(const char* path, CkptHead& H, std::vector<int>& leaves, std::vect
   if (H.ncol <= 0 || H.ncol > (1ll << 30) || H.NG <= 0 || H.NG > (1ll << 36)) return bad("bad sizes");
   leaves.resize((size_t)H.ncol * 3);
   if (std::fread(leaves.data(), sizeof(int), leaves.size(), f) != leaves.size()) return bad("truncated leaves");
+  if (H.nz <= 0 || H.nz > (1 << 20)) return bad("bad sizes");
+  zf.resize((size_t)H.nz + 1);
+  if (std::fread(zf.data(), sizeof(double), zf.size(), f) != zf.size()) return bad("truncated layer faces");
   uint64_t h = fnv1a(&H, sizeof(H));
   h = fnv1a(leaves.data(), leaves.size() * sizeof(int), h);
+  h = fnv1a(zf.data(), zf.size() * sizeof(double), h);
   std::vector<double> tmp;
   std::vector<double>& q = state ? *state : tmp;
   q.resize((size_t)H.NG * kFields);
@@ -590,12 +615,14 @@ int sem_checkpoint_write(sem_mesh* mh, const double* q, double time, long long s
   SEM_CUDA_TRY(cudaStreamSynchronize(st));
   uint64_t h = fnv1a(&H, sizeof(H));
   h = fnv1a(leaves.data(), leaves.size() * sizeof(int), h);
+  h = fnv1a(m.zf.data(), m.zf.size() * sizeof(double), h);
   h = fnv1a(host.data(), host.size() * sizeof(double), h);
   const std::string tmp = std::string(path) + ".tmp";
   FILE* f = std::fopen(tmp.c_str(), "wb");
   if (!f) return fail(SEM_ERR_IO, "cannot create " + tmp);
   bool ok = std::fwrite(&H, sizeof(H), 1, f) == 1 &&
             std::fwrite(leaves.data(), sizeof(int), leaves.size(), f) == leaves.size() &&
+            std::fwrite(m.zf.data(), sizeof(double), m.zf.size(), f) == m.zf.size() &&
             std::fwrite(host.data(), sizeof(double), host.size(), f) == host.size() &&
             std::fwrite(&h, sizeof(h), 1, f) == 1;
   ok = (std::fclose(f) == 0) && ok;
@@ -611,7 +638,8 @@ int sem_checkpoint_read_mesh(const char* path, sem_mesh** out, double* time, lon
   *out = nullptr;
   CkptHead H;
   std::vector<int> leaves;
-  int rc = read_ckpt(path, H, leaves, nullptr);
+  std::vector<double> zf;
+  int rc = read_ckpt(path, H, leaves, zf, nullptr);
   if (rc) return rc;
   sem_mesh_desc d;
   std::memset(&d, 0, sizeof(d));
@@ -619,6 +647,7 @@ int sem_checkpoint_read_mesh(const char* path, sem_mesh** out, double* time, lon
   d.periodic_x = H.px; d.periodic_y = H.py; d.lvl_max = H.lvl_max;
   d.n_leaves = (int)H.ncol;
   d.leaves = leaves.data();
+  d.z_faces = zf.data();
   if ((rc = sem_mesh_create(&d, out))) return rc;
   if ((*out)->m.NG != H.NG) {
     sem_mesh_destroy(*out);
@@ -634,11 +663,11 @@ int sem_checkpoint_read_state(const char* path, sem_mesh* mh, double* q, cudaStr
   if (!path || !mh || !q) return fail(SEM_ERR_ARG, "NULL argument");
   CkptHead H;
   std::vector<int> leaves;
-  std::vector<double> host;
-  int rc = read_ckpt(path, H, leaves, &host);
+  std::vector<double> host, zf;
+  int rc = read_ckpt(path, H, leaves, zf, &host);
   if (rc) return rc;
   const Mesh& m = mh->m;
-  bool same = H.NG == m.NG && H.ncol == m.Ncol();
+  bool same = H.NG == m.NG && H.ncol == m.Ncol() && zf == m.zf;
   for (long long c = 0; same && c < m.Ncol(); ++c)
     same = leaves[3 * c] == m.leaves[c].l && leaves[3 * c + 1] == m.leaves[c].i &&
            leaves[3 * c + 2] == m.leaves[c].j;
@@ -705,6 +734,7 @@ int sem_transfer_plan(const sem_mesh* oldh, const int8_t* flags, sem_mesh** out)
   m.Lx = o.Lx; m.Ly = o.Ly; m.Lz = o.Lz;
   m.nx = o.nx; m.ny = o.ny; m.nz = o.nz; m.N = o.N;
   m.px = o.px; m.py = o.py; m.lvl_max = o.lvl_max;
+  m.zf = o.zf;
   m.leaves = nl;
   rc = build_mesh(m);   // sorts the leaves into Morton order
   if (rc) {

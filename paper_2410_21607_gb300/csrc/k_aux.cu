@@ -51,7 +51,8 @@ struct AdaptArgs {
   double f;
   double thr[SEM_MAX_THRESHOLDS];
   int var[SEM_MAX_THRESHOLDS];    // SEM_CRIT_* per threshold
-  double gx[16], gy[16], gz;      // 2 / h per level, 2 / hz
+  double gx[16], gy[16];          // 2 / h per level
+  const double* hzk;              // [nz] layer thicknesses
 };
 
 template <int N, int EQ>
@@ -116,7 +117,7 @@ adapt_column(const AdaptArgs A) {
             d[qv][2] += Dc * sQ[qv][lz];
           }
         }
-        const double gx = A.gx[lev], gy = A.gy[lev], gz = A.gz;
+        const double gx = A.gx[lev], gy = A.gy[lev], gz = 2.0 / A.hzk[k];
         for (int qv = 0; qv < 4; ++qv) {
           d[qv][0] *= gx;
           d[qv][1] *= gy;
@@ -197,7 +198,7 @@ int launch_adapt(Mesh& m, const sem_params& p, const double* q, int8_t* flags, d
     A.gx[l] = 2.0 / m.hx(l);
     A.gy[l] = 2.0 / m.hy(l);
   }
-  A.gz = 2.0 / m.hz();
+  A.hzk = D.hzk;
   if (A.need_grad) {
     int rc = upload_aux_constants();
     if (rc) return rc;

@@ -96,7 +96,9 @@ struct PhysArgs {
   int nz, NZ, NZr, smag;
   long long NG;
   double cs;
-  double geo[16][4];    // hx, hy, hz, J per level
+  double geo[16][2];    // hx, hy per level
+  const double* hzk;     // [nz] layer thicknesses (same type as the state when float)
+  const float* hzk32;
   // synthetic heating: amplitude heat_q0 tanh(t / heat_ramp) at the time of
   // the state (0: off), ring radius and width, cut-off radius, depth
   double heat_amp, heat_r0, heat_width, heat_rmax, heat_ztop;
@@ -129,17 +131,14 @@ physics_column(const PhysArgs A) {
   const int i = t % n1, j = (t / n1) % n1, c = t / Nq;
   const int ab = i + n1 * j;
   const int lev = A.col_level[col];
-  const R hx = geo_at<R>(A, lev, 0), hy = geo_at<R>(A, lev, 1), hz = geo_at<R>(A, lev, 2);
-  const R J = geo_at<R>(A, lev, 3);
+  const R hx = geo_at<R>(A, lev, 0), hy = geo_at<R>(A, lev, 1);
   const R gx = (R)2 / hx, gy = (R)2 / hy;
-  const R sx = hy * hz * (R)0.25, sy = hx * hz * (R)0.25;   // J dxi/dx, J deta/dy
   const R delta = (hx + hy) / (R)(2 * N);
   const R csd = (R)A.cs * delta;
   const R cs2 = csd * csd;
   const int hm = act ? A.hmap[(long long)col * Nq + ab] : 0;
   const R wi = act ? PTab<R>::w(N, i) : (R)0, wj = act ? PTab<R>::w(N, j) : (R)0;
   const R wc = act ? PTab<R>::w(N, c) : (R)0;
-  const R wJ = wi * wj * wc * J;
   const R* q = (const R*)A.q;
   const R* hw = (const R*)A.hang_w;
   const R* ref = (const R*)A.ref;
@@ -147,6 +146,11 @@ physics_column(const PhysArgs A) {
   R* rc = (R*)A.rc;
   for (int k = 0; k < A.nz; ++k) {
     const int kz = k * N + c;
+    // the layer's thickness: Jacobian and the weak-form factors J dxi/dx, J deta/dy
+    const R hz = (R)A.hzk[k];
+    const R J = hx * hy * hz * (R)0.125;
+    const R sx = hy * hz * (R)0.25, sy = hx * hz * (R)0.25;
+    const R wJ = wi * wj * wc * J;
     R r[kFields] = {0, 0, 0, 0, 0};
     R rfac = (R)1;
     if (act) {
@@ -325,10 +329,8 @@ physics_lines(const PhysArgs A) {
   const int i = ab % n1, j = ab / n1;
   const int lc = ab % n1, lo = ab / n1;   // x-line (j, c) = (lo, lc), y-line (i, c) = (lo, lc)
   const int lev = A.col_level[col];
-  const float hx = (float)A.geo[lev][0], hy = (float)A.geo[lev][1], hz = (float)A.geo[lev][2];
-  const float J = (float)A.geo[lev][3];
+  const float hx = (float)A.geo[lev][0], hy = (float)A.geo[lev][1];
   const float gx = 2.f / hx, gy = 2.f / hy;
-  const float sx = hy * hz * 0.25f, sy = hx * hz * 0.25f;
   const float csd = (float)A.cs * ((hx + hy) / (float)(2 * N));
   const float cs2 = csd * csd;
   const int hm = A.hmap[(long long)col * Nq + ab];
@@ -343,6 +345,9 @@ physics_lines(const PhysArgs A) {
     const int k = ch * KL + kk;
     const bool act = k < A.nz;
     const int kz0 = k * N;
+    const float hz = act ? A.hzk32[k] : 0.f;   // the layer's thickness
+    const float J = hx * hy * hz * 0.125f;
+    const float sx = hy * hz * 0.25f, sy = hx * hz * 0.25f;
     float r[kFields][n1];
 #pragma unroll
     for (int f = 0; f < kFields; ++f)
@@ -565,11 +570,12 @@ int launch_physics(Mesh& m, const sem_params& p, const void* q, bool mixed, void
   A.col_x0 = D.col_x0;
   A.col_y0 = D.col_y0;
   A.zk = D.zk;
+  A.hzk = D.hzk;
+  A.hzk32 = D.hzk32;
   for (int l = 0; l < 16; ++l) {
     A.geo[l][0] = m.hx(l);
     A.geo[l][1] = m.hy(l);
-    A.geo[l][2] = m.hz();
-    A.geo[l][3] = m.hx(l) * m.hy(l) * m.hz() * 0.125;
+
   }
   ProfScope ps("physics", st);
   const int ncol = (int)m.Ncol();

@@ -103,12 +103,17 @@ struct VolArgs {
   double geo[kLev][8];
   float geof[kLev][8];
   const float* ref32;
+  const double* hzk;    // [nz] layer thicknesses (geo holds the values for unit thickness)
+  const float* hzk32;
   const float4* ref4;   // [NZ] packed p0, rho0, (rho theta)0, 1/(rho theta)0 (float32)
 };
 
 template <typename R> __device__ __forceinline__ const R* geo_of(const VolArgs& A, int l);
 template <> __device__ __forceinline__ const double* geo_of<double>(const VolArgs& A, int l) { return A.geo[l]; }
 template <> __device__ __forceinline__ const float* geo_of<float>(const VolArgs& A, int l) { return A.geof[l]; }
+template <typename R> __device__ __forceinline__ const R* hz_of(const VolArgs& A);
+template <> __device__ __forceinline__ const double* hz_of<double>(const VolArgs& A) { return A.hzk; }
+template <> __device__ __forceinline__ const float* hz_of<float>(const VolArgs& A) { return A.hzk32; }
 template <typename R> __device__ __forceinline__ const R* ref_of(const VolArgs& A);
 template <> __device__ __forceinline__ const double* ref_of<double>(const VolArgs& A) { return A.ref; }
 template <> __device__ __forceinline__ const float* ref_of<float>(const VolArgs& A) { return A.ref32; }
@@ -190,15 +195,18 @@ volume_column(const VolArgs A) {
     wc = Tab<R>::w(N, c);
   }
   // weak-form factors: J dxi/dx = hy hz / 4 etc.
-  const R sx = geo[4], sy = geo[5], sz = geo[6];
-  const R wJ = wi * wj * wc * geo[3];
+  // per unit layer thickness; scaled by the layer's thickness below
+  const R sx1 = geo[4], sy1 = geo[5], sz = geo[6];
+  const R wJ1 = wi * wj * wc * geo[3];
   const R two = (R)2;
-  const R gx = two / geo[0], gy = two / geo[1], gz = two / geo[2];
+  const R gx = two / geo[0], gy = two / geo[1];
   const R g = par_g<R>(A), fc = par_f<R>(A), gam = par_gam<R>(A);
   const R* refR = ref_of<R>(A);
   R* rc = (R*)A.rc;
 
   for (int k = 0; k < A.nz; ++k) {
+    const R hk = hz_of<R>(A)[k];
+    const R sx = sx1 * hk, sy = sy1 * hk, wJ = wJ1 * hk, gz = two / hk;
     const int kz = k * N + c;
     R S[kFields] = {0, 0, 0, 0, 0};
     R pw[5] = {0, 0, 0, 0, 0};  // EQ 1: u, v, w, rho, rho' kept for the strong terms
@@ -597,6 +605,7 @@ __device__ __forceinline__ void pencil_body(const VolArgs& A, const int col, flo
     const int k = ch * KL + kk;
     const bool act = part && k < A.nz;
     const int kz0 = k * N;
+    const float hk = act ? __ldg(A.hzk32 + k) : 0.f;   // layer thickness
     float2 r[kFields][CP];
 #pragma unroll
     for (int f = 0; f < kFields; ++f)
@@ -613,7 +622,7 @@ __device__ __forceinline__ void pencil_body(const VolArgs& A, const int col, flo
         load_node<N>(A, hm, kz, v);
         const float wc = c_wf[N][c];
         NodeTerms T;
-        node_terms(A, v, kz, wj * wc * sx, wi * wc * sy, wi * wj * sz, wi * wj * wc * J, T);
+        node_terms(A, v, kz, wj * wc * sx * hk, wi * wc * sy * hk, wi * wj * sz, wi * wj * wc * J * hk, T);
 #pragma unroll
         for (int f = 0; f < kFields; ++f) {
           myX[f * FS + c] = T.fx[f];
@@ -782,6 +791,7 @@ __device__ __forceinline__ void lines_body(const VolArgs& A, const int col, floa
     const int k = ch * KL + kk;
     const bool act = part && k < A.nz;
     const int kz0 = k * N;
+    const float hk = act ? __ldg(A.hzk32 + k) : 0.f;   // layer thickness
     float rz[kFields][n1];
 #pragma unroll
     for (int f = 0; f < kFields; ++f)
@@ -797,7 +807,7 @@ __device__ __forceinline__ void lines_body(const VolArgs& A, const int col, floa
         load_node<N>(A, hm, kz, v);
         const float wc = c_wf[N][c];
         NodeTerms T;
-        node_terms(A, v, kz, wj * wc * sx, wi * wc * sy, wi * wj * sz, wi * wj * wc * J, T);
+        node_terms(A, v, kz, wj * wc * sx * hk, wi * wc * sy * hk, wi * wj * sz, wi * wj * wc * J * hk, T);
 #pragma unroll
         for (int f = 0; f < kFields; ++f) {
           zX[f * n1 + c] = T.fx[f];
@@ -963,6 +973,8 @@ static VolArgs make_vol_args(Mesh& m, const sem_params& p, const void* q, bool m
   A.col_level = D.col_level;
   A.ref = D.ref;
   A.ref32 = D.ref32;
+  A.hzk = D.hzk;
+  A.hzk32 = D.hzk32;
   A.ref4 = reinterpret_cast<const float4*>(D.ref32 + (size_t)m.NZ * kRef);
   A.Ncol = (int)m.Ncol();
   A.nz = m.nz;
@@ -990,7 +1002,7 @@ static VolArgs make_vol_args(Mesh& m, const sem_params& p, const void* q, bool m
     A.bin[7] = 0.f;
   }
   for (int l = 0; l < kLev; ++l) {
-    const double hx = m.hx(l), hy = m.hy(l), hz = m.hz();
+    const double hx = m.hx(l), hy = m.hy(l), hz = 1.0;   // per unit layer thickness
     const double g[8] = {hx, hy, hz, hx * hy * hz * 0.125, hy * hz * 0.25, hx * hz * 0.25,
                          hx * hy * 0.25, 0.0};
     for (int k = 0; k < 8; ++k) {

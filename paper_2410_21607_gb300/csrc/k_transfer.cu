@@ -95,6 +95,7 @@ struct TrArgs {
   int nz, NZ;
   double Lx, Ly, Lz;
   int nx, ny;
+  const double* hzk;   // [nz] layer thicknesses
 };
 
 template <int N>
@@ -129,7 +130,7 @@ transfer_local(const TrArgs A) {
   const int lev = A.new_level[col];
   const double hx = A.Lx / (double)((long long)A.nx << lev);
   const double hy = A.Ly / (double)((long long)A.ny << lev);
-  const double wJ = act ? c_tw[N][i] * c_tw[N][j] * c_tw[N][c] * hx * hy * (A.Lz / A.nz) * 0.125 : 0.0;
+  const double wJ1 = act ? c_tw[N][i] * c_tw[N][j] * c_tw[N][c] * hx * hy * 0.125 : 0.0;  // per unit thickness
   const int nsrc = kind == 2 ? 4 : 1;
   for (int k = 0; k < A.nz; ++k) {
     const int kz = k * N + c;
@@ -162,6 +163,7 @@ transfer_local(const TrArgs A) {
             }
         }
       }
+      const double wJ = wJ1 * A.hzk[k];
       for (int f = 0; f < kFields; ++f) r[f] *= wJ;
       if (c == 0 && k > 0)
         for (int f = 0; f < kFields; ++f) r[f] += sC[(k - 1) & 1][f][ab];
@@ -428,6 +430,7 @@ int launch_transfer(Mesh& o, Mesh& m, const double* qold, double* qnew, cudaStre
   A.Lz = m.Lz;
   A.nx = m.nx;
   A.ny = m.ny;
+  A.hzk = D.hzk;
   const int nc = (int)m.Ncol();
   switch (m.N) {
     case 2: launch_local<2>(A, nc, st); break;

@@ -88,7 +88,8 @@ struct Mesh {
   long long Ne() const { return Ncol() * nz; }
   double hx(int l) const { return Lx / (double)((long long)nx << l); }
   double hy(int l) const { return Ly / (double)((long long)ny << l); }
-  double hz() const { return Lz / nz; }
+  std::vector<double> zf;            // [nz + 1] layer faces
+  double hz(int k) const { return zf[k + 1] - zf[k]; }
   int NZr() const { return (NZ + 3) & ~3; }  // level stride of the column residual scratch
 };
 
@@ -125,6 +126,8 @@ struct DeviceTables {
   double* xh = nullptr;         // [NH]
   double* yh = nullptr;
   double* zk = nullptr;         // [NZ]
+  double* hzk = nullptr;        // [nz] layer thicknesses, float64 and float32
+  float* hzk32 = nullptr;
   void* scratch = nullptr;      // column residuals
   size_t scratch_bytes = 0;
   int* status = nullptr;        // device status word

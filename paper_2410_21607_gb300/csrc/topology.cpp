@@ -461,8 +461,8 @@ int build_mesh(Mesh& m) {
   m.zk.assign(m.NZ, 0.0);
   for (int k = 0; k < m.nz; ++k)
     for (int c = 0; c <= N; ++c) {
-      m.Mz[k * N + c] += B.w[c] * m.hz() * 0.5;
-      m.zk[k * N + c] = k * m.hz() + 0.5 * (1.0 + B.xi[c]) * m.hz();
+      m.Mz[k * N + c] += B.w[c] * m.hz(k) * 0.5;
+      m.zk[k * N + c] = m.zf[k] + 0.5 * (1.0 + B.xi[c]) * m.hz(k);
     }
   m.zk[0] = 0.0;
   m.zk[m.NZ - 1] = m.Lz;

@@ -48,7 +48,8 @@ class MeshDesc(C.Structure):
     _fields_ = [("Lx", C.c_double), ("Ly", C.c_double), ("Lz", C.c_double),
                 ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("N", C.c_int),
                 ("periodic_x", C.c_int), ("periodic_y", C.c_int), ("lvl_max", C.c_int),
-                ("n_leaves", C.c_int), ("leaves", C.POINTER(C.c_int))]
+                ("n_leaves", C.c_int), ("leaves", C.POINTER(C.c_int)),
+                ("z_faces", C.POINTER(C.c_double))]
 
 
 class MeshInfo(C.Structure):
@@ -221,13 +222,19 @@ class Mesh:
         return (5, self.NG)
 
 
-def sem_mesh_create(Lx, Ly, Lz, nx, ny, nz, N, leaves=None, periodic=(True, True), lvl_max=0):
-    d = MeshDesc(Lx, Ly, Lz, nx, ny, nz, N, int(periodic[0]), int(periodic[1]), lvl_max, 0, None)
-    keep = None
+def sem_mesh_create(Lx, Ly, Lz, nx, ny, nz, N, leaves=None, periodic=(True, True), lvl_max=0,
+                    z_faces=None):
+    d = MeshDesc(Lx, Ly, Lz, nx, ny, nz, N, int(periodic[0]), int(periodic[1]), lvl_max, 0, None, None)
+    keep = keep_z = None
     if leaves is not None and len(leaves):
         keep = np.ascontiguousarray(np.asarray(leaves, dtype=np.int32).reshape(-1, 3))
         d.n_leaves = len(keep)
         d.leaves = keep.ctypes.data_as(C.POINTER(C.c_int))
+    if z_faces is not None:
+        keep_z = np.ascontiguousarray(np.asarray(z_faces, dtype=np.float64))
+        if keep_z.shape != (nz + 1,):
+            raise ValueError("z_faces needs nz + 1 values")
+        d.z_faces = keep_z.ctypes.data_as(C.POINTER(C.c_double))
     h = C.c_void_p()
     _check(LIB.sem_mesh_create(C.byref(d), C.byref(h)))
     return Mesh(h.value)

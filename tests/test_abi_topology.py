@@ -58,9 +58,10 @@ def _lib_Q(sem, m):
     return sp.csr_matrix((vals, (rows, cols)), shape=(m.Ne * n1 ** 3, m.NG)), leaves
 
 
-def _compare_with_oracle(sem, L, nx, nz, N, leaves, periodic):
-    m = sem.sem_mesh_create(L, L, 10e3, nx, nx, nz, N, leaves=leaves, periodic=periodic, lvl_max=4)
-    o = om.OracleMesh(L, L, 10e3, nx, nx, nz, N, leaves=leaves, periodic=periodic)
+def _compare_with_oracle(sem, L, nx, nz, N, leaves, periodic, z_faces=None):
+    m = sem.sem_mesh_create(L, L, 10e3, nx, nx, nz, N, leaves=leaves, periodic=periodic, lvl_max=4,
+                            z_faces=z_faces)
+    o = om.OracleMesh(L, L, 10e3, nx, nx, nz, N, leaves=leaves, periodic=periodic, z_faces=z_faces)
     assert m.NG == o.NG
     perm = node_perm(sem.sem_mesh_coords_host(m), o.XG)
     Q, lv = _lib_Q(sem, m)
@@ -80,6 +81,20 @@ def _compare_with_oracle(sem, L, nx, nz, N, leaves, periodic):
 @pytest.mark.parametrize("periodic", [(True, True), (False, False), (True, False)])
 def test_topology_matches_oracle_two_level(sem, N, periodic):
     _compare_with_oracle(sem, 80e3, 4, 2, N, two_level_leaves(), periodic)
+
+
+@pytest.mark.parametrize("N", [3, 4])
+def test_topology_matches_oracle_stretched_layers(sem, N):
+    """Layer faces of a stretched grid: same numbering, Q and lumped mass as
+    the oracle's, and the z levels of the nodes follow the faces."""
+    from tests.helpers import stretched_faces
+    zf = stretched_faces(10e3, 3, 1.5)
+    m, o = _compare_with_oracle(sem, 80e3, 4, 3, N, two_level_leaves(), (True, True), z_faces=zf)
+    z = np.unique(np.round(sem.sem_mesh_coords_host(m)[2], 6))
+    assert np.allclose(z[::N], zf)
+    with pytest.raises(sem.SemError) as e:
+        sem.sem_mesh_create(80e3, 80e3, 10e3, 2, 2, 3, 4, z_faces=[0.0, 6e3, 5e3, 10e3])
+    assert e.value.code == sem.SEM_ERR_ARG
 
 
 @pytest.mark.parametrize("seed", range(4))
@@ -145,17 +160,19 @@ def test_uniform_counts_and_info(sem):
 
 
 def _fake_checkpoint(path, ncol_leaves, NG, corrupt=None):
-    """A checkpoint file in the library's layout (header, leaves, state, FNV-1a)."""
+    """A checkpoint file in the library's layout (header, leaves, layer faces,
+    state, FNV-1a)."""
     import struct
-    head = struct.pack("<8s4d8i3q", b"SEMCKPT1", 80e3, 80e3, 10e3, 1.5, 2, 2, 1, 4, 1, 1, 0, 0,
+    head = struct.pack("<8s4d8i3q", b"SEMCKPT2", 80e3, 80e3, 10e3, 1.5, 2, 2, 1, 4, 1, 1, 0, 0,
                        len(ncol_leaves), NG, 7)
     leaves = np.asarray(ncol_leaves, dtype=np.int32).tobytes()
+    faces = np.array([0.0, 10e3]).tobytes()
     state = np.arange(5 * NG, dtype=np.float64).tobytes()
     h = 1469598103934665603
-    for b in head + leaves + state:
+    for b in head + leaves + faces + state:
         h ^= b
         h = (h * 1099511628211) & 0xFFFFFFFFFFFFFFFF
-    data = head + leaves + state + struct.pack("<Q", h)
+    data = head + leaves + faces + state + struct.pack("<Q", h)
     if corrupt == "truncate":
         data = data[:-100]
     elif corrupt == "flip":

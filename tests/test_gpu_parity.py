@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 from oracle import adapt, diag, mesh as om, refstate, rhs as orhs, rk as ork, transfer as otr  # noqa: E402
 from synth.vortex import random_state, vortex_state, VortexSpec  # noqa: E402
-from tests.helpers import group_rel_l2, node_perm  # noqa: E402
+from tests.helpers import group_rel_l2, node_perm, stretched_faces  # noqa: E402
 from tests.test_oracle_mesh import two_level_leaves  # noqa: E402
 
 
@@ -34,9 +34,10 @@ def sem():
 PRM = refstate.Params()
 
 
-def make_pair(sem, L, Lz, nx, nz, N, leaves=None, periodic=(True, True), lvl_max=3):
-    m = sem.sem_mesh_create(L, L, Lz, nx, nx, nz, N, leaves=leaves, periodic=periodic, lvl_max=lvl_max)
-    o = om.OracleMesh(L, L, Lz, nx, nx, nz, N, leaves=leaves, periodic=periodic)
+def make_pair(sem, L, Lz, nx, nz, N, leaves=None, periodic=(True, True), lvl_max=3, z_faces=None):
+    m = sem.sem_mesh_create(L, L, Lz, nx, nx, nz, N, leaves=leaves, periodic=periodic, lvl_max=lvl_max,
+                            z_faces=z_faces)
+    o = om.OracleMesh(L, L, Lz, nx, nx, nz, N, leaves=leaves, periodic=periodic, z_faces=z_faces)
     xyz = sem.sem_mesh_coords_host(m)
     perm = node_perm(xyz, o.XG)
     return m, o, xyz.T, perm
@@ -70,6 +71,9 @@ MESHES = {
                              periodic=(False, False)),
     "uniform-5x4x3-N6": dict(L=500e3, Lz=12e3, nx=5, nz=3, N=6),
     "uniform-3x3x2-N2": dict(L=300e3, Lz=12e3, nx=3, nz=2, N=2),
+    # layers thickening upwards (top to bottom thickness 2.5), non-conforming
+    "stretched-twolevel-N4": dict(L=300e3, Lz=12e3, nx=4, nz=3, N=4, leaves=two_level_leaves(),
+                                  z_faces=stretched_faces(12e3, 3, 1.5)),
 }
 
 
@@ -88,7 +92,7 @@ def test_rhs_fp64_matches_oracle(sem, name, eqset):
     assert np.all(err <= 1e-12), err
 
 
-@pytest.mark.parametrize("name", ["uniform-6x6x4-N4", "twolevel-N4"])
+@pytest.mark.parametrize("name", ["uniform-6x6x4-N4", "twolevel-N4", "stretched-twolevel-N4"])
 @pytest.mark.parametrize("eqset", ["C", "NC"])
 def test_rhs_mixed_matches_oracle(sem, name, eqset):
     m, o, X, perm = make_pair(sem, **MESHES[name])
@@ -102,7 +106,8 @@ def test_rhs_mixed_matches_oracle(sem, name, eqset):
     assert np.all(err <= 1e-4), err
 
 
-@pytest.mark.parametrize("name", ["twolevel-N4", "twolevel-17-layers-N4", "uniform-5x4x3-N6"])
+@pytest.mark.parametrize("name", ["twolevel-N4", "twolevel-17-layers-N4", "uniform-5x4x3-N6",
+                                  "stretched-twolevel-N4"])
 def test_every_element_kernel_variant_matches_oracle(sem, name):
     """Each launch variant of the mixed element kernel (z-pencil and line
     exchange, every layers-per-CTA count) gives the
@@ -219,7 +224,7 @@ def test_adapt_flags_match_oracle(sem, name):
 CRIT = {"speed": 0, "vorticity": 1, "pv": 2}
 
 
-@pytest.mark.parametrize("name", ["uniform-6x6x4-N4", "twolevel-N4", "uniform-5x4x3-N6"])
+@pytest.mark.parametrize("name", ["uniform-6x6x4-N4", "twolevel-N4", "uniform-5x4x3-N6", "stretched-twolevel-N4"])
 @pytest.mark.parametrize("eqset", ["C", "NC"])
 @pytest.mark.parametrize("variables", [("vorticity",) * 3, ("pv",) * 3, ("speed", "vorticity", "pv")])
 def test_adapt_flags_alternative_criteria_match_oracle(sem, name, eqset, variables):
@@ -433,13 +438,14 @@ def test_mixed_stage_with_mirrors_matches_oracle(sem):
     assert sem.sem_status(m) == 0
 
 
-@pytest.mark.parametrize("name", ["uniform-6x6x4-N4", "twolevel-N4", "uniform-3x3x2-N2", "uniform-5x4x3-N6"])
+@pytest.mark.parametrize("name", ["uniform-6x6x4-N4", "twolevel-N4", "uniform-3x3x2-N2", "uniform-5x4x3-N6",
+                                  "stretched-twolevel-N4"])
 def test_step_mixed_increment_form_matches_oracle(sem, name):
     """sem_step_mixed (float32 stage increments, one float64 accumulation per
     step) against ten float64 oracle steps."""
     m, o, X, perm = make_pair(sem, **MESHES[name])
     q_o = vortex_state(o.XG, o.Lz)
-    dt = 1.0 if name != "uniform-5x4x3-N6" else 0.5
+    dt = 0.5 if name in ("uniform-5x4x3-N6", "stretched-twolevel-N4") else 1.0
     q_ref = q_o.copy()
     for _ in range(10):
         q_ref = ork.rk_step(o, PRM, q_ref, dt)
@@ -544,25 +550,27 @@ def test_mixed_pressure_both_branches(sem):
     assert np.all(err <= 1e-4), err
 
 
+@pytest.mark.parametrize("name", ["twolevel-N4", "stretched-twolevel-N4"])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_checkpoint_resume_is_bitwise(sem, prec, tmp_path):
+def test_checkpoint_resume_is_bitwise(sem, prec, tmp_path, name):
     """Six steps straight through equal three steps, checkpoint, a fresh mesh
     and state read back from the file, and three more steps, bit for bit."""
-    m, o, X, perm = make_pair(sem, **MESHES["twolevel-N4"])
+    m, o, X, perm = make_pair(sem, **MESHES[name])
     q0 = dev(vortex_state(o.XG, o.Lz)[:, perm])
     p = sem.sem_params_default(precision=prec)
+    dt = 0.5 if "stretched" in name else 1.0
 
     def steps(mesh, q, n):
         if prec == 0:
             w1, w2 = torch.empty_like(q), torch.empty_like(q)
             for _ in range(n):
-                sem.sem_step(mesh, p, q, w1, w2, 1.0)
+                sem.sem_step(mesh, p, q, w1, w2, dt)
         else:
             q32 = torch.empty(q.shape, dtype=torch.float32, device="cuda")
             work = torch.empty((10, mesh.NG), dtype=torch.float32, device="cuda")
             sem.sem_mirror(mesh, q, q32)
             for _ in range(n):
-                sem.sem_step_mixed(mesh, p, q, q32, work, 1.0)
+                sem.sem_step_mixed(mesh, p, q, q32, work, dt)
         return q
 
     a = steps(m, q0.clone(), 6)

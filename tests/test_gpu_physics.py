@@ -58,7 +58,8 @@ def test_physics_rhs_fp64_matches_oracle(sem, name, eqset):
     assert np.linalg.norm(dT_o[1]) > 0 and np.linalg.norm(dT_o[0]) > 0
 
 
-@pytest.mark.parametrize("name", ["uniform-6x6x4-N4", "twolevel-N4"])
+@pytest.mark.parametrize("name", ["uniform-6x6x4-N4", "twolevel-N4", "stretched-twolevel-N4", "uniform-3x3x2-N2",
+                                  "twolevel-N3-open", "uniform-5x4x3-N6"])
 @pytest.mark.parametrize("eqset", ["C", "NC"])
 def test_physics_rhs_mixed_matches_oracle(sem, name, eqset):
     m, o, X, perm = make_pair(sem, **MESHES[name])
