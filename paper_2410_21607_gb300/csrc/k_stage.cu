@@ -1322,6 +1322,15 @@ struct BatchImpl {
   int* d_counter = nullptr;   // [3]
   int* d_status = nullptr;
   cudaStream_t cap = nullptr;
+  // branch streams: instances with their own launches whose column residuals
+  // are small enough (kBranchBytes) run side by side (each keeps its stage
+  // order), forked from and joined to the step's stream; larger ones run one
+  // after another on it, so that their residuals stay in L2 between the
+  // element and the gather kernel
+  std::vector<char> branch;
+  std::vector<cudaStream_t> br;
+  std::vector<cudaEvent_t> br_done;
+  cudaEvent_t fork = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   std::vector<const void*> key;  // arrays and dt the device tables were built for
@@ -1340,6 +1349,9 @@ static void batch_free(BatchImpl* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->cap) cudaStreamDestroy(b->cap);
+  for (cudaStream_t x : b->br) cudaStreamDestroy(x);
+  for (cudaEvent_t x : b->br_done) cudaEventDestroy(x);
+  if (b->fork) cudaEventDestroy(b->fork);
   void* ptrs[] = {b->d_vol, b->d_inc, b->d_N, b->d_tiles, b->d_off, b->d_counter, b->d_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -1403,6 +1415,26 @@ int batch_create(Mesh* const* meshes, int n, void** out) {
     e = cudaMemcpy(b->d_off, soff.data(), sizeof(int) * soff.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  {
+    constexpr long long kBranchBytes = 16ll << 20;
+    b->branch.assign(n, 0);
+    int nbig = 0;
+    for (int k = 0; k < n; ++k) {
+      const Mesh& m = *meshes[k];
+      b->branch[k] = b->big[k] && m.Ncol() * m.Nq * kFields * m.NZr() * (long long)sizeof(float) <= kBranchBytes;
+      nbig += b->branch[k];
+    }
+    const int nbr = std::min(nbig, 4);
+    if (nbr > 0 && e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int i = 0; i < nbr && e == cudaSuccess; ++i) {
+      cudaStream_t x = nullptr;
+      cudaEvent_t ev = nullptr;
+      e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
+      if (e == cudaSuccess) b->br.push_back(x);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e == cudaSuccess) b->br_done.push_back(ev);
+    }
+  }
   for (int v = 0; v < kNumBatch && e == cudaSuccess; ++v)
     e = cudaFuncSetAttribute(kBatch[v].kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kBatch[v].smem());
@@ -1468,31 +1500,44 @@ static int batch_tune(BatchImpl* b, cudaStream_t st) {
 
 static void batch_enqueue(BatchImpl* b, cudaStream_t st) {
   const int n = (int)b->meshes.size();
-  const int igrid = std::max(1, std::min((b->total_nodes + 255) / 256, b->nsm * 8));
+  const int igrid = std::max(1, std::min((b->total_nodes + 255) / 256, b->nsm * 64));
+  const int nbr = (int)b->br.size();
+  if (nbr > 0) {
+    cudaEventRecord(b->fork, st);
+    for (int i = 0; i < nbr; ++i) cudaStreamWaitEvent(b->br[i], b->fork, 0);
+  }
+  // instances with their own launches: all three stages, on a branch stream
+  // or on the step's stream
+  int bi = 0;
+  for (int k = 0; k < n; ++k) {
+    if (!b->big[k]) continue;
+    cudaStream_t s2 = b->branch[k] ? b->br[bi++ % nbr] : st;
+    Mesh& m = *b->meshes[k];
+    for (int stage = 0; stage < 3; ++stage) {
+      launch_pencil_n(b->h_vol[(stage == 0 ? 0 : n) + k], m.N, m.nz, s2, m.pencil_variant);
+      const IncArgs& B = b->h_inc[stage * n + k];
+      const int blocks = grid_cap(B.NG, 64);   // as in the single-mesh step
+      if (stage == 0) dss_inc<0><<<blocks, 256, 0, s2>>>(B);
+      else if (stage == 1) dss_inc<1><<<blocks, 256, 0, s2>>>(B);
+      else dss_inc<2><<<blocks, 256, 0, s2>>>(B);
+    }
+  }
+  // the others: persistent column queue and concatenated increment kernel
   for (int stage = 0; stage < 3; ++stage) {
     if (b->ntiles > 0) {
       cudaMemsetAsync(b->d_counter + stage, 0, sizeof(int), st);
       batch_volume(b, b->variant, b->d_vol + (stage == 0 ? 0 : n), b->d_counter + stage, st);
     }
-    for (int k = 0; k < n; ++k)
-      if (b->big[k]) {
-        Mesh& m = *b->meshes[k];
-        launch_pencil_n(b->h_vol[(stage == 0 ? 0 : n) + k], m.N, m.nz, st, m.pencil_variant);
-      }
     const int ns = b->nsmall;
     if (ns > 0 && b->total_nodes > 0) {
       if (stage == 0) dss_inc_batch<0><<<igrid, 256, 0, st>>>(b->d_inc, b->d_off, ns, b->total_nodes, b->d_status);
       else if (stage == 1) dss_inc_batch<1><<<igrid, 256, 0, st>>>(b->d_inc + ns, b->d_off, ns, b->total_nodes, b->d_status);
       else dss_inc_batch<2><<<igrid, 256, 0, st>>>(b->d_inc + 2 * ns, b->d_off, ns, b->total_nodes, b->d_status);
     }
-    for (int k = 0; k < n; ++k) {
-      if (!b->big[k]) continue;
-      const IncArgs& B = b->h_inc[stage * n + k];
-      const int blocks = grid_cap(B.NG);
-      if (stage == 0) dss_inc<0><<<blocks, 256, 0, st>>>(B);
-      else if (stage == 1) dss_inc<1><<<blocks, 256, 0, st>>>(B);
-      else dss_inc<2><<<blocks, 256, 0, st>>>(B);
-    }
+  }
+  for (int i = 0; i < nbr; ++i) {
+    cudaEventRecord(b->br_done[i], b->br[i]);
+    cudaStreamWaitEvent(st, b->br_done[i], 0);
   }
 }
 

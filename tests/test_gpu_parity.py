@@ -496,14 +496,21 @@ def _instance_mesh(sem, nx, nz, N, L, levels, radius):
 
 
 @pytest.mark.parametrize("use_graph", [False, True])
-def test_batched_steps_equal_single_mesh_steps(sem, use_graph):
+@pytest.mark.parametrize("with_big", [False, True])
+def test_batched_steps_equal_single_mesh_steps(sem, use_graph, with_big):
     """One persistent launch per stage over five meshes of different order,
-    size and refinement gives the same states as stepping each mesh alone."""
+    size and refinement gives the same states as stepping each mesh alone.
+    With with_big, two meshes large enough to fill the GPU (at least 2 x SMs
+    columns) join them: they keep their own tuned launches, on branch streams
+    that run beside the shared queue."""
     specs = [(4, 2, 3, 300e3, 0), (4, 3, 4, 300e3, 1), (3, 2, 5, 300e3, 0),
              (3, 2, 6, 300e3, 1), (5, 17, 2, 300e3, 0)]
+    dts = [0.5, 0.25, 0.4, 0.2, 1.0]
+    if with_big:
+        specs += [(18, 1, 2, 300e3, 0), (20, 2, 3, 300e3, 0)]
+        dts += [0.5, 0.5]
     meshes = [_instance_mesh(sem, nx, nz, N, L, lev, 120e3) for nx, nz, N, L, lev in specs]
     p = sem.sem_params_default(precision=sem.SEM_PREC_MIXED)
-    dts = [0.5, 0.25, 0.4, 0.2, 1.0]
     init = [dev(random_state(sem.sem_mesh_coords_host(m).T, 24e3, 30 + k)) for k, m in enumerate(meshes)]
 
     def fresh():
@@ -514,15 +521,19 @@ def test_batched_steps_equal_single_mesh_steps(sem, use_graph):
             sem.sem_mirror(m, q, a)
         return qs, q32, work
 
-    qa, a32, wa = fresh()
-    for _ in range(2):
-        for k, m in enumerate(meshes):
-            sem.sem_step_mixed(m, p, qa[k], a32[k], wa[k], dts[k])
+    # the batch first: it tunes the large meshes' element kernels, which the
+    # single-mesh steps then use as well
     qb, b32, wb = fresh()
     batch = sem.sem_batch_create(meshes)
     for _ in range(2):
         sem.sem_batch_step_mixed(batch, p, qb, b32, wb, dts, use_graph=use_graph)
+    qa, a32, wa = fresh()
+    for _ in range(2):
+        for k, m in enumerate(meshes):
+            sem.sem_step_mixed(m, p, qa[k], a32[k], wa[k], dts[k])
     torch.cuda.synchronize()
+    if with_big:
+        assert min(m.Ncol for m in meshes[-2:]) >= 2 * torch.cuda.get_device_properties(0).multi_processor_count
     for k in range(len(meshes)):
         d = (qa[k] - qb[k]).abs().max().item()
         scale = qa[k].abs().max().item()
