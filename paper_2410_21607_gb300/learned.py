@@ -21,6 +21,13 @@ the criterion alone, and the criterion with the network, where an element is
 refined when either the current criterion or the network's prediction for
 `ahead` steps later asks for it, and coarsened only when both do (the
 criterion stays the fallback).
+
+Real adaptive runs (adaptive_run, adaptive_comparison): the same two
+schedules drive actual remeshes with solution transfer every `ahead`
+seconds, from a mesh refined by the criterion on the initial vortex, and are
+compared with the base mesh refined uniformly to lvl_max (the reference):
+final maximum wind, remesh count, missed-refinement rate between remeshes,
+element count and throughput.
 """
 import numpy as np
 
@@ -144,4 +151,121 @@ def gain_experiment(sem, torch, mesh, states, dt, n_train, steps=400, every=10, 
     res["level_criterion"] = float(np.mean([r["mean_level"] for r in res["criterion"]]))
     res["level_learned"] = float(np.mean([r["mean_level"] for r in res["learned"]]))
     res["remeshes"] = res["criterion"][0]["remeshes"]
+    res["net"] = net
     return res
+
+
+def element_levels(sem, torch, mesh, device):
+    """Refinement level of every element (column level, repeated over the layers)."""
+    lv = sem.sem_mesh_leaves_host(mesh)
+    return torch.from_numpy(np.repeat(lv[:, 0].astype(np.int64), mesh.nz)).to(device)
+
+
+def adaptive_run(sem, torch, spec, L, Lz, nx, nz, N, lvl_max, thresholds, dt, t_end,
+                 remesh_s=50.0, check_s=10.0, net=None, scales=(1e-3, 10.0, 10.0, 1.0, 1.0),
+                 uniform_level=None, physics=None):
+    """A real adaptive run: the mesh is refined and coarsened every remesh_s
+    seconds with the solution transferred (Algorithm 3), by the criterion's
+    flags alone (net None) or by the criterion combined with the network's
+    prediction for remesh_s later (refine if either asks, coarsen only if
+    both do).  The initial mesh is refined by the criterion on the initial
+    vortex.  With uniform_level the mesh is the base refined uniformly to that
+    level and never adapted (the reference).  Returns the final maximum wind,
+    the remesh count, the missed-refinement rate (checks every check_s between
+    remeshes), the mean element count and DOF-updates/s including remeshes.
+    physics: extra step parameters (for example the Smagorinsky stress)."""
+    import time
+    from synth.vortex import vortex_state
+    dev = "cuda"
+    p_step = sem.sem_params_default(precision=sem.SEM_PREC_MIXED, **(physics or {}))
+    p_crit = sem.sem_params_default(thresholds=list(thresholds), lvl_max=lvl_max)
+    thr = list(thresholds)
+    sc = np.asarray(scales, dtype=np.float32)
+    if uniform_level is not None:
+        m = sem.sem_mesh_create(L, L, Lz, nx << uniform_level, nx << uniform_level, nz, N)
+    else:
+        m = sem.sem_mesh_create(L, L, Lz, nx, nx, nz, N, lvl_max=lvl_max)
+        for _ in range(lvl_max):
+            q = torch.from_numpy(vortex_state(sem.sem_mesh_coords_host(m).T, Lz, spec)).to(dev)
+            fl = np.maximum(sem.sem_adapt_flags_host(m, p_crit, q), 0)
+            if not fl.any():
+                break
+            m = sem.sem_transfer_plan(m, fl)
+    q = torch.from_numpy(vortex_state(sem.sem_mesh_coords_host(m).T, Lz, spec)).to(dev)
+
+    def buffers(mesh, q):
+        q32 = torch.empty(q.shape, dtype=torch.float32, device=dev)
+        work = torch.empty((10, mesh.NG), dtype=torch.float32, device=dev)
+        sem.sem_mirror(mesh, q, q32)
+        return q32, work
+
+    q32, work = buffers(m, q)
+    steps = int(round(t_end / dt))
+    k_remesh, k_check = int(round(remesh_s / dt)), int(round(check_s / dt))
+    missed = want = remeshes = 0
+    dof = 0
+    elems = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(steps):
+        remesh_now = s > 0 and s % k_remesh == 0
+        if uniform_level is None and (remesh_now or (s > 0 and s % k_check == 0)):
+            flags = torch.empty(m.Ne, dtype=torch.int8, device=dev)
+            cmax = torch.empty(m.Ne, dtype=torch.float64, device=dev)
+            sem.sem_adapt_flags(m, p_crit, q, flags, cmax)
+            lev = element_levels(sem, torch, m, dev)
+            T = target_level(cmax, thr)
+            if not remesh_now:
+                missed += int((T > lev).sum())
+                want += int((T > 0).sum())
+            else:
+                fl = flags.long()
+                if net is not None:
+                    F = torch.empty((m.Ne, 136), dtype=torch.float32, device=dev)
+                    sem.sem_mlp_features(m, q, sc, F)
+                    F[:, 135] = lev.float()
+                    pred = torch.empty(m.Ne, dtype=torch.int8, device=dev)
+                    sem.sem_mlp_predict_flags(net, F, pred)
+                    pred = pred.long()
+                    pred = torch.where(lev >= lvl_max, torch.clamp(pred, max=0), pred)
+                    pred = torch.where(lev <= 0, torch.clamp(pred, min=0), pred)
+                    fl = torch.where((fl > 0) | (pred > 0), 1, torch.where((fl < 0) & (pred < 0), -1, 0))
+                fl_host = fl.to(torch.int8).cpu().numpy()
+                if fl_host.any():
+                    new = sem.sem_transfer_plan(m, fl_host)
+                    q2 = torch.empty((5, new.NG), dtype=torch.float64, device=dev)
+                    sem.sem_transfer(m, new, q, q2)
+                    m, q = new, q2
+                    q32, work = buffers(m, q)
+                    remeshes += 1
+        sem.sem_step_mixed(m, p_step, q, q32, work, dt)
+        dof += 15 * m.Ne * (N + 1) ** 3
+        elems.append(m.Ne)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    status = sem.sem_status(m)
+    wind = sem.sem_diag(m, p_step, q, 0.5 * L)["max_wind"] if status == 0 else float("nan")
+    return {"max_wind": wind, "remeshes": remeshes, "missed_rate": missed / max(want, 1),
+            "mean_elements": float(np.mean(elems)), "dof_updates_per_s": dof / wall,
+            "seconds": wall, "status": status}
+
+
+def adaptive_comparison(sem, torch, specs, net, L=150e3, Lz=24e3, nx=24, nz=2, N=4,
+                        thresholds=(15.0, 25.0), dt=0.25, t_end=400.0, physics=None):
+    """For each vortex: the uniform finest mesh (reference), the criterion
+    schedule and the criterion-plus-network schedule; max-wind errors of the
+    two schedules against the reference."""
+    lvl_max = len(thresholds)
+    out = []
+    for spec in specs:
+        ref = adaptive_run(sem, torch, spec, L, Lz, nx, nz, N, lvl_max, thresholds, dt, t_end,
+                           uniform_level=lvl_max, physics=physics)
+        cri = adaptive_run(sem, torch, spec, L, Lz, nx, nz, N, lvl_max, thresholds, dt, t_end,
+                           physics=physics)
+        lrn = adaptive_run(sem, torch, spec, L, Lz, nx, nz, N, lvl_max, thresholds, dt, t_end, net=net,
+                           physics=physics)
+        w = ref["max_wind"]
+        out.append({"reference": ref, "criterion": cri, "learned": lrn,
+                    "wind_err_criterion": abs(cri["max_wind"] - w) / w,
+                    "wind_err_learned": abs(lrn["max_wind"] - w) / w})
+    return out

@@ -6,7 +6,9 @@ trajectories to predict the criterion's flags 50 steps ahead and scheduled on
 the other two.  At the same remesh count (every 50 steps) the
 criterion-plus-network schedule must miss fewer refinements (checked every
 10 steps) than the criterion alone, while the criterion stays the fallback
-for coarsening.
+for coarsening.  The same schedules then drive real remeshes with solution
+transfer on a held-out vortex and must follow the uniformly refined
+reference's maximum wind.
 """
 import pytest
 
@@ -37,3 +39,17 @@ def test_learned_schedule_misses_fewer_refinements(sem):
     assert res["loss_last"] < 0.2 * res["loss_first"]
     assert res["remeshes"] == 9
     assert res["missed_learned"] < 0.95 * res["missed_criterion"], res
+    # the trained network driving real remeshes (with transfer) on a held-out
+    # vortex for 150 s: the run stays finite and follows the uniform reference
+    spec = translating_vortices()[8]
+    args = (sem, torch, spec, L, Lz, 24, 2, 4, 2, (15.0, 25.0), 0.25, 150.0)
+    phys = dict(smag_cs=0.5)
+    ref = learned.adaptive_run(*args, uniform_level=2, physics=phys)
+    cri = learned.adaptive_run(*args, physics=phys)
+    lrn = learned.adaptive_run(*args, net=res["net"], physics=phys)
+    for r in (ref, cri, lrn):
+        assert r["status"] == 0
+    assert 1 <= cri["remeshes"] <= 2 and 1 <= lrn["remeshes"] <= 2
+    assert cri["mean_elements"] < 0.5 * ref["mean_elements"]
+    for r in (cri, lrn):
+        assert abs(r["max_wind"] - ref["max_wind"]) <= 0.05 * ref["max_wind"]
