@@ -486,6 +486,47 @@ def test_autotune_then_step_parity(sem):
     assert np.all(err <= 1e-4), err
 
 
+@pytest.mark.parametrize("name", ["twolevel-N4", "twolevel-17-layers-N4", "stretched-twolevel-N4"])
+def test_every_variant_step_matches_oracle(sem, name):
+    """The increment-form step through each element-kernel variant (z-pencil
+    and line exchange, every layers-per-CTA count): two steps within 1e-4 of
+    the oracle, the mirror equal to the state rounded to float32, and the
+    line-exchange variants (the same arithmetic per node) within 1e-5 of each
+    other in the state's change."""
+    spec = dict(MESHES.get(name, {}))
+    if name == "twolevel-17-layers-N4":
+        spec = dict(L=300e3, Lz=24e3, nx=4, nz=17, N=4, leaves=two_level_leaves())
+    m, o, X, perm = make_pair(sem, **spec)
+    q_o = vortex_state(o.XG, o.Lz)
+    q_ref = q_o.copy()
+    for _ in range(2):
+        q_ref = ork.rk_step(o, PRM, q_ref, 0.5)
+    p = sem.sem_params_default(precision=sem.SEM_PREC_MIXED)
+    q0 = dev(q_o[:, perm])
+    q32 = torch.empty(q0.shape, dtype=torch.float32, device="cuda")
+    sem.sem_mirror(m, q0, q32)
+    rows, _ = sem.sem_autotune(m, p, q32, 1)
+    z = X[:, 2]
+    lines = []
+    for row in range(len(rows)):
+        sem.sem_autotune_select(m, row)
+        q = q0.clone()
+        sem.sem_mirror(m, q, q32)
+        work = torch.full((10, m.NG), float("nan"), dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            sem.sem_step_mixed(m, p, q, q32, work, 0.5)
+        got = host(q)
+        err = group_rel_l2(full_fields(got, z), full_fields(q_ref[:, perm], z))
+        assert np.all(err <= 1e-4), (row, rows[row], err)
+        np.testing.assert_allclose(host(q32), got, rtol=2.4e-7, atol=1e-30)
+        if rows[row][3] == 1:
+            lines.append(got)
+    assert len(lines) >= 2
+    for got in lines[1:]:
+        assert np.all(group_rel_l2(got - q_o[:, perm], lines[0] - q_o[:, perm]) <= 1e-5)
+    assert sem.sem_status(m) == 0
+
+
 def _instance_mesh(sem, nx, nz, N, L, levels, radius):
     from synth.workloads import geometric_flags
     m = sem.sem_mesh_create(L, L, 24e3, nx, nx, nz, N, lvl_max=max(levels, 1))
