@@ -264,33 +264,6 @@ void launch_n(const PhysArgs& A, int eq, int ncol, cudaStream_t st) {
   else physics_column<N, 1, R><<<ncol, threads, 0, st>>>(A);
 }
 
-// R(z) of the absorbing layer per level, rebuilt when gamma or z_d change
-int ensure_sponge(Mesh& m, const sem_params& p) {
-  DeviceTables& D = *m.dev;
-  if (D.spg && D.spg_key[0] == p.sponge_gamma && D.spg_key[1] == p.sponge_depth) return SEM_OK;
-  std::vector<double> R(m.NZ);
-  std::vector<float> R32(m.NZ);
-  const double pi = 3.14159265358979323846;
-  for (int k = 0; k < m.NZ; ++k) {
-    const double z = m.zk[k];
-    const double a = 0.5 * pi * (1.0 - (m.Lz - z) / p.sponge_depth);
-    const double s = std::sin(a);
-    double r = std::min(1.0, std::max(0.0, p.sponge_gamma * s * s));
-    if (!(z >= m.Lz - p.sponge_depth)) r = 0.0;
-    R[k] = r;
-    R32[k] = (float)r;
-  }
-  if (!D.spg) {
-    SEM_CUDA_TRY(cudaMalloc((void**)&D.spg, (size_t)m.NZ * sizeof(double)));
-    SEM_CUDA_TRY(cudaMalloc((void**)&D.spg32, (size_t)m.NZ * sizeof(float)));
-  }
-  SEM_CUDA_TRY(cudaMemcpy(D.spg, R.data(), R.size() * sizeof(double), cudaMemcpyHostToDevice));
-  SEM_CUDA_TRY(cudaMemcpy(D.spg32, R32.data(), R32.size() * sizeof(float), cudaMemcpyHostToDevice));
-  D.spg_key[0] = p.sponge_gamma;
-  D.spg_key[1] = p.sponge_depth;
-  return SEM_OK;
-}
-
 // Mixed form, conservative set: the same terms with the thread layout of the
 // line-exchange element kernel (coalesced z-line loads and residual updates).
 // Thread (layer kk, line ab) owns the vertical line of N+1 nodes of its
@@ -340,6 +313,7 @@ physics_lines(const PhysArgs A) {
   const float* ref = (const float*)A.ref;
   const float* spg = (const float*)A.spg;
   float* rc = (float*)A.rc;
+  const bool heat = A.heat_amp != 0.0;
   const int nchunk = (A.nz + KL - 1) / KL;
   for (int ch = 0; ch < nchunk; ++ch) {
     const int k = ch * KL + kk;
@@ -356,6 +330,14 @@ physics_lines(const PhysArgs A) {
     float rho[n1];
     float* zV = sV + kk * LS + ab * LW;   // this thread's z-line, + comp n1 + c
     if (act) {
+      {
+        // the residuals this thread updates at the end of the chunk: start
+        // bringing them into L1 now
+        const float* dp = rc + ((long long)((long long)col * Nq + ab) * kFields) * A.NZr + kz0;
+#pragma unroll
+        for (int f = 0; f < kFields; ++f)
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(dp + (long long)f * A.NZr));
+      }
 #pragma unroll
       for (int c = 0; c < n1; ++c) {
         const int kz = kz0 + c;
@@ -377,7 +359,7 @@ physics_lines(const PhysArgs A) {
           }
         }
         rho[c] = __ldg(ref + (long long)kz * kRef + 3) + v[0];
-        const float inv = 1.f / rho[c];
+        const float inv = __frcp_rn(rho[c]);   // = 1 / rho, correctly rounded
         zV[0 * n1 + c] = v[1] * inv;
         zV[1 * n1 + c] = v[2] * inv;
         zV[2 * n1 + c] = v[3] * inv;
@@ -387,7 +369,7 @@ physics_lines(const PhysArgs A) {
 #pragma unroll
           for (int f = 0; f < kFields; ++f) r[f][c] = wJ * (-Rz * v[f]);
         }
-        if (A.heat_amp != 0.0) {
+        if (heat) {
           const double x = A.col_x0[col] + 0.5 * (1.0 + p_xi[N][i]) * A.geo[lev][0];
           const double y = A.col_y0[col] + 0.5 * (1.0 + p_xi[N][j]) * A.geo[lev][1];
           const float Q = (float)heating_at(A, x, y, A.zk[kz]);
@@ -500,7 +482,7 @@ physics_lines(const PhysArgs A) {
       const bool top = (k == A.nz - 1);
       // fields with a contribution: the layer touches all, the stress the
       // momentum, the heating the theta equation
-      const bool lay = spg != nullptr, heat = A.heat_amp != 0.0;
+      const bool lay = spg != nullptr;
 #pragma unroll
       for (int f = 0; f < kFields; ++f) {
         if (f == 0 && !lay) continue;
@@ -540,12 +522,42 @@ int launch_lines(const PhysArgs& A, int ncol, cudaStream_t st) {
 
 }  // namespace
 
+// Absorbing-layer rate R(z) per level (float64 and float32 tables), rebuilt
+// when gamma or the depth change.
+int ensure_sponge(Mesh& m, const sem_params& p) {
+  DeviceTables& D = *m.dev;
+  if (D.spg && D.spg_key[0] == p.sponge_gamma && D.spg_key[1] == p.sponge_depth) return SEM_OK;
+  std::vector<double> R(m.NZ);
+  std::vector<float> R32(m.NZ);
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < m.NZ; ++k) {
+    const double z = m.zk[k];
+    const double a = 0.5 * pi * (1.0 - (m.Lz - z) / p.sponge_depth);
+    const double s = std::sin(a);
+    double r = std::min(1.0, std::max(0.0, p.sponge_gamma * s * s));
+    if (!(z >= m.Lz - p.sponge_depth)) r = 0.0;
+    R[k] = r;
+    R32[k] = (float)r;
+  }
+  if (!D.spg) {
+    SEM_CUDA_TRY(cudaMalloc((void**)&D.spg, (size_t)m.NZ * sizeof(double)));
+    SEM_CUDA_TRY(cudaMalloc((void**)&D.spg32, (size_t)m.NZ * sizeof(float)));
+  }
+  SEM_CUDA_TRY(cudaMemcpy(D.spg, R.data(), R.size() * sizeof(double), cudaMemcpyHostToDevice));
+  SEM_CUDA_TRY(cudaMemcpy(D.spg32, R32.data(), R32.size() * sizeof(float), cudaMemcpyHostToDevice));
+  D.spg_key[0] = p.sponge_gamma;
+  D.spg_key[1] = p.sponge_depth;
+  return SEM_OK;
+}
+
 int launch_physics(Mesh& m, const sem_params& p, const void* q, bool mixed, void* scratch,
-                   double time, cudaStream_t st) {
+                   double time, cudaStream_t st, bool sponge_done) {
   int rc = upload_constants();
   if (rc) return rc;
   DeviceTables& D = *m.dev;
-  const bool sponge = p.sponge_gamma > 0.0;
+  const bool sponge = p.sponge_gamma > 0.0 && !sponge_done;
+  const double heat_amp = p.heat_q0 > 0.0 ? p.heat_q0 * std::tanh(time / p.heat_ramp) : 0.0;
+  if (!sponge && !(p.smag_cs > 0.0) && heat_amp == 0.0) return SEM_OK;   // nothing to add
   if (sponge && (rc = ensure_sponge(m, p))) return rc;
   PhysArgs A;
   A.q = q;
@@ -562,7 +574,7 @@ int launch_physics(Mesh& m, const sem_params& p, const void* q, bool mixed, void
   A.smag = p.smag_cs > 0.0;
   A.NG = m.NG;
   A.cs = p.smag_cs;
-  A.heat_amp = p.heat_q0 > 0.0 ? p.heat_q0 * std::tanh(time / p.heat_ramp) : 0.0;
+  A.heat_amp = heat_amp;
   A.heat_r0 = p.heat_r0;
   A.heat_width = p.heat_width;
   A.heat_rmax = p.heat_rmax;

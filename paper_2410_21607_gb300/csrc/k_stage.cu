@@ -106,6 +106,8 @@ struct VolArgs {
   const double* hzk;    // [nz] layer thicknesses (geo holds the values for unit thickness)
   const float* hzk32;
   const float4* ref4;   // [NZ] packed p0, rho0, (rho theta)0, 1/(rho theta)0 (float32)
+  const float* spg32;   // [NZ] absorbing-layer rate R(z): the line-exchange kernel adds
+                        // -R q' (weak form, collocated) when set; null: not added here
 };
 
 template <typename R> __device__ __forceinline__ const R* geo_of(const VolArgs& A, int l);
@@ -820,6 +822,12 @@ __device__ __forceinline__ void lines_body(const VolArgs& A, const int col, floa
         rz[1][c] += T.su;
         rz[2][c] += T.sv;
         rz[3][c] += T.sw;
+        if (A.spg32) {
+          // absorbing layer (Sec. 4): -R(z) q' at the node, weighted like the sources
+          const float wR = (wi * wj * wc * J * hk) * __ldg(A.spg32 + kz);
+#pragma unroll
+          for (int f = 0; f < kFields; ++f) rz[f][c] = fmaf(-wR, v[f], rz[f][c]);
+        }
       }
 #pragma unroll
       for (int f = 0; f < kFields; ++f) sT[(f * KL + kk) * Nq + ab] = rz[f][N];
@@ -962,6 +970,22 @@ static int launch_pencil_n(const VolArgs& A, int N, int nz, cudaStream_t st, int
   return kPencil[variant].launch(A, st);
 }
 
+// Mixed conservative set on a line-exchange variant: the element kernel adds
+// the absorbing layer itself (it holds every node's state), so the physics
+// pass leaves it out (done = true).
+static int element_sponge(Mesh& m, const sem_params& p, VolArgs& A, bool& done) {
+  done = false;
+  if (!(p.sponge_gamma > 0.0) || p.eqset != SEM_EQ_CONSERVATIVE) return SEM_OK;
+  int v = m.pencil_variant;
+  if (v < 0 || v >= kNumPencil || kPencil[v].N != m.N) v = pencil_default(m.N, m.nz);
+  if (v < 0 || kPencil[v].kind != 1) return SEM_OK;
+  const int rc = ensure_sponge(m, p);
+  if (rc) return rc;
+  A.spg32 = m.dev->spg32;
+  done = true;
+  return SEM_OK;
+}
+
 static VolArgs make_vol_args(Mesh& m, const sem_params& p, const void* q, bool mixed, void* scratch) {
   DeviceTables& D = *m.dev;
   VolArgs A;
@@ -976,6 +1000,7 @@ static VolArgs make_vol_args(Mesh& m, const sem_params& p, const void* q, bool m
   A.hzk = D.hzk;
   A.hzk32 = D.hzk32;
   A.ref4 = reinterpret_cast<const float4*>(D.ref32 + (size_t)m.NZ * kRef);
+  A.spg32 = nullptr;
   A.Ncol = (int)m.Ncol();
   A.nz = m.nz;
   A.NZ = m.NZ;
@@ -1128,10 +1153,13 @@ int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float
   for (int stage = 0; stage < 3; ++stage) {
     // element work on the stage state's mirror
     VolArgs A = make_vol_args(m, p, stage == 0 ? (const void*)q32 : (const void*)qs32, true, nullptr);
+    bool sponge_done = false;
+    if ((rc = element_sponge(m, p, A, sponge_done))) return rc;
     if ((rc = launch_pencil_n(A, m.N, m.nz, st, m.pencil_variant))) return rc;
     SEM_CUDA_TRY(cudaGetLastError());
     if (physics_on(p) &&
-        (rc = launch_physics(m, p, A.q, true, nullptr, p.time + (stage == 0 ? 0.0 : (stage == 1 ? dt : 0.5 * dt)), st)))
+        (rc = launch_physics(m, p, A.q, true, nullptr, p.time + (stage == 0 ? 0.0 : (stage == 1 ? dt : 0.5 * dt)),
+                             st, sponge_done)))
       return rc;
     IncArgs B;
     B.rc = (const float*)D.scratch;
@@ -1685,7 +1713,9 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
   }
   VolArgs A = make_vol_args(m, p, mixed ? (const void*)qs32 : (const void*)s.qs, mixed, s.scratch);
   const int eq = p.eqset;
+  bool sponge_done = false;
   if (mixed && eq == SEM_EQ_CONSERVATIVE) {
+    if ((rc = element_sponge(m, p, A, sponge_done))) return rc;
     if ((rc = launch_pencil_n(A, m.N, m.nz, st, m.pencil_variant))) return rc;
   } else switch (m.N) {
     case 2: launch_volume_n<2>(A, eq, mixed, st); break;
@@ -1697,7 +1727,8 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
   }
   SEM_CUDA_TRY(cudaGetLastError());
   if (physics_on(p) &&
-      (rc = launch_physics(m, p, mixed ? (const void*)qs32 : (const void*)s.qs, mixed, s.scratch, s.time, st)))
+      (rc = launch_physics(m, p, mixed ? (const void*)qs32 : (const void*)s.qs, mixed, s.scratch, s.time, st,
+                           sponge_done)))
     return rc;
   DssArgs B;
   B.rc = s.scratch ? s.scratch : D.scratch;

@@ -76,6 +76,40 @@ def test_physics_rhs_mixed_matches_oracle(sem, name, eqset):
     assert np.all(err <= 1e-4 * np.maximum(ratio, 1.0)), (err, ratio)
 
 
+@pytest.mark.parametrize("name", ["twolevel-N4", "stretched-twolevel-N4", "uniform-5x4x3-N6"])
+def test_physics_rhs_every_variant_matches_oracle(sem, name):
+    """Mixed tendency with both terms through each element-kernel variant: a
+    line-exchange variant adds the absorbing layer itself and the physics pass
+    only the stress, a z-pencil variant leaves both to the physics pass."""
+    m, o, X, perm = make_pair(sem, **MESHES[name])
+    q_o = random_state(o.XG, o.Lz, 24)
+    T_o = orhs.rhs(o, q_o, refstate.Params(**PHYS))
+    dT_o = T_o - orhs.rhs(o, q_o, refstate.Params())
+    ratio = group_rel_l2(T_o, 0 * T_o) / np.maximum(group_rel_l2(dT_o, 0 * dT_o), 1e-300)
+    q = dev(q_o[:, perm])
+    q32 = torch.empty(q.shape, dtype=torch.float32, device="cuda")
+    sem.sem_mirror(m, q, q32)
+    rows, _ = sem.sem_autotune(m, sem.sem_params_default(precision=1), q32, 1)
+    kinds = set()
+    for row in range(len(rows)):
+        sem.sem_autotune_select(m, row)
+        T = _gpu_rhs(sem, m, q, "C", 1, **PHYS)
+        dT = T - _gpu_rhs(sem, m, q, "C", 1)
+        assert np.all(group_rel_l2(T, T_o[:, perm]) <= 1e-4), rows[row]
+        err = group_rel_l2(dT, dT_o[:, perm])
+        assert np.all(err <= 1e-4 * np.maximum(ratio, 1.0)), (rows[row], err, ratio)
+        kinds.add(rows[row][3])
+    assert kinds == {0, 1}
+    # the absorbing layer alone (no physics pass at all on a line variant)
+    sp = dict(sponge_gamma=0.02, sponge_depth=6000.0)
+    dS_o = orhs.rhs(o, q_o, refstate.Params(**sp)) - orhs.rhs(o, q_o, refstate.Params())
+    sem.sem_autotune_select(m, -1)
+    dS = _gpu_rhs(sem, m, q, "C", 1, **sp) - _gpu_rhs(sem, m, q, "C", 1)
+    ratio = group_rel_l2(T_o, 0 * T_o) / np.maximum(group_rel_l2(dS_o, 0 * dS_o), 1e-300)
+    assert np.all(group_rel_l2(dS, dS_o[:, perm]) <= 1e-4 * np.maximum(ratio, 1.0))
+    assert sem.sem_status(m) == 0
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_physics_steps_match_oracle(sem, prec):
     """Ten SSP-RK3 steps of 1 s with both terms on the two-level mesh, in the
