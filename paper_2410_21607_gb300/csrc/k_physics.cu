@@ -554,13 +554,14 @@ int ensure_sponge(Mesh& m, const sem_params& p) {
 }
 
 int launch_physics(Mesh& m, const sem_params& p, const void* q, bool mixed, void* scratch,
-                   double time, cudaStream_t st, bool sponge_done) {
+                   double time, cudaStream_t st, bool sponge_done, bool smag_done) {
   int rc = upload_constants();
   if (rc) return rc;
   DeviceTables& D = *m.dev;
   const bool sponge = p.sponge_gamma > 0.0 && !sponge_done;
   const double heat_amp = p.heat_q0 > 0.0 ? p.heat_q0 * std::tanh(time / p.heat_ramp) : 0.0;
-  if (!sponge && !(p.smag_cs > 0.0) && heat_amp == 0.0) return SEM_OK;   // nothing to add
+  const bool smag = p.smag_cs > 0.0 && !smag_done;
+  if (!sponge && !smag && heat_amp == 0.0) return SEM_OK;   // nothing to add
   if (sponge && (rc = ensure_sponge(m, p))) return rc;
   PhysArgs A;
   A.q = q;
@@ -574,7 +575,7 @@ int launch_physics(Mesh& m, const sem_params& p, const void* q, bool mixed, void
   A.nz = m.nz;
   A.NZ = m.NZ;
   A.NZr = m.NZr();
-  A.smag = p.smag_cs > 0.0;
+  A.smag = smag;
   A.NG = m.NG;
   A.cs = p.smag_cs;
   A.heat_amp = heat_amp;

@@ -108,6 +108,8 @@ struct VolArgs {
   const float4* ref4;   // [NZ] packed p0, rho0, (rho theta)0, 1/(rho theta)0 (float32)
   const float* spg32;   // [NZ] absorbing-layer rate R(z): the line-exchange kernel adds
                         // -R q' (weak form, collocated) when set; null: not added here
+  float smag[kLev][3];  // per level (C_s Delta)^2, 2/hx, 2/hy: the horizontal
+                        // Smagorinsky stress, for the kernels that add it
 };
 
 template <typename R> __device__ __forceinline__ const R* geo_of(const VolArgs& A, int l);
@@ -767,13 +769,132 @@ __host__ __device__ constexpr int lines_smem_floats() {
   return 2 * KL * lines_ls<N, KL>() + kFields * KL * (N + 1) * (N + 1) + 2 * kFields * (N + 1) * (N + 1);
 }
 
+// Horizontal Smagorinsky stress (Sec. 4) of one layer chunk, added to the
+// z-line owners' residuals rz (momentum rows) inside the element kernel, so
+// the state is not read again and the residual not re-written by a separate
+// pass.  Same steps and thread roles as the separate stress pass: z-line
+// owners form u, v, w; x-/y-line owners differentiate their lines; z-line
+// owners form nu_t = (C_s Delta)^2 |S_h| and the weighted fluxes of rho tau;
+// line owners contract them in weak form; z-line owners add them up.  The
+// components live in sX and sY (free once the inviscid add-back is done).
+template <int N, int KL, int LWV, int LSV>
+__device__ __forceinline__ void smag_phases(const VolArgs& A, float* smem, const bool act, const int kk,
+                                            const int ab, const int lc, const int lo, const int hm,
+                                            const int kz0, const int lev, const float wi, const float wj,
+                                            const float sxk, const float syk, float (&rz)[kFields][N + 1]) {
+  constexpr int n1 = N + 1;
+  float* zV = smem + kk * LSV + ab * LWV;   // this thread's z-line, + comp n1 + c
+  const float cs2 = A.smag[lev][0], gx = A.smag[lev][1], gy = A.smag[lev][2];
+  float rho[n1];
+  __syncthreads();   // every add-back has read its fluxes: the buffers are free
+  if (act) {
+#pragma unroll
+    for (int c = 0; c < n1; ++c) {
+      const int kz = kz0 + c;
+      float v[kFields];
+      load_node<N>(A, hm, kz, v);
+      rho[c] = __ldg(A.ref4 + kz).y + v[0];
+      const float inv = __frcp_rn(rho[c]);
+      zV[0 * n1 + c] = v[1] * inv;
+      zV[1 * n1 + c] = v[2] * inv;
+      zV[2 * n1 + c] = v[3] * inv;
+    }
+  }
+  __syncthreads();
+  if (act) {
+    // derivatives along the x-line (nodes (m, lo, lc)) and the y-line (nodes (lo, m, lc))
+    float* bx = smem + kk * LSV + lo * n1 * LWV + lc;
+    float* by = smem + kk * LSV + lo * LWV + lc;
+#pragma unroll
+    for (int cp = 0; cp < 3; ++cp) {
+      float F[n1], G[n1];
+#pragma unroll
+      for (int m = 0; m < n1; ++m) {
+        F[m] = bx[m * LWV + cp * n1];
+        G[m] = by[m * n1 * LWV + cp * n1];
+      }
+#pragma unroll
+      for (int o = 0; o < n1; ++o) {
+        float ax_ = 0.f, ay_ = 0.f;
+#pragma unroll
+        for (int m = 0; m < n1; ++m) {
+          ax_ = fmaf(c_Df[N][o * n1 + m], F[m], ax_);
+          ay_ = fmaf(c_Df[N][o * n1 + m], G[m], ay_);
+        }
+        bx[o * LWV + (3 + cp) * n1] = ax_ * gx;
+        by[o * n1 * LWV + (6 + cp) * n1] = ay_ * gy;
+      }
+    }
+  }
+  __syncthreads();
+  if (act) {
+    // eddy viscosity and weighted fluxes of rho tau at the thread's nodes
+#pragma unroll
+    for (int c = 0; c < n1; ++c) {
+      const float ux = zV[3 * n1 + c], vx = zV[4 * n1 + c], wx = zV[5 * n1 + c];
+      const float uy = zV[6 * n1 + c], vy = zV[7 * n1 + c], wy = zV[8 * n1 + c];
+      const float sxy = 0.5f * (uy + vx);
+      const float s2 = 2.f * (ux * ux + vy * vy + 2.f * sxy * sxy);
+      const float nut = cs2 * (s2 > 0.f ? s2 * rsqrtf(s2) : 0.f);
+      const float kv = rho[c] * nut;
+      const float wc = c_wf[N][c];
+      const float ax = wj * wc * sxk, ay = wi * wc * syk;
+      zV[3 * n1 + c] = ax * (-2.f * kv * ux);
+      zV[4 * n1 + c] = ax * (-2.f * kv * sxy);
+      zV[5 * n1 + c] = ax * (-kv * wx);
+      zV[6 * n1 + c] = ay * (-2.f * kv * sxy);
+      zV[7 * n1 + c] = ay * (-2.f * kv * vy);
+      zV[8 * n1 + c] = ay * (-kv * wy);
+    }
+  }
+  __syncthreads();
+  if (act) {
+    // weak contraction of the line's fluxes, written back onto its nodes
+    float* bx = smem + kk * LSV + lo * n1 * LWV + lc;
+    float* by = smem + kk * LSV + lo * LWV + lc;
+#pragma unroll
+    for (int cp = 0; cp < 3; ++cp) {
+      float F[n1], G[n1];
+#pragma unroll
+      for (int m = 0; m < n1; ++m) {
+        F[m] = bx[m * LWV + (3 + cp) * n1];
+        G[m] = by[m * n1 * LWV + (6 + cp) * n1];
+      }
+#pragma unroll
+      for (int o = 0; o < n1; ++o) {
+        float ax_ = 0.f, ay_ = 0.f;
+#pragma unroll
+        for (int m = 0; m < n1; ++m) {
+          ax_ = fmaf(c_Dwf[N][o * n1 + m], F[m], ax_);
+          ay_ = fmaf(c_Dwf[N][o * n1 + m], G[m], ay_);
+        }
+        bx[o * LWV + (3 + cp) * n1] = ax_;
+        by[o * n1 * LWV + (6 + cp) * n1] = ay_;
+      }
+    }
+  }
+  __syncthreads();
+  if (act) {
+#pragma unroll
+    for (int cp = 0; cp < 3; ++cp)
+#pragma unroll
+      for (int c = 0; c < n1; ++c) rz[1 + cp][c] += zV[(3 + cp) * n1 + c] + zV[(6 + cp) * n1 + c];
+  }
+}
+
 // Body shared by the single-mesh kernel (one CTA per column) and the batched
 // persistent kernel.  Threads t >= KL (N+1)^2 of a larger CTA take part in
 // the barriers only.
-template <int N, int KL>
+template <int N, int KL, bool SMAG = false>
 __device__ __forceinline__ void lines_body(const VolArgs& A, const int col, float* smem, const int t) {
   constexpr int n1 = N + 1, Nq = n1 * n1;
   constexpr int LW = lines_lw<N>(), LS = lines_ls<N, KL>();
+  // SMAG: the stress phases keep 9 components per node (u, v, w, their x and
+  // y derivatives, then the weighted fluxes) in sX and sY, reused as one
+  // buffer with layer stride LSV
+  constexpr int LWV = (9 * n1) | 1;
+  constexpr int LSV = Nq * LWV + ((32 / KL - (Nq * LWV) % 32) % 32 + 32) % 32;
+  static_assert(!SMAG || LSV <= 2 * LS, "stress components do not fit the flux buffers");
   float* sX = smem;                       // [kk][LS]: x fluxes, then x contractions
   float* sY = sX + KL * LS;               // [kk][LS]: the same for y
   float* sT = sY + KL * LS;               // [f][kk][ab]: z part of the top-node residual
@@ -829,8 +950,10 @@ __device__ __forceinline__ void lines_body(const VolArgs& A, const int col, floa
           for (int f = 0; f < kFields; ++f) rz[f][c] = fmaf(-wR, v[f], rz[f][c]);
         }
       }
+      if constexpr (!SMAG) {
 #pragma unroll
-      for (int f = 0; f < kFields; ++f) sT[(f * KL + kk) * Nq + ab] = rz[f][N];
+        for (int f = 0; f < kFields; ++f) sT[(f * KL + kk) * Nq + ab] = rz[f][N];
+      }
     }
     __syncthreads();
     if (act) {
@@ -866,14 +989,35 @@ __device__ __forceinline__ void lines_body(const VolArgs& A, const int col, floa
       }
     }
     __syncthreads();
+    if constexpr (SMAG) {
+      if (act) {
+#pragma unroll
+        for (int f = 0; f < kFields; ++f)
+#pragma unroll
+          for (int c = 0; c < n1; ++c) rz[f][c] += zX[f * n1 + c] + zY[f * n1 + c];
+      }
+      smag_phases<N, KL, LWV, LSV>(A, smem, act, kk, ab, lc, lo, hm, kz0, lev, wi, wj, sx * hk, sy * hk, rz);
+      // the full top-node value of each layer, for the layer above
+      if (act) {
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) sT[(f * KL + kk) * Nq + ab] = rz[f][N];
+      }
+      __syncthreads();
+    }
     if (act) {
+      if constexpr (!SMAG) {
 #pragma unroll
-      for (int f = 0; f < kFields; ++f)
+        for (int f = 0; f < kFields; ++f)
 #pragma unroll
-        for (int c = 0; c < n1; ++c) rz[f][c] += zX[f * n1 + c] + zY[f * n1 + c];
+          for (int c = 0; c < n1; ++c) rz[f][c] += zX[f * n1 + c] + zY[f * n1 + c];
+      }
       // vertical DSS: the bottom node takes the full top-node value of the
-      // layer below (its z part from sT, its x and y parts still in sX, sY)
-      if (kk > 0) {
+      // layer below (its z part from sT, its x and y parts still in sX, sY;
+      // with SMAG all of it from sT)
+      if (kk > 0 && SMAG) {
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) rz[f][0] += sT[(f * KL + kk - 1) * Nq + ab];
+      } else if (kk > 0) {
         const float* pX = sX + (kk - 1) * LS + ab * LW;
         const float* pY = sY + (kk - 1) * LS + ab * LW;
 #pragma unroll
@@ -912,6 +1056,28 @@ volume_lines_mixed(const VolArgs A) {
   lines_body<N, KL>(A, blockIdx.x, smem, threadIdx.x);
 }
 
+// The same with the horizontal Smagorinsky stress added (N = 4 variants).
+template <int N, int KL, int MB>
+__global__ void __launch_bounds__(KL * (N + 1) * (N + 1), MB)
+volume_lines_smag(const VolArgs A) {
+  extern __shared__ __align__(16) float smem[];
+  lines_body<N, KL, true>(A, blockIdx.x, smem, threadIdx.x);
+}
+
+template <int N, int KL, int MB>
+static int launch_lines_smag(const VolArgs& A, cudaStream_t st) {
+  const size_t sm = sizeof(float) * lines_smem_floats<N, KL>();
+  static bool attr = false;
+  if (!attr) {
+    SEM_CUDA_TRY(cudaFuncSetAttribute(volume_lines_smag<N, KL, MB>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr = true;
+  }
+  ProfScope ps("volume_mixed", st);
+  volume_lines_smag<N, KL, MB><<<A.Ncol, KL * (N + 1) * (N + 1), sm, st>>>(A);
+  return SEM_OK;
+}
+
 template <int N, int KL, int MB>
 static int launch_lines(const VolArgs& A, cudaStream_t st) {
   const size_t sm = sizeof(float) * lines_smem_floats<N, KL>();
@@ -933,6 +1099,7 @@ struct PencilVariant {
   int N, KL, MB;
   int (*launch)(const VolArgs&, cudaStream_t);
   int kind;         // 0: z-pencil volume_pencil_mixed; 1: line-exchange volume_lines_mixed
+  int (*launch_smag)(const VolArgs&, cudaStream_t);   // with the stress added; null: none
 };
 static const PencilVariant kPencil[] = {
     {2, 16, 2, launch_pencil<2, 16, 2>},    {2, 16, 4, launch_lines<2, 16, 4>, 1},
@@ -940,8 +1107,10 @@ static const PencilVariant kPencil[] = {
     {3, 16, 2, launch_pencil<3, 16, 2>},    {3, 16, 2, launch_lines<3, 16, 2>, 1},
     {3, 8, 4, launch_lines<3, 8, 4>, 1},
     {4, 8, 2, launch_pencil<4, 8, 2>},      {4, 16, 2, launch_pencil<4, 16, 2>},
-    {4, 16, 2, launch_lines<4, 16, 2>, 1},  {4, 8, 4, launch_lines<4, 8, 4>, 1},
-    {4, 8, 2, launch_lines<4, 8, 2>, 1},    {4, 4, 8, launch_lines<4, 4, 8>, 1},
+    {4, 16, 2, launch_lines<4, 16, 2>, 1, launch_lines_smag<4, 16, 2>},
+    {4, 8, 4, launch_lines<4, 8, 4>, 1, launch_lines_smag<4, 8, 4>},
+    {4, 8, 2, launch_lines<4, 8, 2>, 1, launch_lines_smag<4, 8, 2>},
+    {4, 4, 8, launch_lines<4, 4, 8>, 1, launch_lines_smag<4, 4, 8>},
     {5, 8, 2, launch_pencil<5, 8, 2>},      {5, 8, 2, launch_lines<5, 8, 2>, 1},
     {5, 4, 4, launch_lines<5, 4, 4>, 1},
     {6, 4, 2, launch_pencil<6, 4, 2>},      {6, 8, 1, launch_lines<6, 8, 1>, 1},
@@ -964,25 +1133,40 @@ static int pencil_default(int N, int nz) {
   return best;
 }
 
-static int launch_pencil_n(const VolArgs& A, int N, int nz, cudaStream_t st, int variant = -1) {
+static int launch_pencil_n(const VolArgs& A, int N, int nz, cudaStream_t st, int variant = -1,
+                           bool smag = false) {
   if (variant < 0 || variant >= kNumPencil || kPencil[variant].N != N) variant = pencil_default(N, nz);
   if (variant < 0) return fail(SEM_ERR_UNSUPPORTED, "order N not compiled");
+  if (smag) return kPencil[variant].launch_smag(A, st);
   return kPencil[variant].launch(A, st);
 }
 
 // Mixed conservative set on a line-exchange variant: the element kernel adds
-// the absorbing layer itself (it holds every node's state), so the physics
-// pass leaves it out (done = true).
-static int element_sponge(Mesh& m, const sem_params& p, VolArgs& A, bool& done) {
-  done = false;
-  if (!(p.sponge_gamma > 0.0) || p.eqset != SEM_EQ_CONSERVATIVE) return SEM_OK;
+// the absorbing layer itself (it holds every node's state), and, where the
+// variant has a stress-adding form, the horizontal Smagorinsky stress too;
+// the physics pass leaves out what it added (sponge_done, smag_done).
+static int element_terms(Mesh& m, const sem_params& p, VolArgs& A, bool& sponge_done, bool& smag_done) {
+  sponge_done = smag_done = false;
+  if (p.eqset != SEM_EQ_CONSERVATIVE) return SEM_OK;
   int v = m.pencil_variant;
   if (v < 0 || v >= kNumPencil || kPencil[v].N != m.N) v = pencil_default(m.N, m.nz);
   if (v < 0 || kPencil[v].kind != 1) return SEM_OK;
-  const int rc = ensure_sponge(m, p);
-  if (rc) return rc;
-  A.spg32 = m.dev->spg32;
-  done = true;
+  if (p.sponge_gamma > 0.0) {
+    const int rc = ensure_sponge(m, p);
+    if (rc) return rc;
+    A.spg32 = m.dev->spg32;
+    sponge_done = true;
+  }
+  if (p.smag_cs > 0.0 && kPencil[v].launch_smag) {
+    for (int l = 0; l < kLev; ++l) {
+      const double hx = m.hx(l), hy = m.hy(l);
+      const double csd = p.smag_cs * (hx + hy) / (2.0 * m.N);
+      A.smag[l][0] = (float)(csd * csd);
+      A.smag[l][1] = (float)(2.0 / hx);
+      A.smag[l][2] = (float)(2.0 / hy);
+    }
+    smag_done = true;
+  }
   return SEM_OK;
 }
 
@@ -1153,13 +1337,13 @@ int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float
   for (int stage = 0; stage < 3; ++stage) {
     // element work on the stage state's mirror
     VolArgs A = make_vol_args(m, p, stage == 0 ? (const void*)q32 : (const void*)qs32, true, nullptr);
-    bool sponge_done = false;
-    if ((rc = element_sponge(m, p, A, sponge_done))) return rc;
-    if ((rc = launch_pencil_n(A, m.N, m.nz, st, m.pencil_variant))) return rc;
+    bool sponge_done = false, smag_done = false;
+    if ((rc = element_terms(m, p, A, sponge_done, smag_done))) return rc;
+    if ((rc = launch_pencil_n(A, m.N, m.nz, st, m.pencil_variant, smag_done))) return rc;
     SEM_CUDA_TRY(cudaGetLastError());
     if (physics_on(p) &&
         (rc = launch_physics(m, p, A.q, true, nullptr, p.time + (stage == 0 ? 0.0 : (stage == 1 ? dt : 0.5 * dt)),
-                             st, sponge_done)))
+                             st, sponge_done, smag_done)))
       return rc;
     IncArgs B;
     B.rc = (const float*)D.scratch;
@@ -1713,10 +1897,10 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
   }
   VolArgs A = make_vol_args(m, p, mixed ? (const void*)qs32 : (const void*)s.qs, mixed, s.scratch);
   const int eq = p.eqset;
-  bool sponge_done = false;
+  bool sponge_done = false, smag_done = false;
   if (mixed && eq == SEM_EQ_CONSERVATIVE) {
-    if ((rc = element_sponge(m, p, A, sponge_done))) return rc;
-    if ((rc = launch_pencil_n(A, m.N, m.nz, st, m.pencil_variant))) return rc;
+    if ((rc = element_terms(m, p, A, sponge_done, smag_done))) return rc;
+    if ((rc = launch_pencil_n(A, m.N, m.nz, st, m.pencil_variant, smag_done))) return rc;
   } else switch (m.N) {
     case 2: launch_volume_n<2>(A, eq, mixed, st); break;
     case 3: launch_volume_n<3>(A, eq, mixed, st); break;
@@ -1728,7 +1912,7 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
   SEM_CUDA_TRY(cudaGetLastError());
   if (physics_on(p) &&
       (rc = launch_physics(m, p, mixed ? (const void*)qs32 : (const void*)s.qs, mixed, s.scratch, s.time, st,
-                           sponge_done)))
+                           sponge_done, smag_done)))
     return rc;
   DssArgs B;
   B.rc = s.scratch ? s.scratch : D.scratch;

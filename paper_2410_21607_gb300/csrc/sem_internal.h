@@ -203,9 +203,10 @@ int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float
 inline bool physics_on(const sem_params& p) {
   return p.smag_cs > 0.0 || p.sponge_gamma > 0.0 || p.heat_q0 > 0.0;
 }
-// sponge_done: the element kernel has added the absorbing layer already
+// sponge_done, smag_done: the element kernel has added the absorbing layer,
+// the Smagorinsky stress already
 int launch_physics(Mesh& m, const sem_params& p, const void* q, bool mixed, void* scratch,
-                   double time, cudaStream_t st, bool sponge_done = false);
+                   double time, cudaStream_t st, bool sponge_done = false, bool smag_done = false);
 // absorbing-layer rate tables D.spg / D.spg32 for p's gamma and depth
 int ensure_sponge(Mesh& m, const sem_params& p);
 
