@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 from oracle import mesh as om, refstate, rhs as orhs, rk as ork  # noqa: E402
 from synth.vortex import random_state, vortex_state  # noqa: E402
 from tests.helpers import group_rel_l2, node_perm  # noqa: E402
-from tests.test_gpu_parity import MESHES, dev, full_fields, host, make_pair  # noqa: E402
+from tests.test_gpu_parity import MESHES, dev, full_fields, host, make_pair, two_level_leaves  # noqa: E402
 
 PHYS = dict(smag_cs=0.21, sponge_gamma=0.02, sponge_depth=6000.0)
 
@@ -76,12 +76,22 @@ def test_physics_rhs_mixed_matches_oracle(sem, name, eqset):
     assert np.all(err <= 1e-4 * np.maximum(ratio, 1.0)), (err, ratio)
 
 
-@pytest.mark.parametrize("name", ["twolevel-N4", "stretched-twolevel-N4", "uniform-5x4x3-N6"])
+def _spec(name):
+    if name == "twolevel-17-layers-N4":   # several layer chunks per column for every variant
+        return dict(L=300e3, Lz=24e3, nx=4, nz=17, N=4, leaves=two_level_leaves())
+    return MESHES[name]
+
+
+@pytest.mark.parametrize("name", ["twolevel-N4", "stretched-twolevel-N4", "twolevel-17-layers-N4",
+                                  "uniform-5x4x3-N6"])
 def test_physics_rhs_every_variant_matches_oracle(sem, name):
-    """Mixed tendency with both terms through each element-kernel variant: a
-    line-exchange variant adds the absorbing layer itself and the physics pass
-    only the stress, a z-pencil variant leaves both to the physics pass."""
-    m, o, X, perm = make_pair(sem, **MESHES[name])
+    """Mixed tendency with both terms through each element-kernel variant: an
+    order-4 line-exchange variant adds both terms in the element kernel, other
+    line-exchange variants the absorbing layer (the physics pass the stress),
+    a z-pencil variant leaves both to the physics pass.  17 layers give every
+    variant several layer chunks, so the carry of the top-node values (with
+    the stress) between chunks is exercised."""
+    m, o, X, perm = make_pair(sem, **_spec(name))
     q_o = random_state(o.XG, o.Lz, 24)
     T_o = orhs.rhs(o, q_o, refstate.Params(**PHYS))
     dT_o = T_o - orhs.rhs(o, q_o, refstate.Params())
@@ -110,11 +120,13 @@ def test_physics_rhs_every_variant_matches_oracle(sem, name):
     assert sem.sem_status(m) == 0
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_physics_steps_match_oracle(sem, prec):
-    """Ten SSP-RK3 steps of 1 s with both terms on the two-level mesh, in the
+@pytest.mark.parametrize("prec,name", [(0, "twolevel-N4"), (1, "twolevel-N4"), (1, "twolevel-17-layers-N4")])
+def test_physics_steps_match_oracle(sem, prec, name):
+    """Ten SSP-RK3 steps with both terms on a two-level mesh (1 s; 0.25 s on
+    the 17-layer mesh, whose thin layers bound the acoustic step), in the
     float64 form (sem_step) and the mixed increment form (sem_step_mixed)."""
-    m, o, X, perm = make_pair(sem, **MESHES["twolevel-N4"])
+    m, o, X, perm = make_pair(sem, **_spec(name))
+    dt = 0.25 if name == "twolevel-17-layers-N4" else 1.0
     q_o = vortex_state(o.XG, o.Lz)
     prm = refstate.Params(**PHYS)
     p = sem.sem_params_default(precision=prec, **PHYS)
@@ -122,18 +134,20 @@ def test_physics_steps_match_oracle(sem, prec):
     if prec == 0:
         w1, w2 = torch.empty_like(q), torch.empty_like(q)
         for _ in range(10):
-            sem.sem_step(m, p, q, w1, w2, 1.0)
+            sem.sem_step(m, p, q, w1, w2, dt)
     else:
         q32 = torch.empty(q.shape, dtype=torch.float32, device="cuda")
         work = torch.empty((10, m.NG), dtype=torch.float32, device="cuda")
         sem.sem_mirror(m, q, q32)
         for _ in range(10):
-            sem.sem_step_mixed(m, p, q, q32, work, 1.0)
+            sem.sem_step_mixed(m, p, q, q32, work, dt)
     for _ in range(10):
-        q_o = ork.rk_step(o, prm, q_o, 1.0)
+        q_o = ork.rk_step(o, prm, q_o, dt)
     z = X[:, 2]
     err = group_rel_l2(full_fields(host(q), z), full_fields(q_o[:, perm], z))
     assert np.all(err <= (1e-12 if prec == 0 else 1e-4)), err
+    pert = group_rel_l2(host(q), q_o[:, perm])       # the perturbation fields themselves
+    assert np.all(pert <= (1e-10 if prec == 0 else 1e-3)), pert
     assert sem.sem_status(m) == 0
 
 
