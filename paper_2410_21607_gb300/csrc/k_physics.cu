@@ -22,7 +22,10 @@
 //
 // R is the arithmetic type: double for the float64 form, float for the mixed
 // form (float32 mirror of the state, float32 residuals).  The mixed form of
-// the conservative set uses physics_lines (below) instead.
+// the conservative set uses physics_lines (below) instead, and only for what
+// the element kernel has not added: a line-exchange element kernel adds the
+// absorbing layer, and at order 4 the stress as well (k_stage.cu), in which
+// case this pass runs for the heating alone, if at all.
 #include <algorithm>
 #include <cmath>
 #include <vector>
