@@ -31,6 +31,23 @@ WORKLOAD = "uniform-64x64x16-N4"
 METRIC = "DOF-updates/s (RHS+RK stage) vs plain FP64 GPU, at <=1e-3 rel max-wind error"
 
 
+def max_over_ranks(x, world, device):
+    """The largest x over the ranks (a job's step time is its slowest rank's);
+    every rank calls it at the same point.  None stays None on every rank."""
+    if world == 1 or x is None:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_throughput(units_per_rank_step, world, ms):
+    """Units all ranks processed per second at the job's step time ms."""
+    return units_per_rank_step * world / (ms * 1e-3)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -407,12 +424,10 @@ def main():
     torch.cuda.synchronize()
     prof = sem.sem_profile_end()
     ck = clocks.stop()
+    ms = max_over_ranks(ms, world, "cuda")
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
         dist.barrier()
-    value = dof_stage * 3 * world / (ms * 1e-3)
+    value = job_throughput(dof_stage * 3, world, ms)
     status = sem.sem_status(m)
 
     # per-kernel roofline of the timed region
@@ -481,7 +496,7 @@ def main():
             b64 = step(b64, p64)
         e1.record(stream)
         torch.cuda.synchronize()
-        fp64_ms = e0.elapsed_time(e1) / nfp
+        fp64_ms = max_over_ranks(e0.elapsed_time(e1) / nfp, world, "cuda")
     gate = None
     if a.gate_steps > 0:
         bm = new_bufs()
@@ -513,13 +528,13 @@ def main():
             bp = step(bp, pp)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms_p = e0.elapsed_time(e1) / kp
+        ms_p = max_over_ranks(e0.elapsed_time(e1) / kp, world, "cuda")
         sem.sem_profile_begin()
         for _ in range(kp):
             bp = step(bp, pp)
         torch.cuda.synchronize()
         pr = sem.sem_profile_end()
-        physics_res = {"params": pphys, "ms_per_step": ms_p, "value": dof_stage * 3 / (ms_p * 1e-3),
+        physics_res = {"params": pphys, "ms_per_step": ms_p, "value": job_throughput(dof_stage * 3, world, ms_p),
                        "step_time_ratio": ms_p / ms,
                        "kernels_ms_avg": {k: v[1] / max(v[0], 1) for k, v in pr.items()},
                        "status": sem.sem_status(m)}
@@ -577,7 +592,7 @@ def main():
             stream.wait_event(ev_out[bi][c])
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / ke
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / ke, world, "cuda")
     assert all(torch.equal(houts[0], hb) for hb in houts[1:]), "the streamed steps disagree"
     nbytes = 5 * NG * 8
 
@@ -609,13 +624,13 @@ def main():
                        "l2": "inputs larger than L2 (state 3 x 170 MB + residual scratch)",
                        "parallelism": f"replicas x{world}"},
             "fp64_form": None if fp64_ms is None else {
-                "ms_per_step": fp64_ms, "value": dof_stage * 3 * world / (fp64_ms * 1e-3),
+                "ms_per_step": fp64_ms, "value": job_throughput(dof_stage * 3, world, fp64_ms),
                 "speedup_mixed_over_fp64": fp64_ms / ms},
             "gate": gate,
             "roofline": roof, "kernels": kernels, "autotune": tune, "batched": batched,
             "learned": learned_res, "amr": amr_res, "physics": physics_res,
             "cpu_baseline": cpu,
-            "e2e": {"value": dof_stage * 3 * world / (e2e_ms * 1e-3), "unit": "DOF-updates/s",
+            "e2e": {"value": job_throughput(dof_stage * 3, world, e2e_ms), "unit": "DOF-updates/s",
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                     "ms_per_step": e2e_ms},
             "gpu_launches": sum(v[0] for v in prof.values()),
