@@ -249,9 +249,6 @@ inline uint64_t skey(int orient, long X, long Y, int lev, int idx) {
   return (1ull << 62) | ((uint64_t)orient << 61) | ((uint64_t)lev << 57) |
          ((uint64_t)idx << 50) | ((uint64_t)X << 25) | (uint64_t)Y;
 }
-inline uint64_t ikey(long c, int a, int b) {
-  return (2ull << 62) | ((uint64_t)a << 53) | ((uint64_t)b << 46) | (uint64_t)c;
-}
 }  // namespace
 
 int build_mesh(Mesh& m) {
@@ -334,7 +331,7 @@ int build_mesh(Mesh& m) {
         p.col = (int)c;
         p.ab = ab;
         if (!eX && !eY) {
-          key = ikey(c, a, b);
+          // inside the cross-section: no key (numbered below without the map)
         } else if (eX && eY) {
           long X = a == 0 ? X0 : X1, Y = b == 0 ? Y0 : Y1;
           int cells[4] = {G.at(X - 1, Y - 1), G.at(X, Y - 1), G.at(X - 1, Y), G.at(X, Y)};
@@ -385,15 +382,19 @@ int build_mesh(Mesh& m) {
           m.hmap[(size_t)c * m.Nq + ab] = -1 - (int)pend.size();
           pend.push_back(p);
         } else {
-          auto it = id.find(key);
-          int h;
-          if (it == id.end()) {
-            h = (int)m.xh.size();
-            id.emplace(key, h);
+          // a node inside the column's cross-section belongs to it alone: a
+          // new index without the map; a shared one is looked up (and
+          // numbered on first sight) in one map operation
+          int h = (int)m.xh.size();
+          bool fresh = true;
+          if (eX || eY) {
+            auto ins = id.try_emplace(key, h);
+            fresh = ins.second;
+            h = ins.first->second;
+          }
+          if (fresh) {
             m.xh.push_back(wrapx(x0 + 0.5 * (1.0 + B.xi[a]) * m.hx(f.l)));
             m.yh.push_back(wrapy(y0 + 0.5 * (1.0 + B.xi[b]) * m.hy(f.l)));
-          } else {
-            h = it->second;
           }
           m.hmap[(size_t)c * m.Nq + ab] = h;
         }
@@ -418,35 +419,36 @@ int build_mesh(Mesh& m) {
       m.hang_w[k * n1 + q] = pend[k].w[q];
     }
   }
-  // transposed constraint (gather lists), sorted by (h, source)
-  struct Ent { int h; int src; double w; };
-  std::vector<Ent> ents;
-  ents.reserve((size_t)ncol * m.Nq + pend.size() * n1);
-  for (long c = 0; c < ncol; ++c)
-    for (int ab = 0; ab < m.Nq; ++ab) {
-      int v = m.hmap[(size_t)c * m.Nq + ab];
-      int src = (int)(c * m.Nq + ab);
-      if (v >= 0) {
-        ents.push_back({v, src, 1.0});
-      } else {
-        int k = -1 - v;
-        for (int q = 0; q <= N; ++q)
-          if (m.hang_w[(size_t)k * n1 + q] != 0.0)
-            ents.push_back({m.hang_h[(size_t)k * n1 + q], src, m.hang_w[(size_t)k * n1 + q]});
+  // transposed constraint (gather lists), sorted by (h, source): the sources
+  // are visited in increasing order, so one counting pass by h and a stable
+  // scatter give that order without a comparison sort
+  auto each_entry = [&](auto&& emit) {
+    for (long c = 0; c < ncol; ++c)
+      for (int ab = 0; ab < m.Nq; ++ab) {
+        const int v = m.hmap[(size_t)c * m.Nq + ab];
+        const int src = (int)(c * m.Nq + ab);
+        if (v >= 0) {
+          emit(v, src, 1.0);
+        } else {
+          const int k = -1 - v;
+          for (int q = 0; q <= N; ++q)
+            if (m.hang_w[(size_t)k * n1 + q] != 0.0) emit(m.hang_h[(size_t)k * n1 + q], src, m.hang_w[(size_t)k * n1 + q]);
+        }
       }
-    }
-  std::sort(ents.begin(), ents.end(), [](const Ent& x, const Ent& y) {
-    return x.h != y.h ? x.h < y.h : x.src < y.src;
-  });
+  };
   m.qt_ptr.assign(m.NH + 1, 0);
-  m.qt_src.resize(ents.size());
-  m.qt_w.resize(ents.size());
-  for (size_t e = 0; e < ents.size(); ++e) {
-    m.qt_ptr[ents[e].h + 1]++;
-    m.qt_src[e] = ents[e].src;
-    m.qt_w[e] = ents[e].w;
-  }
+  each_entry([&](int h, int, double) { m.qt_ptr[h + 1]++; });
   for (long long h = 0; h < m.NH; ++h) m.qt_ptr[h + 1] += m.qt_ptr[h];
+  m.qt_src.resize(m.qt_ptr[m.NH]);
+  m.qt_w.resize(m.qt_ptr[m.NH]);
+  {
+    std::vector<int> next(m.qt_ptr.begin(), m.qt_ptr.end() - 1);
+    each_entry([&](int h, int src, double w) {
+      const int e = next[h]++;
+      m.qt_src[e] = src;
+      m.qt_w[e] = w;
+    });
+  }
   // lumped mass factors
   m.Mh.assign(m.NH, 0.0);
   for (long long h = 0; h < m.NH; ++h)
