@@ -369,7 +369,7 @@ int sem_rhs(sem_mesh* mh, const sem_params* p, const double* q, double* rhs, cud
   int rc = prepare(mh, p);
   if (rc) return rc;
   if (!q || !rhs || q == rhs) return fail(SEM_ERR_ARG, "q and rhs must be distinct device arrays");
-  StageArgs s{nullptr, q, rhs, nullptr, nullptr, 0.0, 0.0, 1.0, 1};
+  StageArgs s{nullptr, q, rhs, nullptr, nullptr, 0.0, 0.0, 1.0, 1, nullptr};
   s.time = p->time;
   return launch_rhs_stage(mh->m, *p, s, st);
 }
@@ -386,7 +386,7 @@ int sem_rk_stage(sem_mesh* mh, const sem_params* p, int stage, const double* qn,
   if (stage < 0 || stage > 2) return fail(SEM_ERR_ARG, "stage must be 0, 1 or 2");
   if (!qn || !qs || !qout || qout == qn || qout == qs)
     return fail(SEM_ERR_ARG, "qout must not alias qn or qs");
-  StageArgs s{qn, qs, qout, nullptr, nullptr, kA[stage], kB[stage], kC[stage] * dt, 0};
+  StageArgs s{qn, qs, qout, nullptr, nullptr, kA[stage], kB[stage], kC[stage] * dt, 0, nullptr};
   s.time = p->time + kT[stage] * dt;
   return launch_rhs_stage(mh->m, *p, s, st);
 }
@@ -401,7 +401,7 @@ int sem_rk_stage_mixed(sem_mesh* mh, const sem_params* p, int stage, const doubl
   if (!qn || !qs || !qs32 || !qout || !qout32 || qout == qn || qout == qs ||
       (const void*)qout32 == (const void*)qs32)
     return fail(SEM_ERR_ARG, "outputs must not alias inputs");
-  StageArgs s{qn, qs, qout, qs32, qout32, kA[stage], kB[stage], kC[stage] * dt, 0};
+  StageArgs s{qn, qs, qout, qs32, qout32, kA[stage], kB[stage], kC[stage] * dt, 0, nullptr};
   s.time = p->time + kT[stage] * dt;
   return launch_rhs_stage(mh->m, *p, s, st);
 }
