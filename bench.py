@@ -128,7 +128,7 @@ class Clocks:
 def cpu_oracle_sample(steps=1, n=32):
     """The CPU oracle on a bounded sample of the workload: an n x n x 16 block
     of the same elements (same element size, order, physics), SSP-RK3 steps.
-    Returns (DOF-updates/s, threads, description)."""
+    Returns (DOF-updates/s, threads, description, seconds, busy threads)."""
     import numpy as np
     from oracle import mesh as om, refstate, rk as ork
     from synth.vortex import vortex_state
@@ -137,15 +137,16 @@ def cpu_oracle_sample(steps=1, n=32):
     q = vortex_state(o.XG, 24e3)
     prm = refstate.Params()
     ork.rk_step(o, prm, q, 0.25)            # warm caches
-    t0 = time.perf_counter()
+    c0, t0 = time.process_time(), time.perf_counter()
     for _ in range(steps):
         q = ork.rk_step(o, prm, q, 0.25)
     dt = time.perf_counter() - t0
+    busy = (time.process_time() - c0) / dt   # threads kept busy on average
     dofs = 5 * o.Ne * o.P * 3 * steps
     threads = int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1))
     desc = (f"{steps} SSP-RK3 step(s) of the oracle on a {n}x{n}x16 block of the same "
             f"elements ({o.Ne} of 65,536; N=4), float64 numpy/scipy")
-    return dofs / dt, threads, desc, dt
+    return dofs / dt, threads, desc, dt, busy
 
 
 def batched_measure(sem, torch, steps=10, warmup=3, refine=True):
@@ -611,9 +612,9 @@ def main():
     if rank == 0:
         cpu = None
         if world == 1 and not a.no_cpu_baseline:
-            v, thr, desc, secs = cpu_oracle_sample()
+            v, thr, desc, secs, busy = cpu_oracle_sample()
             cpu = {"value": v, "unit": "DOF-updates/s", "cores": thr, "kind": "oracle",
-                   "sample": desc, "seconds": secs}
+                   "sample": desc, "seconds": secs, "busy_threads": busy}
         line = {
             "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
