@@ -181,14 +181,14 @@ int sem_mesh_coords(sem_mesh* m, double* coords_dev, cudaStream_t stream);
 int sem_rhs(sem_mesh* m, const sem_params* p, const double* q_dev, double* rhs_dev,
             cudaStream_t stream);
 
-/* sem_rhs without any device allocation.
+/* sem_rhs without any device allocation in the call.
  *
- * For callers that may not allocate device memory when they evaluate the
- * right-hand side: for example code that runs while another allocator (a
- * framework's caching allocator or a memory pool) has reserved all free device
- * memory, so that a new cudaMalloc would fail, or real-time and certified
- * code that forbids device allocation after start-up.  The paper has no
- * counterpart; it is an interface addition of this library.
+ * For callers that must not allocate device memory when they evaluate the
+ * right-hand side: code that runs while another allocator (a framework's
+ * caching allocator or a memory pool) holds all free device memory, so that a
+ * new cudaMalloc would fail, and real-time or certified code whose rules
+ * forbid device allocation after start-up.  The paper has no counterpart; it
+ * is an interface addition of this library.
  *
  * Same inputs, outputs and result as sem_rhs.  Instead of the mesh's own
  * residual scratch it uses one fixed device array of 16 MiB built into the
@@ -196,11 +196,18 @@ int sem_rhs(sem_mesh* m, const sem_params* p, const double* q_dev, double* rhs_d
  * exits), so it serves meshes with Ncol * (N+1)^2 * 5 * NZ4 * 8 <= 16 MiB
  * (NZ4 = NZ rounded up to a multiple of 4)
  * (about 1,000 columns of 16 layers at N = 4); larger meshes get SEM_ERR_ARG
- * before any device work.  The call itself allocates nothing: the mesh must
- * already have its device tables, made by any earlier device call on it (for
- * example sem_mesh_coords), else SEM_ERR_ARG.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress, kept per
- * device); make that first call before any stream capture.  All calls share
+ * before any device work.  The call performs no allocation itself, but it
+ * does not save memory: the mesh must already have its device tables, made
+ * by any earlier device call on it (for example sem_mesh_coords), else
+ * SEM_ERR_ARG, and those tables include the mesh's own residual scratch,
+ * which stays allocated.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, kept per device; the driver may load
+ * the library's device code then); make that first call before any stream
+ * capture.  A call whose reference-state parameters (g, R_d, c_p, p00,
+ * theta_s, N_bv) differ from those of the mesh's previous call uploads the
+ * reference tables with a synchronous copy; under stream capture that case
+ * is refused with SEM_ERR_ARG, so make one call with new parameters before
+ * capturing.  The parameters are validated as in sem_rhs.  All calls share
  * the one array and every element of it that a call reads is first written
  * by the same call, so nothing needs clearing between calls; calls that
  * overlap on the GPU (on different streams, or from several threads) race on
@@ -340,6 +347,18 @@ int sem_diag(sem_mesh* m, const sem_params* p, const double* q_dev, double half_
  * they write a non-finite value; synchronises the stream.  *status_host is 0
  * (clean) or SEM_ERR_NUMERIC. */
 int sem_status(sem_mesh* m, int* status_host, cudaStream_t stream);
+
+/* Host-only check of the library's one-time set-up per device (no GPU
+ * needed).  The library uploads its constant tables and sets its kernel
+ * attributes once per device ordinal, on the first call that needs them on
+ * that device.  This call drives that mechanism for the simulated ordinals
+ * 0..n_devices-1 from n_threads host threads at once (each thread asks for
+ * every ordinal three times, in a different order) and writes to
+ * init_calls_host[d] how many times the set-up ran for ordinal d (1 when the
+ * mechanism is correct).  n_devices in 1..64, n_threads in 1..64, else
+ * SEM_ERR_ARG; an ordinal outside 0..63 is refused by the mechanism itself,
+ * which this call also checks (SEM_ERR_ARG from the call if it were not). */
+int sem_selftest_device_once(int n_devices, int n_threads, int* init_calls_host);
 
 /* Autotuner of the mixed-form element kernel.  Times every launch variant
  * compiled for the mesh's order (layers of a column per CTA, and the number

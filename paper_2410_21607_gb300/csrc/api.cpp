@@ -5,6 +5,8 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
+#include <vector>
 
 #include "sem_internal.h"
 
@@ -145,10 +147,16 @@ int ensure_device(Mesh& m) {
 //   pi0 = 1 + g^2/(c_p theta_s N^2) (exp(-N^2 z/g) - 1),
 //   p0 = p00 pi0^(c_p/R_d),  rho0 = p00 pi0^(c_v/R_d) / (R_d theta0),
 // which satisfies dp0/dz = -rho0 g and p0 = p00 (R_d rho0 theta0 / p00)^gamma.
+bool reference_stale(const Mesh& m, const sem_params& p) {
+  if (!m.dev) return true;
+  const double key[8] = {p.g, p.R_d, p.c_p, p.p00, p.theta_s, p.N_bv, 0, 0};
+  return !(m.dev->ref_valid && std::memcmp(key, m.dev->ref_key, sizeof(key)) == 0);
+}
+
 int ensure_reference(Mesh& m, const sem_params& p) {
   DeviceTables& D = *m.dev;
   double key[8] = {p.g, p.R_d, p.c_p, p.p00, p.theta_s, p.N_bv, 0, 0};
-  if (D.ref_valid && std::memcmp(key, D.ref_key, sizeof(key)) == 0) return SEM_OK;
+  if (!reference_stale(m, p)) return SEM_OK;
   if (!(p.N_bv > 0) || !(p.g > 0) || !(p.c_p > p.R_d) || !(p.R_d > 0))
     return fail(SEM_ERR_ARG, "reference state needs g > 0, N_bv > 0, c_p > R_d > 0");
   const double c_v = p.c_p - p.R_d, N2 = p.N_bv * p.N_bv;
@@ -180,7 +188,7 @@ int ensure_reference(Mesh& m, const sem_params& p) {
   return SEM_OK;
 }
 
-static int check_params(const sem_params* p) {
+int check_params(const sem_params* p) {
   if (!p) return fail(SEM_ERR_ARG, "params is NULL");
   if (p->eqset != SEM_EQ_CONSERVATIVE && p->eqset != SEM_EQ_NONCONSERVATIVE)
     return fail(SEM_ERR_ARG, "unknown equation set");
@@ -790,3 +798,38 @@ int sem_status(sem_mesh* mh, int* status, cudaStream_t st) {
 }
 
 }  // extern "C"
+
+extern "C" int sem_selftest_device_once(int n_devices, int n_threads, int* calls) {
+  if (n_devices < 1 || n_devices > kMaxDevices || n_threads < 1 || n_threads > 64 || !calls)
+    return fail(SEM_ERR_ARG, "n_devices and n_threads must be in 1..64, calls non-NULL");
+  DeviceOnce once;
+  std::vector<std::atomic<int>> cnt(n_devices);
+  for (auto& c : cnt) c.store(0);
+  std::atomic<int> bad{0};
+  std::vector<std::thread> th;
+  for (int t = 0; t < n_threads; ++t)
+    th.emplace_back([&, t] {
+      for (int rep = 0; rep < 3; ++rep)
+        for (int k = 0; k < n_devices; ++k) {
+          const int d = (k + t * 7 + rep) % n_devices;
+          const int rc = device_once_on(once, d, [&] {
+            cnt[d].fetch_add(1);
+            std::this_thread::yield();
+            return (int)SEM_OK;
+          });
+          if (rc != SEM_OK) bad.fetch_add(1);
+        }
+    });
+  for (auto& x : th) x.join();
+  for (int d = 0; d < n_devices; ++d) calls[d] = cnt[d].load();
+  // ordinals beyond the table are refused, and a failed set-up runs again
+  int ran = 0;
+  if (device_once_on(once, kMaxDevices, [&] { ++ran; return (int)SEM_OK; }) != SEM_ERR_ARG || ran)
+    return fail(SEM_ERR_ARG, "device_once accepted an ordinal outside the table");
+  DeviceOnce again;
+  device_once_on(again, 0, [] { return (int)SEM_ERR_CUDA; });
+  if (device_once_on(again, 0, [&] { ++ran; return (int)SEM_OK; }) != SEM_OK || ran != 1)
+    return fail(SEM_ERR_ARG, "device_once did not retry a failed set-up");
+  if (bad.load()) return fail(SEM_ERR_ARG, "device_once failed on a valid ordinal");
+  return SEM_OK;
+}

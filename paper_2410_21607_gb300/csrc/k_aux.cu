@@ -22,17 +22,20 @@ namespace sem {
 
 __constant__ double a_D[kMaxN + 1][(kMaxN + 1) * (kMaxN + 1)];  // [i][m] = h_m'(xi_i)
 
-static int upload_aux_constants() {
-  static bool done = false;
-  if (done) return SEM_OK;
+static int upload_aux_constants_now() {
   double D[kMaxN + 1][(kMaxN + 1) * (kMaxN + 1)] = {};
   for (int N = 2; N <= kMaxN; ++N) {
     const Basis1D& B = basis(N);
     for (int k = 0; k < (N + 1) * (N + 1); ++k) D[N][k] = B.D[k];
   }
   SEM_CUDA_TRY(cudaMemcpyToSymbol(a_D, D, sizeof(D)));
-  done = true;
   return SEM_OK;
+}
+
+// the tables of the current device (uploaded on its first use)
+static int upload_aux_constants() {
+  static DeviceOnce once;
+  return device_once(once, upload_aux_constants_now);
 }
 
 struct AdaptArgs {

@@ -561,8 +561,9 @@ int mlp_adam_api(void* h, float lr, cudaStream_t st) {
 }
 
 int mlp_features_api(Mesh& mesh, const double* q, const float* scales, float* F, cudaStream_t st) {
-  static bool up = false;
-  if (!up) {
+  // the interpolation rows of the current device (uploaded on its first use)
+  static DeviceOnce once;
+  int rc = device_once(once, [] {
     double fw[kMaxN + 1][3][kMaxN + 1] = {};
     for (int N = 2; N <= kMaxN; ++N) {
       const Basis1D& B = basis(N);
@@ -576,8 +577,9 @@ int mlp_features_api(Mesh& mesh, const double* q, const float* scales, float* F,
         }
     }
     SEM_CUDA_TRY(cudaMemcpyToSymbol(c_fw, fw, sizeof(fw)));
-    up = true;
-  }
+    return SEM_OK;
+  });
+  if (rc) return rc;
   DeviceTables& D = *mesh.dev;
   const long long total = mesh.Ne() * 27;
   const int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 16);

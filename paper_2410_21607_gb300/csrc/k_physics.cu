@@ -55,9 +55,7 @@ template <> struct PTab<float> {
   __device__ static float Dw(int N, int k) { return p_Dwf[N][k]; }
 };
 
-int upload_constants() {
-  static bool done = false;
-  if (done) return SEM_OK;
+static int upload_constants_now() {
   constexpr int K = (kMaxN + 1) * (kMaxN + 1);
   double xi[kMaxN + 1][kMaxN + 1] = {}, w[kMaxN + 1][kMaxN + 1] = {}, D[kMaxN + 1][K] = {}, Dw[kMaxN + 1][K] = {};
   float wf[kMaxN + 1][kMaxN + 1] = {}, Df[kMaxN + 1][K] = {}, Dwf[kMaxN + 1][K] = {};
@@ -83,8 +81,13 @@ int upload_constants() {
   SEM_CUDA_TRY(cudaMemcpyToSymbol(p_wf, wf, sizeof(wf)));
   SEM_CUDA_TRY(cudaMemcpyToSymbol(p_Df, Df, sizeof(Df)));
   SEM_CUDA_TRY(cudaMemcpyToSymbol(p_Dwf, Dwf, sizeof(Dwf)));
-  done = true;
   return SEM_OK;
+}
+
+// the tables of the current device (uploaded on its first use)
+int upload_constants() {
+  static DeviceOnce once;
+  return device_once(once, upload_constants_now);
 }
 
 struct PhysArgs {
@@ -516,12 +519,12 @@ physics_lines(const PhysArgs A) {
 template <int N, int KL, int MB>
 int launch_lines(const PhysArgs& A, int ncol, cudaStream_t st) {
   const size_t sm = sizeof(float) * plines_smem_floats<N, KL>();
-  static bool attr = false;
-  if (!attr) {
-    SEM_CUDA_TRY(cudaFuncSetAttribute(physics_lines<N, KL, MB>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    attr = true;
-  }
+  static DeviceOnce attr;
+  int rc = device_once(attr, [&] {
+    SEM_CUDA_TRY(cudaFuncSetAttribute(physics_lines<N, KL, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    return SEM_OK;
+  });
+  if (rc) return rc;
   physics_lines<N, KL, MB><<<ncol, KL * (N + 1) * (N + 1), sm, st>>>(A);
   return SEM_OK;
 }

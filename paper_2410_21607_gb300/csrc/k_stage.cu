@@ -44,9 +44,7 @@ template <> struct Tab<float> {
   __device__ static float D(int N, int k) { return c_Df[N][k]; }
 };
 
-int upload_basis_constants() {
-  static bool done = false;
-  if (done) return SEM_OK;
+static int upload_basis_constants_now() {
   double xi[kMaxN + 1][kMaxN + 1] = {}, w[kMaxN + 1][kMaxN + 1] = {};
   double Dw[kMaxN + 1][(kMaxN + 1) * (kMaxN + 1)] = {};
   double D[kMaxN + 1][(kMaxN + 1) * (kMaxN + 1)] = {};
@@ -78,8 +76,13 @@ int upload_basis_constants() {
   SEM_CUDA_TRY(cudaMemcpyToSymbol(c_wf, wf, sizeof(wf)));
   SEM_CUDA_TRY(cudaMemcpyToSymbol(c_Dwf, Dwf, sizeof(Dwf)));
   SEM_CUDA_TRY(cudaMemcpyToSymbol(c_Df, Df, sizeof(Df)));
-  done = true;
   return SEM_OK;
+}
+
+// the basis tables of the current device (uploaded on its first use)
+int upload_basis_constants() {
+  static DeviceOnce once;
+  return device_once(once, upload_basis_constants_now);
 }
 
 // per-level geometry: hx, hy, hz, J, sx = hy hz/4, sy = hx hz/4, sz = hx hy/4, unused
@@ -734,12 +737,12 @@ static size_t pencil_smem() {
 template <int N, int KL, int MB>
 static int launch_pencil(const VolArgs& A, cudaStream_t st) {
   const size_t sm = pencil_smem<N, KL>();
-  static bool attr = false;
-  if (!attr) {
-    SEM_CUDA_TRY(cudaFuncSetAttribute(volume_pencil_mixed<N, KL, MB>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    attr = true;
-  }
+  static DeviceOnce attr;
+  int rc = device_once(attr, [&] {
+    SEM_CUDA_TRY(cudaFuncSetAttribute(volume_pencil_mixed<N, KL, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    return SEM_OK;
+  });
+  if (rc) return rc;
   ProfScope ps("volume_mixed", st);
   volume_pencil_mixed<N, KL, MB><<<A.Ncol, KL * (N + 1) * (N + 1), sm, st>>>(A);
   return SEM_OK;
@@ -1067,12 +1070,12 @@ volume_lines_smag(const VolArgs A) {
 template <int N, int KL, int MB>
 static int launch_lines_smag(const VolArgs& A, cudaStream_t st) {
   const size_t sm = sizeof(float) * lines_smem_floats<N, KL>();
-  static bool attr = false;
-  if (!attr) {
-    SEM_CUDA_TRY(cudaFuncSetAttribute(volume_lines_smag<N, KL, MB>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    attr = true;
-  }
+  static DeviceOnce attr;
+  int rc = device_once(attr, [&] {
+    SEM_CUDA_TRY(cudaFuncSetAttribute(volume_lines_smag<N, KL, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    return SEM_OK;
+  });
+  if (rc) return rc;
   ProfScope ps("volume_mixed", st);
   volume_lines_smag<N, KL, MB><<<A.Ncol, KL * (N + 1) * (N + 1), sm, st>>>(A);
   return SEM_OK;
@@ -1081,12 +1084,12 @@ static int launch_lines_smag(const VolArgs& A, cudaStream_t st) {
 template <int N, int KL, int MB>
 static int launch_lines(const VolArgs& A, cudaStream_t st) {
   const size_t sm = sizeof(float) * lines_smem_floats<N, KL>();
-  static bool attr = false;
-  if (!attr) {
-    SEM_CUDA_TRY(cudaFuncSetAttribute(volume_lines_mixed<N, KL, MB>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    attr = true;
-  }
+  static DeviceOnce attr;
+  int rc = device_once(attr, [&] {
+    SEM_CUDA_TRY(cudaFuncSetAttribute(volume_lines_mixed<N, KL, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    return SEM_OK;
+  });
+  if (rc) return rc;
   ProfScope ps("volume_mixed", st);
   volume_lines_mixed<N, KL, MB><<<A.Ncol, KL * (N + 1) * (N + 1), sm, st>>>(A);
   return SEM_OK;
@@ -1982,9 +1985,8 @@ extern "C" int sem_rhs_noalloc(sem_mesh* mh, const sem_params* p, const double* 
                                cudaStream_t st) {
   using namespace sem;
   if (!mh || !p || !q || !rhs || q == rhs) return fail(SEM_ERR_ARG, "NULL or aliased argument");
-  if ((p->eqset != SEM_EQ_CONSERVATIVE && p->eqset != SEM_EQ_NONCONSERVATIVE) ||
-      (p->precision != SEM_PREC_FP64 && p->precision != SEM_PREC_MIXED))
-    return fail(SEM_ERR_ARG, "unknown equation set or precision");
+  int rc = check_params(p);   // the same validation as sem_rhs
+  if (rc) return rc;
   Mesh& m = mh->m;
   const size_t need = (size_t)m.Ncol() * m.Nq * kFields * m.NZr() * sizeof(double);
   if (need > kNoAllocScratchBytes)
@@ -1999,8 +2001,16 @@ extern "C" int sem_rhs_noalloc(sem_mesh* mh, const sem_params* p, const double* 
   if (m.dev_id != dev) return fail(SEM_ERR_ARG, "mesh tables live on another device");
   // the terms of the paper's runs keep per-mesh tables that are allocated on first use
   if (physics_on(*p)) return fail(SEM_ERR_UNSUPPORTED, "sem_rhs_noalloc: smag_cs, sponge_gamma and heat_q0 must be 0");
-  int rc = ensure_reference(m, *p);
-  if (rc) return rc;
+  // new reference-state parameters are uploaded with a synchronous copy,
+  // which a stream capture would not record: refuse that case
+  if (reference_stale(m, *p)) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    SEM_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(SEM_ERR_ARG, "sem_rhs_noalloc: new reference-state parameters during stream capture; "
+                               "make one call with them before capturing");
+  }
+  if ((rc = ensure_reference(m, *p))) return rc;
   void* scratch = nullptr;
   if ((rc = noalloc_scratch_address(dev, &scratch))) return rc;
   StageArgs s{nullptr, q, rhs, nullptr, nullptr, 0.0, 0.0, 1.0, 1, scratch};

@@ -26,9 +26,7 @@ __constant__ double c_P[kMaxN + 1][2][(kMaxN + 1) * (kMaxN + 1)];  // child inte
 __constant__ double c_R[kMaxN + 1][2][(kMaxN + 1) * (kMaxN + 1)];  // child L2 projection
 __constant__ double c_tw[kMaxN + 1][kMaxN + 1];                     // LGL weights
 
-static int upload_transfer_constants() {
-  static bool done = false;
-  if (done) return SEM_OK;
+static int upload_transfer_constants_now() {
   static double P[kMaxN + 1][2][(kMaxN + 1) * (kMaxN + 1)] = {};
   static double R[kMaxN + 1][2][(kMaxN + 1) * (kMaxN + 1)] = {};
   static double W[kMaxN + 1][kMaxN + 1] = {};
@@ -79,8 +77,13 @@ static int upload_transfer_constants() {
   SEM_CUDA_TRY(cudaMemcpyToSymbol(c_P, P, sizeof(P)));
   SEM_CUDA_TRY(cudaMemcpyToSymbol(c_R, R, sizeof(R)));
   SEM_CUDA_TRY(cudaMemcpyToSymbol(c_tw, W, sizeof(W)));
-  done = true;
   return SEM_OK;
+}
+
+// the tables of the current device (uploaded on its first use)
+static int upload_transfer_constants() {
+  static DeviceOnce once;
+  return device_once(once, upload_transfer_constants_now);
 }
 
 struct TrArgs {

@@ -1,6 +1,8 @@
 // Internal declarations shared by the host topology and the CUDA kernels.
 #pragma once
+#include <atomic>
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 #include <cuda_runtime.h>
@@ -22,6 +24,36 @@ int fail(int code, const std::string& msg);
     if (e_ != cudaSuccess)                                                       \
       return ::sem::fail(SEM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
   } while (0)
+
+// ---------------------------------------------------------------------------
+// One-time set-up per device.  __constant__ tables and kernel attributes
+// belong to a device: each device ordinal a process uses must get its own
+// upload.  DeviceOnce records, per ordinal, that the set-up has succeeded;
+// device_once runs `init` for the current device at most once (a failed init
+// runs again on the next call), and is safe when several host threads make
+// their first call at the same time.
+constexpr int kMaxDevices = 64;
+struct DeviceOnce {
+  std::atomic<unsigned long long> done{0};
+  std::mutex mu;
+};
+template <class F>
+int device_once_on(DeviceOnce& o, int dev, F&& init) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(SEM_ERR_ARG, "device ordinal out of range");
+  const unsigned long long bit = 1ull << dev;
+  if (o.done.load(std::memory_order_acquire) & bit) return SEM_OK;
+  std::lock_guard<std::mutex> lk(o.mu);
+  if (o.done.load(std::memory_order_relaxed) & bit) return SEM_OK;
+  const int rc = init();
+  if (rc == SEM_OK) o.done.fetch_or(bit, std::memory_order_release);
+  return rc;
+}
+template <class F>
+int device_once(DeviceOnce& o, F&& init) {
+  int dev = 0;
+  SEM_CUDA_TRY(cudaGetDevice(&dev));
+  return device_once_on(o, dev, init);
+}
 
 // ---------------------------------------------------------------------------
 // 1-D LGL basis (host, float64)
@@ -156,7 +188,13 @@ struct DeviceTables {
 constexpr int kRef = 8;  // theta0, pi0, p0, rho0, rhotheta0, dtheta0/dz, 1/(rho theta)0, z
 
 int ensure_device(Mesh& m);
+// reference tables for p (uploaded synchronously when p's reference-state
+// parameters differ from those the tables were made with)
 int ensure_reference(Mesh& m, const sem_params& p);
+// true when ensure_reference(m, p) would upload
+bool reference_stale(const Mesh& m, const sem_params& p);
+// validates every field of p (SEM_ERR_ARG with a message)
+int check_params(const sem_params* p);
 void free_device(Mesh& m);
 
 // kernel launchers (k_*.cu)

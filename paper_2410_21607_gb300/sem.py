@@ -35,6 +35,7 @@ EXPORTS = (
     "sem_mlp_set_params", "sem_mlp_get_grads", "sem_mlp_features", "sem_mlp_forward",
     "sem_mlp_predict_flags", "sem_mlp_backward", "sem_mlp_adam",
     "sem_checkpoint_write", "sem_checkpoint_read_mesh", "sem_checkpoint_read_state",
+    "sem_selftest_device_once",
 )
 
 
@@ -138,6 +139,7 @@ def _load():
         "sem_checkpoint_read_state": (i, [C.c_char_p, vp, vp, vp]),
         "sem_autotune": (i, [vp, C.POINTER(Params), vp, i, C.POINTER(TuneOut), vp]),
         "sem_autotune_select": (i, [vp, i]),
+        "sem_selftest_device_once": (i, [i, i, vp]),
         "sem_profile_end": (i, [C.POINTER(ProfileOut)]),
     }
     for name, (res, args) in sig.items():
@@ -555,3 +557,11 @@ def sem_checkpoint_read_state(path, mesh, q, stream=None):
     _f64(q, mesh.field_shape)
     _check(LIB.sem_checkpoint_read_state(str(path).encode(), mesh.h, _ptr(q), _stream(stream)))
     return q
+
+
+def sem_selftest_device_once(n_devices, n_threads):
+    """Host-only check of the per-device one-time set-up: how many times the
+    set-up ran for each simulated device ordinal (1 each when correct)."""
+    out = (C.c_int * n_devices)()
+    _check(LIB.sem_selftest_device_once(n_devices, n_threads, out))
+    return list(out)

@@ -202,3 +202,13 @@ def test_checkpoint_reading_rejects_bad_files(sem, tmp_path):
     with pytest.raises(sem.SemError) as e:
         sem.sem_checkpoint_read_mesh(garbage)
     assert e.value.code == sem.SEM_ERR_IO
+
+
+def test_one_time_setup_runs_once_per_device(sem):
+    """Constant tables and kernel attributes belong to a device: the library's
+    one-time set-up must run once for each device ordinal (not once per
+    process), also when several host threads make their first call at once."""
+    assert sem.sem_selftest_device_once(8, 16) == [1] * 8
+    assert sem.sem_selftest_device_once(64, 4) == [1] * 64
+    with pytest.raises(sem.SemError):
+        sem.sem_selftest_device_once(65, 1)
