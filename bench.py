@@ -149,6 +149,63 @@ def cpu_oracle_sample(steps=1, n=32):
     return dofs / dt, threads, desc, dt, busy
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu; /proc/cpuinfo as a fallback)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+_ONE_THREAD = """
+import json, sys, time
+sys.path.insert(0, {root!r})
+from bench import cpu_oracle_sample, cpu_small_case
+v, thr, desc, secs, busy = cpu_oracle_sample(steps=1, n={n})
+s = cpu_small_case()
+print(json.dumps(dict(value=v, desc=desc, seconds=secs, busy=busy, small=s)))
+"""
+
+
+def cpu_small_case():
+    """The oracle on the whole small workload: 10 SSP-RK3 steps of 1 s on the
+    6 x 6 x 4, N = 4 mesh (600 x 600 x 24 km, 144 elements)."""
+    from oracle import mesh as om, refstate, rk as ork
+    from synth.vortex import vortex_state
+    o = om.OracleMesh(600e3, 600e3, 24e3, 6, 6, 4, 4)
+    q = vortex_state(o.XG, 24e3)
+    prm = refstate.Params()
+    t0 = time.perf_counter()
+    for _ in range(10):
+        q = ork.rk_step(o, prm, q, 1.0)
+    dt = time.perf_counter() - t0
+    return {"workload": "uniform-6x6x4-N4, 10 SSP-RK3 steps of 1 s", "seconds": dt,
+            "value": 5 * o.Ne * o.P * 3 * 10 / dt}
+
+
+def cpu_one_thread(n=16):
+    """The oracle with its BLAS held to one thread, in a fresh interpreter
+    (the thread count is fixed when numpy loads): an n x n x 16 block, one
+    step, and the whole small workload."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", _ONE_THREAD.format(root=ROOT, n=n)], env=env,
+                       capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr[-300:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
 def batched_measure(sem, torch, steps=10, warmup=3, refine=True):
     """The 16-instance batched workload: one CUDA-graph launch per step over
     all instances (persistent element kernel + gather/increment kernel per
@@ -401,6 +458,9 @@ def main():
         tune = {"variants": [{"layers_per_cta": r[0], "min_ctas_per_sm": r[1], "ms": r[2],
                               "kind": r[3]} for r in rows], "chosen": chosen}
     dof_stage = 5 * m.Ne * (N + 1) ** 3
+    # the arithmetic peaks of this GPU, from the library's FMA probe
+    fp32_peak = sem.sem_peak_probe(sem.SEM_PREC_MIXED, stream)
+    fp64_peak = sem.sem_peak_probe(sem.SEM_PREC_FP64, stream)
     for _ in range(max(a.warmup, 3)):
         bufs = step(bufs, p)
     torch.cuda.synchronize()
@@ -431,27 +491,24 @@ def main():
     value = job_throughput(dof_stage * 3, world, ms)
     status = sem.sem_status(m)
 
-    # per-kernel roofline of the timed region
+    # per-kernel roofline of the timed region, on the method's algorithmic
+    # bytes per RK stage: per global node the float64 stage reads and writes
+    # (qn 40 B, qs 40 B or its float32 mirror 20 B, q_out 40 B and its mirror
+    # 20 B) and the inverse mass (8 or 4 B), plus 4 B of constraint index per
+    # local node.  Mixed: 124 B per global node + 4 B per local node; float64:
+    # 128 + 4.  The element kernel's share is its read of the state (the
+    # mirror, 20 B, or the float64 state, 40 B) and the index; the gather /
+    # stage kernel has the rest.  The column residuals the element kernel
+    # writes and the gather kernel reads back are an intermediate of this
+    # implementation, not algorithmic bytes: they are reported beside them.
     hbm, peak_kind = peaks()
     Ncol, Nq, NZ, NG, NH = m.Ncol, (N + 1) ** 2, m.NZ, m.NG, m.NH
+    NL = m.Ne * (N + 1) ** 3
     rbytes = 4 if a.form == "mixed" else 8
-    # algorithmic bytes per launch: the state read by the element kernel
-    # (float32 mirror or float64), the column residuals written and read back,
-    # the stage's float64 reads (qs; qn on 2 of 3 stages), the float64 output
-    # and its float32 mirror, plus the index and mass tables
-    NZr = (NZ + 3) // 4 * 4
-    alg = {
-        "volume": 5 * rbytes * NG + 4 * Nq * Ncol + 5 * rbytes * Ncol * Nq * NZ,
-        # float64 form: residual read, qs and (2 of 3 stages) qn read, output write
-        "dss_rk": (5 * rbytes * Ncol * Nq * NZ + (1 + 2.0 / 3.0) * 5 * 8 * NG + 5 * 8 * NG
-                   + rbytes * (NH + NZ) + (4 + rbytes) * Ncol * Nq + 4 * NH),
-        # increment form, averaged over its 3 stages: residual read; stage 0
-        # writes d and a mirror and reads the mirror of q_n (12 B/value),
-        # stage 1 also reads d (16 B), stage 2 reads d and q, writes q and its
-        # mirror (24 B)
-        "dss_inc": (5 * 4 * Ncol * Nq * NZ + 5 * NG * (12 + 16 + 24) / 3.0
-                    + 4 * (NH + NZ) + 8 * Ncol * Nq + 4 * NH),
-    }
+    stage_bytes = (124 if a.form == "mixed" else 128) * NG + 4 * NL
+    elem_bytes = 5 * rbytes * NG + 4 * NL
+    resid_bytes = 5 * rbytes * Ncol * Nq * NZ
+    alg = {"volume": elem_bytes, "dss_rk": stage_bytes - elem_bytes, "dss_inc": stage_bytes - elem_bytes}
     kernels = {}
     for name, (launches, tot) in prof.items():
         if name == "mirror":
@@ -459,14 +516,16 @@ def main():
         base = name.rsplit("_", 1)[0]
         avg = tot / max(launches, 1)
         kernels[name] = {"launches": launches, "ms_avg": avg, "share": None,
-                         "alg_bytes": alg[base], "gbs": alg[base] / (avg * 1e-3) / 1e9}
+                         "alg_bytes": alg[base], "gbs": alg[base] / (avg * 1e-3) / 1e9,
+                         "frac": alg[base] / (avg * 1e-3) / 1e9 / hbm,
+                         "intermediate_bytes": resid_bytes}
     tot_all = sum(v[1] for v in prof.values()) or 1.0
     for name in list(kernels):
         kernels[name]["share"] = prof[name][1] / tot_all
     dom = max(kernels, key=lambda k: prof[k][1])
-    # ratio of measured DRAM traffic (ncu, same kernel and workload) to the
-    # algorithmic bytes, kept under profiles/; null until a capture of the
-    # current kernel exists
+    # measured DRAM traffic of the dominant kernel (ncu, same kernel and
+    # workload, kept under profiles/); null until a capture of the current
+    # kernel source exists
     traffic = None
     try:
         import hashlib
@@ -478,13 +537,26 @@ def main():
             traffic = tr[dom]["bytes"]
     except Exception:
         traffic = None
+    flop_node = 300.0        # float32 flop per local node of the element kernel (estimate of the method)
+    dav = kernels[dom]["ms_avg"]
     roof = {"kernel": dom, "bound": "hbm", "achieved": kernels[dom]["gbs"], "peak": hbm,
-            "unit": "GB/s", "frac": kernels[dom]["gbs"] / hbm, "traffic": traffic,
-            "peak_source": peak_kind,
+            "unit": "GB/s", "frac": kernels[dom]["frac"], "traffic": traffic,
+            "alg_bytes": alg[dom.rsplit("_", 1)[0]], "intermediate_bytes": resid_bytes,
+            "traffic_over_alg": None if traffic is None else traffic / alg[dom.rsplit("_", 1)[0]],
+            "peak_source": peak_kind + " (MEASURED_PEAKS.json copy bandwidth)",
+            "alu": {"flop_per_local_node": flop_node,
+                    "achieved_tflops": flop_node * NL / (dav * 1e-3) / 1e12,
+                    "peak_tflops": fp32_peak if a.form == "mixed" else fp64_peak,
+                    "peak_source": "sem_peak_probe (this GPU, FMA chains)",
+                    "frac": flop_node * NL / (dav * 1e-3) / 1e12 / (fp32_peak if a.form == "mixed" else fp64_peak)},
+            "stage": {"alg_bytes": stage_bytes, "ms": ms / 3,
+                      "achieved": stage_bytes / (ms / 3 * 1e-3) / 1e9,
+                      "frac": stage_bytes / (ms / 3 * 1e-3) / 1e9 / hbm},
             "timing": "CUDA events around each launch on its stream, over a second pass of the K timed steps"}
 
     # FP64 form beside it, and the max-wind gate after gate_steps steps
     fp64_ms = None
+    fp64_kernels = None
     if a.form == "mixed":
         b64 = new_bufs()
         for _ in range(2):
@@ -498,6 +570,24 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         fp64_ms = max_over_ranks(e0.elapsed_time(e1) / nfp, world, "cuda")
+        sem.sem_profile_begin()
+        for _ in range(nfp):
+            b64 = step(b64, p64)
+        torch.cuda.synchronize()
+        pr64 = sem.sem_profile_end()
+        st64 = 128 * NG + 4 * NL
+        fp64_kernels = {}
+        for k, (nl, tot) in pr64.items():
+            avg = tot / max(nl, 1)
+            fp64_kernels[k] = {"launches": nl, "ms_avg": avg}
+            if k.startswith("dss_rk"):
+                # the whole stage's algorithmic bytes (128 B per global node +
+                # 4 B per local node) over the gather / stage kernel alone
+                fp64_kernels[k].update(stage_alg_bytes=st64,
+                                       frac_stage_bytes=st64 / (avg * 1e-3) / 1e9 / hbm)
+            if k.startswith("volume"):
+                fp64_kernels[k].update(achieved_tflops=flop_node * NL / (avg * 1e-3) / 1e12,
+                                       frac_fp64_peak=flop_node * NL / (avg * 1e-3) / 1e12 / fp64_peak)
     gate = None
     if a.gate_steps > 0:
         bm = new_bufs()
@@ -613,8 +703,10 @@ def main():
         cpu = None
         if world == 1 and not a.no_cpu_baseline:
             v, thr, desc, secs, busy = cpu_oracle_sample()
+            one = cpu_one_thread()
             cpu = {"value": v, "unit": "DOF-updates/s", "cores": thr, "kind": "oracle",
-                   "sample": desc, "seconds": secs, "busy_threads": busy}
+                   "sample": desc, "seconds": secs, "busy_threads": busy, "cpu_model": cpu_model(),
+                   "one_thread": one, "small_workload_all_threads": cpu_small_case()}
         line = {
             "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -626,7 +718,10 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "fp64_form": None if fp64_ms is None else {
                 "ms_per_step": fp64_ms, "value": job_throughput(dof_stage * 3, world, fp64_ms),
-                "speedup_mixed_over_fp64": fp64_ms / ms},
+                "speedup_mixed_over_fp64": fp64_ms / ms, "kernels": fp64_kernels,
+                "stage_frac": (128 * NG + 4 * NL) / (fp64_ms / 3 * 1e-3) / 1e9 / hbm},
+            "peaks": {"hbm_gbs": hbm, "hbm_source": peak_kind, "fp32_tflops": fp32_peak,
+                      "fp64_tflops": fp64_peak, "fma_source": "sem_peak_probe"},
             "gate": gate,
             "roofline": roof, "kernels": kernels, "autotune": tune, "batched": batched,
             "learned": learned_res, "amr": amr_res, "physics": physics_res,

@@ -324,6 +324,28 @@ int sem_adapt_flags(sem_mesh* m, const sem_params* p, const double* q_dev,
 int sem_adapt_flags_host(sem_mesh* m, const sem_params* p, const double* q_dev,
                          int8_t* flags_host, cudaStream_t stream);
 
+/* The same rule (Sec. 3.1) evaluated for other levels than the mesh's own:
+ * level_dev ([Ne] int8 device array, element order as above) gives each
+ * element's level; with level_dev NULL every element is taken at level_all
+ * (0..lvl_max, else SEM_ERR_ARG).  The geometry (element sizes for the
+ * derivatives of the vorticity and potential-vorticity criteria) stays the
+ * mesh's own.  Used to schedule adaptation on levels a caller tracks itself
+ * (the flag at the element's level: +1 is a refinement the criterion wants),
+ * and for the labels of a flag predictor (the flag each level would get). */
+int sem_adapt_flags_levels(sem_mesh* m, const sem_params* p, const double* q_dev,
+                           const int8_t* level_dev, int level_all, int8_t* flags_dev,
+                           double* cmax_dev, cudaStream_t stream);
+
+/* Merges the criterion's flags with a predictor's (a learned schedule that
+ * keeps the criterion as its fallback): out = +1 where either asks for
+ * refinement, -1 where both ask for coarsening, else 0; a request the
+ * element's level cannot take (+1 at lvl_max, -1 at level 0) counts as 0.
+ * crit_dev, pred_dev, level_dev, out_dev: [n] int8 device arrays (out may
+ * alias crit or pred).  The paper has no predictor; the merge is this
+ * library's reading of "the criterion stays the fallback". */
+int sem_merge_flags(const int8_t* crit_dev, const int8_t* pred_dev, const int8_t* level_dev,
+                    int lvl_max, long long n, int8_t* out_dev, cudaStream_t stream);
+
 /* Host only: the mesh after one adaptation pass driven by element flags
  * (Sec. 3.1: whole-column horizontal refinement, four-sibling coarsening,
  * one level per pass, 2:1 balance).  The new mesh remembers where each new
@@ -347,6 +369,15 @@ int sem_diag(sem_mesh* m, const sem_params* p, const double* q_dev, double half_
  * they write a non-finite value; synchronises the stream.  *status_host is 0
  * (clean) or SEM_ERR_NUMERIC. */
 int sem_status(sem_mesh* m, int* status_host, cudaStream_t stream);
+
+/* Arithmetic-rate probe: the float32 (precision = SEM_PREC_MIXED) or float64
+ * (SEM_PREC_FP64) FMA rate of the current GPU in TFLOP/s (2 flop per FMA),
+ * from independent FMA chains in 8 blocks of 256 threads per SM; best of
+ * three timed launches after a warm-up (CUDA events on `stream`).  The
+ * denominators of the element kernels' ALU rooflines.  Allocates and frees
+ * a small output buffer (stream-ordered); synchronises the stream.  The
+ * paper has no counterpart. */
+int sem_peak_probe(int precision, double* tflops_host, cudaStream_t stream);
 
 /* Host-only check of the library's one-time set-up per device (no GPU
  * needed).  The library uploads its constant tables and sets its kernel

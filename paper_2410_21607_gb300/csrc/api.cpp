@@ -36,7 +36,7 @@ void free_device(Mesh& m) {
   if (m.dev_id >= 0 && cur != m.dev_id) cudaSetDevice(m.dev_id);
   DeviceTables& D = *m.dev;
   void* ptrs[] = {D.hmap, D.hang_h, D.hang_w, D.qt_ptr, D.qt_src, D.qt_w, D.Minv_h, D.Minv_z,
-                  D.Mh, D.Mz, D.Minv_h32, D.Minv_z32, D.qt_w32, D.qt_rec_src, D.qt_rec_w, D.hang_w32, D.mirror, D.spg, D.spg32, D.ref, D.ref32, D.col_level, D.col_x0, D.col_y0, D.xh, D.yh, D.zk, D.hzk, D.hzk32, D.scratch,
+                  D.Mh, D.Mz, D.Minv_h32, D.Minv_z32, D.qt_w32, D.qt_rec_src, D.qt_rec_w, D.qt_rec_unit, D.hang_w32, D.mirror, D.spg, D.spg32, D.ref, D.ref32, D.col_level, D.col_x0, D.col_y0, D.xh, D.yh, D.zk, D.hzk, D.hzk32, D.scratch,
                   D.status, D.org, D.elem_cmax, D.elem_flags, D.diag_buf,
                   D.tr_comp_ptr, D.tr_nodes, D.tr_A_ptr, D.tr_A_col, D.tr_A_val, D.tr_coupled};
   for (void* p : ptrs)
@@ -69,10 +69,17 @@ int ensure_device(Mesh& m) {
   for (size_t k = 0; k < hw32.size(); ++k) hw32[k] = (float)m.hang_w[k];
   // compact Q_h^T records: the up to 4 sources of a horizontal node and their
   // weights side by side (one 16-byte load each), in the CSR order
-  std::vector<int> rsrc((size_t)m.NH * 4, -1);
+  std::vector<int> rsrc((size_t)m.NH * 4, -1), runit((size_t)m.NH * 4, -1);
   std::vector<float> rw((size_t)m.NH * 4, 0.f);
   for (long long h = 0; h < m.NH; ++h) {
     const int beg = m.qt_ptr[h], cnt = m.qt_ptr[h + 1] - beg;
+    bool unit = cnt <= 4;
+    for (int e = 0; e < cnt && unit; ++e) unit = m.qt_w[beg + e] == 1.0;
+    if (unit) {
+      for (int e = 0; e < cnt; ++e) runit[(size_t)h * 4 + e] = m.qt_src[beg + e];
+    } else {
+      runit[(size_t)h * 4] = -2;
+    }
     if (cnt > 4) {
       rsrc[(size_t)h * 4] = -2;
       continue;
@@ -105,7 +112,7 @@ int ensure_device(Mesh& m) {
       (rc = upload(D.hzk, hzk)) || (rc = upload(D.hzk32, hzk32)) ||
       (rc = upload(D.Minv_h32, minvh32)) || (rc = upload(D.Minv_z32, minvz32)) ||
       (rc = upload(D.qt_w32, qtw32)) || (rc = upload(D.hang_w32, hw32)) ||
-      (rc = upload(D.qt_rec_src, rsrc)) || (rc = upload(D.qt_rec_w, rw)) ||
+      (rc = upload(D.qt_rec_src, rsrc)) || (rc = upload(D.qt_rec_w, rw)) || (rc = upload(D.qt_rec_unit, runit)) ||
       (rc = upload(D.col_x0, cx0)) || (rc = upload(D.col_y0, cy0))) {
     free_device(m);
     return rc;
@@ -713,6 +720,25 @@ int sem_adapt_flags(sem_mesh* mh, const sem_params* p, const double* q, int8_t* 
   if (!q || !flags) return fail(SEM_ERR_ARG, "NULL argument");
   if (p->lvl_max > p->n_thresholds) return fail(SEM_ERR_ARG, "need one threshold per level");
   return launch_adapt(mh->m, *p, q, flags, cmax, st);
+}
+
+int sem_adapt_flags_levels(sem_mesh* mh, const sem_params* p, const double* q, const int8_t* level,
+                           int level_all, int8_t* flags, double* cmax, cudaStream_t st) {
+  int rc = prepare(mh, p);
+  if (rc) return rc;
+  if (!q || !flags) return fail(SEM_ERR_ARG, "NULL argument");
+  if (p->lvl_max > p->n_thresholds) return fail(SEM_ERR_ARG, "need one threshold per level");
+  if (!level && (level_all < 0 || level_all > p->lvl_max))
+    return fail(SEM_ERR_ARG, "level_all must be in 0..lvl_max when no level array is given");
+  return launch_adapt(mh->m, *p, q, flags, cmax, st, level, level ? -1 : level_all);
+}
+
+int sem_merge_flags(const int8_t* crit, const int8_t* pred, const int8_t* level, int lvl_max, long long n,
+                    int8_t* out, cudaStream_t st) {
+  if (n < 0 || (n > 0 && (!crit || !pred || !level || !out))) return fail(SEM_ERR_ARG, "NULL argument");
+  if (lvl_max < 0) return fail(SEM_ERR_ARG, "lvl_max must be >= 0");
+  if (n == 0) return SEM_OK;
+  return launch_merge_flags(crit, pred, level, lvl_max, n, out, st);
 }
 
 int sem_adapt_flags_host(sem_mesh* mh, const sem_params* p, const double* q, int8_t* flags_host,

@@ -56,6 +56,11 @@ struct AdaptArgs {
   int var[SEM_MAX_THRESHOLDS];    // SEM_CRIT_* per threshold
   double gx[16], gy[16];          // 2 / h per level
   const double* hzk;              // [nz] layer thicknesses
+  // level the rule is evaluated for: per element (elem_level, [Ne]), or one
+  // level for every element (level_all >= 0), else the column's own level;
+  // the geometry always uses the column's level
+  const int8_t* elem_level;
+  int level_all;
 };
 
 template <int N, int EQ>
@@ -70,7 +75,7 @@ adapt_column(const AdaptArgs A) {
   const int i = t % n1, j = (t / n1) % n1, c = t / Nq;
   const int ab = i + n1 * j;
   const int hm = act ? A.hmap[(long long)col * Nq + ab] : 0;
-  const int lev = A.col_level[col];
+  const int geo_lev = A.col_level[col];
   for (int k = 0; k < A.nz; ++k) {
     double s = 0.0, zeta = 0.0, pv = 0.0, rho = 1.0;
     if (act) {
@@ -120,7 +125,7 @@ adapt_column(const AdaptArgs A) {
             d[qv][2] += Dc * sQ[qv][lz];
           }
         }
-        const double gx = A.gx[lev], gy = A.gy[lev], gz = 2.0 / A.hzk[k];
+        const double gx = A.gx[geo_lev], gy = A.gy[geo_lev], gz = 2.0 / A.hzk[k];
         for (int qv = 0; qv < 4; ++qv) {
           d[qv][0] *= gx;
           d[qv][1] *= gy;
@@ -149,6 +154,7 @@ adapt_column(const AdaptArgs A) {
         for (int w = 1; w < NW; ++w) mx[cv] = fmax(mx[cv], red[cv][w]);
       }
       const long long e = (long long)col * A.nz + k;
+      const int lev = A.elem_level ? (int)A.elem_level[e] : (A.level_all >= 0 ? A.level_all : geo_lev);
       int flag = 0;
       if (lev < A.lvl_max && mx[A.var[lev]] > A.thr[lev]) flag = 1;
       else if (lev > 0 && mx[A.var[lev - 1]] <= A.thr[lev - 1]) flag = -1;
@@ -173,9 +179,11 @@ static void launch_adapt_n(const AdaptArgs& A, int ncol, int eq, cudaStream_t st
 }
 
 int launch_adapt(Mesh& m, const sem_params& p, const double* q, int8_t* flags, double* cmax,
-                 cudaStream_t st) {
+                 cudaStream_t st, const int8_t* elem_level, int level_all) {
   DeviceTables& D = *m.dev;
   AdaptArgs A;
+  A.elem_level = elem_level;
+  A.level_all = level_all;
   A.q = q;
   A.hmap = D.hmap;
   A.hang_h = D.hang_h;
@@ -276,6 +284,31 @@ int launch_diag(Mesh& m, const sem_params& p, const double* q, double hw, sem_di
   if (mm < 0) return fail(SEM_ERR_ARG, "no node inside the diagnostic sub-domain");
   out->max_wind = mx;
   out->max_mean_wind = mm;
+  return SEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Criterion flags merged with a predictor's flags (the learned schedule, the
+// criterion kept as the fallback): refine when either asks, coarsen only when
+// both do, keep otherwise; a request the element's level cannot take (refine
+// at lvl_max, coarsen at level 0) counts as keep.
+__global__ void merge_flags_kernel(const int8_t* crit, const int8_t* pred, const int8_t* level, int lvl_max,
+                                   long long n, int8_t* out) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int L = level[e];
+    int c = crit[e], p = pred[e];
+    if (L >= lvl_max) { c = c > 0 ? 0 : c; p = p > 0 ? 0 : p; }
+    if (L <= 0) { c = c < 0 ? 0 : c; p = p < 0 ? 0 : p; }
+    out[e] = (int8_t)((c > 0 || p > 0) ? 1 : ((c < 0 && p < 0) ? -1 : 0));
+  }
+}
+
+int launch_merge_flags(const int8_t* crit, const int8_t* pred, const int8_t* level, int lvl_max, long long n,
+                       int8_t* out, cudaStream_t st) {
+  const long long blocks = std::max<long long>(1, std::min<long long>((n + 255) / 256, 152 * 8));
+  merge_flags_kernel<<<(int)blocks, 256, 0, st>>>(crit, pred, level, lvl_max, n, out);
+  SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;
 }
 

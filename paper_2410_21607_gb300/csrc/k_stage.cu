@@ -363,6 +363,7 @@ struct DssArgs {
   const void* qt_w;       // double (FP64 form) or float (mixed form)
   const void* Minv_h;     // double or float
   const void* Minv_z;
+  const int4* qt_rec_unit;  // FP64 form: unit-weight Q_h^T records
   const double* qn;
   const double* qs;
   double* out;
@@ -374,40 +375,74 @@ struct DssArgs {
   int* status;
 };
 
-// FP64 form: float64 throughout.
+// FP64 form: float64 throughout.  The float64 pipe of this part is narrow
+// (1/64 of the float32 rate), so the kernel issues float64 instructions only
+// for the arithmetic itself: node indices are 32-bit (an unsigned division by
+// NZ runs on the integer pipe), a horizontal node whose Q_h^T weights are all
+// exactly 1 (every node away from 2:1 faces) adds its sources with plain
+// additions (the first one is a load), and the stage update is specialised:
+//   MODE 0  out = s T                    (right-hand side only)
+//   MODE 1  out = qs + s T               (a = 0, b = 1: the first SSP-RK3 stage)
+//   MODE 2  out = a qn + b qs + s T      (any a, b)
+// with s = c dt / M.  Every sum is formed in the order of the CSR lists, so
+// the results are those of a plain fma loop over the lists, bit for bit.
+template <int MODE>
 __global__ void __launch_bounds__(256) dss_stage_fp64(const DssArgs A) {
   const double* rc = (const double*)A.rc;
   const double* qtw = (const double*)A.qt_w;
   const double* mh = (const double*)A.Minv_h;
   const double* mz = (const double*)A.Minv_z;
+  const unsigned NZ = (unsigned)A.NZ, NG = (unsigned)A.NG;
+  const long long NGl = A.NG;
+  const int NZr = A.NZr;
   int bad = 0;
-  for (long long gidx = (long long)blockIdx.x * blockDim.x + threadIdx.x; gidx < A.NG;
-       gidx += (long long)gridDim.x * blockDim.x) {
-    const long long h = gidx / A.NZ;
-    const int kz = (int)(gidx - h * A.NZ);
-    const int beg = __ldg(A.qt_ptr + h), end = __ldg(A.qt_ptr + h + 1);
-    const double s = A.cdt * (__ldg(mh + h) * __ldg(mz + kz));
-    const bool lid = (kz == 0) || (kz == A.NZ - 1);
-    double acc[kFields] = {0, 0, 0, 0, 0};
-    for (int e = beg; e < end; ++e) {
-      const double w = __ldg(qtw + e);
-      const double* p = rc + (long long)__ldg(A.qt_src + e) * kFields * A.NZr + kz;
+  for (unsigned gidx = blockIdx.x * blockDim.x + threadIdx.x; gidx < NG; gidx += gridDim.x * blockDim.x) {
+    const unsigned h = gidx / NZ;
+    const int kz = (int)(gidx - h * NZ);
+    // the stage state first, so that its latency overlaps the gather's
+    double qsv[kFields];
 #pragma unroll
-      for (int fl = 0; fl < kFields; ++fl) acc[fl] = fma(w, __ldg(p + (long long)fl * A.NZr), acc[fl]);
+    for (int fl = 0; fl < kFields; ++fl)
+      if (MODE >= 1) qsv[fl] = __ldg(A.qs + fl * NGl + gidx);
+    const double s = A.cdt * (__ldg(mh + h) * __ldg(mz + kz));
+    const bool lid = (kz == 0) || (kz == (int)NZ - 1);
+    double acc[kFields];
+    const int4 r = __ldg(A.qt_rec_unit + h);
+    if (r.x >= 0) {
+      const double* p = rc + (size_t)r.x * kFields * NZr + kz;
+#pragma unroll
+      for (int fl = 0; fl < kFields; ++fl) acc[fl] = __ldg(p + fl * NZr);
+      auto add = [&](int src) {
+        const double* pe = rc + (size_t)src * kFields * NZr + kz;
+#pragma unroll
+        for (int fl = 0; fl < kFields; ++fl) acc[fl] += __ldg(pe + fl * NZr);
+      };
+      if (r.y >= 0) {
+        add(r.y);
+        if (r.z >= 0) {
+          add(r.z);
+          if (r.w >= 0) add(r.w);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int fl = 0; fl < kFields; ++fl) acc[fl] = 0.0;
+      const int beg = __ldg(A.qt_ptr + h), end = __ldg(A.qt_ptr + h + 1);
+      for (int e = beg; e < end; ++e) {
+        const double w = __ldg(qtw + e);
+        const double* p = rc + (size_t)__ldg(A.qt_src + e) * kFields * NZr + kz;
+#pragma unroll
+        for (int fl = 0; fl < kFields; ++fl) acc[fl] = fma(w, __ldg(p + fl * NZr), acc[fl]);
+      }
     }
 #pragma unroll
     for (int fl = 0; fl < kFields; ++fl) {
-      const long long o = (long long)fl * A.NG + gidx;
       const double T = (fl == 3 && lid) ? 0.0 : acc[fl];
       double val;
-      if (A.rhs_only) {
-        val = T * s;
-      } else {
-        val = A.b * __ldg(A.qs + o);
-        if (A.a != 0.0) val = fma(A.a, __ldg(A.qn + o), val);
-        val = fma(s, T, val);
-      }
-      A.out[o] = val;
+      if (MODE == 0) val = T * s;
+      else if (MODE == 1) val = fma(s, T, qsv[fl]);
+      else val = fma(s, T, fma(A.a, __ldg(A.qn + fl * NGl + gidx), A.b * qsv[fl]));
+      A.out[fl * NGl + gidx] = val;
       bad |= nonfinite_bits(val);
     }
   }
@@ -1890,6 +1925,7 @@ int launch_mirror(const double* q, float* q32, long long n, cudaStream_t st) {
 int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStream_t st) {
   int rc = upload_basis_constants();
   if (rc) return rc;
+  if (m.NG * kFields >= (1ll << 31)) return fail(SEM_ERR_ARG, "mesh too large for 32-bit node indexing");
   DeviceTables& D = *m.dev;
   const bool mixed = p.precision == SEM_PREC_MIXED;
   const float* qs32 = s.qs32;
@@ -1924,6 +1960,7 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
   B.qt_w = mixed ? (const void*)D.qt_w32 : (const void*)D.qt_w;
   B.Minv_h = mixed ? (const void*)D.Minv_h32 : (const void*)D.Minv_h;
   B.Minv_z = mixed ? (const void*)D.Minv_z32 : (const void*)D.Minv_z;
+  B.qt_rec_unit = reinterpret_cast<const int4*>(D.qt_rec_unit);
   B.qn = s.qn;
   B.qs = s.qs;
   B.out = s.out;
@@ -1941,8 +1978,12 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
     ProfScope ps(mixed ? "dss_rk_mixed" : "dss_rk_fp64", st);
     if (mixed)
       dss_stage_mixed<<<grid_cap(m.NG), 256, 0, st>>>(B);
+    else if (s.rhs_only)
+      dss_stage_fp64<0><<<grid_cap(m.NG), 256, 0, st>>>(B);
+    else if (s.a == 0.0 && s.b == 1.0)
+      dss_stage_fp64<1><<<grid_cap(m.NG), 256, 0, st>>>(B);
     else
-      dss_stage_fp64<<<grid_cap(m.NG), 256, 0, st>>>(B);
+      dss_stage_fp64<2><<<grid_cap(m.NG), 256, 0, st>>>(B);
   }
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;

@@ -146,6 +146,8 @@ struct DeviceTables {
   float* qt_w32 = nullptr;
   int* qt_rec_src = nullptr;    // [NH][4]: Q_h^T sources of h when it has at most 4 (-1: unused), else -2 (use the CSR lists)
   float* qt_rec_w = nullptr;    // [NH][4]: their float32 weights
+  int* qt_rec_unit = nullptr;   // [NH][4]: the sources of h when it has at most 4 and all their
+                                // weights are exactly 1 (-1: unused), else -2 (use the CSR lists)
   float* hang_w32 = nullptr;
   float* mirror = nullptr;      // float32 state mirror scratch [5][NG]
   double* Mh = nullptr;
@@ -211,7 +213,9 @@ struct StageArgs {
 };
 int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStream_t st);
 int launch_adapt(Mesh& m, const sem_params& p, const double* q, int8_t* flags, double* cmax,
-                 cudaStream_t st);
+                 cudaStream_t st, const int8_t* elem_level = nullptr, int level_all = -1);
+int launch_merge_flags(const int8_t* crit, const int8_t* pred, const int8_t* level, int lvl_max, long long n,
+                       int8_t* out, cudaStream_t st);
 int launch_diag(Mesh& m, const sem_params& p, const double* q, double half_width,
                 sem_diag_out* out, cudaStream_t st);
 int launch_transfer(Mesh& oldm, Mesh& newm, const double* qold, double* qnew, cudaStream_t st);

@@ -6,11 +6,12 @@ forward/backward/Adam); this module only sequences the calls and does the
 integer bookkeeping of element levels with torch tensor ops.
 
 Protocol.  The solver runs trajectories; every `every` steps it records each
-element's features (sem_mlp_features) and the criterion's per-element maximum
-speed (sem_adapt_flags).  A training row pairs the features at step t, with
-the element's level set to L, with the criterion's flag for level L at step
-t + ahead (Sec. 3.1 rule: +1 above threshold(L+1), -1 at or below
-threshold(L), else 0), for every L in 0..lvl_max.
+element's features (sem_mlp_features) and the criterion's flag for every
+level L in 0..lvl_max (sem_adapt_flags_levels: the Sec. 3.1 rule evaluated
+as if the element were at level L).  A training row pairs the features at
+step t, with the element's level set to L, with that flag at step t + ahead.
+The rule itself, and the merge of the criterion's and the network's flags
+(sem_merge_flags), run in the library; this module only selects and counts.
 
 Scheduling (element levels kept as a virtual level per element on the fixed
 solver mesh, so that the comparison isolates the scheduling): every `ahead`
@@ -32,46 +33,47 @@ element count and throughput.
 import numpy as np
 
 
-def target_level(cmax, thresholds):
-    """Number of thresholds the element maximum speed exceeds (Sec. 3.1)."""
-    t = (cmax > thresholds[0]).long()
-    for thr in thresholds[1:]:
-        t = t + (cmax > thr).long()
-    return t
+def level_flags(sem, torch, mesh, p_crit, q, lvl_max):
+    """The criterion's flag for every element at each level 0..lvl_max
+    ([lvl_max + 1, Ne] int8, on the device)."""
+    out = torch.empty((lvl_max + 1, mesh.Ne), dtype=torch.int8, device=q.device)
+    for L in range(lvl_max + 1):
+        sem.sem_adapt_flags_levels(mesh, p_crit, q, out[L], level_all=L)
+    return out
 
 
 def trajectory(sem, torch, mesh, p_step, p_crit, q0, dt, steps, every, scales):
-    """[(features, cmax)] every `every` steps of a mixed-form run from q0."""
+    """[(features, per-level criterion flags)] every `every` steps of a
+    mixed-form run from q0."""
     q = q0.clone()
     q32 = torch.empty(q.shape, dtype=torch.float32, device=q.device)
     work = torch.empty((10, mesh.NG), dtype=torch.float32, device=q.device)
     sem.sem_mirror(mesh, q, q32)
-    flags = torch.empty(mesh.Ne, dtype=torch.int8, device=q.device)
     out = []
     for s in range(steps + 1):
         if s % every == 0:
-            cmax = torch.empty(mesh.Ne, dtype=torch.float64, device=q.device)
-            sem.sem_adapt_flags(mesh, p_crit, q, flags, cmax)
+            fl = level_flags(sem, torch, mesh, p_crit, q, p_crit.lvl_max)
             F = torch.empty((mesh.Ne, 136), dtype=torch.float32, device=q.device)
             sem.sem_mlp_features(mesh, q, scales, F)
-            out.append((F, cmax))
+            out.append((F, fl))
         if s < steps:
             sem.sem_step_mixed(mesh, p_step, q, q32, work, dt)
     return out
 
 
-def training_rows(torch, snaps, ahead, every, thresholds, lvl_max):
+def training_rows(torch, snaps, ahead, every, lvl_max):
+    """Features at t with the level set to L, labelled by the criterion's
+    flag for level L at t + ahead (classes 0, 1, 2 = coarsen, keep, refine)."""
     k = ahead // every
     Fs, Ys = [], []
     for i in range(len(snaps) - k):
         F = snaps[i][0]
-        T = target_level(snaps[i + k][1], thresholds)
+        later = snaps[i + k][1]
         for L in range(lvl_max + 1):
             G = F.clone()
             G[:, 135] = float(L)
-            y = torch.where(T > L, 2, torch.where(T < L, 0, 1)).to(torch.int8)
             Fs.append(G)
-            Ys.append(y)
+            Ys.append((later[L] + 1).to(torch.int8))
     return torch.cat(Fs), torch.cat(Ys)
 
 
@@ -94,20 +96,20 @@ def train(sem, torch, F, Y, iters=1500, batch=65536, seed=1, lr=1e-3):
     return net, first, last
 
 
-def schedule(sem, torch, snaps, ahead, every, thresholds, lvl_max, net=None):
+def schedule(sem, torch, snaps, ahead, every, lvl_max, net=None):
     """Missed-refinement rate, mean refined levels and remesh count."""
     Ne = snaps[0][0].shape[0]
     dev = snaps[0][0].device
-    L = torch.zeros(Ne, dtype=torch.long, device=dev)
+    L = torch.zeros(Ne, dtype=torch.int8, device=dev)
     k = ahead // every
     missed = want = 0
     refined = 0.0
     remesh = 0
-    for i, (F, cmax) in enumerate(snaps):
-        T = target_level(cmax, thresholds)
+    for i, (F, fl_lv) in enumerate(snaps):
+        # the criterion's flag at each element's own (tracked) level
+        now = fl_lv.gather(0, L.long()[None]).squeeze(0)
         if i % k == 0:
             remesh += 1
-            now = (T > L).long() - ((T < L) & (L > 0)).long()
             if net is None:
                 fl = now
             else:
@@ -115,13 +117,11 @@ def schedule(sem, torch, snaps, ahead, every, thresholds, lvl_max, net=None):
                 G[:, 135] = L.float()
                 pred = torch.empty(Ne, dtype=torch.int8, device=dev)
                 sem.sem_mlp_predict_flags(net, G, pred)
-                pred = pred.long()
-                fl = torch.where((now > 0) | (pred > 0), 1,
-                                 torch.where((now < 0) & (pred < 0), -1, 0))
-            L = torch.clamp(L + fl, 0, lvl_max)
+                fl = sem.sem_merge_flags(now, pred, L, lvl_max)
+            L = (L + fl).clamp_(0, lvl_max)
         else:
-            missed += int((T > L).sum())
-            want += int((T > 0).sum())
+            missed += int((now > 0).sum())
+            want += int((fl_lv[0] > 0).sum())
         refined += float(L.float().mean())
     return {"missed_rate": missed / max(want, 1), "mean_level": refined / len(snaps),
             "remeshes": remesh}
@@ -137,15 +137,15 @@ def gain_experiment(sem, torch, mesh, states, dt, n_train, steps=400, every=10, 
     sc = np.asarray(scales, dtype=np.float32)
     trajs = [trajectory(sem, torch, mesh, p_step, p_crit, q0, dt, steps, every, sc) for q0 in states]
     status = sem.sem_status(mesh)
-    parts = [training_rows(torch, t, ahead, every, thresholds, lvl_max) for t in trajs[:n_train]]
+    parts = [training_rows(torch, t, ahead, every, lvl_max) for t in trajs[:n_train]]
     F = torch.cat([a for a, _ in parts])
     Y = torch.cat([b for _, b in parts])
     net, loss0, loss1 = train(sem, torch, F, Y, iters=iters, seed=seed)
     res = {"status": status, "rows": int(F.shape[0]), "loss_first": loss0, "loss_last": loss1,
            "criterion": [], "learned": []}
     for t in trajs[n_train:]:
-        res["criterion"].append(schedule(sem, torch, t, ahead, every, thresholds, lvl_max))
-        res["learned"].append(schedule(sem, torch, t, ahead, every, thresholds, lvl_max, net))
+        res["criterion"].append(schedule(sem, torch, t, ahead, every, lvl_max))
+        res["learned"].append(schedule(sem, torch, t, ahead, every, lvl_max, net))
     res["missed_criterion"] = float(np.mean([r["missed_rate"] for r in res["criterion"]]))
     res["missed_learned"] = float(np.mean([r["missed_rate"] for r in res["learned"]]))
     res["level_criterion"] = float(np.mean([r["mean_level"] for r in res["criterion"]]))
@@ -156,9 +156,9 @@ def gain_experiment(sem, torch, mesh, states, dt, n_train, steps=400, every=10, 
 
 
 def element_levels(sem, torch, mesh, device):
-    """Refinement level of every element (column level, repeated over the layers)."""
+    """Refinement level of every element (column level, repeated over the layers), int8."""
     lv = sem.sem_mesh_leaves_host(mesh)
-    return torch.from_numpy(np.repeat(lv[:, 0].astype(np.int64), mesh.nz)).to(device)
+    return torch.from_numpy(np.repeat(lv[:, 0].astype(np.int8), mesh.nz)).to(device)
 
 
 def adaptive_run(sem, torch, spec, L, Lz, nx, nz, N, lvl_max, thresholds, dt, t_end,
@@ -179,7 +179,6 @@ def adaptive_run(sem, torch, spec, L, Lz, nx, nz, N, lvl_max, thresholds, dt, t_
     dev = "cuda"
     p_step = sem.sem_params_default(precision=sem.SEM_PREC_MIXED, **(physics or {}))
     p_crit = sem.sem_params_default(thresholds=list(thresholds), lvl_max=lvl_max)
-    thr = list(thresholds)
     sc = np.asarray(scales, dtype=np.float32)
     if uniform_level is not None:
         m = sem.sem_mesh_create(L, L, Lz, nx << uniform_level, nx << uniform_level, nz, N)
@@ -211,26 +210,24 @@ def adaptive_run(sem, torch, spec, L, Lz, nx, nz, N, lvl_max, thresholds, dt, t_
         remesh_now = s > 0 and s % k_remesh == 0
         if uniform_level is None and (remesh_now or (s > 0 and s % k_check == 0)):
             flags = torch.empty(m.Ne, dtype=torch.int8, device=dev)
-            cmax = torch.empty(m.Ne, dtype=torch.float64, device=dev)
-            sem.sem_adapt_flags(m, p_crit, q, flags, cmax)
-            lev = element_levels(sem, torch, m, dev)
-            T = target_level(cmax, thr)
+            sem.sem_adapt_flags(m, p_crit, q, flags)
             if not remesh_now:
-                missed += int((T > lev).sum())
-                want += int((T > 0).sum())
+                # a missed refinement: the criterion wants more than the mesh has
+                base = torch.empty(m.Ne, dtype=torch.int8, device=dev)
+                sem.sem_adapt_flags_levels(m, p_crit, q, base, level_all=0)
+                missed += int((flags > 0).sum())
+                want += int((base > 0).sum())
             else:
-                fl = flags.long()
+                fl = flags
                 if net is not None:
+                    lev = element_levels(sem, torch, m, dev)
                     F = torch.empty((m.Ne, 136), dtype=torch.float32, device=dev)
                     sem.sem_mlp_features(m, q, sc, F)
                     F[:, 135] = lev.float()
                     pred = torch.empty(m.Ne, dtype=torch.int8, device=dev)
                     sem.sem_mlp_predict_flags(net, F, pred)
-                    pred = pred.long()
-                    pred = torch.where(lev >= lvl_max, torch.clamp(pred, max=0), pred)
-                    pred = torch.where(lev <= 0, torch.clamp(pred, min=0), pred)
-                    fl = torch.where((fl > 0) | (pred > 0), 1, torch.where((fl < 0) & (pred < 0), -1, 0))
-                fl_host = fl.to(torch.int8).cpu().numpy()
+                    fl = sem.sem_merge_flags(flags, pred, lev, lvl_max)
+                fl_host = fl.cpu().numpy()
                 if fl_host.any():
                     new = sem.sem_transfer_plan(m, fl_host)
                     q2 = torch.empty((5, new.NG), dtype=torch.float64, device=dev)

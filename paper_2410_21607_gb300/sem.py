@@ -35,7 +35,7 @@ EXPORTS = (
     "sem_mlp_set_params", "sem_mlp_get_grads", "sem_mlp_features", "sem_mlp_forward",
     "sem_mlp_predict_flags", "sem_mlp_backward", "sem_mlp_adam",
     "sem_checkpoint_write", "sem_checkpoint_read_mesh", "sem_checkpoint_read_state",
-    "sem_selftest_device_once",
+    "sem_selftest_device_once", "sem_peak_probe", "sem_adapt_flags_levels", "sem_merge_flags",
 )
 
 
@@ -140,6 +140,9 @@ def _load():
         "sem_autotune": (i, [vp, C.POINTER(Params), vp, i, C.POINTER(TuneOut), vp]),
         "sem_autotune_select": (i, [vp, i]),
         "sem_selftest_device_once": (i, [i, i, vp]),
+        "sem_peak_probe": (i, [i, C.POINTER(d), vp]),
+        "sem_adapt_flags_levels": (i, [vp, C.POINTER(Params), vp, vp, i, vp, vp, vp]),
+        "sem_merge_flags": (i, [vp, vp, vp, i, C.c_longlong, vp, vp]),
         "sem_profile_end": (i, [C.POINTER(ProfileOut)]),
     }
     for name, (res, args) in sig.items():
@@ -167,6 +170,11 @@ def _ptr(t):
     if not t.is_contiguous():
         raise ValueError("tensor must be contiguous")
     return t.data_ptr()
+
+
+def _torch():
+    import torch
+    return torch
 
 
 def _stream(stream):
@@ -349,6 +357,31 @@ def sem_adapt_flags(mesh, params, q, flags, cmax=None, stream=None):
     _check(LIB.sem_adapt_flags(mesh.h, C.byref(params), _ptr(q), _ptr(flags), _ptr(cmax),
                                _stream(stream)))
     return flags
+
+
+def sem_adapt_flags_levels(mesh, params, q, flags, level=None, level_all=-1, cmax=None, stream=None):
+    """The criterion's flags for the per-element levels `level` (int8 device
+    tensor [Ne]) or, with level None, for every element at level_all."""
+    _f64(q, mesh.field_shape)
+    if level is not None and (level.dtype != _torch().int8 or level.numel() != mesh.Ne):
+        raise ValueError("level: int8 tensor of one level per element")
+    _check(LIB.sem_adapt_flags_levels(mesh.h, C.byref(params), _ptr(q), _ptr(level), int(level_all),
+                                      _ptr(flags), _ptr(cmax), _stream(stream)))
+    return flags
+
+
+def sem_merge_flags(crit, pred, level, lvl_max, out=None, stream=None):
+    """Criterion flags merged with a predictor's (int8 device tensors [n]):
+    refine if either asks, coarsen only if both do, within the level bounds."""
+    n = crit.numel()
+    for t in (crit, pred, level):
+        if t.dtype != _torch().int8 or t.numel() != n:
+            raise ValueError("crit, pred and level: int8 tensors of equal length")
+    if out is None:
+        out = _torch().empty_like(crit)
+    _check(LIB.sem_merge_flags(_ptr(crit), _ptr(pred), _ptr(level), int(lvl_max), n, _ptr(out),
+                               _stream(stream)))
+    return out
 
 
 def sem_adapt_flags_host(mesh, params, q, stream=None):
@@ -565,3 +598,10 @@ def sem_selftest_device_once(n_devices, n_threads):
     out = (C.c_int * n_devices)()
     _check(LIB.sem_selftest_device_once(n_devices, n_threads, out))
     return list(out)
+
+
+def sem_peak_probe(precision, stream=None):
+    """float32 (SEM_PREC_MIXED) or float64 (SEM_PREC_FP64) FMA rate, TFLOP/s."""
+    out = C.c_double()
+    _check(LIB.sem_peak_probe(precision, C.byref(out), _stream(stream)))
+    return out.value

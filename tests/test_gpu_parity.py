@@ -64,6 +64,13 @@ def full_fields(q, z, eqset="C"):
     return out
 
 
+def increment_err(got, q0, ref):
+    """Relative L2 error of the state's change (got - q0 against ref - q0)
+    per field group: the dynamics, not the reference state that dominates
+    the full fields."""
+    return group_rel_l2(got - q0, ref - q0)
+
+
 MESHES = {
     "uniform-6x6x4-N4": dict(L=600e3, Lz=24e3, nx=6, nz=4, N=4),
     "twolevel-N4": dict(L=300e3, Lz=12e3, nx=4, nz=2, N=4, leaves=two_level_leaves()),
@@ -71,6 +78,7 @@ MESHES = {
                              periodic=(False, False)),
     "uniform-5x4x3-N6": dict(L=500e3, Lz=12e3, nx=5, nz=3, N=6),
     "uniform-3x3x2-N2": dict(L=300e3, Lz=12e3, nx=3, nz=2, N=2),
+    "twolevel-N5": dict(L=300e3, Lz=12e3, nx=4, nz=2, N=5, leaves=two_level_leaves()),
     # layers thickening upwards (top to bottom thickness 2.5), non-conforming
     "stretched-twolevel-N4": dict(L=300e3, Lz=12e3, nx=4, nz=3, N=4, leaves=two_level_leaves(),
                                   z_faces=stretched_faces(12e3, 3, 1.5)),
@@ -92,7 +100,7 @@ def test_rhs_fp64_matches_oracle(sem, name, eqset):
     assert np.all(err <= 1e-12), err
 
 
-@pytest.mark.parametrize("name", ["uniform-6x6x4-N4", "twolevel-N4", "stretched-twolevel-N4"])
+@pytest.mark.parametrize("name", ["uniform-6x6x4-N4", "twolevel-N4", "stretched-twolevel-N4", "twolevel-N5"])
 @pytest.mark.parametrize("eqset", ["C", "NC"])
 def test_rhs_mixed_matches_oracle(sem, name, eqset):
     m, o, X, perm = make_pair(sem, **MESHES[name])
@@ -107,7 +115,7 @@ def test_rhs_mixed_matches_oracle(sem, name, eqset):
 
 
 @pytest.mark.parametrize("name", ["twolevel-N4", "twolevel-17-layers-N4", "uniform-5x4x3-N6",
-                                  "stretched-twolevel-N4"])
+                                  "stretched-twolevel-N4", "twolevel-N5"])
 def test_every_element_kernel_variant_matches_oracle(sem, name):
     """Each launch variant of the mixed element kernel (z-pencil and line
     exchange, every layers-per-CTA count) gives the
@@ -168,9 +176,11 @@ def test_ten_rk3_steps_uniform_6x6x4(sem, prec):
     err = group_rel_l2(full_fields(got, z), full_fields(q_ref[:, perm], z))
     tol = 1e-12 if prec == 0 else 1e-4
     assert np.all(err <= tol), err
-    # the perturbation itself, not only the full field
+    # the perturbation itself, and the change over the ten steps
     pert = group_rel_l2(got, q_ref[:, perm])
     assert np.all(pert <= (1e-11 if prec == 0 else 1e-3)), pert
+    inc = increment_err(got, q_o[:, perm], q_ref[:, perm])
+    assert np.all(inc <= (1e-10 if prec == 0 else 1e-4)), inc
     assert sem.sem_status(m) == 0
 
 
@@ -434,18 +444,20 @@ def test_mixed_stage_with_mirrors_matches_oracle(sem):
     z = X[:, 2]
     err = group_rel_l2(full_fields(got, z), full_fields(q_ref[:, perm], z))
     assert np.all(err <= 1e-4), err
+    inc = increment_err(got, q_o[:, perm], q_ref[:, perm])
+    assert np.all(inc <= 1e-4), inc
     np.testing.assert_allclose(host(q32), got, rtol=2.4e-7, atol=1e-30)
     assert sem.sem_status(m) == 0
 
 
 @pytest.mark.parametrize("name", ["uniform-6x6x4-N4", "twolevel-N4", "uniform-3x3x2-N2", "uniform-5x4x3-N6",
-                                  "stretched-twolevel-N4"])
+                                  "stretched-twolevel-N4", "twolevel-N5"])
 def test_step_mixed_increment_form_matches_oracle(sem, name):
     """sem_step_mixed (float32 stage increments, one float64 accumulation per
     step) against ten float64 oracle steps."""
     m, o, X, perm = make_pair(sem, **MESHES[name])
     q_o = vortex_state(o.XG, o.Lz)
-    dt = 0.5 if name in ("uniform-5x4x3-N6", "stretched-twolevel-N4") else 1.0
+    dt = 0.5 if name in ("uniform-5x4x3-N6", "stretched-twolevel-N4", "twolevel-N5") else 1.0
     q_ref = q_o.copy()
     for _ in range(10):
         q_ref = ork.rk_step(o, PRM, q_ref, dt)
@@ -462,6 +474,8 @@ def test_step_mixed_increment_form_matches_oracle(sem, name):
     assert np.all(err <= 1e-4), err
     pert = group_rel_l2(got, q_ref[:, perm])
     assert np.all(pert <= 1e-3), pert
+    inc = increment_err(got, q_o[:, perm], q_ref[:, perm])
+    assert np.all(inc <= 1e-4), inc
     np.testing.assert_allclose(host(q32), got, rtol=2.4e-7, atol=1e-30)
     assert sem.sem_status(m) == 0
 
@@ -486,7 +500,7 @@ def test_autotune_then_step_parity(sem):
     assert np.all(err <= 1e-4), err
 
 
-@pytest.mark.parametrize("name", ["twolevel-N4", "twolevel-17-layers-N4", "stretched-twolevel-N4"])
+@pytest.mark.parametrize("name", ["twolevel-N4", "twolevel-17-layers-N4", "stretched-twolevel-N4", "twolevel-N5"])
 def test_every_variant_step_matches_oracle(sem, name):
     """The increment-form step through each element-kernel variant (z-pencil
     and line exchange, every layers-per-CTA count): two steps within 1e-4 of
@@ -518,6 +532,8 @@ def test_every_variant_step_matches_oracle(sem, name):
         got = host(q)
         err = group_rel_l2(full_fields(got, z), full_fields(q_ref[:, perm], z))
         assert np.all(err <= 1e-4), (row, rows[row], err)
+        inc = increment_err(got, q_o[:, perm], q_ref[:, perm])
+        assert np.all(inc <= 1e-4), (row, rows[row], inc)
         np.testing.assert_allclose(host(q32), got, rtol=2.4e-7, atol=1e-30)
         if rows[row][3] == 1:
             lines.append(got)
@@ -581,6 +597,57 @@ def test_batched_steps_equal_single_mesh_steps(sem, use_graph, with_big):
         assert d <= 1e-13 * scale, (k, d)
         assert torch.equal(a32[k], b32[k]) or (a32[k] - b32[k]).abs().max().item() <= 1e-6
     assert sem.sem_batch_status(batch) == 0
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+@pytest.mark.parametrize("with_big", [False, True])
+def test_batched_steps_match_oracle(sem, use_graph, with_big):
+    """The batched step against the oracle: meshes of orders 3, 4, 5 and 6,
+    each refined by one level inside 120 km (2:1 faces), plus an unrefined
+    order-4 mesh, run together by sem_batch_step_mixed (the persistent
+    column-queue element kernel and the concatenated increment kernel, with
+    or without graph replay); with with_big, two meshes large enough for their
+    own launches join them.  After two steps every instance's state is within
+    1e-4 (relative L2 per field group) of two float64 oracle steps on its own
+    mesh, in the full fields and in the change of the state."""
+    specs = [(4, 2, 3, 300e3, 1), (4, 2, 4, 300e3, 1), (3, 2, 5, 300e3, 1),
+             (3, 2, 6, 300e3, 1), (5, 3, 4, 300e3, 0)]
+    dts = [0.5, 0.5, 0.4, 0.25, 0.5]
+    if with_big:
+        specs += [(18, 1, 2, 300e3, 0), (20, 2, 3, 300e3, 0)]
+        dts += [0.5, 0.5]
+    meshes = [_instance_mesh(sem, nx, nz, N, L, lev, 120e3) for nx, nz, N, L, lev in specs]
+    p = sem.sem_params_default(precision=sem.SEM_PREC_MIXED)
+    oracles, perms, init = [], [], []
+    for k, (m, (nx, nz, N, L, lev)) in enumerate(zip(meshes, specs)):
+        o = om.OracleMesh(L, L, 24e3, nx, nx, nz, N, leaves=[tuple(x) for x in sem.sem_mesh_leaves_host(m)])
+        perm = node_perm(sem.sem_mesh_coords_host(m), o.XG)
+        q_o = random_state(o.XG, 24e3, 40 + k)
+        oracles.append((o, q_o))
+        perms.append(perm)
+        init.append(dev(q_o[:, perm]))
+    if with_big:
+        assert min(m.Ncol for m in meshes[-2:]) >= 2 * torch.cuda.get_device_properties(0).multi_processor_count
+    assert sum(1 for m, s in zip(meshes, specs) if s[4] and m.Ncol > s[0] ** 2) == 4
+    qs = [q.clone() for q in init]
+    q32 = [torch.empty(q.shape, dtype=torch.float32, device="cuda") for q in qs]
+    work = [torch.empty((10, q.shape[1]), dtype=torch.float32, device="cuda") for q in qs]
+    for m, q, a in zip(meshes, qs, q32):
+        sem.sem_mirror(m, q, a)
+    batch = sem.sem_batch_create(meshes)
+    for _ in range(2):
+        sem.sem_batch_step_mixed(batch, p, qs, q32, work, dts, use_graph=use_graph)
+    assert sem.sem_batch_status(batch) == 0
+    for k, ((o, q_o), perm, m) in enumerate(zip(oracles, perms, meshes)):
+        q_ref = q_o
+        for _ in range(2):
+            q_ref = ork.rk_step(o, PRM, q_ref, dts[k])
+        got = host(qs[k])
+        z = o.XG[perm, 2]
+        err = group_rel_l2(full_fields(got, z), full_fields(q_ref[:, perm], z))
+        assert np.all(err <= 1e-4), (k, specs[k], err)
+        inc = increment_err(got, q_o[:, perm], q_ref[:, perm])
+        assert np.all(inc <= 1e-4), (k, specs[k], inc)
 
 
 def test_mixed_pressure_both_branches(sem):

@@ -7,8 +7,10 @@ The added terms are checked on their own (tendency with them minus tendency
 without, on both sides) as well as in the total, so that a small term cannot
 hide under the tolerance of the inviscid part.  Float64: total 1e-12, added
 terms 1e-9 (the difference of two float64 tendencies).  Mixed: total 1e-4,
-added terms 1e-4 times the ratio of the total to the added norm (float32
-rounding of the total carries into the difference).
+added terms ADDED_TOL of their own norm (the float32 rounding of the total
+carries into the difference of the two mixed tendencies, so the bound on the
+added terms is looser than on the total, but it is relative to the terms
+themselves: a wrong term fails it whatever the size of the total).
 """
 import numpy as np
 import pytest
@@ -22,6 +24,7 @@ from tests.helpers import group_rel_l2, node_perm  # noqa: E402
 from tests.test_gpu_parity import MESHES, dev, full_fields, host, make_pair, two_level_leaves  # noqa: E402
 
 PHYS = dict(smag_cs=0.21, sponge_gamma=0.02, sponge_depth=6000.0)
+ADDED_TOL = 1e-3
 
 
 @pytest.fixture(scope="module")
@@ -73,7 +76,7 @@ def test_physics_rhs_mixed_matches_oracle(sem, name, eqset):
     assert np.all(group_rel_l2(T, T_o[:, perm]) <= 1e-4)
     ratio = group_rel_l2(T_o, 0 * T_o) / np.maximum(group_rel_l2(dT_o, 0 * dT_o), 1e-300)
     err = group_rel_l2(dT, dT_o[:, perm])
-    assert np.all(err <= 1e-4 * np.maximum(ratio, 1.0)), (err, ratio)
+    assert np.all(err <= ADDED_TOL), (err, ratio)
 
 
 def _spec(name):
@@ -107,7 +110,7 @@ def test_physics_rhs_every_variant_matches_oracle(sem, name):
         dT = T - _gpu_rhs(sem, m, q, "C", 1)
         assert np.all(group_rel_l2(T, T_o[:, perm]) <= 1e-4), rows[row]
         err = group_rel_l2(dT, dT_o[:, perm])
-        assert np.all(err <= 1e-4 * np.maximum(ratio, 1.0)), (rows[row], err, ratio)
+        assert np.all(err <= ADDED_TOL), (rows[row], err, ratio)
         kinds.add(rows[row][3])
     assert kinds == {0, 1}
     # the absorbing layer alone (no physics pass at all on a line variant)
@@ -116,7 +119,8 @@ def test_physics_rhs_every_variant_matches_oracle(sem, name):
     sem.sem_autotune_select(m, -1)
     dS = _gpu_rhs(sem, m, q, "C", 1, **sp) - _gpu_rhs(sem, m, q, "C", 1)
     ratio = group_rel_l2(T_o, 0 * T_o) / np.maximum(group_rel_l2(dS_o, 0 * dS_o), 1e-300)
-    assert np.all(group_rel_l2(dS, dS_o[:, perm]) <= 1e-4 * np.maximum(ratio, 1.0))
+    err = group_rel_l2(dS, dS_o[:, perm])
+    assert np.all(err <= ADDED_TOL), (err, ratio)
     assert sem.sem_status(m) == 0
 
 
@@ -181,7 +185,7 @@ HEAT = dict(heat_q0=0.005, heat_r0=27.5e3, heat_width=10e3, heat_rmax=60e3, heat
 def test_heating_rhs_matches_oracle(sem, name, eqset):
     """Heating source at t = 3 s: float64 total 1e-12 and the source alone
     1e-10 (only the theta equation moves); mixed total 1e-4 and the source
-    alone 1e-4 times the ratio of the total to the source."""
+    alone ADDED_TOL of its own norm."""
     m, o, X, perm = make_pair(sem, **MESHES[name])
     q_o = random_state(o.XG, o.Lz, 23, eqset)
     prm = refstate.Params(time=3.0, **HEAT)
@@ -198,7 +202,7 @@ def test_heating_rhs_matches_oracle(sem, name, eqset):
     dTm = Tm - _gpu_rhs(sem, m, q, eqset, 1)
     assert np.all(group_rel_l2(Tm, T_o[:, perm]) <= 1e-4)
     ratio = max(np.linalg.norm(T_o[4]) / np.linalg.norm(dT_o[4]), 1.0)
-    assert np.linalg.norm(dTm[4] - dT_o[4, perm]) <= 1e-4 * ratio * np.linalg.norm(dT_o[4])
+    assert np.linalg.norm(dTm[4] - dT_o[4, perm]) <= ADDED_TOL * np.linalg.norm(dT_o[4]), ratio
 
 
 @pytest.mark.parametrize("prec", [0, 1])
