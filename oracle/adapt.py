@@ -94,19 +94,22 @@ def criterion_pv(mesh, qG, prm, eqset="C"):
 CRITERIA = {"speed": criterion_speed, "vorticity": criterion_vorticity, "pv": criterion_pv}
 
 
-def criterion_flags(mesh, qG, prm, thresholds, lvl_max, eqset="C", variables=None):
+def criterion_flags(mesh, qG, prm, thresholds, lvl_max, eqset="C", variables=None, levels=None):
     """adapt(e) in {-1, 0, 1} for every element; also returns max_k C_{k,e}
     of the variable of the element's refinement test (threshold(lvl+1), or
     threshold(lvl) at lvl_max).  variables[l] names the variable compared
-    with threshold(l+1) (default: speed at every level)."""
+    with threshold(l+1) (default: speed at every level).  levels (one per
+    element, default the mesh's own) are the levels lvl the rule is applied
+    with; the variables are always evaluated on the mesh itself."""
     thr = np.asarray(thresholds, dtype=np.float64)
     if variables is None:
         variables = ["speed"] * len(thr)
+    lvls = mesh.level if levels is None else np.asarray(levels)
     cm = {name: CRITERIA[name](mesh, qG, prm, eqset).max(axis=1) for name in set(variables)}
     flags = np.zeros(mesh.Ne, dtype=np.int8)
     cmax = np.zeros(mesh.Ne)
     for e in range(mesh.Ne):
-        lv = int(mesh.level[e])
+        lv = int(lvls[e])
         refine = lv < lvl_max and cm[variables[lv]][e] > thr[lv]
         coarsen = lv > 0 and cm[variables[lv - 1]][e] <= thr[lv - 1]
         flags[e] = 1 if refine else (-1 if coarsen else 0)

@@ -819,7 +819,7 @@ int sem_status(sem_mesh* mh, int* status, cudaStream_t st) {
   SEM_CUDA_TRY(cudaMemcpyAsync(&v, mh->m.dev->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   SEM_CUDA_TRY(cudaMemsetAsync(mh->m.dev->status, 0, sizeof(int), st));
   SEM_CUDA_TRY(cudaStreamSynchronize(st));
-  *status = v ? SEM_ERR_NUMERIC : SEM_OK;
+  *status = (v & 4) ? SEM_ERR_TIMEOUT : (v ? SEM_ERR_NUMERIC : SEM_OK);
   return SEM_OK;
 }
 

@@ -111,6 +111,7 @@ struct VolArgs {
   const float4* ref4;   // [NZ] packed p0, rho0, (rho theta)0, 1/(rho theta)0 (float32)
   const float* spg32;   // [NZ] absorbing-layer rate R(z): the line-exchange kernel adds
                         // -R q' (weak form, collocated) when set; null: not added here
+  int* status;          // device status word (bit 4: a bounded device wait ran out)
   float smag[kLev][3];  // per level (C_s Delta)^2, 2/hx, 2/hy: the horizontal
                         // Smagorinsky stress, for the kernels that add it
 };
@@ -1102,6 +1103,276 @@ volume_lines_smag(const VolArgs A) {
   lines_body<N, KL, true>(A, blockIdx.x, smem, threadIdx.x);
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core variant of the line-exchange element kernel (kind 2, order 4).
+//
+// The x and y contractions of a layer chunk run on the fifth-generation
+// tensor cores instead of the line owners' FMAs: with the rows of an MMA
+// operand the (line, field, layer) triples of one direction and its K the
+// N+1 = 5 nodes of a line (padded to 8), the contraction with the weak
+// derivative matrix is D[row][n] = sum_k A[row][k] B[n][k], B[n][k] =
+// w_k D_kn (padded to 16 x 8).  One chunk of KL = 4 layers has 500 rows per
+// direction: 4 tiles of M = 128, 8 MMAs (tcgen05.mma kind::tf32, N = 16,
+// K = 8) per product.  float32 accuracy needs three products per tile
+// (A_hi B_hi + A_lo B_hi + A_hi B_lo with hi = the value rounded to tf32 and
+// lo = the rest, "3xTF32"), so 24 MMAs per chunk, issued by one thread, with
+// the accumulators in tensor memory (128 columns per CTA).  The z-line
+// owners write the flux components as hi and lo parts into the K-major
+// operand layout (core matrices of 8 rows x 16 bytes, no swizzle); after the
+// MMAs each warp reads its 32 lanes of every tile (tcgen05.ld) and scatters
+// the 5 outputs of its rows onto the nodes' positions of the line-exchange
+// layout (reusing the operand buffers), from where the z-line owners add
+// them up as in lines_body.  Everything else (pointwise terms, z contraction
+// on registers, absorbing layer, vertical direct stiffness summation,
+// residual stores) is lines_body's.  Waits on the MMA completion barrier are
+// bounded; a wait that runs out sets bit 4 of the status word.
+namespace tcg {
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// shared-memory matrix descriptor: start address, leading (K) and stride
+// (M/N) byte offsets between core matrices, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// instruction descriptor of kind::tf32: f32 accumulator, tf32 A and B, both
+// K-major, N >> 3 and M >> 4
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+// byte offset of element (row r, k) in a K-major tf32 operand of 8 K columns
+__device__ __forceinline__ int aoff(int r, int k) {
+  return (r & 7) * 16 + (k & 3) * 4 + (k >> 2) * 128 + (r >> 3) * 256;
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t id, int acc) {
+  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+               "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+               :: "r"(d), "l"(a), "l"(b), "r"(id), "r"(acc) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 24); ++it) {
+    uint32_t ok;
+    asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
+                 "selp.u32 %0, 1, 0, q;\n}" : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
+}
+}  // namespace tcg
+
+constexpr int kTcKL = 4, kTcThreads = 128, kTcRows = 512, kTcCols = 128;
+constexpr int kTcOpBytes = kTcRows * 32;   // one operand (512 rows x 8 tf32)
+__host__ __device__ constexpr size_t tc_smem_bytes() {
+  // A: x hi, x lo, y hi, y lo; B: hi, lo; sT, sP; barrier and TMEM address
+  return 4 * kTcOpBytes + 2 * 512 + sizeof(float) * (kFields * kTcKL * 25 + 2 * kFields * 25) + 16;
+}
+
+template <int MB>
+__global__ void __launch_bounds__(kTcThreads, MB) volume_lines_tc(const VolArgs A) {
+  constexpr int N = 4, n1 = 5, Nq = 25, KL = kTcKL;
+  constexpr int LW = lines_lw<N>(), LS = lines_ls<N, KL>();
+  static_assert(KL * LS * 4 <= 2 * kTcOpBytes, "staging must fit two operand buffers");
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  unsigned char* opA = tsm;                                   // [4][kTcOpBytes]
+  unsigned char* opB = tsm + 4 * kTcOpBytes;                  // [2][512]
+  float* sT = reinterpret_cast<float*>(opB + 1024);           // [f][kk][ab]
+  float* sP = sT + kFields * KL * Nq;                         // [2][f][ab]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sP + 2 * kFields * Nq);
+  uint32_t* taddr_s = reinterpret_cast<uint32_t*>(mbar + 1);
+  float* stX = reinterpret_cast<float*>(opA);                 // staging after the MMAs
+  float* stY = reinterpret_cast<float*>(opA + 2 * kTcOpBytes);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int col = blockIdx.x;
+  // zero the operands (their K padding stays zero), write B = w_k D_kn
+  for (int q = t; q < kTcOpBytes; q += kTcThreads) reinterpret_cast<uint32_t*>(opA)[q] = 0u;
+  for (int q = t; q < 256; q += kTcThreads) reinterpret_cast<uint32_t*>(opB)[q] = 0u;
+  __syncthreads();
+  {
+    const int nn = t >> 3, k = t & 7;   // 128 threads: rows n = 0..15, k = 0..7
+    const float v = (nn < n1 && k < n1) ? c_Dwf[N][nn * n1 + k] : 0.f;
+    const float hi = tcg::tf32_rna(v);
+    *reinterpret_cast<float*>(opB + tcg::aoff(nn, k)) = hi;
+    *reinterpret_cast<float*>(opB + 512 + tcg::aoff(nn, k)) = v - hi;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(tcg::smem_u32(taddr_s)), "r"(kTcCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (t == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(tcg::smem_u32(mbar)));
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t taddr = *taddr_s;
+  const uint32_t bar = tcg::smem_u32(mbar);
+
+  const bool part = t < KL * Nq;
+  const int kk = t % KL, ab = part ? t / KL : 0;
+  const int i = ab % n1, j = ab / n1;
+  const int lev = A.col_level[col];
+  const float* geo = A.geof[lev];
+  const float sx = geo[4], sy = geo[5], sz = geo[6], J = geo[3];
+  const int hm = part ? A.hmap[(long long)col * Nq + ab] : 0;
+  const float wi = c_wf[N][i], wj = c_wf[N][j];
+  float* rc = (float*)A.rc;
+  const int nchunk = (A.nz + KL - 1) / KL;
+  bool ok = true;
+  for (int ch = 0; ch < nchunk && ok; ++ch) {
+    const int k = ch * KL + kk;
+    const bool act = part && k < A.nz;
+    const int kz0 = k * N;
+    const float hk = act ? __ldg(A.hzk32 + k) : 0.f;
+    float rz[kFields][n1];
+#pragma unroll
+    for (int f = 0; f < kFields; ++f)
+#pragma unroll
+      for (int c = 0; c < n1; ++c) rz[f][c] = 0.f;
+    if (act) {
+#pragma unroll
+      for (int c = 0; c < n1; ++c) {
+        float v[kFields];
+        const int kz = kz0 + c;
+        load_node<N>(A, hm, kz, v);
+        const float wc = c_wf[N][c];
+        NodeTerms T;
+        node_terms(A, v, kz, wj * wc * sx * hk, wi * wc * sy * hk, wi * wj * sz, wi * wj * wc * J * hk, T);
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) {
+          const int rx = kk + 4 * (f + 5 * (c + 5 * j)), ry = kk + 4 * (f + 5 * (c + 5 * i));
+          const float xh = tcg::tf32_rna(T.fx[f]), yh = tcg::tf32_rna(T.fy[f]);
+          *reinterpret_cast<float*>(opA + tcg::aoff(rx, i)) = xh;
+          *reinterpret_cast<float*>(opA + kTcOpBytes + tcg::aoff(rx, i)) = T.fx[f] - xh;
+          *reinterpret_cast<float*>(opA + 2 * kTcOpBytes + tcg::aoff(ry, j)) = yh;
+          *reinterpret_cast<float*>(opA + 3 * kTcOpBytes + tcg::aoff(ry, j)) = T.fy[f] - yh;
+        }
+#pragma unroll
+        for (int f = 0; f < kFields; ++f)
+#pragma unroll
+          for (int c2 = 0; c2 < n1; ++c2) rz[f][c2] = fmaf(c_Dwf[N][c2 * n1 + c], T.fz[f], rz[f][c2]);
+        rz[1][c] += T.su;
+        rz[2][c] += T.sv;
+        rz[3][c] += T.sw;
+        if (A.spg32) {
+          const float wR = (wi * wj * wc * J * hk) * __ldg(A.spg32 + kz);
+#pragma unroll
+          for (int f = 0; f < kFields; ++f) rz[f][c] = fmaf(-wR, v[f], rz[f][c]);
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) sT[(f * KL + kk) * Nq + ab] = rz[f][N];
+    }
+    // the operands are complete: make them visible to the tensor cores
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (t == 0) {
+      constexpr uint32_t id = tcg::idesc_tf32(128, 16);
+      const uint32_t a0 = tcg::smem_u32(opA), b0 = tcg::smem_u32(opB);
+      const uint64_t bh = tcg::sdesc(b0, 128, 256), bl = tcg::sdesc(b0 + 512, 128, 256);
+#pragma unroll
+      for (int d = 0; d < 2; ++d)
+#pragma unroll
+        for (int tl = 0; tl < 4; ++tl) {
+          const uint32_t dcol = taddr + (uint32_t)((d * 4 + tl) * 16);
+          const uint32_t ah = a0 + (uint32_t)(2 * d * kTcOpBytes + tl * 4096);
+          const uint64_t dah = tcg::sdesc(ah, 128, 256), dal = tcg::sdesc(ah + kTcOpBytes, 128, 256);
+          tcg::mma_tf32(dcol, dah, bh, id, 0);
+          tcg::mma_tf32(dcol, dal, bh, id, 1);
+          tcg::mma_tf32(dcol, dah, bl, id, 1);
+        }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   :: "r"(bar) : "memory");
+    }
+    ok = tcg::mbar_wait(bar, (uint32_t)(ch & 1));
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      // each warp: its 32 lanes (rows) of the 8 tiles; scatter the 5 outputs
+#pragma unroll
+      for (int d = 0; d < 2; ++d)
+#pragma unroll
+        for (int tl = 0; tl < 4; ++tl) {
+          float o[8];
+          tcg::ld8(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)((d * 4 + tl) * 16), o);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          const int r = tl * 128 + 32 * warp + lane;
+          if (r < 500) {
+            const int rk = r % 4, rf = (r / 4) % 5, rcn = (r / 20) % 5, rl = r / 100;
+            float* st = (d == 0 ? stX : stY) + rk * LS + rf * n1 + rcn;
+#pragma unroll
+            for (int nn = 0; nn < n1; ++nn) st[(d == 0 ? nn + n1 * rl : rl + n1 * nn) * LW] = o[nn];
+          }
+        }
+    } else if (lane == 0) {
+      atomicOr(A.status, 4);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (!ok) break;
+    if (act) {
+      const float* zX = stX + kk * LS + ab * LW;
+      const float* zY = stY + kk * LS + ab * LW;
+#pragma unroll
+      for (int f = 0; f < kFields; ++f)
+#pragma unroll
+        for (int c = 0; c < n1; ++c) rz[f][c] += zX[f * n1 + c] + zY[f * n1 + c];
+      if (kk > 0) {
+        const float* pX = stX + (kk - 1) * LS + ab * LW;
+        const float* pY = stY + (kk - 1) * LS + ab * LW;
+#pragma unroll
+        for (int f = 0; f < kFields; ++f)
+          rz[f][0] += sT[(f * KL + kk - 1) * Nq + ab] + pX[f * n1 + N] + pY[f * n1 + N];
+      } else if (ch > 0) {
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) rz[f][0] += sP[((ch - 1) & 1) * kFields * Nq + f * Nq + ab];
+      }
+      if (kk == KL - 1) {
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) sP[(ch & 1) * kFields * Nq + f * Nq + ab] = rz[f][N];
+      }
+      float* dst = rc + ((long long)((long long)col * Nq + ab) * kFields) * A.NZr + kz0;
+      const bool top = (k == A.nz - 1);
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) {
+        float* df = dst + (long long)f * A.NZr;
+        *reinterpret_cast<float4*>(df) = make_float4(rz[f][0], rz[f][1], rz[f][2], rz[f][3]);
+        if (top) df[N] = rz[f][N];
+      }
+    }
+    // the staging (operand) buffers are read: the next chunk may write them
+    __syncthreads();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(kTcCols));
+}
+
+template <int MB>
+static int launch_lines_tc(const VolArgs& A, cudaStream_t st) {
+  const size_t sm = tc_smem_bytes();
+  static DeviceOnce attr;
+  int rc = device_once(attr, [&] {
+    SEM_CUDA_TRY(cudaFuncSetAttribute(volume_lines_tc<MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    return SEM_OK;
+  });
+  if (rc) return rc;
+  ProfScope ps("volume_mixed", st);
+  volume_lines_tc<MB><<<A.Ncol, kTcThreads, sm, st>>>(A);
+  return SEM_OK;
+}
+
 template <int N, int KL, int MB>
 static int launch_lines_smag(const VolArgs& A, cudaStream_t st) {
   const size_t sm = sizeof(float) * lines_smem_floats<N, KL>();
@@ -1136,7 +1407,8 @@ static int launch_lines(const VolArgs& A, cudaStream_t st) {
 struct PencilVariant {
   int N, KL, MB;
   int (*launch)(const VolArgs&, cudaStream_t);
-  int kind;         // 0: z-pencil volume_pencil_mixed; 1: line-exchange volume_lines_mixed
+  int kind;         // 0: z-pencil volume_pencil_mixed; 1: line-exchange volume_lines_mixed;
+                    // 2: line exchange with the x, y contractions on tensor cores (volume_lines_tc)
   int (*launch_smag)(const VolArgs&, cudaStream_t);   // with the stress added; null: none
 };
 static const PencilVariant kPencil[] = {
@@ -1149,6 +1421,7 @@ static const PencilVariant kPencil[] = {
     {4, 8, 4, launch_lines<4, 8, 4>, 1, launch_lines_smag<4, 8, 4>},
     {4, 8, 2, launch_lines<4, 8, 2>, 1, launch_lines_smag<4, 8, 2>},
     {4, 4, 8, launch_lines<4, 4, 8>, 1, launch_lines_smag<4, 4, 8>},
+    {4, kTcKL, 3, launch_lines_tc<3>, 2},
     {5, 8, 2, launch_pencil<5, 8, 2>},      {5, 8, 2, launch_lines<5, 8, 2>, 1},
     {5, 4, 4, launch_lines<5, 4, 4>, 1},
     {6, 4, 2, launch_pencil<6, 4, 2>},      {6, 8, 1, launch_lines<6, 8, 1>, 1},
@@ -1223,6 +1496,7 @@ static VolArgs make_vol_args(Mesh& m, const sem_params& p, const void* q, bool m
   A.hzk32 = D.hzk32;
   A.ref4 = reinterpret_cast<const float4*>(D.ref32 + (size_t)m.NZ * kRef);
   A.spg32 = nullptr;
+  A.status = D.status;
   A.Ncol = (int)m.Ncol();
   A.nz = m.nz;
   A.NZ = m.NZ;

@@ -42,9 +42,9 @@ def level_flags(sem, torch, mesh, p_crit, q, lvl_max):
     return out
 
 
-def trajectory(sem, torch, mesh, p_step, p_crit, q0, dt, steps, every, scales):
-    """[(features, per-level criterion flags)] every `every` steps of a
-    mixed-form run from q0."""
+def trajectory(sem, torch, mesh, p_step, p_crits, q0, dt, steps, every, scales):
+    """Every `every` steps of a mixed-form run from q0: (features, [per-level
+    criterion flags for each parameter set in p_crits])."""
     q = q0.clone()
     q32 = torch.empty(q.shape, dtype=torch.float32, device=q.device)
     work = torch.empty((10, mesh.NG), dtype=torch.float32, device=q.device)
@@ -52,28 +52,39 @@ def trajectory(sem, torch, mesh, p_step, p_crit, q0, dt, steps, every, scales):
     out = []
     for s in range(steps + 1):
         if s % every == 0:
-            fl = level_flags(sem, torch, mesh, p_crit, q, p_crit.lvl_max)
+            fls = [level_flags(sem, torch, mesh, pc, q, pc.lvl_max) for pc in p_crits]
             F = torch.empty((mesh.Ne, 136), dtype=torch.float32, device=q.device)
             sem.sem_mlp_features(mesh, q, scales, F)
-            out.append((F, fl))
+            out.append((F, fls))
         if s < steps:
             sem.sem_step_mixed(mesh, p_step, q, q32, work, dt)
     return out
 
 
+def window_label(torch, snaps, i, k, L, which=0):
+    """Label for level L at snapshot i: what the criterion asks of an element
+    at level L over the next k checks (i+1 .. i+k): refine (2) if it asks for
+    refinement at any of them, coarsen (0) if it asks for coarsening at all
+    of them, keep (1) otherwise.  A schedule that remeshes every k checks
+    needs exactly this to miss no refinement before its next remesh."""
+    fl = torch.stack([snaps[i + j][1][which][L] for j in range(1, k + 1)])
+    up = (fl > 0).any(dim=0)
+    down = (fl < 0).all(dim=0)
+    return torch.where(up, 2, torch.where(down, 0, 1)).to(torch.int8)
+
+
 def training_rows(torch, snaps, ahead, every, lvl_max):
-    """Features at t with the level set to L, labelled by the criterion's
-    flag for level L at t + ahead (classes 0, 1, 2 = coarsen, keep, refine)."""
+    """Features at t with the level set to L, labelled by window_label over
+    the `ahead` steps after t (classes 0, 1, 2 = coarsen, keep, refine)."""
     k = ahead // every
     Fs, Ys = [], []
     for i in range(len(snaps) - k):
         F = snaps[i][0]
-        later = snaps[i + k][1]
         for L in range(lvl_max + 1):
             G = F.clone()
             G[:, 135] = float(L)
             Fs.append(G)
-            Ys.append((later[L] + 1).to(torch.int8))
+            Ys.append(window_label(torch, snaps, i, k, L))
     return torch.cat(Fs), torch.cat(Ys)
 
 
@@ -96,8 +107,11 @@ def train(sem, torch, F, Y, iters=1500, batch=65536, seed=1, lr=1e-3):
     return net, first, last
 
 
-def schedule(sem, torch, snaps, ahead, every, lvl_max, net=None):
-    """Missed-refinement rate, mean refined levels and remesh count."""
+def schedule(sem, torch, snaps, ahead, every, lvl_max, net=None, which=0):
+    """Missed-refinement rate, mean refined levels and remesh count of the
+    schedule that remeshes every `ahead` steps by the criterion's flags of
+    parameter set `which` (and the network's, if given); missed refinements
+    are counted against the flags of parameter set 0 (the paper's criterion)."""
     Ne = snaps[0][0].shape[0]
     dev = snaps[0][0].device
     L = torch.zeros(Ne, dtype=torch.int8, device=dev)
@@ -105,9 +119,11 @@ def schedule(sem, torch, snaps, ahead, every, lvl_max, net=None):
     missed = want = 0
     refined = 0.0
     remesh = 0
-    for i, (F, fl_lv) in enumerate(snaps):
+    for i, (F, fls) in enumerate(snaps):
+        fl_lv = fls[0]
         # the criterion's flag at each element's own (tracked) level
-        now = fl_lv.gather(0, L.long()[None]).squeeze(0)
+        now = fls[which].gather(0, L.long()[None]).squeeze(0)
+        judge = fl_lv.gather(0, L.long()[None]).squeeze(0)
         if i % k == 0:
             remesh += 1
             if net is None:
@@ -120,38 +136,57 @@ def schedule(sem, torch, snaps, ahead, every, lvl_max, net=None):
                 fl = sem.sem_merge_flags(now, pred, L, lvl_max)
             L = (L + fl).clamp_(0, lvl_max)
         else:
-            missed += int((now > 0).sum())
+            missed += int((judge > 0).sum())
             want += int((fl_lv[0] > 0).sum())
         refined += float(L.float().mean())
     return {"missed_rate": missed / max(want, 1), "mean_level": refined / len(snaps),
             "remeshes": remesh}
 
 
-def gain_experiment(sem, torch, mesh, states, dt, n_train, steps=400, every=10, ahead=50,
-                    thresholds=(15.0, 25.0), scales=(1e-3, 10.0, 10.0, 1.0, 1.0), iters=1500, seed=1):
-    """Train on the first n_train initial states' trajectories, compare the
-    two schedules on the others.  Returns a dict of the measured numbers."""
+def gain_experiment(sem, torch, mesh, states, dt, n_train, steps=400, every=10,
+                    intervals=(50, 75, 100), thresholds=(15.0, 25.0),
+                    control_scales=(0.95, 0.9, 0.85, 0.8, 0.75, 0.7, 0.65, 0.6),
+                    scales=(1e-3, 10.0, 10.0, 1.0, 1.0), iters=1500, seed=1):
+    """Train one network per remesh interval K on the first n_train initial
+    states' trajectories (labels: window_label over the K steps ahead) and
+    compare, on the other trajectories and for every K, the criterion alone
+    with the criterion plus the network (missed-refinement rate against the
+    paper's criterion, mean level, remesh count).  Control at each K: the
+    criterion alone with every threshold scaled by the largest factor of
+    control_scales at which it refines at least as much as the learned
+    schedule (so that the comparison is at equal refined-element count)."""
     lvl_max = len(thresholds)
     p_step = sem.sem_params_default(precision=sem.SEM_PREC_MIXED)
-    p_crit = sem.sem_params_default(thresholds=list(thresholds), lvl_max=lvl_max)
+    p_crits = [sem.sem_params_default(thresholds=[f * t for t in thresholds], lvl_max=lvl_max)
+               for f in (1.0,) + tuple(control_scales)]
     sc = np.asarray(scales, dtype=np.float32)
-    trajs = [trajectory(sem, torch, mesh, p_step, p_crit, q0, dt, steps, every, sc) for q0 in states]
+    trajs = [trajectory(sem, torch, mesh, p_step, p_crits, q0, dt, steps, every, sc) for q0 in states]
     status = sem.sem_status(mesh)
-    parts = [training_rows(torch, t, ahead, every, lvl_max) for t in trajs[:n_train]]
-    F = torch.cat([a for a, _ in parts])
-    Y = torch.cat([b for _, b in parts])
-    net, loss0, loss1 = train(sem, torch, F, Y, iters=iters, seed=seed)
-    res = {"status": status, "rows": int(F.shape[0]), "loss_first": loss0, "loss_last": loss1,
-           "criterion": [], "learned": []}
-    for t in trajs[n_train:]:
-        res["criterion"].append(schedule(sem, torch, t, ahead, every, lvl_max))
-        res["learned"].append(schedule(sem, torch, t, ahead, every, lvl_max, net))
-    res["missed_criterion"] = float(np.mean([r["missed_rate"] for r in res["criterion"]]))
-    res["missed_learned"] = float(np.mean([r["missed_rate"] for r in res["learned"]]))
-    res["level_criterion"] = float(np.mean([r["mean_level"] for r in res["criterion"]]))
-    res["level_learned"] = float(np.mean([r["mean_level"] for r in res["learned"]]))
-    res["remeshes"] = res["criterion"][0]["remeshes"]
-    res["net"] = net
+    res = {"status": status, "intervals": list(intervals), "by_interval": []}
+    held = trajs[n_train:]
+    mean = lambda rs, key: float(np.mean([r[key] for r in rs]))
+    for K in intervals:
+        parts = [training_rows(torch, t, K, every, lvl_max) for t in trajs[:n_train]]
+        F = torch.cat([a for a, _ in parts])
+        Y = torch.cat([b for _, b in parts])
+        net, loss0, loss1 = train(sem, torch, F, Y, iters=iters, seed=seed)
+        cri = [schedule(sem, torch, t, K, every, lvl_max) for t in held]
+        lrn = [schedule(sem, torch, t, K, every, lvl_max, net) for t in held]
+        row = {"interval": K, "rows": int(F.shape[0]), "loss_first": loss0, "loss_last": loss1,
+               "remeshes": cri[0]["remeshes"],
+               "missed_criterion": mean(cri, "missed_rate"), "missed_learned": mean(lrn, "missed_rate"),
+               "level_criterion": mean(cri, "mean_level"), "level_learned": mean(lrn, "mean_level")}
+        # control: lowered thresholds, criterion alone, at least the learned refinement
+        row["control"] = None
+        for w, f in enumerate(control_scales, start=1):
+            ctl = [schedule(sem, torch, t, K, every, lvl_max, which=w) for t in held]
+            if mean(ctl, "mean_level") >= row["level_learned"]:
+                row["control"] = {"threshold_scale": f, "missed": mean(ctl, "missed_rate"),
+                                  "level": mean(ctl, "mean_level")}
+                break
+        res["by_interval"].append(row)
+        if K == intervals[0]:
+            res["net"] = net
     return res
 
 

@@ -186,3 +186,23 @@ def test_wind_diagnostics_on_analytic_fields():
     q2 = q.copy()
     q2[1, s] = 100.0 * ref["rho0"][s]
     assert diag.wind_diagnostics(m, q2, PRM)["max_wind"] == pytest.approx(2.0)
+
+
+def test_criterion_at_given_levels_equals_the_rule_at_those_levels():
+    """criterion_flags with levels=L gives, element by element, what the rule
+    gives on a mesh whose elements are at L: checked against a mesh whose
+    elements all have level 0 (levels=0 must equal the default there) and
+    against the three-level hand example's flags shifted by hand."""
+    from synth.vortex import vortex_state
+    m = mesh.OracleMesh(600e3, 600e3, 24e3, 4, 4, 2, 4)
+    q = vortex_state(m.XG, 24e3)
+    thr = [5.0, 10.0, 15.0]
+    f0, c0 = adapt.criterion_flags(m, q, PRM, thr, 3)
+    g0, d0 = adapt.criterion_flags(m, q, PRM, thr, 3, levels=np.zeros(m.Ne, dtype=int))
+    assert np.array_equal(f0, g0) and np.array_equal(c0, d0)
+    speed = adapt.CRITERIA["speed"](m, q, PRM, "C").max(axis=1)
+    for L in range(4):
+        fl, _ = adapt.criterion_flags(m, q, PRM, thr, 3, levels=np.full(m.Ne, L))
+        T = (speed[:, None] > np.array(thr)[None]).sum(axis=1)     # thresholds exceeded
+        want = np.where(T > L, 1, np.where(T < L, -1, 0))
+        assert np.array_equal(fl, want), L
