@@ -216,7 +216,7 @@ def batched_measure(sem, torch, steps=10, warmup=3, refine=True):
     if not refine:
         import dataclasses
         insts = [dataclasses.replace(it, levels=0) for it in insts]
-    meshes, qs, q32, work, dts, dof = [], [], [], [], [], 0
+    meshes, qs, q32, work, dts, dof, init = [], [], [], [], [], 0, []
     p = sem.sem_params_default(precision=sem.SEM_PREC_MIXED)
     for k, it in enumerate(insts):
         m = sem.sem_mesh_create(it.L, it.L, it.Lz, it.nx, it.nx, it.nz, it.N, lvl_max=max(it.levels, 1))
@@ -226,6 +226,7 @@ def batched_measure(sem, torch, steps=10, warmup=3, refine=True):
         spec = VortexSpec(vmax=it.vmax, rmw=it.rmw, seed=1000 + k)
         q = torch.from_numpy(vortex_state(sem.sem_mesh_coords_host(m).T, it.Lz, spec)).cuda()
         meshes.append(m)
+        init.append(q.clone())
         qs.append(q)
         q32.append(torch.empty(q.shape, dtype=torch.float32, device="cuda"))
         work.append(torch.empty((10, q.shape[1]), dtype=torch.float32, device="cuda"))
@@ -258,13 +259,34 @@ def batched_measure(sem, torch, steps=10, warmup=3, refine=True):
     ms_graph = timed(lambda: sem.sem_batch_step_mixed(batch, p, qs, q32, work, dts, True, stream))
     ms_nograph = timed(lambda: sem.sem_batch_step_mixed(batch, p, qs, q32, work, dts, False, stream))
     status = sem.sem_batch_status(batch)
+    # max-wind gate: every instance after gate_steps batched (graph) steps
+    # against its float64 single-mesh run from the same initial state
+    gate_steps = 20
+    p64 = sem.sem_params_default(precision=sem.SEM_PREC_FP64)
+    for k, m in enumerate(meshes):
+        qs[k].copy_(init[k])
+        sem.sem_mirror(m, qs[k], q32[k], stream)
+    for _ in range(gate_steps):
+        sem.sem_batch_step_mixed(batch, p, qs, q32, work, dts, True, stream)
+    errs = []
+    for k, m in enumerate(meshes):
+        q64 = init[k].clone()
+        w1, w2 = torch.empty_like(q64), torch.empty_like(q64)
+        for _ in range(gate_steps):
+            sem.sem_step(m, p64, q64, w1, w2, dts[k], stream)
+        hw = 0.5 * insts[k].L    # the whole box
+        a, b = sem.sem_diag(m, p64, qs[k], hw), sem.sem_diag(m, p64, q64, hw)
+        errs.append(abs(a["max_wind"] - b["max_wind"]) / b["max_wind"])
+    gate = {"steps": gate_steps, "max_wind_rel_err_max": max(errs), "max_wind_rel_err": errs,
+            "how": "each instance, batched mixed steps against its own float64 single-mesh steps",
+            "status": sem.sem_batch_status(batch)}
     return {"workload": "16 seeded instances, bases 8..48, N 3..6, "
                         + ("0..3 levels" if refine else "unrefined"),
             "instances": len(insts), "elements": int(sum(m.Ne for m in meshes)),
             "dof_per_stage": dof, "ms_per_step_graph": ms_graph, "ms_per_step_batched_no_graph": ms_nograph,
             "ms_per_step_sequential": ms_seq,
             "value_graph": dof * 3 / (ms_graph * 1e-3), "value_sequential": dof * 3 / (ms_seq * 1e-3),
-            "speedup": ms_seq / ms_graph, "status": status,
+            "speedup": ms_seq / ms_graph, "status": status, "gate": gate,
             "launches_per_step_graph": 1, "launches_per_step_sequential": 6 * len(insts)}
 
 
@@ -286,7 +308,9 @@ def amr_measure(sem, torch, steps=500, t_amr=50):
     pc = sem.sem_params_default(thresholds=thr, lvl_max=3)
     stream = torch.cuda.current_stream()
     history = []
+    flag_log = []
     dof = 0
+    m0, q0 = m, q.clone()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     remesh_s = 0.0
@@ -305,6 +329,7 @@ def amr_measure(sem, torch, steps=500, t_amr=50):
             torch.cuda.synchronize()
             r0 = time.perf_counter()
             flags = sem.sem_adapt_flags_host(m, pc, q, stream)
+            flag_log.append(flags)
             new = sem.sem_transfer_plan(m, flags)
             qn = torch.empty((5, new.NG), dtype=torch.float64, device="cuda")
             sem.sem_transfer(m, new, q, qn, stream)
@@ -314,9 +339,30 @@ def amr_measure(sem, torch, steps=500, t_amr=50):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     d = sem.sem_diag(m, pc, q)
+    status = sem.sem_status(m)
+    # the float64 form on the same remesh schedule (the recorded flags
+    # replayed, so the meshes are the same): the max-wind gate
+    p64 = sem.sem_params_default(precision=sem.SEM_PREC_FP64)
+    m64, q64, s = m0, q0, 0
+    for r in range(len(flag_log) + 1):
+        w1, w2 = torch.empty_like(q64), torch.empty_like(q64)
+        for _ in range(min(t_amr, steps - s)):
+            sem.sem_step(m64, p64, q64, w1, w2, dt, stream)
+            s += 1
+        if r < len(flag_log):
+            new = sem.sem_transfer_plan(m64, flag_log[r])
+            qn = torch.empty((5, new.NG), dtype=torch.float64, device="cuda")
+            sem.sem_transfer(m64, new, q64, qn, stream)
+            m64, q64 = new, qn
+    d64 = sem.sem_diag(m64, pc, q64)
     return {"workload": "32x32x8 base N=4, level 3 inside 150 km, thresholds [5,10,15], remesh every 50",
             "steps": steps, "wall_s": wall, "remesh_s": remesh_s, "dof_updates_per_s": dof / wall,
-            "history": history, "status": sem.sem_status(m), "max_wind": d["max_wind"]}
+            "history": history, "status": status, "max_wind": d["max_wind"],
+            "gate": {"max_wind_fp64": d64["max_wind"],
+                     "max_wind_rel_err": abs(d["max_wind"] - d64["max_wind"]) / d64["max_wind"],
+                     "max_mean_wind_rel_err": abs(d["max_mean_wind"] - d64["max_mean_wind"]) / d64["max_mean_wind"],
+                     "how": "float64 form through the same meshes (the mixed run's flags replayed)",
+                     "status_fp64": sem.sem_status(m64)}}
 
 
 def learned_measure(sem, torch):
@@ -354,7 +400,10 @@ def learned_measure(sem, torch):
                                r["learned"]["dof_updates_per_s"]] for r in runs],
         "seconds": [[r["reference"]["seconds"], r["criterion"]["seconds"], r["learned"]["seconds"]]
                     for r in runs],
-        "status": max(max(r[k]["status"] for k in ("reference", "criterion", "learned")) for r in runs)}
+        "gate_max_wind_rel_err": [r["gate_max_wind_rel_err"] for r in runs],
+        "gate": "mixed learned run against the float64 form on the same remesh schedule (flags replayed)",
+        "status": max(max(r[k]["status"] for k in ("reference", "criterion", "learned", "learned_fp64"))
+                      for r in runs)}
     out["seconds"] = time.perf_counter() - t0
     return out
 

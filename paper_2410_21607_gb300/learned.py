@@ -198,7 +198,7 @@ def element_levels(sem, torch, mesh, device):
 
 def adaptive_run(sem, torch, spec, L, Lz, nx, nz, N, lvl_max, thresholds, dt, t_end,
                  remesh_s=50.0, check_s=10.0, net=None, scales=(1e-3, 10.0, 10.0, 1.0, 1.0),
-                 uniform_level=None, physics=None):
+                 uniform_level=None, physics=None, replay=None, fp64=False):
     """A real adaptive run: the mesh is refined and coarsened every remesh_s
     seconds with the solution transferred (Algorithm 3), by the criterion's
     flags alone (net None) or by the criterion combined with the network's
@@ -208,11 +208,16 @@ def adaptive_run(sem, torch, spec, L, Lz, nx, nz, N, lvl_max, thresholds, dt, t_
     level and never adapted (the reference).  Returns the final maximum wind,
     the remesh count, the missed-refinement rate (checks every check_s between
     remeshes), the mean element count and DOF-updates/s including remeshes.
-    physics: extra step parameters (for example the Smagorinsky stress)."""
+    physics: extra step parameters (for example the Smagorinsky stress).
+    The flags of every remesh are returned (flag_log); replay runs the same
+    remesh schedule from such a log instead of deciding (same meshes), and
+    fp64 steps in the float64 form instead of the mixed one: the two
+    together give the float64 run on the mixed run's schedule."""
     import time
     from synth.vortex import vortex_state
     dev = "cuda"
-    p_step = sem.sem_params_default(precision=sem.SEM_PREC_MIXED, **(physics or {}))
+    p_step = sem.sem_params_default(precision=sem.SEM_PREC_FP64 if fp64 else sem.SEM_PREC_MIXED,
+                                    **(physics or {}))
     p_crit = sem.sem_params_default(thresholds=list(thresholds), lvl_max=lvl_max)
     sc = np.asarray(scales, dtype=np.float32)
     if uniform_level is not None:
@@ -228,6 +233,8 @@ def adaptive_run(sem, torch, spec, L, Lz, nx, nz, N, lvl_max, thresholds, dt, t_
     q = torch.from_numpy(vortex_state(sem.sem_mesh_coords_host(m).T, Lz, spec)).to(dev)
 
     def buffers(mesh, q):
+        if fp64:
+            return torch.empty_like(q), torch.empty_like(q)
         q32 = torch.empty(q.shape, dtype=torch.float32, device=dev)
         work = torch.empty((10, mesh.NG), dtype=torch.float32, device=dev)
         sem.sem_mirror(mesh, q, q32)
@@ -239,11 +246,23 @@ def adaptive_run(sem, torch, spec, L, Lz, nx, nz, N, lvl_max, thresholds, dt, t_
     missed = want = remeshes = 0
     dof = 0
     elems = []
+    flag_log = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for s in range(steps):
         remesh_now = s > 0 and s % k_remesh == 0
-        if uniform_level is None and (remesh_now or (s > 0 and s % k_check == 0)):
+        if uniform_level is None and replay is not None:
+            if remesh_now:
+                fl_host = replay[len(flag_log)]
+                flag_log.append(fl_host)
+                if fl_host.any():
+                    new = sem.sem_transfer_plan(m, fl_host)
+                    q2 = torch.empty((5, new.NG), dtype=torch.float64, device=dev)
+                    sem.sem_transfer(m, new, q, q2)
+                    m, q = new, q2
+                    q32, work = buffers(m, q)
+                    remeshes += 1
+        elif uniform_level is None and (remesh_now or (s > 0 and s % k_check == 0)):
             flags = torch.empty(m.Ne, dtype=torch.int8, device=dev)
             sem.sem_adapt_flags(m, p_crit, q, flags)
             if not remesh_now:
@@ -263,6 +282,7 @@ def adaptive_run(sem, torch, spec, L, Lz, nx, nz, N, lvl_max, thresholds, dt, t_
                     sem.sem_mlp_predict_flags(net, F, pred)
                     fl = sem.sem_merge_flags(flags, pred, lev, lvl_max)
                 fl_host = fl.cpu().numpy()
+                flag_log.append(fl_host)
                 if fl_host.any():
                     new = sem.sem_transfer_plan(m, fl_host)
                     q2 = torch.empty((5, new.NG), dtype=torch.float64, device=dev)
@@ -270,7 +290,10 @@ def adaptive_run(sem, torch, spec, L, Lz, nx, nz, N, lvl_max, thresholds, dt, t_
                     m, q = new, q2
                     q32, work = buffers(m, q)
                     remeshes += 1
-        sem.sem_step_mixed(m, p_step, q, q32, work, dt)
+        if fp64:
+            sem.sem_step(m, p_step, q, q32, work, dt)
+        else:
+            sem.sem_step_mixed(m, p_step, q, q32, work, dt)
         dof += 15 * m.Ne * (N + 1) ** 3
         elems.append(m.Ne)
     torch.cuda.synchronize()
@@ -279,7 +302,7 @@ def adaptive_run(sem, torch, spec, L, Lz, nx, nz, N, lvl_max, thresholds, dt, t_
     wind = sem.sem_diag(m, p_step, q, 0.5 * L)["max_wind"] if status == 0 else float("nan")
     return {"max_wind": wind, "remeshes": remeshes, "missed_rate": missed / max(want, 1),
             "mean_elements": float(np.mean(elems)), "dof_updates_per_s": dof / wall,
-            "seconds": wall, "status": status}
+            "seconds": wall, "status": status, "flag_log": flag_log}
 
 
 def adaptive_comparison(sem, torch, specs, net, L=150e3, Lz=24e3, nx=24, nz=2, N=4,
@@ -296,8 +319,13 @@ def adaptive_comparison(sem, torch, specs, net, L=150e3, Lz=24e3, nx=24, nz=2, N
                            physics=physics)
         lrn = adaptive_run(sem, torch, spec, L, Lz, nx, nz, N, lvl_max, thresholds, dt, t_end, net=net,
                            physics=physics)
+        # the float64 form on the learned run's remesh schedule: the max-wind
+        # gate of the mixed form
+        l64 = adaptive_run(sem, torch, spec, L, Lz, nx, nz, N, lvl_max, thresholds, dt, t_end,
+                           physics=physics, replay=lrn["flag_log"], fp64=True)
         w = ref["max_wind"]
-        out.append({"reference": ref, "criterion": cri, "learned": lrn,
+        out.append({"reference": ref, "criterion": cri, "learned": lrn, "learned_fp64": l64,
                     "wind_err_criterion": abs(cri["max_wind"] - w) / w,
-                    "wind_err_learned": abs(lrn["max_wind"] - w) / w})
+                    "wind_err_learned": abs(lrn["max_wind"] - w) / w,
+                    "gate_max_wind_rel_err": abs(lrn["max_wind"] - l64["max_wind"]) / l64["max_wind"]})
     return out

@@ -8,7 +8,8 @@ criterion-plus-network schedule must miss fewer refinements (checked every
 10 steps) than the criterion alone, while the criterion stays the fallback
 for coarsening.  The same schedules then drive real remeshes with solution
 transfer on a held-out vortex and must follow the uniformly refined
-reference's maximum wind.
+reference's maximum wind; the mixed form's maximum wind on the learned
+schedule must be within 1e-3 of the float64 form's on the same meshes.
 """
 import pytest
 
@@ -57,3 +58,8 @@ def test_learned_schedule_misses_fewer_refinements(sem):
     assert cri["mean_elements"] < 0.5 * ref["mean_elements"]
     for r in (cri, lrn):
         assert abs(r["max_wind"] - ref["max_wind"]) <= 0.05 * ref["max_wind"]
+    # the max-wind gate of the mixed form on the learned schedule: the float64
+    # form through the same meshes (its flags replayed) within 1e-3
+    l64 = learned.adaptive_run(*args, physics=phys, replay=lrn["flag_log"], fp64=True)
+    assert l64["status"] == 0 and l64["remeshes"] == lrn["remeshes"]
+    assert abs(lrn["max_wind"] - l64["max_wind"]) <= 1e-3 * l64["max_wind"], (lrn["max_wind"], l64["max_wind"])
