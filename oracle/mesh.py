@@ -19,6 +19,22 @@ coordinates, following the modified DSS described at the end of Sec. 3.1:
 
 The local element vector is q_L = Q q_G and the assembled residual is Q^T r_L.
 
+Warped layers (non-affine elements): with warp = (A, kx, ky) the layer
+surfaces are curved, every node of the box mesh moving vertically to
+    z = zeta + A sin(2 pi kx (x + Lx/2) / Lx) sin(2 pi ky (y + Ly/2) / Ly) sin(pi zeta / Lz),
+which keeps the lids flat and the lateral periodicity.  Topology (global
+nodes, Q) is built on the box coordinates; the heights of the global nodes
+come from the warp and the local heights are z_L = Q z_G, so that hanging
+nodes lie on the coarse side's face (the mesh stays watertight).  Every
+element is the isoparametric image of the reference cube through its nodal
+coordinates: at each node the Jacobian matrix dx_d/dxi_i comes from the
+derivative matrix applied to the element's coordinates, and its inverse
+gives d xi_i / dx_d and the derivative operators
+    G_d[k, l] = sum_i (d xi_i / dx_d)(x_k) d psi_l / d xi_i (xi_k),
+with the quadrature weights w_k det(dx/dxi)(x_k).  Without a warp the
+elements are the axis-aligned boxes and the operators are the closed forms
+of element_ops.
+
 Test infrastructure only (see oracle/__init__.py).
 """
 import numpy as np
@@ -29,7 +45,7 @@ from . import basis
 
 class OracleMesh:
     def __init__(self, Lx, Ly, Lz, nx, ny, nz, N, leaves=None,
-                 periodic=(True, True), z_faces=None):
+                 periodic=(True, True), z_faces=None, warp=None):
         self.Lx, self.Ly, self.Lz = float(Lx), float(Ly), float(Lz)
         self.nx, self.ny, self.nz, self.N = int(nx), int(ny), int(nz), int(N)
         # layer faces 0 = z_0 < z_1 < ... < z_nz = Lz (uniform by default; a
@@ -48,8 +64,11 @@ class OracleMesh:
         self.leaves = [tuple(int(v) for v in t) for t in leaves]
         self._check_tiling()
         self.xi, self.w = basis.lgl_nodes_weights(self.N)
+        self.warp = None if warp is None else tuple(float(v) for v in warp)
         self._build_elements()
         self._build_global_nodes()
+        if self.warp is not None:
+            self._apply_warp()
 
     # ------------------------------------------------------------------
     def _check_tiling(self):
@@ -248,6 +267,45 @@ class OracleMesh:
         self.z_top = np.abs(XG[:, 2] - self.Lz) < 1e-9 * self.Lz
 
     # ------------------------------------------------------------------
+    def warp_height(self, x, y, zeta):
+        """Height of the point (x, y, zeta) of the box under the warp."""
+        A, kx, ky = self.warp
+        return zeta + A * (np.sin(2 * np.pi * kx * (x + 0.5 * self.Lx) / self.Lx)
+                           * np.sin(2 * np.pi * ky * (y + 0.5 * self.Ly) / self.Ly)
+                           * np.sin(np.pi * zeta / self.Lz))
+
+    def _apply_warp(self):
+        """Heights of the global nodes from the warp, local heights Q z_G, and
+        the isoparametric metric at every local node of every element."""
+        self.XG_box = self.XG.copy()
+        self.XG = self.XG.copy()
+        self.XG[:, 2] = self.warp_height(self.XG[:, 0], self.XG[:, 1], self.XG[:, 2])
+        self.X = self.X.copy()
+        self.X[:, :, 2] = (self.Q @ self.XG[:, 2]).reshape(self.Ne, self.P)
+        D = basis.derivative_matrix(self.N)
+        I = np.eye(self.N + 1)
+        Dref = (np.kron(I, np.kron(I, D)), np.kron(I, np.kron(D, I)), np.kron(D, np.kron(I, I)))
+        self.G_elem = np.zeros((self.Ne, 3, self.P, self.P))
+        w3 = self.w[self.li] * self.w[self.lj] * self.w[self.lk]
+        self.detJ = np.zeros((self.Ne, self.P))
+        for e in range(self.Ne):
+            # Jm[k, d, i] = d x_d / d xi_i at node k
+            Jm = np.stack([np.stack([Dref[i] @ self.X[e, :, d] for i in range(3)], axis=1)
+                           for d in range(3)], axis=1)
+            det = np.linalg.det(Jm)
+            if np.any(det <= 0):
+                raise ValueError("the warp folds an element (non-positive Jacobian)")
+            inv = np.linalg.inv(Jm)          # inv[k, i, d] = d xi_i / d x_d
+            for d in range(3):
+                self.G_elem[e, d] = sum(inv[:, i, d][:, None] * Dref[i] for i in range(3))
+            self.detJ[e] = det
+        self.wJ = w3[None, :] * self.detJ
+        NL = self.Ne * self.P
+        self.M = self.QT @ self.wJ.reshape(NL)
+        self.z_bottom = np.abs(self.XG[:, 2]) < 1e-9 * self.Lz
+        self.z_top = np.abs(self.XG[:, 2] - self.Lz) < 1e-9 * self.Lz
+
+    # ------------------------------------------------------------------
     def to_local(self, qG):
         """Scatter: q_L = Q q_G.  qG: (F, NG) -> (F, Ne, P)."""
         qG = np.atleast_2d(qG)
@@ -277,7 +335,12 @@ class OracleMesh:
 
     def op_groups(self):
         """(level, element indices, (G_x, G_y, G_z)) for every group of
-        elements that share their derivative operators (level and layer)."""
+        elements that share their derivative operators (level and layer);
+        with a warp every element is its own group."""
+        if self.warp is not None:
+            for e in range(self.Ne):
+                yield int(self.level[e]), np.array([e]), tuple(self.G_elem[e])
+            return
         for lev in np.unique(self.level):
             for k in range(self.nz):
                 es = np.nonzero((self.level == lev) & (self.layer == k))[0]

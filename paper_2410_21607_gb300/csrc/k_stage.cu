@@ -376,19 +376,33 @@ struct DssArgs {
   int* status;
 };
 
+// x / 4 for a float64 x, exactly: the exponent field drops by 2 with integer
+// operations when x and x / 4 are normal numbers (the float64 pipe of this
+// part is narrow), else a float64 multiplication (zero, subnormals, Inf, NaN).
+__device__ __forceinline__ double quarter_exact(double x) {
+  const int hi = __double2hiint(x);
+  const unsigned e = ((unsigned)hi >> 20) & 0x7FFu;
+  if (e > 2u && e < 0x7FFu) return __hiloint2double(hi - (2 << 20), __double2loint(x));
+  return x * 0.25;
+}
+
 // FP64 form: float64 throughout.  The float64 pipe of this part is narrow
 // (1/64 of the float32 rate), so the kernel issues float64 instructions only
 // for the arithmetic itself: node indices are 32-bit (an unsigned division by
-// NZ runs on the integer pipe), a horizontal node whose Q_h^T weights are all
-// exactly 1 (every node away from 2:1 faces) adds its sources with plain
-// additions (the first one is a load), and the stage update is specialised:
-//   MODE 0  out = s T                    (right-hand side only)
-//   MODE 1  out = qs + s T               (a = 0, b = 1: the first SSP-RK3 stage)
-//   MODE 2  out = a qn + b qs + s T      (any a, b)
-// with s = c dt / M.  Every sum is formed in the order of the CSR lists, so
-// the results are those of a plain fma loop over the lists, bit for bit.
+// NZ runs on the integer pipe), c dt / M_z(kz) comes from a table the block
+// fills once, a horizontal node whose Q_h^T weights are all exactly 1 (every
+// node away from 2:1 faces) adds its sources with plain additions (the first
+// one is a load), and the stage update is specialised:
+//   MODE 0  out = s T                         (right-hand side only)
+//   MODE 1  out = qs + s T                    (a = 0, b = 1: the first SSP-RK3 stage)
+//   MODE 2  out = a qn + b qs + s T           (any a, b)
+//   MODE 3  out = (3 qn + (qs + 4 s T)) / 4   (a = 3/4, b = 1/4: the second SSP-RK3
+//                                              stage; the division by 4 is exact)
+// with s = c dt / M.  Every sum of the gather is formed in the order of the
+// CSR lists.  The block's table needs NZ doubles of dynamic shared memory.
 template <int MODE>
 __global__ void __launch_bounds__(256) dss_stage_fp64(const DssArgs A) {
+  extern __shared__ double s_cmz[];   // [NZ]: c dt / M_z(kz) (4 c dt / M_z for MODE 3)
   const double* rc = (const double*)A.rc;
   const double* qtw = (const double*)A.qt_w;
   const double* mh = (const double*)A.Minv_h;
@@ -396,6 +410,9 @@ __global__ void __launch_bounds__(256) dss_stage_fp64(const DssArgs A) {
   const unsigned NZ = (unsigned)A.NZ, NG = (unsigned)A.NG;
   const long long NGl = A.NG;
   const int NZr = A.NZr;
+  const double cdt = MODE == 3 ? 4.0 * A.cdt : A.cdt;
+  for (int k = threadIdx.x; k < (int)NZ; k += blockDim.x) s_cmz[k] = cdt * __ldg(mz + k);
+  __syncthreads();
   int bad = 0;
   for (unsigned gidx = blockIdx.x * blockDim.x + threadIdx.x; gidx < NG; gidx += gridDim.x * blockDim.x) {
     const unsigned h = gidx / NZ;
@@ -405,7 +422,7 @@ __global__ void __launch_bounds__(256) dss_stage_fp64(const DssArgs A) {
 #pragma unroll
     for (int fl = 0; fl < kFields; ++fl)
       if (MODE >= 1) qsv[fl] = __ldg(A.qs + fl * NGl + gidx);
-    const double s = A.cdt * (__ldg(mh + h) * __ldg(mz + kz));
+    const double s = __ldg(mh + h) * s_cmz[kz];
     const bool lid = (kz == 0) || (kz == (int)NZ - 1);
     double acc[kFields];
     const int4 r = __ldg(A.qt_rec_unit + h);
@@ -442,6 +459,7 @@ __global__ void __launch_bounds__(256) dss_stage_fp64(const DssArgs A) {
       double val;
       if (MODE == 0) val = T * s;
       else if (MODE == 1) val = fma(s, T, qsv[fl]);
+      else if (MODE == 3) val = quarter_exact(fma(3.0, __ldg(A.qn + fl * NGl + gidx), fma(s, T, qsv[fl])));
       else val = fma(s, T, fma(A.a, __ldg(A.qn + fl * NGl + gidx), A.b * qsv[fl]));
       A.out[fl * NGl + gidx] = val;
       bad |= nonfinite_bits(val);
@@ -2252,12 +2270,18 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
     ProfScope ps(mixed ? "dss_rk_mixed" : "dss_rk_fp64", st);
     if (mixed)
       dss_stage_mixed<<<grid_cap(m.NG), 256, 0, st>>>(B);
-    else if (s.rhs_only)
-      dss_stage_fp64<0><<<grid_cap(m.NG), 256, 0, st>>>(B);
-    else if (s.a == 0.0 && s.b == 1.0)
-      dss_stage_fp64<1><<<grid_cap(m.NG), 256, 0, st>>>(B);
-    else
-      dss_stage_fp64<2><<<grid_cap(m.NG), 256, 0, st>>>(B);
+    else {
+      const size_t sm = sizeof(double) * m.NZ;
+      if (sm > 48 * 1024) return fail(SEM_ERR_UNSUPPORTED, "more than 6144 vertical levels");
+      if (s.rhs_only)
+        dss_stage_fp64<0><<<grid_cap(m.NG), 256, sm, st>>>(B);
+      else if (s.a == 0.0 && s.b == 1.0)
+        dss_stage_fp64<1><<<grid_cap(m.NG), 256, sm, st>>>(B);
+      else if (s.a == 0.75 && s.b == 0.25)
+        dss_stage_fp64<3><<<grid_cap(m.NG), 256, sm, st>>>(B);
+      else
+        dss_stage_fp64<2><<<grid_cap(m.NG), 256, sm, st>>>(B);
+    }
   }
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;

@@ -114,7 +114,12 @@ def schedule(sem, torch, snaps, ahead, every, lvl_max, net=None, which=0):
     are counted against the flags of parameter set 0 (the paper's criterion)."""
     Ne = snaps[0][0].shape[0]
     dev = snaps[0][0].device
+    # start from the levels the criterion gives the initial state (lvl_max
+    # passes of one level each), as an adaptive run starts from a mesh
+    # refined by the criterion
     L = torch.zeros(Ne, dtype=torch.int8, device=dev)
+    for _ in range(lvl_max):
+        L = (L + snaps[0][1][which].gather(0, L.long()[None]).squeeze(0)).clamp_(0, lvl_max)
     k = ahead // every
     missed = want = 0
     refined = 0.0

@@ -62,10 +62,11 @@ def test_weak_equals_assembled_strong_divergence_on_conforming_mesh():
     np.testing.assert_allclose(T[0], -strong, atol=1e-12 * np.abs(strong).max())
 
 
-def _mms(eqset, n, N=4, stretch=0.0):
+def _mms(eqset, n, N=4, stretch=0.0, warp=None):
     """Max relative error of the oracle tendency against the exact one for a
     smooth periodic manufactured state on an n x n x n mesh (layer faces
-    stretched by tests.helpers.stretched_faces when stretch > 0)."""
+    stretched by tests.helpers.stretched_faces when stretch > 0; warped
+    layers, OracleMesh's warp, when warp is given)."""
     Lx, Lz = 40e3, 10e3
     x, y, z = sy.symbols("x y z", real=True)
     g, f, gam = PRM.g, PRM.f, PRM.gamma
@@ -104,7 +105,7 @@ def _mms(eqset, n, N=4, stretch=0.0):
                 -w * sy.diff(th0, z) - adv(thp)]
     from tests.helpers import stretched_faces
     m = mesh.OracleMesh(Lx, Lx, Lz, n, n, n, N,
-                        z_faces=stretched_faces(Lz, n, stretch) if stretch > 0 else None)
+                        z_faces=stretched_faces(Lz, n, stretch) if stretch > 0 else None, warp=warp)
     X = m.XG
     ev = lambda e: np.broadcast_to(sy.lambdify((x, y, z), e, "numpy")(X[:, 0], X[:, 1], X[:, 2]),
                                    (m.NG,)).astype(float)
