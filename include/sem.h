@@ -82,6 +82,23 @@ typedef struct {
   const double* z_faces;  /* host, [nz + 1] layer faces 0 = z_0 < z_1 < ... < z_nz = Lz
                              (a stretched vertical grid; every element stays an
                              axis-aligned box), or NULL for nz equal layers */
+  /* Warped layers (non-affine elements; 0 = none): every node moves vertically
+   * to z = zeta + warp_amplitude sin(2 pi warp_kx (x + Lx/2) / Lx)
+   * sin(2 pi warp_ky (y + Ly/2) / Ly) sin(pi zeta / Lz) (zeta its height on the
+   * box mesh): curved layer surfaces, flat lids, periodic.  Each element is the
+   * isoparametric image of the reference cube through its nodal coordinates
+   * (Sec. 3's LGL basis), with float64 metric terms and Jacobian per node and
+   * the lumped mass per node; hanging nodes take the coarse face's
+   * interpolated height (Sec. 3.1), so the mesh stays watertight.  A
+   * non-positive Jacobian gives SEM_ERR_ARG.  On warped meshes the right-hand
+   * side, the stages and steps (float64 and mixed forms), the speed
+   * criterion, coordinates and diagnostics are available; the Smagorinsky
+   * stress, the absorbing layer, the heating, the vorticity and
+   * potential-vorticity criteria, adaptation (sem_transfer_plan), batching and
+   * checkpoints give SEM_ERR_UNSUPPORTED, and the mixed conservative form
+   * uses the line-exchange element kernels only. */
+  double warp_amplitude;
+  int warp_kx, warp_ky;
 } sem_mesh_desc;
 
 typedef struct sem_mesh sem_mesh;

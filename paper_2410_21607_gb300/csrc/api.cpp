@@ -38,7 +38,9 @@ void free_device(Mesh& m) {
   void* ptrs[] = {D.hmap, D.hang_h, D.hang_w, D.qt_ptr, D.qt_src, D.qt_w, D.Minv_h, D.Minv_z,
                   D.Mh, D.Mz, D.Minv_h32, D.Minv_z32, D.qt_w32, D.qt_rec_src, D.qt_rec_w, D.qt_rec_unit, D.hang_w32, D.mirror, D.spg, D.spg32, D.ref, D.ref32, D.col_level, D.col_x0, D.col_y0, D.xh, D.yh, D.zk, D.hzk, D.hzk32, D.scratch,
                   D.status, D.org, D.elem_cmax, D.elem_flags, D.diag_buf,
-                  D.tr_comp_ptr, D.tr_nodes, D.tr_A_ptr, D.tr_A_col, D.tr_A_val, D.tr_coupled};
+                  D.tr_comp_ptr, D.tr_nodes, D.tr_A_ptr, D.tr_A_col, D.tr_A_val, D.tr_coupled,
+                  D.zG, D.metric, D.metric32, D.Minv_g, D.Minv_g32, D.refG, D.refH, D.refG32, D.refH32,
+                  D.ref4G, D.ref4H};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete m.dev;
@@ -132,6 +134,32 @@ int ensure_device(Mesh& m) {
     free_device(m);
     return fail(SEM_ERR_CUDA, std::string("device allocation: ") + cudaGetErrorString(e));
   }
+  if (m.warped()) {
+    std::vector<float> met32(m.metric.size()), mg32(m.Mg.size());
+    std::vector<double> minvg(m.Mg.size());
+    for (size_t k = 0; k < m.metric.size(); ++k) met32[k] = (float)m.metric[k];
+    for (size_t k = 0; k < m.Mg.size(); ++k) {
+      minvg[k] = 1.0 / m.Mg[k];
+      mg32[k] = (float)minvg[k];
+    }
+    const size_t nh = m.zH.size() ? m.zH.size() : 1;
+    cudaError_t e2 = cudaSuccess;
+    if ((rc = upload(D.zG, m.zG)) || (rc = upload(D.metric, m.metric)) || (rc = upload(D.metric32, met32)) ||
+        (rc = upload(D.Minv_g, minvg)) || (rc = upload(D.Minv_g32, mg32))) {
+      free_device(m);
+      return rc;
+    }
+    e2 = cudaMalloc((void**)&D.refG, (size_t)m.NG * kRef * sizeof(double));
+    if (e2 == cudaSuccess) e2 = cudaMalloc((void**)&D.refH, nh * kRef * sizeof(double));
+    if (e2 == cudaSuccess) e2 = cudaMalloc((void**)&D.refG32, (size_t)m.NG * kRef * sizeof(float));
+    if (e2 == cudaSuccess) e2 = cudaMalloc((void**)&D.refH32, nh * kRef * sizeof(float));
+    if (e2 == cudaSuccess) e2 = cudaMalloc((void**)&D.ref4G, (size_t)m.NG * 4 * sizeof(float));
+    if (e2 == cudaSuccess) e2 = cudaMalloc((void**)&D.ref4H, nh * 4 * sizeof(float));
+    if (e2 != cudaSuccess) {
+      free_device(m);
+      return fail(SEM_ERR_CUDA, std::string("device allocation: ") + cudaGetErrorString(e2));
+    }
+  }
   if (!m.origin.empty()) {
     std::vector<int> org((size_t)m.Ncol() * 6);
     for (long long c = 0; c < m.Ncol(); ++c) {
@@ -167,29 +195,57 @@ int ensure_reference(Mesh& m, const sem_params& p) {
   if (!(p.N_bv > 0) || !(p.g > 0) || !(p.c_p > p.R_d) || !(p.R_d > 0))
     return fail(SEM_ERR_ARG, "reference state needs g > 0, N_bv > 0, c_p > R_d > 0");
   const double c_v = p.c_p - p.R_d, N2 = p.N_bv * p.N_bv;
-  std::vector<double> ref((size_t)m.NZ * kRef);
-  std::vector<float> ref32((size_t)m.NZ * (kRef + 4));
-  for (int k = 0; k < m.NZ; ++k) {
-    const double z = m.zk[k];
+  // one row: theta0, pi0, p0, rho0, (rho theta)0, dtheta0/dz, 1/(rho theta)0, z
+  auto row = [&](double z, double* r) {
     const double th0 = p.theta_s * std::exp(N2 * z / p.g);
     const double pi0 = 1.0 + p.g * p.g / (p.c_p * p.theta_s * N2) * (std::exp(-N2 * z / p.g) - 1.0);
-    if (!(pi0 > 0)) return fail(SEM_ERR_ARG, "reference state: Exner pressure <= 0 below the lid");
+    if (!(pi0 > 0)) return false;
     const double p0 = p.p00 * std::pow(pi0, p.c_p / p.R_d);
     const double rho0 = p.p00 * std::pow(pi0, c_v / p.R_d) / (p.R_d * th0);
-    const double r[kRef] = {th0, pi0, p0, rho0, rho0 * th0, th0 * N2 / p.g, 1.0 / (rho0 * th0), z};
-    for (int q = 0; q < kRef; ++q) {
-      ref[(size_t)k * kRef + q] = r[q];
-      ref32[(size_t)k * kRef + q] = (float)r[q];
+    const double v[kRef] = {th0, pi0, p0, rho0, rho0 * th0, th0 * N2 / p.g, 1.0 / (rho0 * th0), z};
+    for (int q = 0; q < kRef; ++q) r[q] = v[q];
+    return true;
+  };
+  // a table of rows at heights z[0..n): float64, float32 and packed float32
+  // rows (p0, rho0, (rho theta)0, 1/(rho theta)0)
+  auto table = [&](const std::vector<double>& z, std::vector<double>& t64, std::vector<float>& t32,
+                   std::vector<float>& t4) {
+    const size_t n = z.size();
+    t64.assign(n * kRef, 0.0);
+    t32.assign(n * kRef, 0.f);
+    t4.assign(n * 4, 0.f);
+    for (size_t k = 0; k < n; ++k) {
+      double* r = &t64[k * kRef];
+      if (!row(z[k], r)) return false;
+      for (int q = 0; q < kRef; ++q) t32[k * kRef + q] = (float)r[q];
+      t4[k * 4 + 0] = (float)r[2];
+      t4[k * 4 + 1] = (float)r[3];
+      t4[k * 4 + 2] = (float)r[4];
+      t4[k * 4 + 3] = (float)r[6];
     }
-    // packed rows after the table: p0, rho0, (rho theta)0, 1/(rho theta)0
-    float* r4 = ref32.data() + (size_t)m.NZ * kRef + (size_t)k * 4;
-    r4[0] = (float)p0;
-    r4[1] = (float)rho0;
-    r4[2] = (float)(rho0 * th0);
-    r4[3] = (float)(1.0 / (rho0 * th0));
-  }
+    return true;
+  };
+  std::vector<double> ref;
+  std::vector<float> ref32, r4;
+  if (!table(m.zk, ref, ref32, r4)) return fail(SEM_ERR_ARG, "reference state: Exner pressure <= 0 below the lid");
+  ref32.insert(ref32.end(), r4.begin(), r4.end());   // packed rows after the table
   SEM_CUDA_TRY(cudaMemcpy(D.ref, ref.data(), ref.size() * sizeof(double), cudaMemcpyHostToDevice));
   SEM_CUDA_TRY(cudaMemcpy(D.ref32, ref32.data(), ref32.size() * sizeof(float), cudaMemcpyHostToDevice));
+  if (m.warped()) {
+    // warped layers: the reference state at every node's own height
+    std::vector<double> g64, h64;
+    std::vector<float> g32, h32, g4, h4;
+    if (!table(m.zG, g64, g32, g4) || !table(m.zH, h64, h32, h4))
+      return fail(SEM_ERR_ARG, "reference state: Exner pressure <= 0 below the lid");
+    SEM_CUDA_TRY(cudaMemcpy(D.refG, g64.data(), g64.size() * sizeof(double), cudaMemcpyHostToDevice));
+    SEM_CUDA_TRY(cudaMemcpy(D.refG32, g32.data(), g32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    SEM_CUDA_TRY(cudaMemcpy(D.ref4G, g4.data(), g4.size() * sizeof(float), cudaMemcpyHostToDevice));
+    if (!h64.empty()) {
+      SEM_CUDA_TRY(cudaMemcpy(D.refH, h64.data(), h64.size() * sizeof(double), cudaMemcpyHostToDevice));
+      SEM_CUDA_TRY(cudaMemcpy(D.refH32, h32.data(), h32.size() * sizeof(float), cudaMemcpyHostToDevice));
+      SEM_CUDA_TRY(cudaMemcpy(D.ref4H, h4.data(), h4.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+  }
   std::memcpy(D.ref_key, key, sizeof(key));
   D.ref_valid = true;
   return SEM_OK;
@@ -289,6 +345,13 @@ int sem_mesh_create(const sem_mesh_desc* d, sem_mesh** out) {
     for (int k = 0; k < m.nz; ++k) m.zf[k] = k * (m.Lz / m.nz);
     m.zf[m.nz] = m.Lz;
   }
+  if (!std::isfinite(d->warp_amplitude) || (d->warp_amplitude != 0.0 && (d->warp_kx < 0 || d->warp_ky < 0))) {
+    delete mh;
+    return fail(SEM_ERR_ARG, "warp: finite amplitude and non-negative wave numbers");
+  }
+  m.warp_A = d->warp_amplitude;
+  m.warp_kx = d->warp_kx;
+  m.warp_ky = d->warp_ky;
   if (d->n_leaves == 0) {
     for (int j = 0; j < d->ny; ++j)
       for (int i = 0; i < d->nx; ++i) m.leaves.push_back({0, i, j});
@@ -340,7 +403,7 @@ int sem_mesh_coords_host(const sem_mesh* mh, double* xyz) {
       long long g = h * m.NZ + k;
       xyz[g] = m.xh[h];
       xyz[m.NG + g] = m.yh[h];
-      xyz[2 * m.NG + g] = m.zk[k];
+      xyz[2 * m.NG + g] = m.warped() ? m.zG[g] : m.zk[k];
     }
   return SEM_OK;
 }
@@ -369,7 +432,7 @@ int sem_mesh_mass_host(const sem_mesh* mh, double* M) {
   if (!mh || !M) return fail(SEM_ERR_ARG, "NULL argument");
   const Mesh& m = mh->m;
   for (long long h = 0; h < m.NH; ++h)
-    for (int k = 0; k < m.NZ; ++k) M[h * m.NZ + k] = m.Mh[h] * m.Mz[k];
+    for (int k = 0; k < m.NZ; ++k) M[h * m.NZ + k] = m.warped() ? m.Mg[h * m.NZ + k] : m.Mh[h] * m.Mz[k];
   return SEM_OK;
 }
 
@@ -613,6 +676,7 @@ int sem_checkpoint_write(sem_mesh* mh, const double* q, double time, long long s
                          cudaStream_t st) {
   if (!mh || !q || !path) return fail(SEM_ERR_ARG, "NULL argument");
   const Mesh& m = mh->m;
+  if (m.warped()) return fail(SEM_ERR_UNSUPPORTED, "checkpoints of warped meshes are not built");
   CkptHead H;
   std::memset(&H, 0, sizeof(H));
   std::memcpy(H.magic, kMagic, 8);
@@ -758,6 +822,7 @@ int sem_transfer_plan(const sem_mesh* oldh, const int8_t* flags, sem_mesh** out)
   if (!oldh || !flags || !out) return fail(SEM_ERR_ARG, "NULL argument");
   *out = nullptr;
   const Mesh& o = oldh->m;
+  if (o.warped()) return fail(SEM_ERR_UNSUPPORTED, "adaptation of warped meshes is not built");
   std::vector<Leaf> nl;
   std::vector<Origin> org;
   int rc = adapt_leaves(o, flags, nl, org);

@@ -45,6 +45,8 @@ struct AdaptArgs {
   const double* hang_w;
   const int* col_level;
   const double* ref;
+  const double* refG;             // warped layers: reference rows per node and hanging line, else null
+  const double* refH;
   int8_t* flags;
   double* cmax;
   int nz, NZ;
@@ -94,7 +96,9 @@ adapt_column(const AdaptArgs A) {
       }
       double ss = __dadd_rn(__dadd_rn(__dmul_rn(v[1], v[1]), __dmul_rn(v[2], v[2])), __dmul_rn(v[3], v[3]));
       s = __dsqrt_rn(ss);
-      const double* rf = A.ref + (long long)kz * kRef;
+      const double* rf = !A.refG ? A.ref + (long long)kz * kRef
+                         : (hm >= 0 ? A.refG + ((long long)hm * A.NZ + kz) * kRef
+                                    : A.refH + ((long long)(-1 - hm) * A.NZ + kz) * kRef);
       rho = rf[3] + v[0];
       if (EQ == 0) s = __ddiv_rn(s, __dadd_rn(rf[3], v[0]));
       if (A.need_grad) {
@@ -190,6 +194,8 @@ int launch_adapt(Mesh& m, const sem_params& p, const double* q, int8_t* flags, d
   A.hang_w = D.hang_w;
   A.col_level = D.col_level;
   A.ref = D.ref;
+  A.refG = m.warped() ? D.refG : nullptr;
+  A.refH = m.warped() ? D.refH : nullptr;
   A.flags = flags;
   A.cmax = cmax;
   A.nz = m.nz;
@@ -210,6 +216,8 @@ int launch_adapt(Mesh& m, const sem_params& p, const double* q, int8_t* flags, d
     A.gy[l] = 2.0 / m.hy(l);
   }
   A.hzk = D.hzk;
+  if (A.need_grad && m.warped())
+    return fail(SEM_ERR_UNSUPPORTED, "warped layers: the vorticity and potential-vorticity criteria are not built");
   if (A.need_grad) {
     int rc = upload_aux_constants();
     if (rc) return rc;
@@ -231,7 +239,7 @@ int launch_adapt(Mesh& m, const sem_params& p, const double* q, int8_t* flags, d
 __global__ void __launch_bounds__(256)
 diag_level(const double* q, const double* xh, const double* yh, const double* Mh,
            const double* ref, long long NH, int NZ, long long NG, double hw, int eq,
-           double* out /*[NZ][4]*/) {
+           const double* refG, const double* Minv_g, double* out /*[NZ][4]*/) {
   __shared__ double s_max[256], s_num[256], s_den[256];
   const int kz = blockIdx.x;
   const double rho0 = ref[(long long)kz * kRef + 3];
@@ -241,10 +249,13 @@ diag_level(const double* q, const double* xh, const double* yh, const double* Mh
     const long long g = h * NZ + kz;
     const double U = q[NG + g], V = q[2 * NG + g];
     double s = sqrt(U * U + V * V);
-    if (eq == 0) s = s / (rho0 + q[g]);
+    // warped layers: the node's own reference density and lumped mass (the
+    // level means are then over a grid level, not a height)
+    if (eq == 0) s = s / ((refG ? refG[g * kRef + 3] : rho0) + q[g]);
+    const double wm = Minv_g ? 1.0 / Minv_g[g] : Mh[h];
     mx = fmax(mx, s);
-    num += Mh[h] * s;
-    den += Mh[h];
+    num += wm * s;
+    den += wm;
   }
   s_max[threadIdx.x] = mx;
   s_num[threadIdx.x] = num;
@@ -270,6 +281,7 @@ int launch_diag(Mesh& m, const sem_params& p, const double* q, double hw, sem_di
                 cudaStream_t st) {
   DeviceTables& D = *m.dev;
   diag_level<<<m.NZ, 256, 0, st>>>(q, D.xh, D.yh, D.Mh, D.ref, m.NH, m.NZ, m.NG, hw, p.eqset,
+                                    m.warped() ? D.refG : nullptr, m.warped() ? D.Minv_g : nullptr,
                                     D.diag_buf);
   SEM_CUDA_TRY(cudaGetLastError());
   std::vector<double> buf((size_t)m.NZ * 4);
@@ -314,7 +326,7 @@ int launch_merge_flags(const int8_t* crit, const int8_t* pred, const int8_t* lev
 
 // ---------------------------------------------------------------------------
 __global__ void coords_kernel(const double* xh, const double* yh, const double* zk, long long NH,
-                              int NZ, double* xyz) {
+                              int NZ, const double* zG, double* xyz) {
   const long long NG = NH * NZ;
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < NG;
        g += (long long)gridDim.x * blockDim.x) {
@@ -322,14 +334,14 @@ __global__ void coords_kernel(const double* xh, const double* yh, const double* 
     const int k = (int)(g - h * NZ);
     xyz[g] = xh[h];
     xyz[NG + g] = yh[h];
-    xyz[2 * NG + g] = zk[k];
+    xyz[2 * NG + g] = zG ? zG[g] : zk[k];
   }
 }
 
 int launch_coords(Mesh& m, double* xyz, cudaStream_t st) {
   DeviceTables& D = *m.dev;
   long long blocks = std::min<long long>((m.NG + 255) / 256, 152 * 16);
-  coords_kernel<<<(int)blocks, 256, 0, st>>>(D.xh, D.yh, D.zk, m.NH, m.NZ, xyz);
+  coords_kernel<<<(int)blocks, 256, 0, st>>>(D.xh, D.yh, D.zk, m.NH, m.NZ, m.warped() ? D.zG : nullptr, xyz);
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;
 }

@@ -112,6 +112,16 @@ struct VolArgs {
   const float* spg32;   // [NZ] absorbing-layer rate R(z): the line-exchange kernel adds
                         // -R q' (weak form, collocated) when set; null: not added here
   int* status;          // device status word (bit 4: a bounded device wait ran out)
+  // warped layers: per-node metric z_xi, z_eta, z_zeta [Ncol][Nq][nz][N+1][3] and the
+  // reference state at every node's height (global nodes [NG], hanging lines [Nhang][NZ])
+  const double* metric;
+  const float* metric32;
+  const double* refG;
+  const double* refH;
+  const float* refG32;
+  const float* refH32;
+  const float4* ref4G;
+  const float4* ref4H;
   float smag[kLev][3];  // per level (C_s Delta)^2, 2/hx, 2/hy: the horizontal
                         // Smagorinsky stress, for the kernels that add it
 };
@@ -134,6 +144,25 @@ template <> __device__ __forceinline__ float par_f<float>(const VolArgs& A) { re
 template <typename R> __device__ __forceinline__ R par_gam(const VolArgs& A);
 template <> __device__ __forceinline__ double par_gam<double>(const VolArgs& A) { return A.gamma; }
 template <> __device__ __forceinline__ float par_gam<float>(const VolArgs& A) { return A.gammaf; }
+
+template <typename R> __device__ __forceinline__ const R* refG_of(const VolArgs& A);
+template <> __device__ __forceinline__ const double* refG_of<double>(const VolArgs& A) { return A.refG; }
+template <> __device__ __forceinline__ const float* refG_of<float>(const VolArgs& A) { return A.refG32; }
+template <typename R> __device__ __forceinline__ const R* refH_of(const VolArgs& A);
+template <> __device__ __forceinline__ const double* refH_of<double>(const VolArgs& A) { return A.refH; }
+template <> __device__ __forceinline__ const float* refH_of<float>(const VolArgs& A) { return A.refH32; }
+template <typename R> __device__ __forceinline__ const R* metric_of(const VolArgs& A);
+template <> __device__ __forceinline__ const double* metric_of<double>(const VolArgs& A) { return A.metric; }
+template <> __device__ __forceinline__ const float* metric_of<float>(const VolArgs& A) { return A.metric32; }
+
+// Reference-state row of node (column line hm, level kz): per level on box
+// meshes, at the node's own height on warped ones.
+template <typename R, bool W>
+__device__ __forceinline__ const R* ref_row(const VolArgs& A, int hm, int kz) {
+  if (!W) return ref_of<R>(A) + (long long)kz * kRef;
+  if (hm >= 0) return refG_of<R>(A) + ((long long)hm * A.NZ + kz) * kRef;
+  return refH_of<R>(A) + ((long long)(-1 - hm) * A.NZ + kz) * kRef;
+}
 
 template <typename R> __device__ __forceinline__ R r_log1p(R x);
 template <> __device__ __forceinline__ double r_log1p<double>(double x) { return log1p(x); }
@@ -165,7 +194,14 @@ __device__ __forceinline__ void gather_node(const VolArgs& A, int hm, int kz, R 
   }
 }
 
-template <int N, int EQ, typename R>
+// W: warped layers.  The weak fluxes are then the contravariant ones,
+// J grad xi_i . F, with (per node, hx, hy of the column and z_xi, z_eta,
+// z_zeta from the metric table)
+//   J grad xi = (hy/2 z_zeta, 0, 0), J grad eta = (0, hx/2 z_zeta, 0),
+//   J grad zeta = (-hy/2 z_xi, -hx/2 z_eta, hx hy/4), J = hx hy z_zeta / 4,
+// and the strong derivatives of the paper's set d/dx = 2/hx (d/dxi - z_xi/z_zeta d/dzeta),
+// d/dy = 2/hy (d/deta - z_eta/z_zeta d/dzeta), d/dz = 1/z_zeta d/dzeta.
+template <int N, int EQ, typename R, bool W = false>
 __global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
 volume_column(const VolArgs A) {
   constexpr int n1 = N + 1, Nq = n1 * n1, P = n1 * n1 * n1;
@@ -214,15 +250,30 @@ volume_column(const VolArgs A) {
 
   for (int k = 0; k < A.nz; ++k) {
     const R hk = hz_of<R>(A)[k];
-    const R sx = sx1 * hk, sy = sy1 * hk, wJ = wJ1 * hk, gz = two / hk;
+    R sx = sx1 * hk, sy = sy1 * hk, wJ = wJ1 * hk, gz = two / hk;
     const int kz = k * N + c;
     R S[kFields] = {0, 0, 0, 0, 0};
     R pw[5] = {0, 0, 0, 0, 0};  // EQ 1: u, v, w, rho, rho' kept for the strong terms
     R th0dz = 0;
+    R cxw = 0, cyw = 0;         // W: z-direction weights of the x and y fluxes
+    R rzx = 0, rzy = 0;         // W: z_xi / z_zeta, z_eta / z_zeta
+    if (W && act) {
+      const R* mt = metric_of<R>(A) + ((((long long)col * Nq + ab) * A.nz + k) * n1 + c) * 3;
+      const R zx = mt[0], zy = mt[1], zz = mt[2];
+      const R hx = geo[0], hy = geo[1];
+      sx = (R)0.5 * hy * zz;               // J grad xi . e_x
+      sy = (R)0.5 * hx * zz;               // J grad eta . e_y
+      cxw = -(R)0.5 * hy * zx * wi * wj;   // weighted J grad zeta . e_x
+      cyw = -(R)0.5 * hx * zy * wi * wj;   // weighted J grad zeta . e_y
+      wJ = wi * wj * wc * geo[6] * zz;     // w J, geo[6] = hx hy / 4
+      gz = (R)1 / zz;
+      rzx = zx / zz;
+      rzy = zy / zz;
+    }
     if (act) {
       R v[kFields];
       gather_node<N, R>(A, hm, kz, v);
-      const R* rf = refR + (long long)kz * kRef;
+      const R* rf = ref_row<R, W>(A, hm, kz);
       const R p0 = rf[2], rho0 = rf[3], rt0 = rf[4], inv_rt0 = rf[6];
       const R rp = v[0];
       const R rho = rho0 + rp;
@@ -233,11 +284,23 @@ volume_column(const VolArgs A) {
         const R pp = p0 * r_expm1<R>(gam * r_log1p<R>(Tp * inv_rt0));
         const R rt = rt0 + Tp;
         const R ax = wj * wc * sx, ay = wi * wc * sy, az = wi * wj * sz;
-        sF[0][t] = U * ax;            sF[1][t] = V * ay;            sF[2][t] = W * az;
-        sF[3][t] = (U * u + pp) * ax; sF[4][t] = U * vv * ay;       sF[5][t] = U * w * az;
-        sF[6][t] = V * u * ax;        sF[7][t] = (V * vv + pp) * ay; sF[8][t] = V * w * az;
-        sF[9][t] = W * u * ax;        sF[10][t] = W * vv * ay;      sF[11][t] = (W * w + pp) * az;
-        sF[12][t] = rt * u * ax;      sF[13][t] = rt * vv * ay;     sF[14][t] = rt * w * az;
+        if (!W) {
+          sF[0][t] = U * ax;            sF[1][t] = V * ay;            sF[2][t] = W * az;
+          sF[3][t] = (U * u + pp) * ax; sF[4][t] = U * vv * ay;       sF[5][t] = U * w * az;
+          sF[6][t] = V * u * ax;        sF[7][t] = (V * vv + pp) * ay; sF[8][t] = V * w * az;
+          sF[9][t] = W * u * ax;        sF[10][t] = W * vv * ay;      sF[11][t] = (W * w + pp) * az;
+          sF[12][t] = rt * u * ax;      sF[13][t] = rt * vv * ay;     sF[14][t] = rt * w * az;
+        } else {
+          const R Fx[kFields] = {U, U * u + pp, V * u, W * u, rt * u};
+          const R Fy[kFields] = {V, U * vv, V * vv + pp, W * vv, rt * vv};
+          const R Fz[kFields] = {W, U * w, V * w, W * w + pp, rt * w};
+#pragma unroll
+          for (int fl = 0; fl < kFields; ++fl) {
+            sF[3 * fl + 0][t] = Fx[fl] * ax;
+            sF[3 * fl + 1][t] = Fy[fl] * ay;
+            sF[3 * fl + 2][t] = Fz[fl] * az + Fx[fl] * cxw + Fy[fl] * cyw;
+          }
+        }
         S[1] = wJ * (fc * V);
         S[2] = wJ * (-fc * U);
         S[3] = wJ * (-rp * g);
@@ -250,6 +313,7 @@ volume_column(const VolArgs A) {
         sF[0][t] = rho * u * ax;
         sF[1][t] = rho * vv * ay;
         sF[2][t] = rho * w * az;
+        if (W) sF[2][t] += rho * u * cxw + rho * vv * cyw;
         sF[3][t] = u;
         sF[4][t] = vv;
         sF[5][t] = w;
@@ -294,8 +358,13 @@ volume_column(const VolArgs A) {
             ay_ += Dwj[m] * sF[3 + qv][i + n1 * m + Nq * c];
             az_ += Dwc[m] * sF[3 + qv][i + n1 * j + Nq * m];
           }
-          dq[qv][0] = ax_ * gx;
-          dq[qv][1] = ay_ * gy;
+          if (W) {
+            dq[qv][0] = (ax_ - rzx * az_) * gx;
+            dq[qv][1] = (ay_ - rzy * az_) * gy;
+          } else {
+            dq[qv][0] = ax_ * gx;
+            dq[qv][1] = ay_ * gy;
+          }
           dq[qv][2] = az_ * gz;
         }
         const R u = pw[0], vv = pw[1], w = pw[2], inv = pw[3], rp = pw[4];
@@ -365,6 +434,7 @@ struct DssArgs {
   const void* Minv_h;     // double or float
   const void* Minv_z;
   const int4* qt_rec_unit;  // FP64 form: unit-weight Q_h^T records
+  const void* Minv_g;       // warped layers: inverse lumped mass per node (double or float), else null
   const double* qn;
   const double* qs;
   double* out;
@@ -422,7 +492,7 @@ __global__ void __launch_bounds__(256) dss_stage_fp64(const DssArgs A) {
 #pragma unroll
     for (int fl = 0; fl < kFields; ++fl)
       if (MODE >= 1) qsv[fl] = __ldg(A.qs + fl * NGl + gidx);
-    const double s = __ldg(mh + h) * s_cmz[kz];
+    const double s = A.Minv_g ? cdt * __ldg((const double*)A.Minv_g + gidx) : __ldg(mh + h) * s_cmz[kz];
     const bool lid = (kz == 0) || (kz == (int)NZ - 1);
     double acc[kFields];
     const int4 r = __ldg(A.qt_rec_unit + h);
@@ -483,7 +553,7 @@ __global__ void __launch_bounds__(256) dss_stage_mixed(const DssArgs A) {
     const long long h = gidx / A.NZ;
     const int kz = (int)(gidx - h * A.NZ);
     const int beg = __ldg(A.qt_ptr + h), end = __ldg(A.qt_ptr + h + 1);
-    const float s = cdt * (__ldg(mh + h) * __ldg(mz + kz));
+    const float s = A.Minv_g ? cdt * __ldg((const float*)A.Minv_g + gidx) : cdt * (__ldg(mh + h) * __ldg(mz + kz));
     const bool lid = (kz == 0) || (kz == A.NZ - 1);
     float acc[kFields] = {0, 0, 0, 0, 0};
     for (int e = beg; e < end; ++e) {
@@ -524,7 +594,10 @@ static void launch_volume(const VolArgs& A, cudaStream_t st) {
   constexpr int P = (N + 1) * (N + 1) * (N + 1);
   constexpr int nt = (P + 31) / 32 * 32;
   ProfScope ps(sizeof(R) == 8 ? "volume_fp64" : "volume_mixed", st);
-  volume_column<N, EQ, R><<<A.Ncol, nt, 0, st>>>(A);
+  if (A.metric)
+    volume_column<N, EQ, R, true><<<A.Ncol, nt, 0, st>>>(A);
+  else
+    volume_column<N, EQ, R><<<A.Ncol, nt, 0, st>>>(A);
 }
 
 template <int N>
@@ -626,6 +699,32 @@ __device__ __forceinline__ void node_terms(const VolArgs& A, const float (&v)[kF
   o.fz[2] = V * w * az;
   o.fz[3] = (W * w + pp) * az;
   o.fz[4] = rt * w * az;
+  o.su = wJ * (A.ff * V);
+  o.sv = wJ * (-A.ff * U);
+  o.sw = wJ * (-rp * A.gf);
+}
+
+// The same on warped layers: the reference row comes with the node (its own
+// height), and the weak fluxes are the contravariant ones (the z-direction
+// flux takes the x and y fluxes with the weights cx, cy of J grad zeta).
+__device__ __forceinline__ void node_terms_w(const VolArgs& A, const float (&v)[kFields], const float4 ra,
+                                             const float ax, const float ay, const float az, const float cx,
+                                             const float cy, const float wJ, NodeTerms& o) {
+  const float p0 = ra.x, rho0 = ra.y, rt0 = ra.z, inv_rt0 = ra.w;
+  const float rp = v[0], U = v[1], V = v[2], W = v[3], Tp = v[4];
+  const float inv = __frcp_rn(rho0 + rp);
+  const float u = U * inv, vv = V * inv, w = W * inv;
+  const float pp = p0 * pow1p_m1(Tp * inv_rt0, A.bin, A.gammaf);
+  const float rt = rt0 + Tp;
+  const float Fx[kFields] = {U, U * u + pp, V * u, W * u, rt * u};
+  const float Fy[kFields] = {V, U * vv, V * vv + pp, W * vv, rt * vv};
+  const float Fz[kFields] = {W, U * w, V * w, W * w + pp, rt * w};
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) {
+    o.fx[f] = Fx[f] * ax;
+    o.fy[f] = Fy[f] * ay;
+    o.fz[f] = fmaf(Fy[f], cy, fmaf(Fx[f], cx, Fz[f] * az));
+  }
   o.su = wJ * (A.ff * V);
   o.sv = wJ * (-A.ff * U);
   o.sw = wJ * (-rp * A.gf);
@@ -942,7 +1041,7 @@ __device__ __forceinline__ void smag_phases(const VolArgs& A, float* smem, const
 // Body shared by the single-mesh kernel (one CTA per column) and the batched
 // persistent kernel.  Threads t >= KL (N+1)^2 of a larger CTA take part in
 // the barriers only.
-template <int N, int KL, bool SMAG = false>
+template <int N, int KL, bool SMAG = false, bool W = false>
 __device__ __forceinline__ void lines_body(const VolArgs& A, const int col, float* smem, const int t) {
   constexpr int n1 = N + 1, Nq = n1 * n1;
   constexpr int LW = lines_lw<N>(), LS = lines_ls<N, KL>();
@@ -987,7 +1086,20 @@ __device__ __forceinline__ void lines_body(const VolArgs& A, const int col, floa
         load_node<N>(A, hm, kz, v);
         const float wc = c_wf[N][c];
         NodeTerms T;
-        node_terms(A, v, kz, wj * wc * sx * hk, wi * wc * sy * hk, wi * wj * sz, wi * wj * wc * J * hk, T);
+        float wJn = wi * wj * wc * J * hk;
+        if constexpr (!W) {
+          node_terms(A, v, kz, wj * wc * sx * hk, wi * wc * sy * hk, wi * wj * sz, wJn, T);
+        } else {
+          // warped layers: metric of the node and the reference state at its height
+          const float* mt = A.metric32 + ((((long long)col * Nq + ab) * A.nz + k) * n1 + c) * 3;
+          const float zx = __ldg(mt), zy = __ldg(mt + 1), zz = __ldg(mt + 2);
+          const float hx = geo[0], hy = geo[1];
+          const float4 ra = hm >= 0 ? __ldg(A.ref4G + (long long)hm * A.NZ + kz)
+                                    : __ldg(A.ref4H + (long long)(-1 - hm) * A.NZ + kz);
+          wJn = wi * wj * wc * sz * zz;
+          node_terms_w(A, v, ra, wj * wc * 0.5f * hy * zz, wi * wc * 0.5f * hx * zz, wi * wj * sz,
+                       -wi * wj * 0.5f * hy * zx, -wi * wj * 0.5f * hx * zy, wJn, T);
+        }
 #pragma unroll
         for (int f = 0; f < kFields; ++f) {
           zX[f * n1 + c] = T.fx[f];
@@ -1002,7 +1114,7 @@ __device__ __forceinline__ void lines_body(const VolArgs& A, const int col, floa
         rz[3][c] += T.sw;
         if (A.spg32) {
           // absorbing layer (Sec. 4): -R(z) q' at the node, weighted like the sources
-          const float wR = (wi * wj * wc * J * hk) * __ldg(A.spg32 + kz);
+          const float wR = wJn * __ldg(A.spg32 + kz);
 #pragma unroll
           for (int f = 0; f < kFields; ++f) rz[f][c] = fmaf(-wR, v[f], rz[f][c]);
         }
@@ -1111,6 +1223,14 @@ __global__ void __launch_bounds__(KL * (N + 1) * (N + 1), MB)
 volume_lines_mixed(const VolArgs A) {
   extern __shared__ __align__(16) float smem[];
   lines_body<N, KL>(A, blockIdx.x, smem, threadIdx.x);
+}
+
+// The same on warped layers (non-affine elements).
+template <int N, int KL, int MB>
+__global__ void __launch_bounds__(KL * (N + 1) * (N + 1), MB)
+volume_lines_warp(const VolArgs A) {
+  extern __shared__ __align__(16) float smem[];
+  lines_body<N, KL, false, true>(A, blockIdx.x, smem, threadIdx.x);
 }
 
 // The same with the horizontal Smagorinsky stress added (N = 4 variants).
@@ -1411,11 +1531,15 @@ static int launch_lines(const VolArgs& A, cudaStream_t st) {
   static DeviceOnce attr;
   int rc = device_once(attr, [&] {
     SEM_CUDA_TRY(cudaFuncSetAttribute(volume_lines_mixed<N, KL, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    SEM_CUDA_TRY(cudaFuncSetAttribute(volume_lines_warp<N, KL, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     return SEM_OK;
   });
   if (rc) return rc;
   ProfScope ps("volume_mixed", st);
-  volume_lines_mixed<N, KL, MB><<<A.Ncol, KL * (N + 1) * (N + 1), sm, st>>>(A);
+  if (A.metric32)
+    volume_lines_warp<N, KL, MB><<<A.Ncol, KL * (N + 1) * (N + 1), sm, st>>>(A);
+  else
+    volume_lines_mixed<N, KL, MB><<<A.Ncol, KL * (N + 1) * (N + 1), sm, st>>>(A);
   return SEM_OK;
 }
 
@@ -1465,6 +1589,8 @@ static int pencil_default(int N, int nz) {
 static int launch_pencil_n(const VolArgs& A, int N, int nz, cudaStream_t st, int variant = -1,
                            bool smag = false) {
   if (variant < 0 || variant >= kNumPencil || kPencil[variant].N != N) variant = pencil_default(N, nz);
+  // warped layers: the line-exchange kernels only
+  if (A.metric32 && variant >= 0 && kPencil[variant].kind != 1) variant = pencil_default(N, nz);
   if (variant < 0) return fail(SEM_ERR_UNSUPPORTED, "order N not compiled");
   if (smag) return kPencil[variant].launch_smag(A, st);
   return kPencil[variant].launch(A, st);
@@ -1515,6 +1641,15 @@ static VolArgs make_vol_args(Mesh& m, const sem_params& p, const void* q, bool m
   A.ref4 = reinterpret_cast<const float4*>(D.ref32 + (size_t)m.NZ * kRef);
   A.spg32 = nullptr;
   A.status = D.status;
+  const bool w = m.warped();
+  A.metric = w ? D.metric : nullptr;
+  A.metric32 = w ? D.metric32 : nullptr;
+  A.refG = D.refG;
+  A.refH = D.refH;
+  A.refG32 = D.refG32;
+  A.refH32 = D.refH32;
+  A.ref4G = reinterpret_cast<const float4*>(D.ref4G);
+  A.ref4H = reinterpret_cast<const float4*>(D.ref4H);
   A.Ncol = (int)m.Ncol();
   A.nz = m.nz;
   A.NZ = m.NZ;
@@ -1580,6 +1715,7 @@ struct IncArgs {
   const float4* qt_rec_w;
   const float* Minv_h;
   const float* Minv_z;
+  const float* Minv_g;  // warped layers: inverse lumped mass per node, else null
   const float* q32;   // mirror of q_n
   float* d;           // increment, updated in place
   float* qs32;        // stages 0, 1: mirror of the next stage state
@@ -1606,7 +1742,7 @@ __device__ __forceinline__ void inc_body(const IncArgs& A, const int gidx, int& 
     if (STAGE == 1) q32v[fl] = __ldg(A.q32 + o);
     if (STAGE == 2) qv[fl] = A.q[o];
   }
-  const float s = A.cdt * (__ldg(A.Minv_h + h) * __ldg(A.Minv_z + kz));
+  const float s = A.Minv_g ? A.cdt * __ldg(A.Minv_g + gidx) : A.cdt * (__ldg(A.Minv_h + h) * __ldg(A.Minv_z + kz));
   const bool lid = (kz == 0) || (kz == A.NZ - 1);
   float acc[kFields] = {0, 0, 0, 0, 0};
   // Q_h^T gather, in the order of the CSR lists: from the compact record
@@ -1661,6 +1797,8 @@ int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float
                       cudaStream_t st) {
   int rc = upload_basis_constants();
   if (rc) return rc;
+  if (m.warped() && physics_on(p))
+    return fail(SEM_ERR_UNSUPPORTED, "warped layers: the stress, absorbing layer and heating are not built");
   DeviceTables& D = *m.dev;
   float* d = work32;
   float* qs32 = work32 + (size_t)kFields * m.NG;
@@ -1684,6 +1822,7 @@ int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float
     B.qt_rec_w = reinterpret_cast<const float4*>(D.qt_rec_w);
     B.Minv_h = D.Minv_h32;
     B.Minv_z = D.Minv_z32;
+    B.Minv_g = m.warped() ? D.Minv_g32 : nullptr;
     B.q32 = q32;
     B.d = d;
     B.qs32 = qs32;
@@ -1721,6 +1860,7 @@ int autotune_pencil(Mesh& m, const sem_params& p, const float* q32, int reps, se
   out->n_variants = 0;
   for (int v = 0; v < kNumPencil && out->n_variants < SEM_TUNE_MAX; ++v) {
     if (kPencil[v].N != m.N) continue;
+    if (m.warped() && kPencil[v].kind != 1) continue;   // warped layers: line exchange only
     for (int w = 0; w < 2; ++w) kPencil[v].launch(A, st);
     cudaEventRecord(e0, st);
     for (int r = 0; r < reps; ++r) kPencil[v].launch(A, st);
@@ -1761,6 +1901,7 @@ int select_pencil(Mesh& m, int row) {
   int k = 0;
   for (int v = 0; v < kNumPencil && k < SEM_TUNE_MAX; ++v) {
     if (kPencil[v].N != m.N) continue;
+    if (m.warped() && kPencil[v].kind != 1) continue;   // the rows sem_autotune lists
     if (k == row) {
       m.pencil_variant = v;
       return SEM_OK;
@@ -1913,6 +2054,11 @@ int batch_create(Mesh* const* meshes, int n, void** out) {
   b->big.assign(n, 0);
   for (int k = 0; k < n; ++k) {
     Mesh& m = *meshes[k];
+    if (m.warped()) {
+      batch_free(b);
+      delete b;
+      return fail(SEM_ERR_UNSUPPORTED, "batched steps of warped meshes are not built");
+    }
     if ((rc = ensure_device(m))) { batch_free(b); delete b; return rc; }
     Ns[k] = m.N;
     // meshes with enough columns to fill the GPU keep their own tuned
@@ -2120,6 +2266,7 @@ int batch_step_mixed(void* h, const sem_params& p, double* const* q, float* cons
         B.qt_rec_w = reinterpret_cast<const float4*>(D.qt_rec_w);
         B.Minv_h = D.Minv_h32;
         B.Minv_z = D.Minv_z32;
+        B.Minv_g = nullptr;   // batched meshes are box meshes
         B.q32 = q32[k];
         B.d = work32[k];
         B.qs32 = qs32;
@@ -2218,6 +2365,8 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
   int rc = upload_basis_constants();
   if (rc) return rc;
   if (m.NG * kFields >= (1ll << 31)) return fail(SEM_ERR_ARG, "mesh too large for 32-bit node indexing");
+  if (m.warped() && physics_on(p))
+    return fail(SEM_ERR_UNSUPPORTED, "warped layers: the stress, absorbing layer and heating are not built");
   DeviceTables& D = *m.dev;
   const bool mixed = p.precision == SEM_PREC_MIXED;
   const float* qs32 = s.qs32;
@@ -2253,6 +2402,7 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
   B.Minv_h = mixed ? (const void*)D.Minv_h32 : (const void*)D.Minv_h;
   B.Minv_z = mixed ? (const void*)D.Minv_z32 : (const void*)D.Minv_z;
   B.qt_rec_unit = reinterpret_cast<const int4*>(D.qt_rec_unit);
+  B.Minv_g = !m.warped() ? nullptr : (mixed ? (const void*)D.Minv_g32 : (const void*)D.Minv_g);
   B.qn = s.qn;
   B.qs = s.qs;
   B.out = s.out;

@@ -122,10 +122,20 @@ struct Mesh {
   double hy(int l) const { return Ly / (double)((long long)ny << l); }
   std::vector<double> zf;            // [nz + 1] layer faces
   double hz(int k) const { return zf[k + 1] - zf[k]; }
+  // warped layers (warp.cpp): amplitude (m) and wave numbers; A = 0: boxes
+  double warp_A = 0.0;
+  int warp_kx = 1, warp_ky = 1;
+  bool warped() const { return warp_A != 0.0; }
+  std::vector<double> zG;            // [NG] node heights
+  std::vector<double> zH;            // [Nhang][NZ] heights of the hanging lines' nodes
+  std::vector<double> metric;        // [Ncol][Nq][nz][N+1][3] z_xi, z_eta, z_zeta
+  std::vector<double> Mg;            // [NG] lumped mass per global node
   int NZr() const { return (NZ + 3) & ~3; }  // level stride of the column residual scratch
 };
 
 int build_mesh(Mesh& m);                       // numbering from leaves (host)
+int build_warp(Mesh& m);                       // warped-layer geometry (warp.cpp)
+double warp_height(const Mesh& m, double x, double y, double zeta);
 int check_leaves(const Mesh& m);               // tiling + balance
 int adapt_leaves(const Mesh& old, const int8_t* flags, std::vector<Leaf>& out,
                  std::vector<Origin>& origin);
@@ -182,6 +192,18 @@ struct DeviceTables {
   // the params the ref tables were built with
   double ref_key[8] = {0};
   bool ref_valid = false;
+  // warped layers: per-node tables (null on box meshes)
+  double* zG = nullptr;         // [NG] node heights
+  double* metric = nullptr;     // [Ncol][Nq][nz][N+1][3] z_xi, z_eta, z_zeta
+  float* metric32 = nullptr;
+  double* Minv_g = nullptr;     // [NG] inverse lumped mass per node
+  float* Minv_g32 = nullptr;
+  double* refG = nullptr;       // [NG][kRef] reference state at each node's height
+  double* refH = nullptr;       // [Nhang][NZ][kRef] ... at each hanging-line node's height
+  float* refG32 = nullptr;      // float32 copies
+  float* refH32 = nullptr;
+  float* ref4G = nullptr;       // [NG][4] packed p0, rho0, (rho theta)0, 1/(rho theta)0
+  float* ref4H = nullptr;       // [Nhang][NZ][4]
   // absorbing-layer rate R(z) per level (float64 and float32) and its key
   double* spg = nullptr;
   float* spg32 = nullptr;

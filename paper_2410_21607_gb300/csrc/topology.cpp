@@ -470,6 +470,7 @@ int build_mesh(Mesh& m) {
   m.zk[m.NZ - 1] = m.Lz;
   for (long long h = 0; h < m.NH; ++h)
     if (!(m.Mh[h] > 0.0)) return fail(SEM_ERR_TOPOLOGY, "non-positive lumped mass");
+  if (m.warped()) return build_warp(m);
   return SEM_OK;
 }
 

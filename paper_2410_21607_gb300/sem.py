@@ -50,7 +50,8 @@ class MeshDesc(C.Structure):
                 ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("N", C.c_int),
                 ("periodic_x", C.c_int), ("periodic_y", C.c_int), ("lvl_max", C.c_int),
                 ("n_leaves", C.c_int), ("leaves", C.POINTER(C.c_int)),
-                ("z_faces", C.POINTER(C.c_double))]
+                ("z_faces", C.POINTER(C.c_double)),
+                ("warp_amplitude", C.c_double), ("warp_kx", C.c_int), ("warp_ky", C.c_int)]
 
 
 class MeshInfo(C.Structure):
@@ -233,8 +234,11 @@ class Mesh:
 
 
 def sem_mesh_create(Lx, Ly, Lz, nx, ny, nz, N, leaves=None, periodic=(True, True), lvl_max=0,
-                    z_faces=None):
-    d = MeshDesc(Lx, Ly, Lz, nx, ny, nz, N, int(periodic[0]), int(periodic[1]), lvl_max, 0, None, None)
+                    z_faces=None, warp=None):
+    """warp = (amplitude, kx, ky): warped layers (sem_mesh_desc), None: boxes."""
+    wa, wx, wy = (0.0, 1, 1) if warp is None else (float(warp[0]), int(warp[1]), int(warp[2]))
+    d = MeshDesc(Lx, Ly, Lz, nx, ny, nz, N, int(periodic[0]), int(periodic[1]), lvl_max, 0, None, None,
+                 wa, wx, wy)
     keep = keep_z = None
     if leaves is not None and len(leaves):
         keep = np.ascontiguousarray(np.asarray(leaves, dtype=np.int32).reshape(-1, 3))

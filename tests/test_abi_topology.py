@@ -212,3 +212,26 @@ def test_one_time_setup_runs_once_per_device(sem):
     assert sem.sem_selftest_device_once(64, 4) == [1] * 64
     with pytest.raises(sem.SemError):
         sem.sem_selftest_device_once(65, 1)
+
+
+@pytest.mark.parametrize("nonconforming", [False, True])
+def test_warped_mesh_host_tables_match_oracle(sem, nonconforming):
+    """Warped layers: the library's node heights (coordinates) and per-node
+    lumped mass equal the oracle's isoparametric construction."""
+    leaves = two_level_leaves() if nonconforming else None
+    m = sem.sem_mesh_create(300e3, 300e3, 12e3, 4, 4, 2, 4, leaves=leaves, warp=(700.0, 1, 2))
+    o = om.OracleMesh(300e3, 300e3, 12e3, 4, 4, 2, 4, leaves=leaves, warp=(700.0, 1, 2))
+    xyz = sem.sem_mesh_coords_host(m)
+    perm = node_perm(xyz, o.XG)
+    np.testing.assert_allclose(xyz.T, o.XG[perm], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(sem.sem_mesh_mass_host(m), o.M[perm], rtol=1e-13)
+    assert np.abs(xyz[2] - o.XG_box[perm, 2]).max() > 300.0
+
+
+def test_warped_mesh_refusals(sem):
+    with pytest.raises(sem.SemError):        # folds the elements
+        sem.sem_mesh_create(300e3, 300e3, 12e3, 4, 4, 2, 4, warp=(6000.0, 1, 1))
+    m = sem.sem_mesh_create(300e3, 300e3, 12e3, 4, 4, 2, 4, warp=(700.0, 1, 1), lvl_max=2)
+    with pytest.raises(sem.SemError) as e:   # adaptation of warped meshes is not built
+        sem.sem_transfer_plan(m, np.ones(m.Ne, dtype=np.int8))
+    assert e.value.code == sem.SEM_ERR_UNSUPPORTED

@@ -34,10 +34,10 @@ def sem():
 PRM = refstate.Params()
 
 
-def make_pair(sem, L, Lz, nx, nz, N, leaves=None, periodic=(True, True), lvl_max=3, z_faces=None):
+def make_pair(sem, L, Lz, nx, nz, N, leaves=None, periodic=(True, True), lvl_max=3, z_faces=None, warp=None):
     m = sem.sem_mesh_create(L, L, Lz, nx, nx, nz, N, leaves=leaves, periodic=periodic, lvl_max=lvl_max,
-                            z_faces=z_faces)
-    o = om.OracleMesh(L, L, Lz, nx, nx, nz, N, leaves=leaves, periodic=periodic, z_faces=z_faces)
+                            z_faces=z_faces, warp=warp)
+    o = om.OracleMesh(L, L, Lz, nx, nx, nz, N, leaves=leaves, periodic=periodic, z_faces=z_faces, warp=warp)
     xyz = sem.sem_mesh_coords_host(m)
     perm = node_perm(xyz, o.XG)
     return m, o, xyz.T, perm

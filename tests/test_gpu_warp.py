@@ -1,0 +1,163 @@
+"""GPU parity on warped layers (non-affine elements): the right-hand side,
+the stages and steps of both forms through the C ABI against the oracle's
+general isoparametric discretisation (oracle/mesh.py, warp), on conforming
+and non-conforming meshes.
+
+Tolerances as in tests/test_gpu_parity.py: float64 1e-12 (tendencies), mixed
+form 1e-4 (tendencies, states and their change over the steps).  The metric
+terms are float64 tables on both forms' inputs (the mixed form reads them
+rounded once to float32).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import adapt, refstate, rhs as orhs, rk as ork  # noqa: E402
+from synth.vortex import random_state, vortex_state  # noqa: E402
+from tests.helpers import group_rel_l2  # noqa: E402
+from tests.test_gpu_parity import dev, full_fields, host, increment_err, make_pair  # noqa: E402
+from tests.test_oracle_mesh import two_level_leaves  # noqa: E402
+
+PRM = refstate.Params()
+WMESH = {
+    "warped-4x4x2-N4": dict(L=300e3, Lz=12e3, nx=4, nz=2, N=4, warp=(700.0, 1, 1)),
+    "warped-twolevel-N4": dict(L=300e3, Lz=12e3, nx=4, nz=2, N=4, leaves=two_level_leaves(), warp=(700.0, 1, 2)),
+    "warped-twolevel-17-layers-N4": dict(L=300e3, Lz=24e3, nx=4, nz=17, N=4, leaves=two_level_leaves(),
+                                         warp=(400.0, 2, 1)),
+    "warped-twolevel-N3": dict(L=300e3, Lz=12e3, nx=4, nz=3, N=3, leaves=two_level_leaves(), warp=(700.0, 1, 1)),
+}
+
+
+@pytest.fixture(scope="module")
+def sem():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_21607_gb300 import build
+    build.build()
+    from paper_2410_21607_gb300 import sem as s
+    return s
+
+
+@pytest.mark.parametrize("name", list(WMESH))
+@pytest.mark.parametrize("eqset", ["C", "NC"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_warped_rhs_matches_oracle(sem, name, eqset, prec):
+    m, o, X, perm = make_pair(sem, **WMESH[name])
+    q_o = random_state(o.XG, o.Lz, 51, eqset)
+    T_o = orhs.rhs(o, q_o, PRM, eqset)
+    p = sem.sem_params_default(eqset=0 if eqset == "C" else 1, precision=prec)
+    q = dev(q_o[:, perm])
+    out = torch.full_like(q, float("nan"))
+    sem.sem_rhs(m, p, q, out)
+    err = group_rel_l2(host(out), T_o[:, perm])
+    assert np.all(err <= (1e-12 if prec == 0 else 1e-4)), err
+    assert sem.sem_status(m) == 0
+
+
+def test_warped_every_line_variant_matches_oracle(sem):
+    """On warped meshes the autotuner lists the line-exchange variants only;
+    each gives the mixed tendency within 1e-4 (several layer chunks)."""
+    m, o, X, perm = make_pair(sem, **WMESH["warped-twolevel-17-layers-N4"])
+    q_o = random_state(o.XG, o.Lz, 52)
+    T_o = orhs.rhs(o, q_o, PRM)
+    p = sem.sem_params_default(precision=sem.SEM_PREC_MIXED)
+    q = dev(q_o[:, perm])
+    q32 = torch.empty(q.shape, dtype=torch.float32, device="cuda")
+    sem.sem_mirror(m, q, q32)
+    rows, _ = sem.sem_autotune(m, p, q32, 1)
+    assert len(rows) >= 2 and {r[3] for r in rows} == {1}
+    for row in range(len(rows)):
+        sem.sem_autotune_select(m, row)
+        out = torch.full_like(q, float("nan"))
+        sem.sem_rhs(m, p, q, out)
+        assert np.all(group_rel_l2(host(out), T_o[:, perm]) <= 1e-4), rows[row]
+
+
+@pytest.mark.parametrize("name", ["warped-4x4x2-N4", "warped-twolevel-N4"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_warped_steps_match_oracle(sem, name, prec):
+    """Five SSP-RK3 steps of 1 s from the balanced vortex: the float64 form
+    (sem_step) within 1e-10 of the oracle's steps, the mixed increment form
+    (sem_step_mixed) within 1e-4 in the full fields and in the change."""
+    m, o, X, perm = make_pair(sem, **WMESH[name])
+    q_o = vortex_state(o.XG, o.Lz)
+    q_ref = q_o.copy()
+    for _ in range(5):
+        q_ref = ork.rk_step(o, PRM, q_ref, 1.0)
+    q = dev(q_o[:, perm])
+    p = sem.sem_params_default(precision=prec)
+    if prec == 0:
+        w1, w2 = torch.empty_like(q), torch.empty_like(q)
+        for _ in range(5):
+            sem.sem_step(m, p, q, w1, w2, 1.0)
+    else:
+        q32 = torch.empty(q.shape, dtype=torch.float32, device="cuda")
+        work = torch.empty((10, m.NG), dtype=torch.float32, device="cuda")
+        sem.sem_mirror(m, q, q32)
+        for _ in range(5):
+            sem.sem_step_mixed(m, p, q, q32, work, 1.0)
+    got = host(q)
+    z = X[:, 2]
+    tol = 1e-10 if prec == 0 else 1e-4
+    assert np.all(group_rel_l2(full_fields(got, z), full_fields(q_ref[:, perm], z)) <= tol)
+    assert np.all(increment_err(got, q_o[:, perm], q_ref[:, perm]) <= tol)
+    assert sem.sem_status(m) == 0
+
+
+def test_warped_rest_state_mass_and_coordinates(sem):
+    m, o, X, perm = make_pair(sem, **WMESH["warped-twolevel-N4"])
+    M = sem.sem_mesh_mass_host(m)
+    q = dev(random_state(o.XG, o.Lz, 5)[:, perm])
+    out = torch.empty_like(q)
+    for prec in (0, 1):
+        for eq in (0, 1):
+            z0 = torch.zeros_like(q)
+            rest = torch.full_like(q, 7.0)
+            sem.sem_rhs(m, sem.sem_params_default(eqset=eq, precision=prec), z0, rest)
+            assert torch.count_nonzero(rest).item() == 0
+        sem.sem_rhs(m, sem.sem_params_default(precision=prec), q, out)
+        T = host(out)
+        tol = 1e-13 if prec == 0 else 1e-6
+        assert abs(np.sum(M * T[0])) <= tol * np.sum(np.abs(M * T[0]))
+    xyz = torch.empty(3, m.NG, dtype=torch.float64, device="cuda")
+    sem.sem_mesh_coords(m, xyz)
+    assert np.array_equal(host(xyz), sem.sem_mesh_coords_host(m))
+
+
+def test_warped_speed_criterion_and_diagnostics(sem):
+    m, o, X, perm = make_pair(sem, **WMESH["warped-twolevel-N4"])
+    q_o = vortex_state(o.XG, o.Lz)
+    lv = sem.sem_mesh_leaves_host(m)
+    oleaf = {tuple(l): c for c, l in enumerate(o.leaves)}
+    emap = np.array([oleaf[tuple(l)] * o.nz + k for l in lv for k in range(o.nz)])
+    thr = [5.0, 10.0, 15.0]
+    fl_o, cmax_o = adapt.criterion_flags(o, q_o, PRM, thr, 3)
+    p = sem.sem_params_default(thresholds=thr, lvl_max=3)
+    flags = torch.empty(m.Ne, dtype=torch.int8, device="cuda")
+    cmax = torch.empty(m.Ne, dtype=torch.float64, device="cuda")
+    sem.sem_adapt_flags(m, p, dev(q_o[:, perm]), flags, cmax)
+    np.testing.assert_allclose(host(cmax), cmax_o[emap], rtol=1e-14)
+    tie = np.min(np.abs(cmax_o[emap][:, None] - np.array(thr)[None]), axis=1) <= 1e-12 * max(thr)
+    assert np.array_equal(host(flags)[~tie], fl_o[emap][~tie])
+    d = sem.sem_diag(m, p, dev(q_o[:, perm]), 150e3)
+    sp = np.hypot(q_o[1], q_o[2]) / (refstate.reference_state(o.XG[:, 2], PRM)["rho0"] + q_o[0])
+    assert abs(d["max_wind"] - sp.max()) <= 1e-12 * sp.max()
+
+
+def test_warped_refusals(sem):
+    m, o, X, perm = make_pair(sem, **WMESH["warped-4x4x2-N4"])
+    q = dev(random_state(o.XG, o.Lz, 5)[:, perm])
+    out = torch.empty_like(q)
+    for kw in (dict(smag_cs=0.21), dict(sponge_gamma=0.1, sponge_depth=3000.0), dict(heat_q0=1e-3)):
+        with pytest.raises(sem.SemError) as e:
+            sem.sem_rhs(m, sem.sem_params_default(**kw), q, out)
+        assert e.value.code == sem.SEM_ERR_UNSUPPORTED, kw
+    with pytest.raises(sem.SemError) as e:
+        p = sem.sem_params_default(thresholds=[1e-4, 2e-4, 3e-4], lvl_max=3, criterion=[1, 1, 1])
+        sem.sem_adapt_flags(m, p, q, torch.empty(m.Ne, dtype=torch.int8, device="cuda"))
+    assert e.value.code == sem.SEM_ERR_UNSUPPORTED
+    with pytest.raises(sem.SemError) as e:
+        sem.sem_batch_create([m])
+    assert e.value.code == sem.SEM_ERR_UNSUPPORTED
