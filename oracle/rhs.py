@@ -167,3 +167,24 @@ def rhs(mesh, qG, prm, eqset="C"):
     T = R / mesh.M[None, :]
     T[3, mesh.z_bottom | mesh.z_top] = 0.0
     return T
+
+
+def scalar_advection_residual(mesh, phiG, c, form="weak"):
+    """Assembled residual Q^T r of the advection of a scalar, phi_t + div(c phi) = 0
+    with a constant velocity c, in the discretisation of the divergence terms
+    above: "weak" r_l = sum_k w_k J grad psi_l(x_k) . c phi_k (the form the
+    right-hand side uses), or the skew-symmetric split "skew" = (weak +
+    strong) / 2 with the collocated strong term r_l = -w_l J c . grad phi(x_l).
+    Used to study the discrete energy phi^T Q^T r (no lid condition)."""
+    phiL = mesh.to_local(phiG)[0]
+    r = np.zeros_like(phiL)
+    for lev, es, G in mesh.op_groups():
+        W = mesh.wJ[es]
+        f = phiL[es]
+        weak = sum((W * c[d] * f) @ G[d] for d in range(3))
+        if form == "weak":
+            r[es] = weak
+        else:
+            strong = -W * sum(c[d] * (f @ G[d].T) for d in range(3))
+            r[es] = 0.5 * (weak + strong)
+    return mesh.assemble(r[None])[0]

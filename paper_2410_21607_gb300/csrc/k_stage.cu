@@ -157,9 +157,9 @@ template <> __device__ __forceinline__ const float* metric_of<float>(const VolAr
 
 // Reference-state row of node (column line hm, level kz): per level on box
 // meshes, at the node's own height on warped ones.
-template <typename R, bool W>
+template <typename R, bool WARP>
 __device__ __forceinline__ const R* ref_row(const VolArgs& A, int hm, int kz) {
-  if (!W) return ref_of<R>(A) + (long long)kz * kRef;
+  if (!WARP) return ref_of<R>(A) + (long long)kz * kRef;
   if (hm >= 0) return refG_of<R>(A) + ((long long)hm * A.NZ + kz) * kRef;
   return refH_of<R>(A) + ((long long)(-1 - hm) * A.NZ + kz) * kRef;
 }
@@ -201,7 +201,7 @@ __device__ __forceinline__ void gather_node(const VolArgs& A, int hm, int kz, R 
 //   J grad zeta = (-hy/2 z_xi, -hx/2 z_eta, hx hy/4), J = hx hy z_zeta / 4,
 // and the strong derivatives of the paper's set d/dx = 2/hx (d/dxi - z_xi/z_zeta d/dzeta),
 // d/dy = 2/hy (d/deta - z_eta/z_zeta d/dzeta), d/dz = 1/z_zeta d/dzeta.
-template <int N, int EQ, typename R, bool W = false>
+template <int N, int EQ, typename R, bool WARP = false>
 __global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
 volume_column(const VolArgs A) {
   constexpr int n1 = N + 1, Nq = n1 * n1, P = n1 * n1 * n1;
@@ -257,7 +257,7 @@ volume_column(const VolArgs A) {
     R th0dz = 0;
     R cxw = 0, cyw = 0;         // W: z-direction weights of the x and y fluxes
     R rzx = 0, rzy = 0;         // W: z_xi / z_zeta, z_eta / z_zeta
-    if (W && act) {
+    if (WARP && act) {
       const R* mt = metric_of<R>(A) + ((((long long)col * Nq + ab) * A.nz + k) * n1 + c) * 3;
       const R zx = mt[0], zy = mt[1], zz = mt[2];
       const R hx = geo[0], hy = geo[1];
@@ -273,7 +273,7 @@ volume_column(const VolArgs A) {
     if (act) {
       R v[kFields];
       gather_node<N, R>(A, hm, kz, v);
-      const R* rf = ref_row<R, W>(A, hm, kz);
+      const R* rf = ref_row<R, WARP>(A, hm, kz);
       const R p0 = rf[2], rho0 = rf[3], rt0 = rf[4], inv_rt0 = rf[6];
       const R rp = v[0];
       const R rho = rho0 + rp;
@@ -284,7 +284,7 @@ volume_column(const VolArgs A) {
         const R pp = p0 * r_expm1<R>(gam * r_log1p<R>(Tp * inv_rt0));
         const R rt = rt0 + Tp;
         const R ax = wj * wc * sx, ay = wi * wc * sy, az = wi * wj * sz;
-        if (!W) {
+        if (!WARP) {
           sF[0][t] = U * ax;            sF[1][t] = V * ay;            sF[2][t] = W * az;
           sF[3][t] = (U * u + pp) * ax; sF[4][t] = U * vv * ay;       sF[5][t] = U * w * az;
           sF[6][t] = V * u * ax;        sF[7][t] = (V * vv + pp) * ay; sF[8][t] = V * w * az;
@@ -313,7 +313,7 @@ volume_column(const VolArgs A) {
         sF[0][t] = rho * u * ax;
         sF[1][t] = rho * vv * ay;
         sF[2][t] = rho * w * az;
-        if (W) sF[2][t] += rho * u * cxw + rho * vv * cyw;
+        if (WARP) sF[2][t] += rho * u * cxw + rho * vv * cyw;
         sF[3][t] = u;
         sF[4][t] = vv;
         sF[5][t] = w;
@@ -358,7 +358,7 @@ volume_column(const VolArgs A) {
             ay_ += Dwj[m] * sF[3 + qv][i + n1 * m + Nq * c];
             az_ += Dwc[m] * sF[3 + qv][i + n1 * j + Nq * m];
           }
-          if (W) {
+          if (WARP) {
             dq[qv][0] = (ax_ - rzx * az_) * gx;
             dq[qv][1] = (ay_ - rzy * az_) * gy;
           } else {
@@ -1041,7 +1041,7 @@ __device__ __forceinline__ void smag_phases(const VolArgs& A, float* smem, const
 // Body shared by the single-mesh kernel (one CTA per column) and the batched
 // persistent kernel.  Threads t >= KL (N+1)^2 of a larger CTA take part in
 // the barriers only.
-template <int N, int KL, bool SMAG = false, bool W = false>
+template <int N, int KL, bool SMAG = false, bool WARP = false>
 __device__ __forceinline__ void lines_body(const VolArgs& A, const int col, float* smem, const int t) {
   constexpr int n1 = N + 1, Nq = n1 * n1;
   constexpr int LW = lines_lw<N>(), LS = lines_ls<N, KL>();
@@ -1087,7 +1087,7 @@ __device__ __forceinline__ void lines_body(const VolArgs& A, const int col, floa
         const float wc = c_wf[N][c];
         NodeTerms T;
         float wJn = wi * wj * wc * J * hk;
-        if constexpr (!W) {
+        if constexpr (!WARP) {
           node_terms(A, v, kz, wj * wc * sx * hk, wi * wc * sy * hk, wi * wj * sz, wJn, T);
         } else {
           // warped layers: metric of the node and the reference state at its height
