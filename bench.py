@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--gate-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched", default="both", choices=["both", "refined", "unrefined"],
+                    help="which instance sets of the batched workload to run (profiler runs keep "
+                         "the device footprint small with the unrefined one)")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-amr", action="store_true")
     ap.add_argument("--no-physics", action="store_true")
@@ -206,7 +209,7 @@ def cpu_one_thread(n=16):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def batched_measure(sem, torch, steps=10, warmup=3, refine=True):
+def batched_measure(sem, torch, steps=10, warmup=3, refine=True, rates=None):
     """The 16-instance batched workload: one CUDA-graph launch per step over
     all instances (persistent element kernel + gather/increment kernel per
     stage) against stepping the instances one after another."""
@@ -280,14 +283,53 @@ def batched_measure(sem, torch, steps=10, warmup=3, refine=True):
     gate = {"steps": gate_steps, "max_wind_rel_err_max": max(errs), "max_wind_rel_err": errs,
             "how": "each instance, batched mixed steps against its own float64 single-mesh steps",
             "status": sem.sem_batch_status(batch)}
+    # the rate the mix of orders predicts from single-mesh rates per order:
+    # total DOF-updates over the sum of each instance's DOF-updates at its
+    # order's rate
+    expected = None
+    if rates:
+        dofs = [15 * m.Ne * (it.N + 1) ** 3 for m, it in zip(meshes, insts)]
+        expected = sum(dofs) / sum(d / rates[it.N] for d, it in zip(dofs, insts))
     return {"workload": "16 seeded instances, bases 8..48, N 3..6, "
                         + ("0..3 levels" if refine else "unrefined"),
+            "expected_from_order_rates": expected,
             "instances": len(insts), "elements": int(sum(m.Ne for m in meshes)),
             "dof_per_stage": dof, "ms_per_step_graph": ms_graph, "ms_per_step_batched_no_graph": ms_nograph,
             "ms_per_step_sequential": ms_seq,
             "value_graph": dof * 3 / (ms_graph * 1e-3), "value_sequential": dof * 3 / (ms_seq * 1e-3),
             "speedup": ms_seq / ms_graph, "status": status, "gate": gate,
             "launches_per_step_graph": 1, "launches_per_step_sequential": 6 * len(insts)}
+
+
+def order_rates(sem, torch, steps=10):
+    """Mixed-step throughput of a single uniform mesh of each order N = 3..6
+    (64 x 64 x 16 elements for N <= 4, 48 x 48 x 16 above), autotuned: the
+    per-DOF cost of the orders, against which the batched workload's mix of
+    orders is judged."""
+    from synth.vortex import vortex_state
+    stream = torch.cuda.current_stream()
+    p = sem.sem_params_default(precision=sem.SEM_PREC_MIXED)
+    out = {}
+    for N in (3, 4, 5, 6):
+        n = 48 if N >= 5 else 64
+        m = sem.sem_mesh_create(2048e3 * n / 64, 2048e3 * n / 64, 24e3, n, n, 16, N)
+        q = torch.from_numpy(vortex_state(sem.sem_mesh_coords_host(m).T, 24e3)).cuda()
+        q32 = torch.empty(q.shape, dtype=torch.float32, device="cuda")
+        work = torch.empty((10, m.NG), dtype=torch.float32, device="cuda")
+        sem.sem_mirror(m, q, q32, stream)
+        sem.sem_autotune(m, p, q32, 3, stream)
+        for _ in range(3):
+            sem.sem_step_mixed(m, p, q, q32, work, 0.05, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            sem.sem_step_mixed(m, p, q, q32, work, 0.05, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[N] = 15 * m.Ne * (N + 1) ** 3 / (ms * 1e-3)
+    return out
 
 
 def amr_measure(sem, torch, steps=500, t_amr=50):
@@ -365,6 +407,39 @@ def amr_measure(sem, torch, steps=500, t_amr=50):
                      "status_fp64": sem.sem_status(m64)}}
 
 
+def mlp_forward_measure(sem, torch, rows=1 << 20, reps=20):
+    """Forward throughput of the flag network on `rows` feature rows: the
+    tcgen05 forward (default) and the mma.sync one, TFLOP/s of the three GEMMs
+    against the measured bfloat16 peak."""
+    X = torch.randn((rows, 136), dtype=torch.float32, device="cuda")
+    net = sem.sem_mlp_create(3, rows)
+    prob = torch.empty((rows, 3), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    flop = 2.0 * (136 * 128 + 128 * 128 + 128 * 3) * rows
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = json.load(f)["bf16_tflops"]
+    except Exception:
+        bf16 = 1900.0
+    out = {"rows": rows, "gflop": flop / 1e9, "bf16_peak_tflops": bf16}
+    for tc in (1, 0):
+        sem.sem_mlp_select_forward(net, tc)
+        for _ in range(3):
+            sem.sem_mlp_forward(net, X, prob, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            sem.sem_mlp_forward(net, X, prob, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out["tcgen05" if tc else "mma_sync"] = {"ms": ms, "tflops": flop / (ms * 1e-3) / 1e12,
+                                                "frac_bf16_peak": flop / (ms * 1e-3) / 1e12 / bf16}
+    out["status"] = sem.sem_mlp_status(net)
+    return out
+
+
 def learned_measure(sem, torch):
     """The learned adaptation schedule against the criterion alone (same
     remesh count): ten seeded translating vortices, train on eight."""
@@ -404,6 +479,7 @@ def learned_measure(sem, torch):
         "gate": "mixed learned run against the float64 form on the same remesh schedule (flags replayed)",
         "status": max(max(r[k]["status"] for k in ("reference", "criterion", "learned", "learned_fp64"))
                       for r in runs)}
+    out["forward"] = mlp_forward_measure(sem, torch)
     out["seconds"] = time.perf_counter() - t0
     return out
 
@@ -737,7 +813,12 @@ def main():
 
     batched = None
     if not a.no_batched and a.form == "mixed":
-        batched = [batched_measure(sem, torch), batched_measure(sem, torch, refine=False)]
+        rates = order_rates(sem, torch)
+        batched = ([batched_measure(sem, torch, rates=rates)] if a.batched in ("both", "refined") else []) + \
+                  ([batched_measure(sem, torch, refine=False, rates=rates)]
+                   if a.batched in ("both", "unrefined") else [])
+        batched.append({"order_rates_dof_updates_per_s": {str(k): v for k, v in rates.items()},
+                        "how": "single uniform mesh per order, autotuned mixed steps"})
 
     amr_res = None
     if not a.no_amr and a.form == "mixed":

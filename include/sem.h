@@ -322,6 +322,16 @@ int sem_mlp_predict_flags(sem_mlp* m, const float* feats_dev, int n, int8_t* fla
 int sem_mlp_backward(sem_mlp* m, const float* feats_dev, const int8_t* labels_dev,
                      const float* class_w_host, int n, double* loss_host, cudaStream_t stream);
 int sem_mlp_adam(sem_mlp* m, float lr, cudaStream_t stream);
+/* The forward pass (sem_mlp_forward, sem_mlp_predict_flags and the forward of
+ * sem_mlp_backward) runs on the fifth-generation tensor cores by default
+ * (tcgen05.mma kind::f16, bfloat16 operands in shared memory, float32
+ * accumulators in tensor memory, 128 rows per CTA); tc = 0 selects the
+ * warp-level mma.sync forward instead (same precision contract; kept for
+ * comparison).  sem_mlp_status reads and clears the handle's device status
+ * word (synchronises the stream): SEM_ERR_TIMEOUT if a bounded wait of the
+ * tensor-core forward ran out (its outputs are then not written). */
+int sem_mlp_select_forward(sem_mlp* m, int tc);
+int sem_mlp_status(sem_mlp* m, int* status_host, cudaStream_t stream);
 
 /* q32 = float32 mirror of q ([5][NG]; significand truncated to 24 bits). */
 int sem_mirror(sem_mesh* m, const double* q_dev, float* q32_dev, cudaStream_t stream);

@@ -622,6 +622,16 @@ int sem_mlp_adam(sem_mlp* m, float lr, cudaStream_t st) {
   return mlp_adam_api(m->impl, lr, st);
 }
 
+int sem_mlp_select_forward(sem_mlp* m, int tc) {
+  if (!m) return fail(SEM_ERR_ARG, "NULL argument");
+  return mlp_select_forward(m->impl, tc);
+}
+
+int sem_mlp_status(sem_mlp* m, int* status, cudaStream_t st) {
+  if (!m || !status) return fail(SEM_ERR_ARG, "NULL argument");
+  return mlp_status(m->impl, status, st);
+}
+
 // ---------------------------------------------------------------------------
 // checkpoints: header, leaves, float64 state, FNV-1a checksum of everything
 namespace {

@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 
 #include "sem_internal.h"
+#include "tcgen05.cuh"
 
 namespace sem {
 namespace {
@@ -207,6 +208,192 @@ mlp_forward(const float* __restrict__ X, int n, const __nv_bfloat16* __restrict_
   }
 }
 
+// Forward pass on the fifth-generation tensor cores (tcgen05), the
+// default: persistent CTAs of 128 threads (two per SM) keep the weights in
+// shared memory and walk over tiles of 128 rows, thread t owning row t of a
+// tile (tensor memory lane t).  The three layers are GEMMs of M = 128 rows by N = 128 (16
+// for the 3 logits) by K = 144 (the 136 inputs padded) or 128, as
+// tcgen05.mma.cta_group::1.kind::f16 with bfloat16 operands from shared memory
+// (K-major, no swizzle: core matrices of 8 rows x 8 bfloat16) and float32
+// accumulators in tensor memory (256 columns: layer 1 at 0, layer 2 at 128,
+// layer 3 at 0 again).  Each thread reads its row's accumulators back
+// (tcgen05.ld), adds the bias, applies ReLU, rounds to bfloat16 and writes the
+// next layer's A operand over the previous one (the MMAs that read it have
+// completed).  Same precision contract as mlp_forward; waits on the MMA
+// completion barrier are bounded, a wait that runs out leaves the outputs of
+// the CTA unwritten and sets *err.
+constexpr int TC_ROWS = 128;
+constexpr int TC_X_BYTES = TC_ROWS * 144 * 2;                  // A operand (X, then H1, H2)
+constexpr int TC_W1_BYTES = HID * 144 * 2, TC_W2_BYTES = HID * HID * 2, TC_W3_BYTES = 16 * HID * 2;
+constexpr size_t TC_SMEM = (size_t)TC_X_BYTES + TC_W1_BYTES + TC_W2_BYTES + TC_W3_BYTES +
+                           (2 * HID + 16) * sizeof(float) + 16;
+
+// byte offset of element (row r, k) of a K-major bfloat16 operand with kc
+// core matrices (8 bfloat16 each) along K
+__device__ __forceinline__ int boff(int r, int k, int kc) {
+  return (r & 7) * 16 + (k & 7) * 2 + (k >> 3) * 128 + (r >> 3) * (kc * 128);
+}
+
+__global__ void __launch_bounds__(TC_ROWS, 2)
+mlp_forward_tc(const float* __restrict__ X, int n, const __nv_bfloat16* __restrict__ w1t,
+               const __nv_bfloat16* __restrict__ w2t, const __nv_bfloat16* __restrict__ w3t,
+               const float* __restrict__ P, float* __restrict__ prob, float* __restrict__ Xr,
+               float* __restrict__ H1r, float* __restrict__ H2r, int8_t* __restrict__ flags, int* err) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char* sA = sm;
+  unsigned char* sW1 = sA + TC_X_BYTES;
+  unsigned char* sW2 = sW1 + TC_W1_BYTES;
+  unsigned char* sW3 = sW2 + TC_W2_BYTES;
+  float* sb = reinterpret_cast<float*>(sW3 + TC_W3_BYTES);   // b1 | b2 | b3 (16)
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sb + 2 * HID + 16);
+  uint32_t* taddr_s = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int t = threadIdx.x, warp = t >> 5;
+  // weights: 8 bfloat16 (16 bytes) per core-matrix row; the transposed
+  // arrays hold row n of W^T with k contiguous (zero beyond the inputs)
+  for (int i = t; i < HID * 18; i += TC_ROWS) {
+    const int nn = i / 18, c = i % 18;
+    *reinterpret_cast<uint4*>(sW1 + boff(nn, 8 * c, 18)) = *reinterpret_cast<const uint4*>(w1t + nn * K1P + 8 * c);
+  }
+  for (int i = t; i < HID * 16; i += TC_ROWS) {
+    const int nn = i / 16, c = i % 16;
+    *reinterpret_cast<uint4*>(sW2 + boff(nn, 8 * c, 16)) = *reinterpret_cast<const uint4*>(w2t + nn * K2P + 8 * c);
+  }
+  for (int i = t; i < 16 * 16; i += TC_ROWS) {
+    const int nn = i / 16, c = i % 16;
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(sW3 + boff(nn, 8 * c, 16)) =
+        nn < 8 ? *reinterpret_cast<const uint4*>(w3t + nn * K2P + 8 * c) : z;
+  }
+  for (int i = t; i < HID; i += TC_ROWS) {
+    sb[i] = P[OFF_B1 + i];
+    sb[HID + i] = P[OFF_B2 + i];
+  }
+  if (t < 16) sb[2 * HID + t] = t < OUT ? P[OFF_B3 + t] : 0.f;
+  if (warp == 0) tcg::alloc(taddr_s, 256);
+  if (t == 0) tcg::mbar_init(tcg::smem_u32(mbar), 1);
+  tcg::fence_before();
+  __syncthreads();
+  tcg::fence_after();
+  const uint32_t taddr = *taddr_s, bar = tcg::smem_u32(mbar);
+  const uint32_t aA = tcg::smem_u32(sA), a1 = tcg::smem_u32(sW1), a2 = tcg::smem_u32(sW2), a3 = tcg::smem_u32(sW3);
+  const uint32_t lane_addr = taddr + ((uint32_t)(32 * warp) << 16);
+  bool ok = true;
+  uint32_t phase = 0;   // completions of the barrier so far (three per tile)
+  const int ntiles = (n + TC_ROWS - 1) / TC_ROWS;
+  // persistent: the CTA keeps the weights and walks over tiles of 128 rows
+  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+  const long long row0 = (long long)tile * TC_ROWS;
+  // inputs: the 128 x 136 tile is contiguous; coalesced float4 loads, each
+  // inside one row (136 is a multiple of 4), rounded to bfloat16
+  for (int i = t; i < TC_ROWS * (IN / 4); i += TC_ROWS) {
+    const int r = i / (IN / 4), k = 4 * (i % (IN / 4));
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (row0 + r < n) v = *reinterpret_cast<const float4*>(X + (row0 + r) * IN + k);
+    const unsigned lo = pack_bf16(v.x, v.y), hi = pack_bf16(v.z, v.w);
+    *reinterpret_cast<uint2*>(sA + boff(r, k, 18)) = make_uint2(lo, hi);
+    if (Xr && row0 + r < n)
+      *reinterpret_cast<float4*>(Xr + (row0 + r) * IN + k) = make_float4(bf16r(v.x), bf16r(v.y), bf16r(v.z), bf16r(v.w));
+  }
+  *reinterpret_cast<uint4*>(sA + boff(t, IN, 18)) = make_uint4(0u, 0u, 0u, 0u);   // k = 136..143
+  tcg::fence_async_smem();
+  tcg::fence_before();
+  __syncthreads();
+  tcg::fence_after();
+  const long long row = row0 + t;
+  // layer 1: 9 steps of K = 16 (two core matrices each)
+  if (t == 0) {
+    for (int ks = 0; ks < 9; ++ks)
+      tcg::mma_f16(taddr, tcg::sdesc(aA + 256 * ks, 128, 18 * 128), tcg::sdesc(a1 + 256 * ks, 128, 18 * 128),
+                   tcg::idesc_bf16(128, 128), ks > 0);
+    tcg::commit(bar);
+  }
+  ok = __syncthreads_and(tcg::mbar_wait(bar, phase & 1));   // the same answer in every thread
+  ++phase;
+  tcg::fence_after();
+  // hidden layers: bias, ReLU, bfloat16, written as the next A operand
+  auto hidden = [&](uint32_t col0, const float* bias, float* Hr) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < HID; c0 += 16) {
+      float v[16];
+      tcg::ld16(lane_addr + col0 + c0, v);
+      tcg::wait_ld();
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = bf16r(fmaxf(v[q] + bias[c0 + q], 0.f));
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        *reinterpret_cast<uint4*>(sA + boff(t, c0 + 8 * h, 16)) =
+            make_uint4(pack_bf16(v[8 * h + 0], v[8 * h + 1]), pack_bf16(v[8 * h + 2], v[8 * h + 3]),
+                       pack_bf16(v[8 * h + 4], v[8 * h + 5]), pack_bf16(v[8 * h + 6], v[8 * h + 7]));
+      if (Hr && row < n) {
+#pragma unroll
+        for (int q = 0; q < 16; q += 4)
+          *reinterpret_cast<float4*>(Hr + row * HID + c0 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+      }
+    }
+  };
+  if (ok) hidden(0, sb, H1r);
+  tcg::fence_async_smem();
+  tcg::fence_before();
+  __syncthreads();
+  tcg::fence_after();
+  if (ok && t == 0) {
+    for (int ks = 0; ks < 8; ++ks)
+      tcg::mma_f16(taddr + 128, tcg::sdesc(aA + 256 * ks, 128, 16 * 128), tcg::sdesc(a2 + 256 * ks, 128, 16 * 128),
+                   tcg::idesc_bf16(128, 128), ks > 0);
+    tcg::commit(bar);
+  }
+  ok = __syncthreads_and(ok && tcg::mbar_wait(bar, phase & 1));
+  ++phase;
+  tcg::fence_after();
+  if (ok) hidden(128, sb + HID, H2r);
+  tcg::fence_async_smem();
+  tcg::fence_before();
+  __syncthreads();
+  tcg::fence_after();
+  if (ok && t == 0) {
+    for (int ks = 0; ks < 8; ++ks)
+      tcg::mma_f16(taddr, tcg::sdesc(aA + 256 * ks, 128, 16 * 128), tcg::sdesc(a3 + 256 * ks, 128, 16 * 128),
+                   tcg::idesc_bf16(128, 16), ks > 0);
+    tcg::commit(bar);
+  }
+  ok = __syncthreads_and(ok && tcg::mbar_wait(bar, phase & 1));
+  ++phase;
+  tcg::fence_after();
+  if (ok) {
+    float z[16];
+    tcg::ld16(lane_addr, z);
+    tcg::wait_ld();
+    if (row < n) {
+      const float z0 = z[0] + sb[2 * HID], z1 = z[1] + sb[2 * HID + 1], z2 = z[2] + sb[2 * HID + 2];
+      const float m = fmaxf(z0, fmaxf(z1, z2));
+      const float e0 = expf(z0 - m), e1 = expf(z1 - m), e2 = expf(z2 - m);
+      const float inv = 1.f / (e0 + e1 + e2);
+      if (prob) {
+        prob[row * OUT + 0] = e0 * inv;
+        prob[row * OUT + 1] = e1 * inv;
+        prob[row * OUT + 2] = e2 * inv;
+      }
+      if (flags) {
+        int cls = 0;
+        if (z1 > z0) cls = 1;
+        if (z2 > (cls == 1 ? z1 : z0)) cls = 2;
+        flags[row] = (int8_t)(cls - 1);
+      }
+    }
+  } else if ((t & 31) == 0) {
+    atomicOr(err, 4);
+  }
+  // the next tile overwrites the A operand and the accumulators: every
+  // thread has read its rows
+  tcg::fence_before();
+  __syncthreads();
+  tcg::fence_after();
+  }
+  tcg::fence_before();
+  __syncthreads();
+  if (warp == 0) tcg::dealloc(taddr, 256);
+}
+
 // dZ3 = w_y (p - onehot) / sum(w_y); loss partial sums into acc[0] (sum w_y
 // (-log p_y)) -- acc[1] holds sum w_y from mlp_wsum.
 __global__ void mlp_wsum(const int8_t* __restrict__ y, int n, float w0, float w1, float w2,
@@ -387,8 +574,10 @@ struct MlpImpl {
   float *Xr = nullptr, *H1 = nullptr, *H2 = nullptr, *prob = nullptr, *dz3 = nullptr, *dz2 = nullptr,
         *dz1 = nullptr, *part = nullptr;
   double* acc = nullptr;   // loss, weight sum
+  int* err = nullptr;      // bit 4: a bounded wait of the tensor-core forward ran out
   int step = 0;
   int dev = -1;
+  int forward_tc = 1;      // 1: tcgen05 forward (mlp_forward_tc), 0: mma.sync forward
 };
 
 static int gemm(const float* A, int lda, int tA, const float* B, int ldb, int tB, float* C, int M, int N,
@@ -437,11 +626,15 @@ int mlp_create(unsigned long long seed, int max_rows, void** out) {
   A((void**)&m->dz1, rows * HID * 4);
   A((void**)&m->part, part_floats * 4);
   A((void**)&m->acc, 2 * sizeof(double));
+  A((void**)&m->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(m->err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(m->M1, 0, NPARAM * 4);
   if (e == cudaSuccess) e = cudaMemset(m->M2, 0, NPARAM * 4);
   if (e == cudaSuccess) e = cudaMemset(m->G, 0, NPARAM * 4);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FWD_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
   if (e == cudaSuccess) {
     // Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights from splitmix64 of
     // (seed, index), zero biases
@@ -460,7 +653,8 @@ int mlp_create(unsigned long long seed, int max_rows, void** out) {
   }
   if (e != cudaSuccess) {
     std::string msg = cudaGetErrorString(e);
-    void* ps[] = {m->P, m->R, m->G, m->M1, m->M2, m->wt, m->Xr, m->H1, m->H2, m->prob, m->dz3, m->dz2, m->dz1, m->part, m->acc};
+    void* ps[] = {m->P, m->R, m->G, m->M1, m->M2, m->wt, m->Xr, m->H1, m->H2, m->prob, m->dz3, m->dz2, m->dz1, m->part, m->acc,
+                m->err};
     for (void* p : ps)
       if (p) cudaFree(p);
     delete m;
@@ -500,10 +694,37 @@ int mlp_param_count() { return NPARAM; }
 
 static void launch_forward(MlpImpl* m, const float* X, int n, float* prob, float* Xr, float* H1, float* H2,
                            int8_t* flags, cudaStream_t st) {
+  if (m->forward_tc) {
+    ProfScope ps("mlp_forward_tc", st);
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int tiles = (n + TC_ROWS - 1) / TC_ROWS;
+    mlp_forward_tc<<<std::min(tiles, 2 * nsm), TC_ROWS, TC_SMEM, st>>>(
+        X, n, m->wt, m->wt + W1T_SZ, m->wt + W1T_SZ + W2T_SZ, m->P, prob, Xr, H1, H2, flags, m->err);
+    return;
+  }
   const int grid = (n + FWD_ROWS - 1) / FWD_ROWS;
   ProfScope ps("mlp_forward", st);
   mlp_forward<<<grid, 128, FWD_SMEM, st>>>(X, n, m->wt, m->wt + W1T_SZ, m->wt + W1T_SZ + W2T_SZ, m->P, prob, Xr,
                                             H1, H2, flags);
+}
+
+int mlp_select_forward(void* h, int tc) {
+  MlpImpl* m = (MlpImpl*)h;
+  if (tc != 0 && tc != 1) return fail(SEM_ERR_ARG, "forward: 0 (mma.sync) or 1 (tcgen05)");
+  m->forward_tc = tc;
+  return SEM_OK;
+}
+
+int mlp_status(void* h, int* status, cudaStream_t st) {
+  MlpImpl* m = (MlpImpl*)h;
+  int v = 0;
+  SEM_CUDA_TRY(cudaMemcpyAsync(&v, m->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SEM_CUDA_TRY(cudaMemsetAsync(m->err, 0, sizeof(int), st));
+  SEM_CUDA_TRY(cudaStreamSynchronize(st));
+  *status = v ? SEM_ERR_TIMEOUT : SEM_OK;
+  return SEM_OK;
 }
 
 int mlp_forward_api(void* h, const float* X, int n, float* prob, int8_t* flags, cudaStream_t st) {

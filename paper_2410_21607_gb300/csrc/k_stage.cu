@@ -21,6 +21,7 @@
 #include <mutex>
 
 #include "sem_internal.h"
+#include "tcgen05.cuh"
 
 namespace sem {
 
@@ -446,16 +447,6 @@ struct DssArgs {
   int* status;
 };
 
-// x / 4 for a float64 x, exactly: the exponent field drops by 2 with integer
-// operations when x and x / 4 are normal numbers (the float64 pipe of this
-// part is narrow), else a float64 multiplication (zero, subnormals, Inf, NaN).
-__device__ __forceinline__ double quarter_exact(double x) {
-  const int hi = __double2hiint(x);
-  const unsigned e = ((unsigned)hi >> 20) & 0x7FFu;
-  if (e > 2u && e < 0x7FFu) return __hiloint2double(hi - (2 << 20), __double2loint(x));
-  return x * 0.25;
-}
-
 // FP64 form: float64 throughout.  The float64 pipe of this part is narrow
 // (1/64 of the float32 rate), so the kernel issues float64 instructions only
 // for the arithmetic itself: node indices are 32-bit (an unsigned division by
@@ -466,13 +457,11 @@ __device__ __forceinline__ double quarter_exact(double x) {
 //   MODE 0  out = s T                         (right-hand side only)
 //   MODE 1  out = qs + s T                    (a = 0, b = 1: the first SSP-RK3 stage)
 //   MODE 2  out = a qn + b qs + s T           (any a, b)
-//   MODE 3  out = (3 qn + (qs + 4 s T)) / 4   (a = 3/4, b = 1/4: the second SSP-RK3
-//                                              stage; the division by 4 is exact)
 // with s = c dt / M.  Every sum of the gather is formed in the order of the
 // CSR lists.  The block's table needs NZ doubles of dynamic shared memory.
 template <int MODE>
 __global__ void __launch_bounds__(256) dss_stage_fp64(const DssArgs A) {
-  extern __shared__ double s_cmz[];   // [NZ]: c dt / M_z(kz) (4 c dt / M_z for MODE 3)
+  extern __shared__ double s_cmz[];   // [NZ]: c dt / M_z(kz)
   const double* rc = (const double*)A.rc;
   const double* qtw = (const double*)A.qt_w;
   const double* mh = (const double*)A.Minv_h;
@@ -480,7 +469,7 @@ __global__ void __launch_bounds__(256) dss_stage_fp64(const DssArgs A) {
   const unsigned NZ = (unsigned)A.NZ, NG = (unsigned)A.NG;
   const long long NGl = A.NG;
   const int NZr = A.NZr;
-  const double cdt = MODE == 3 ? 4.0 * A.cdt : A.cdt;
+  const double cdt = A.cdt;
   for (int k = threadIdx.x; k < (int)NZ; k += blockDim.x) s_cmz[k] = cdt * __ldg(mz + k);
   __syncthreads();
   int bad = 0;
@@ -529,7 +518,6 @@ __global__ void __launch_bounds__(256) dss_stage_fp64(const DssArgs A) {
       double val;
       if (MODE == 0) val = T * s;
       else if (MODE == 1) val = fma(s, T, qsv[fl]);
-      else if (MODE == 3) val = quarter_exact(fma(3.0, __ldg(A.qn + fl * NGl + gidx), fma(s, T, qsv[fl])));
       else val = fma(s, T, fma(A.a, __ldg(A.qn + fl * NGl + gidx), A.b * qsv[fl]));
       A.out[fl * NGl + gidx] = val;
       bad |= nonfinite_bits(val);
@@ -541,6 +529,7 @@ __global__ void __launch_bounds__(256) dss_stage_fp64(const DssArgs A) {
 // Mixed form: float32 gather sums and increment c dt R / M, then the float64
 // stage accumulation q_out = a qn + b qs + increment (one or two DFMA per
 // value), and the float32 mirror of q_out for the next stage's element work.
+template <bool WARP = false>
 __global__ void __launch_bounds__(256) dss_stage_mixed(const DssArgs A) {
   const float* rc = (const float*)A.rc;
   const float* qtw = (const float*)A.qt_w;
@@ -553,7 +542,7 @@ __global__ void __launch_bounds__(256) dss_stage_mixed(const DssArgs A) {
     const long long h = gidx / A.NZ;
     const int kz = (int)(gidx - h * A.NZ);
     const int beg = __ldg(A.qt_ptr + h), end = __ldg(A.qt_ptr + h + 1);
-    const float s = A.Minv_g ? cdt * __ldg((const float*)A.Minv_g + gidx) : cdt * (__ldg(mh + h) * __ldg(mz + kz));
+    const float s = WARP ? cdt * __ldg((const float*)A.Minv_g + gidx) : cdt * (__ldg(mh + h) * __ldg(mz + kz));
     const bool lid = (kz == 0) || (kz == A.NZ - 1);
     float acc[kFields] = {0, 0, 0, 0, 0};
     for (int e = beg; e < end; ++e) {
@@ -1264,51 +1253,6 @@ volume_lines_smag(const VolArgs A) {
 // on registers, absorbing layer, vertical direct stiffness summation,
 // residual stores) is lines_body's.  Waits on the MMA completion barrier are
 // bounded; a wait that runs out sets bit 4 of the status word.
-namespace tcg {
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-// shared-memory matrix descriptor: start address, leading (K) and stride
-// (M/N) byte offsets between core matrices, descriptor version 1, no swizzle
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
-}
-// instruction descriptor of kind::tf32: f32 accumulator, tf32 A and B, both
-// K-major, N >> 3 and M >> 4
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-// byte offset of element (row r, k) in a K-major tf32 operand of 8 K columns
-__device__ __forceinline__ int aoff(int r, int k) {
-  return (r & 7) * 16 + (k & 3) * 4 + (k >> 2) * 128 + (r >> 3) * 256;
-}
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t id, int acc) {
-  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-               "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
-               :: "r"(d), "l"(a), "l"(b), "r"(id), "r"(acc) : "memory");
-}
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < (1 << 24); ++it) {
-    uint32_t ok;
-    asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
-                 "selp.u32 %0, 1, 0, q;\n}" : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-__device__ __forceinline__ void ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-#pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
-}
-}  // namespace tcg
 
 constexpr int kTcKL = 4, kTcThreads = 128, kTcRows = 512, kTcCols = 128;
 constexpr int kTcOpBytes = kTcRows * 32;   // one operand (512 rows x 8 tf32)
@@ -1345,9 +1289,7 @@ __global__ void __launch_bounds__(kTcThreads, MB) volume_lines_tc(const VolArgs 
     *reinterpret_cast<float*>(opB + 512 + tcg::aoff(nn, k)) = v - hi;
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 :: "r"(tcg::smem_u32(taddr_s)), "r"(kTcCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    tcg::alloc(taddr_s, kTcCols);
   }
   if (t == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(tcg::smem_u32(mbar)));
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1434,7 +1376,7 @@ __global__ void __launch_bounds__(kTcThreads, MB) volume_lines_tc(const VolArgs 
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                    :: "r"(bar) : "memory");
     }
-    ok = tcg::mbar_wait(bar, (uint32_t)(ch & 1));
+    ok = __syncthreads_and(tcg::mbar_wait(bar, (uint32_t)(ch & 1)));   // the same answer in every thread
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
       // each warp: its 32 lanes (rows) of the 8 tiles; scatter the 5 outputs
@@ -1726,7 +1668,7 @@ struct IncArgs {
   int* status;
 };
 
-template <int STAGE>
+template <int STAGE, bool WARP = false>
 __device__ __forceinline__ void inc_body(const IncArgs& A, const int gidx, int& bad) {
   const int h = (int)((unsigned)gidx / (unsigned)A.NZ);
   const int kz = gidx - h * A.NZ;
@@ -1742,7 +1684,8 @@ __device__ __forceinline__ void inc_body(const IncArgs& A, const int gidx, int& 
     if (STAGE == 1) q32v[fl] = __ldg(A.q32 + o);
     if (STAGE == 2) qv[fl] = A.q[o];
   }
-  const float s = A.Minv_g ? A.cdt * __ldg(A.Minv_g + gidx) : A.cdt * (__ldg(A.Minv_h + h) * __ldg(A.Minv_z + kz));
+  // warped layers: the lumped mass per node (it does not factorise)
+  const float s = WARP ? A.cdt * __ldg(A.Minv_g + gidx) : A.cdt * (__ldg(A.Minv_h + h) * __ldg(A.Minv_z + kz));
   const bool lid = (kz == 0) || (kz == A.NZ - 1);
   float acc[kFields] = {0, 0, 0, 0, 0};
   // Q_h^T gather, in the order of the CSR lists: from the compact record
@@ -1785,11 +1728,11 @@ __device__ __forceinline__ void inc_body(const IncArgs& A, const int gidx, int& 
   }
 }
 
-template <int STAGE>
+template <int STAGE, bool WARP = false>
 __global__ void __launch_bounds__(256) dss_inc(const IncArgs A) {
   int bad = 0;
   for (int gidx = blockIdx.x * blockDim.x + threadIdx.x; gidx < A.NG; gidx += gridDim.x * blockDim.x)
-    inc_body<STAGE>(A, gidx, bad);
+    inc_body<STAGE, WARP>(A, gidx, bad);
   if (STAGE == 2 && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(A.status, 1);
 }
 
@@ -1837,9 +1780,15 @@ int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float
     B.status = D.status;
     ProfScope ps("dss_inc_mixed", st);
     const int blocks = grid_cap(m.NG, 64);
-    if (stage == 0) dss_inc<0><<<blocks, 256, 0, st>>>(B);
-    else if (stage == 1) dss_inc<1><<<blocks, 256, 0, st>>>(B);
-    else dss_inc<2><<<blocks, 256, 0, st>>>(B);
+    if (B.Minv_g) {
+      if (stage == 0) dss_inc<0, true><<<blocks, 256, 0, st>>>(B);
+      else if (stage == 1) dss_inc<1, true><<<blocks, 256, 0, st>>>(B);
+      else dss_inc<2, true><<<blocks, 256, 0, st>>>(B);
+    } else {
+      if (stage == 0) dss_inc<0><<<blocks, 256, 0, st>>>(B);
+      else if (stage == 1) dss_inc<1><<<blocks, 256, 0, st>>>(B);
+      else dss_inc<2><<<blocks, 256, 0, st>>>(B);
+    }
     SEM_CUDA_TRY(cudaGetLastError());
   }
   return SEM_OK;
@@ -2418,7 +2367,9 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
   B.status = D.status;
   {
     ProfScope ps(mixed ? "dss_rk_mixed" : "dss_rk_fp64", st);
-    if (mixed)
+    if (mixed && B.Minv_g)
+      dss_stage_mixed<true><<<grid_cap(m.NG), 256, 0, st>>>(B);
+    else if (mixed)
       dss_stage_mixed<<<grid_cap(m.NG), 256, 0, st>>>(B);
     else {
       const size_t sm = sizeof(double) * m.NZ;
@@ -2427,8 +2378,6 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
         dss_stage_fp64<0><<<grid_cap(m.NG), 256, sm, st>>>(B);
       else if (s.a == 0.0 && s.b == 1.0)
         dss_stage_fp64<1><<<grid_cap(m.NG), 256, sm, st>>>(B);
-      else if (s.a == 0.75 && s.b == 0.25)
-        dss_stage_fp64<3><<<grid_cap(m.NG), 256, sm, st>>>(B);
       else
         dss_stage_fp64<2><<<grid_cap(m.NG), 256, sm, st>>>(B);
     }

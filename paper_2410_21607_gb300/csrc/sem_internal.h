@@ -256,6 +256,8 @@ int mlp_forward_api(void* m, const float* X, int n, float* prob, int8_t* flags, 
 int mlp_backward_api(void* m, const float* X, const int8_t* y, const float* cw, int n, double* loss_host,
                      cudaStream_t st);
 int mlp_adam_api(void* m, float lr, cudaStream_t st);
+int mlp_select_forward(void* m, int tc);
+int mlp_status(void* m, int* status, cudaStream_t st);
 int mlp_features_api(Mesh& mesh, const double* q, const float* scales, float* F, cudaStream_t st);
 int autotune_pencil(Mesh& m, const sem_params& p, const float* q32, int reps, sem_tune_out* out,
                     cudaStream_t st);

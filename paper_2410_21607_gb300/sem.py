@@ -36,6 +36,7 @@ EXPORTS = (
     "sem_mlp_predict_flags", "sem_mlp_backward", "sem_mlp_adam",
     "sem_checkpoint_write", "sem_checkpoint_read_mesh", "sem_checkpoint_read_state",
     "sem_selftest_device_once", "sem_peak_probe", "sem_adapt_flags_levels", "sem_merge_flags",
+    "sem_mlp_select_forward", "sem_mlp_status",
 )
 
 
@@ -144,6 +145,8 @@ def _load():
         "sem_peak_probe": (i, [i, C.POINTER(d), vp]),
         "sem_adapt_flags_levels": (i, [vp, C.POINTER(Params), vp, vp, i, vp, vp, vp]),
         "sem_merge_flags": (i, [vp, vp, vp, i, C.c_longlong, vp, vp]),
+        "sem_mlp_select_forward": (i, [vp, i]),
+        "sem_mlp_status": (i, [vp, C.POINTER(C.c_int), vp]),
         "sem_profile_end": (i, [C.POINTER(ProfileOut)]),
     }
     for name, (res, args) in sig.items():
@@ -608,4 +611,15 @@ def sem_peak_probe(precision, stream=None):
     """float32 (SEM_PREC_MIXED) or float64 (SEM_PREC_FP64) FMA rate, TFLOP/s."""
     out = C.c_double()
     _check(LIB.sem_peak_probe(precision, C.byref(out), _stream(stream)))
+    return out.value
+
+
+def sem_mlp_select_forward(mlp, tc):
+    """1: tcgen05 tensor-core forward (default), 0: mma.sync forward."""
+    _check(LIB.sem_mlp_select_forward(mlp.h, int(tc)))
+
+
+def sem_mlp_status(mlp, stream=None):
+    out = C.c_int()
+    _check(LIB.sem_mlp_status(mlp.h, C.byref(out), _stream(stream)))
     return out.value

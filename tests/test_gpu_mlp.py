@@ -57,8 +57,12 @@ def _batch(n=1000, seed=0):
     return X, y
 
 
-def test_forward_matches_oracle(sem):
+@pytest.mark.parametrize("tc", [1, 0])
+def test_forward_matches_oracle(sem, tc):
+    """tc = 1: the tcgen05 tensor-core forward (default), 0: the mma.sync one;
+    1000 rows (a partial last tile of 128 rows for the tensor-core forward)."""
     net = sem.sem_mlp_create(7, 4096)
+    sem.sem_mlp_select_forward(net, tc)
     params = [p.astype(np.float32).astype(np.float64) for p in omlp.init_params(11)]
     params[1] += 0.05
     params[3] -= 0.02
@@ -76,10 +80,32 @@ def test_forward_matches_oracle(sem):
     srt = np.sort(P_o, axis=1)
     clear = srt[:, 2] - srt[:, 1] > 1e-3
     assert np.array_equal(f[clear], (np.argmax(P_o, axis=1) - 1)[clear])
+    assert sem.sem_mlp_status(net) == 0
 
 
-def test_backward_matches_oracle(sem):
+def test_tensor_core_forward_equals_mma_sync_forward(sem):
+    """The two forwards on the same rows (several CTAs, a ragged last tile):
+    the same bfloat16 products with float32 accumulation in another order."""
+    net = sem.sem_mlp_create(9, 4096)
+    X, _ = _batch(4001, 5)
+    Xd = torch.from_numpy(X).cuda()
+    out = []
+    for tc in (1, 0):
+        sem.sem_mlp_select_forward(net, tc)
+        prob = torch.full((4001, 3), float("nan"), dtype=torch.float32, device="cuda")
+        sem.sem_mlp_forward(net, Xd, prob)
+        out.append(prob.cpu().numpy())
+    assert np.isfinite(out[0]).all()
+    assert rel(out[0], out[1]) <= 1e-4
+    assert sem.sem_mlp_status(net) == 0
+
+
+@pytest.mark.parametrize("tc", [1, 0])
+def test_backward_matches_oracle(sem, tc):
+    """The backward pass after either forward (which stores the rounded
+    inputs and activations it uses)."""
     net = sem.sem_mlp_create(7, 4096)
+    sem.sem_mlp_select_forward(net, tc)
     params = [p.astype(np.float32).astype(np.float64) for p in omlp.init_params(12)]
     sem.sem_mlp_set_params(net, flat(params))
     X, y = _batch(3000, 2)
