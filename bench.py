@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-amr", action="store_true")
     ap.add_argument("--no-physics", action="store_true")
+    ap.add_argument("--no-warped", action="store_true")
     ap.add_argument("--kernel-row", type=int, default=None,
                     help="use this row of the element-kernel variant table instead of autotuning "
                          "(for profiler runs, whose per-launch overhead distorts the timings)")
@@ -405,6 +406,80 @@ def amr_measure(sem, torch, steps=500, t_amr=50):
                      "max_mean_wind_rel_err": abs(d["max_mean_wind"] - d64["max_mean_wind"]) / d64["max_mean_wind"],
                      "how": "float64 form through the same meshes (the mixed run's flags replayed)",
                      "status_fp64": sem.sem_status(m64)}}
+
+
+def warped_measure(sem, torch, steps=20, warmup=3, gate_steps=100, amplitude=600.0, k=4):
+    """The benchmark mesh (64x64x16, N = 4, 2048 km x 24 km) with warped
+    layers: every node lifted by amplitude sin(2 pi k x / Lx) sin(2 pi k y / Ly)
+    sin(pi zeta / Lz) (flat lids), so every element is non-affine and carries
+    float64 metric terms per node.  Mixed increment-form steps, autotuned
+    among the line-exchange variants; per-kernel durations; the algorithmic
+    bytes of the non-affine pass (the affine bytes plus the float32 metric
+    terms, 3 per local node of each column line, and the packed reference
+    state per global node); the max-wind gate against the float64 form on
+    the same mesh."""
+    from synth.vortex import vortex_state
+    L, Lz, n, nz, N, dt = 2048e3, 24e3, 64, 16, 4, 0.25
+    m = sem.sem_mesh_create(L, L, Lz, n, n, nz, N, warp=(amplitude, k, k))
+    q0 = torch.from_numpy(vortex_state(sem.sem_mesh_coords_host(m).T, Lz)).cuda()
+    p = sem.sem_params_default(precision=sem.SEM_PREC_MIXED)
+    p64 = sem.sem_params_default(precision=sem.SEM_PREC_FP64)
+    stream = torch.cuda.current_stream()
+    q = q0.clone()
+    q32 = torch.empty(q.shape, dtype=torch.float32, device="cuda")
+    work = torch.empty((10, m.NG), dtype=torch.float32, device="cuda")
+    sem.sem_mirror(m, q, q32, stream)
+    rows, chosen = sem.sem_autotune(m, p, q32, 5, stream)
+    for _ in range(warmup):
+        sem.sem_step_mixed(m, p, q, q32, work, dt, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        sem.sem_step_mixed(m, p, q, q32, work, dt, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    sem.sem_profile_begin()
+    for _ in range(steps):
+        sem.sem_step_mixed(m, p, q, q32, work, dt, stream)
+    torch.cuda.synchronize()
+    pr = sem.sem_profile_end()
+    NG, NL, Ncol, Nq = m.NG, m.Ne * (N + 1) ** 3, m.Ncol, (N + 1) ** 2
+    metric_bytes = 12 * Ncol * Nq * nz * (N + 1)
+    ref_bytes = 16 * NG
+    elem = 20 * NG + 4 * NL + metric_bytes + ref_bytes
+    stage = 124 * NG + 4 * NL + metric_bytes + ref_bytes
+    hbm, _ = peaks()
+    kern = {}
+    for name, (nl, tot) in pr.items():
+        if name == "mirror":
+            continue
+        avg = tot / max(nl, 1)
+        ab = elem if name.startswith("volume") else stage - elem
+        kern[name] = {"launches": nl, "ms_avg": avg, "alg_bytes": ab,
+                      "frac": ab / (avg * 1e-3) / 1e9 / hbm}
+    # max-wind gate: mixed against float64 steps on the same warped mesh
+    gate = None
+    if gate_steps > 0:
+        qm, qd = q0.clone(), q0.clone()
+        sem.sem_mirror(m, qm, q32, stream)
+        w1, w2 = torch.empty_like(qd), torch.empty_like(qd)
+        for _ in range(gate_steps):
+            sem.sem_step_mixed(m, p, qm, q32, work, dt, stream)
+            sem.sem_step(m, p64, qd, w1, w2, dt, stream)
+        dm, dd = sem.sem_diag(m, p64, qm), sem.sem_diag(m, p64, qd)
+        gate = {"steps": gate_steps, "max_wind_fp64": dd["max_wind"],
+                "max_wind_rel_err": abs(dm["max_wind"] - dd["max_wind"]) / dd["max_wind"]}
+    return {"workload": f"uniform-64x64x16-N4 with warped layers (amplitude {amplitude:g} m, "
+                        f"{k} x {k} periods, flat lids)",
+            "ms_per_step": ms, "value": 3 * 5 * NL / (ms * 1e-3),
+            "autotune": {"variants": [{"layers_per_cta": r[0], "min_ctas_per_sm": r[1], "ms": r[2],
+                                       "kind": r[3]} for r in rows], "chosen": chosen},
+            "alg_bytes": {"element_pass": elem, "stage": stage, "metric": metric_bytes,
+                          "reference_state": ref_bytes},
+            "stage_frac": stage / (ms / 3 * 1e-3) / 1e9 / hbm, "kernels": kern,
+            "gate": gate, "status": sem.sem_status(m)}
 
 
 def mlp_forward_measure(sem, torch, rows=1 << 20, reps=20):
@@ -820,6 +895,9 @@ def main():
         batched.append({"order_rates_dof_updates_per_s": {str(k): v for k, v in rates.items()},
                         "how": "single uniform mesh per order, autotuned mixed steps"})
 
+    warped_res = None
+    if not a.no_warped and a.form == "mixed":
+        warped_res = warped_measure(sem, torch, gate_steps=a.gate_steps)
     amr_res = None
     if not a.no_amr and a.form == "mixed":
         amr_res = amr_measure(sem, torch)
@@ -853,7 +931,7 @@ def main():
                       "fp64_tflops": fp64_peak, "fma_source": "sem_peak_probe"},
             "gate": gate,
             "roofline": roof, "kernels": kernels, "autotune": tune, "batched": batched,
-            "learned": learned_res, "amr": amr_res, "physics": physics_res,
+            "learned": learned_res, "amr": amr_res, "physics": physics_res, "warped": warped_res,
             "cpu_baseline": cpu,
             "e2e": {"value": job_throughput(dof_stage * 3, world, e2e_ms), "unit": "DOF-updates/s",
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,

@@ -1506,6 +1506,7 @@ static const PencilVariant kPencil[] = {
     {4, 8, 2, launch_lines<4, 8, 2>, 1, launch_lines_smag<4, 8, 2>},
     {4, 4, 8, launch_lines<4, 4, 8>, 1, launch_lines_smag<4, 4, 8>},
     {4, kTcKL, 3, launch_lines_tc<3>, 2},
+    {4, 8, 3, launch_lines<4, 8, 3>, 1, launch_lines_smag<4, 8, 3>},
     {5, 8, 2, launch_pencil<5, 8, 2>},      {5, 8, 2, launch_lines<5, 8, 2>, 1},
     {5, 4, 4, launch_lines<5, 4, 4>, 1},
     {6, 4, 2, launch_pencil<6, 4, 2>},      {6, 8, 1, launch_lines<6, 8, 1>, 1},
