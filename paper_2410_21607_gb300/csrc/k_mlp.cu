@@ -239,8 +239,8 @@ mlp_forward_tc(const float* __restrict__ X, int n, const __nv_bfloat16* __restri
                const __nv_bfloat16* __restrict__ w2t, const __nv_bfloat16* __restrict__ w3t,
                const float* __restrict__ P, float* __restrict__ prob, float* __restrict__ Xr,
                float* __restrict__ H1r, float* __restrict__ H2r, int8_t* __restrict__ flags, int* err) {
-  extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char* sA = sm;
+  extern __shared__ __align__(1024) unsigned char sm_tc[];
+  unsigned char* sA = sm_tc;
   unsigned char* sW1 = sA + TC_X_BYTES;
   unsigned char* sW2 = sW1 + TC_W1_BYTES;
   unsigned char* sW3 = sW2 + TC_W2_BYTES;
