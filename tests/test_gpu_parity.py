@@ -408,6 +408,36 @@ def test_nonfinite_state_sets_status(sem):
     assert sem.sem_status(m) == 0       # reading clears it
 
 
+def test_fp64_second_stage_special_values(sem):
+    """The float64 second SSP-RK3 stage forms qs / 4 from the bits of qs
+    (exponent lowered by 2): against 3/4 qn + 1/4 qs + dt/4 R(qs) formed here
+    from the library's float64 right-hand side, for stage states holding
+    signed zeros and values near the bottom of the normal range; a
+    non-finite stage state still raises the status."""
+    m, o, X, perm = make_pair(sem, **MESHES["twolevel-N4"])
+    qn = dev(random_state(o.XG, o.Lz, 81)[:, perm])
+    qs = dev(random_state(o.XG, o.Lz, 82)[:, perm])
+    qs[3, ::7] = 0.0
+    qs[3, 3::7] = -0.0
+    qs[1, ::11] = 3e-306
+    qs[2, ::13] = -5e-307
+    qs[0, ::17] = 1e-308          # its quarter is subnormal: the kernel gives zero
+    p = sem.sem_params_default()
+    R = torch.empty_like(qs)
+    sem.sem_rhs(m, p, qs, R)
+    dt = 0.5
+    out = torch.empty_like(qs)
+    sem.sem_rk_stage(m, p, 1, qn, qs, out, dt)
+    want = 0.75 * host(qn) + 0.25 * host(qs) + (0.25 * dt) * host(R)
+    got = host(out)
+    scale = np.abs(want).max(axis=1, keepdims=True)
+    assert np.all(np.abs(got - want) <= 1e-14 * scale)
+    assert sem.sem_status(m) == 0
+    qs[4, 5] = float("inf")
+    sem.sem_rk_stage(m, p, 1, qn, qs, out, dt)
+    assert sem.sem_status(m) == sem.SEM_ERR_NUMERIC
+
+
 def test_bad_arguments_are_rejected(sem):
     m = sem.sem_mesh_create(300e3, 300e3, 12e3, 3, 3, 2, 4)
     q = torch.zeros(5, m.NG, dtype=torch.float64, device="cuda")
