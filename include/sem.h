@@ -91,12 +91,13 @@ typedef struct {
    * the lumped mass per node; hanging nodes take the coarse face's
    * interpolated height (Sec. 3.1), so the mesh stays watertight.  A
    * non-positive Jacobian gives SEM_ERR_ARG.  On warped meshes the right-hand
-   * side, the stages and steps (float64 and mixed forms), the speed
-   * criterion, coordinates and diagnostics are available; the Smagorinsky
-   * stress, the absorbing layer, the heating, the vorticity and
-   * potential-vorticity criteria, adaptation (sem_transfer_plan), batching and
-   * checkpoints give SEM_ERR_UNSUPPORTED, and the mixed conservative form
-   * uses the line-exchange element kernels only. */
+   * side, the stages and steps (float64 and mixed forms), the terms of the
+   * paper's runs (the horizontal Smagorinsky stress with gradients at constant
+   * height, the absorbing layer and the heating at each node's height), the
+   * speed criterion, coordinates, diagnostics and checkpoints are available;
+   * the vorticity and potential-vorticity criteria, adaptation
+   * (sem_transfer_plan) and batching give SEM_ERR_UNSUPPORTED, and the mixed
+   * conservative form uses the line-exchange element kernels only. */
   double warp_amplitude;
   int warp_kx, warp_ky;
 } sem_mesh_desc;
@@ -446,8 +447,9 @@ int sem_autotune_select(sem_mesh* m, int row);
 
 /* Checkpoint / resume.  sem_checkpoint_write copies the float64 state to the
  * host (synchronises the stream) and writes the mesh description, its leaf
- * columns, its layer faces, the state, `time` and `step`, and a checksum
- * (format SEMCKPT2), through a temporary
+ * columns, its layer faces, its warped-layer parameters, the state, `time`
+ * and `step`, and a checksum (format SEMCKPT3; files of the earlier SEMCKPT2
+ * format give SEM_ERR_IO), through a temporary
  * file renamed into place.  sem_checkpoint_read_mesh rebuilds the mesh (host
  * only; same leaves, hence the same node numbering) and returns time and step;
  * sem_checkpoint_read_state copies the state into q_dev ([5][NG]) after

@@ -39,7 +39,7 @@ void free_device(Mesh& m) {
                   D.Mh, D.Mz, D.Minv_h32, D.Minv_z32, D.qt_w32, D.qt_rec_src, D.qt_rec_w, D.qt_rec_unit, D.hang_w32, D.mirror, D.spg, D.spg32, D.ref, D.ref32, D.col_level, D.col_x0, D.col_y0, D.xh, D.yh, D.zk, D.hzk, D.hzk32, D.scratch,
                   D.status, D.org, D.elem_cmax, D.elem_flags, D.diag_buf,
                   D.tr_comp_ptr, D.tr_nodes, D.tr_A_ptr, D.tr_A_col, D.tr_A_val, D.tr_coupled,
-                  D.zG, D.metric, D.metric32, D.Minv_g, D.Minv_g32, D.refG, D.refH, D.refG32, D.refH32,
+                  D.zG, D.zH, D.metric, D.metric32, D.Minv_g, D.Minv_g32, D.refG, D.refH, D.refG32, D.refH32,
                   D.ref4G, D.ref4H};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -144,7 +144,8 @@ int ensure_device(Mesh& m) {
     }
     const size_t nh = m.zH.size() ? m.zH.size() : 1;
     cudaError_t e2 = cudaSuccess;
-    if ((rc = upload(D.zG, m.zG)) || (rc = upload(D.metric, m.metric)) || (rc = upload(D.metric32, met32)) ||
+    if ((rc = upload(D.zG, m.zG)) || (rc = upload(D.zH, m.zH)) || (rc = upload(D.metric, m.metric)) ||
+        (rc = upload(D.metric32, met32)) ||
         (rc = upload(D.Minv_g, minvg)) || (rc = upload(D.Minv_g32, mg32))) {
       free_device(m);
       return rc;
@@ -635,12 +636,15 @@ int sem_mlp_status(sem_mlp* m, int* status, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // checkpoints: header, leaves, float64 state, FNV-1a checksum of everything
 namespace {
-const char kMagic[8] = {'S', 'E', 'M', 'C', 'K', 'P', 'T', '2'};
+const char kMagic[8] = {'S', 'E', 'M', 'C', 'K', 'P', 'T', '3'};
+const char kMagicV2[8] = {'S', 'E', 'M', 'C', 'K', 'P', 'T', '2'};   // before warped layers
 struct CkptHead {
   char magic[8];
   double Lx, Ly, Lz, time;
   int nx, ny, nz, N, px, py, lvl_max, pad;
   long long ncol, NG, step;
+  double warp_A;              // warped layers (0: box elements)
+  int warp_kx, warp_ky;
 };
 uint64_t fnv1a(const void* p, size_t n, uint64_t h = 1469598103934665603ull) {
   const unsigned char* c = (const unsigned char*)p;
@@ -659,6 +663,7 @@ int read_ckpt(const char* path, CkptHead& H, std::vector<int>& leaves, std::vect
     return fail(SEM_ERR_IO, std::string("checkpoint ") + path + ": " + why);
   };
   if (std::fread(&H, sizeof(H), 1, f) != 1) return bad("truncated header");
+  if (std::memcmp(H.magic, kMagicV2, 8) == 0) return bad("written by an earlier version of the format");
   if (std::memcmp(H.magic, kMagic, 8) != 0) return bad("not a checkpoint");
   if (H.ncol <= 0 || H.ncol > (1ll << 30) || H.NG <= 0 || H.NG > (1ll << 36)) return bad("bad sizes");
   leaves.resize((size_t)H.ncol * 3);
@@ -686,13 +691,13 @@ int sem_checkpoint_write(sem_mesh* mh, const double* q, double time, long long s
                          cudaStream_t st) {
   if (!mh || !q || !path) return fail(SEM_ERR_ARG, "NULL argument");
   const Mesh& m = mh->m;
-  if (m.warped()) return fail(SEM_ERR_UNSUPPORTED, "checkpoints of warped meshes are not built");
   CkptHead H;
   std::memset(&H, 0, sizeof(H));
   std::memcpy(H.magic, kMagic, 8);
   H.Lx = m.Lx; H.Ly = m.Ly; H.Lz = m.Lz; H.time = time;
   H.nx = m.nx; H.ny = m.ny; H.nz = m.nz; H.N = m.N; H.px = m.px; H.py = m.py; H.lvl_max = m.lvl_max;
   H.ncol = m.Ncol(); H.NG = m.NG; H.step = step;
+  H.warp_A = m.warp_A; H.warp_kx = m.warp_kx; H.warp_ky = m.warp_ky;
   std::vector<int> leaves((size_t)m.Ncol() * 3);
   for (long long c = 0; c < m.Ncol(); ++c) {
     leaves[3 * c] = m.leaves[c].l;
@@ -737,6 +742,9 @@ int sem_checkpoint_read_mesh(const char* path, sem_mesh** out, double* time, lon
   d.n_leaves = (int)H.ncol;
   d.leaves = leaves.data();
   d.z_faces = zf.data();
+  d.warp_amplitude = H.warp_A;
+  d.warp_kx = H.warp_kx;
+  d.warp_ky = H.warp_ky;
   if ((rc = sem_mesh_create(&d, out))) return rc;
   if ((*out)->m.NG != H.NG) {
     sem_mesh_destroy(*out);
@@ -756,7 +764,8 @@ int sem_checkpoint_read_state(const char* path, sem_mesh* mh, double* q, cudaStr
   int rc = read_ckpt(path, H, leaves, zf, &host);
   if (rc) return rc;
   const Mesh& m = mh->m;
-  bool same = H.NG == m.NG && H.ncol == m.Ncol() && zf == m.zf;
+  bool same = H.NG == m.NG && H.ncol == m.Ncol() && zf == m.zf && H.warp_A == m.warp_A &&
+              (m.warp_A == 0.0 || (H.warp_kx == m.warp_kx && H.warp_ky == m.warp_ky));
   for (long long c = 0; same && c < m.Ncol(); ++c)
     same = leaves[3 * c] == m.leaves[c].l && leaves[3 * c + 1] == m.leaves[c].i &&
            leaves[3 * c + 2] == m.leaves[c].j;

@@ -111,7 +111,26 @@ struct PhysArgs {
   const double* col_x0;  // [Ncol] column corners
   const double* col_y0;
   const double* zk;      // [NZ] heights of the levels
+  // warped layers (non-affine elements): metric terms z_xi, z_eta, z_zeta per
+  // node of each column line ([Ncol][Nq][nz][N+1][3], same type as the
+  // state), node heights of global and hanging nodes, and the absorbing
+  // layer's parameters (its rate is taken at each node's own height)
+  const void* metric;
+  const double* zG;
+  const double* zH;
+  const void* refG;      // reference state at the nodes' heights [NG][kRef], [Nhang NZ][kRef] (same type)
+  const void* refH;
+  double spg_gamma, spg_depth, Lz;
 };
+
+// R(z) of the absorbing layer at height z: gamma sin^2(pi/2 (1 - (Lz - z) /
+// z_d)) clipped to [0, 1], zero below Lz - z_d (the per-level tables of box
+// meshes hold the same values).
+__device__ __forceinline__ double sponge_at(const PhysArgs& A, double z) {
+  if (!(z >= A.Lz - A.spg_depth)) return 0.0;
+  const double s = sin(0.5 * 3.14159265358979323846 * (1.0 - (A.Lz - z) / A.spg_depth));
+  return fmin(1.0, fmax(0.0, A.spg_gamma * s * s));
+}
 
 // Q of the synthetic heating (K/s) at (x, y, z): ring in r, half sine in z,
 // zero beyond heat_rmax and above heat_ztop.
@@ -125,12 +144,19 @@ __device__ __forceinline__ double heating_at(const PhysArgs& A, double x, double
 template <typename R>
 __device__ __forceinline__ R geo_at(const PhysArgs& A, int l, int k) { return (R)A.geo[l][k]; }
 
-template <int N, int EQ, typename R>
+// WARP: warped layers.  The Jacobian and the weak-form factors come from
+// the node's metric terms (J = hx hy z_zeta / 4, J grad xi = (hy z_zeta / 2,
+// 0, 0), J grad eta = (0, hx z_zeta / 2, 0), J grad zeta = (-hy z_xi / 2,
+// -hx z_eta / 2, hx hy / 4)); the horizontal velocity gradients are taken at
+// constant height, d/dx = (2 / hx) (d/dxi - (z_xi / z_zeta) d/dzeta), and the
+// horizontal stress fluxes enter the zeta contraction through J grad zeta;
+// the absorbing layer and the heating are evaluated at each node's height.
+template <int N, int EQ, typename R, bool WARP = false>
 __global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
 physics_column(const PhysArgs A) {
   constexpr int n1 = N + 1, Nq = n1 * n1, P = n1 * n1 * n1;
   __shared__ R sU[3][P];
-  __shared__ R sF[6][P];
+  __shared__ R sF[WARP ? 9 : 6][P];
   __shared__ R sC[2][kFields][Nq];
   const int col = blockIdx.x, t = threadIdx.x;
   const bool act = t < P;
@@ -150,12 +176,25 @@ physics_column(const PhysArgs A) {
   const R* ref = (const R*)A.ref;
   const R* spg = (const R*)A.spg;
   R* rc = (R*)A.rc;
+  const R* met = (const R*)A.metric;
   for (int k = 0; k < A.nz; ++k) {
     const int kz = k * N + c;
     // the layer's thickness: Jacobian and the weak-form factors J dxi/dx, J deta/dy
     const R hz = (R)A.hzk[k];
-    const R J = hx * hy * hz * (R)0.125;
-    const R sx = hy * hz * (R)0.25, sy = hx * hz * (R)0.25;
+    R J = hx * hy * hz * (R)0.125;
+    R sx = hy * hz * (R)0.25, sy = hx * hz * (R)0.25;
+    R zx = 0, zy = 0, zz = 1;
+    double zn = 0.0;
+    if (WARP && act) {
+      const R* mt = met + ((((long long)col * Nq + ab) * A.nz + k) * n1 + c) * 3;
+      zx = mt[0];
+      zy = mt[1];
+      zz = mt[2];
+      J = hx * hy * zz * (R)0.25;
+      sx = hy * zz * (R)0.5;
+      sy = hx * zz * (R)0.5;
+      zn = hm >= 0 ? A.zG[(long long)hm * A.NZ + kz] : A.zH[(long long)(-1 - hm) * A.NZ + kz];
+    }
     const R wJ = wi * wj * wc * J;
     R r[kFields] = {0, 0, 0, 0, 0};
     R rfac = (R)1;
@@ -179,7 +218,11 @@ physics_column(const PhysArgs A) {
       }
       R u = v[1], vv = v[2], w = v[3];
       if (EQ == 0) {
-        const R rho = ref[(long long)kz * kRef + 3] + v[0];
+        // warped layers: the reference density at the node's own height
+        const R rho0 = !WARP ? ref[(long long)kz * kRef + 3]
+                     : hm >= 0 ? ((const R*)A.refG)[((long long)hm * A.NZ + kz) * kRef + 3]
+                               : ((const R*)A.refH)[((long long)(-1 - hm) * A.NZ + kz) * kRef + 3];
+        const R rho = rho0 + v[0];
         const R inv = (R)1 / rho;
         u *= inv;
         vv *= inv;
@@ -187,7 +230,7 @@ physics_column(const PhysArgs A) {
         rfac = rho;
       }
       if (spg) {
-        const R Rz = spg[kz];
+        const R Rz = WARP ? (R)sponge_at(A, zn) : spg[kz];
 #pragma unroll
         for (int f = 0; f < kFields; ++f) r[f] = wJ * (-Rz * v[f]);
       }
@@ -195,7 +238,7 @@ physics_column(const PhysArgs A) {
         const double hxd = A.geo[lev][0], hyd = A.geo[lev][1];
         const double x = A.col_x0[col] + 0.5 * (1.0 + p_xi[N][i]) * hxd;
         const double y = A.col_y0[col] + 0.5 * (1.0 + p_xi[N][j]) * hyd;
-        const R Q = (R)heating_at(A, x, y, A.zk[kz]);
+        const R Q = (R)heating_at(A, x, y, WARP ? zn : A.zk[kz]);
         r[4] += wJ * (EQ == 0 ? rfac * Q : Q);
       }
       if (A.smag) {
@@ -208,6 +251,7 @@ physics_column(const PhysArgs A) {
       __syncthreads();
       if (act) {
         R ux = 0, uy = 0, vx = 0, vy = 0, wx = 0, wy = 0;
+        R uz = 0, vz = 0, wz = 0;   // zeta derivatives (warped layers)
 #pragma unroll
         for (int m = 0; m < n1; ++m) {
           const R Di = PTab<R>::D(N, i * n1 + m), Dj = PTab<R>::D(N, j * n1 + m);
@@ -218,6 +262,19 @@ physics_column(const PhysArgs A) {
           vy += Dj * sU[1][ly];
           wx += Di * sU[2][lx];
           wy += Dj * sU[2][ly];
+          if (WARP) {
+            const R Dc = PTab<R>::D(N, c * n1 + m);
+            const int lz = i + n1 * j + Nq * m;
+            uz += Dc * sU[0][lz];
+            vz += Dc * sU[1][lz];
+            wz += Dc * sU[2][lz];
+          }
+        }
+        if (WARP) {
+          // derivatives at constant height
+          const R ex = zx / zz, ey = zy / zz;
+          ux -= ex * uz; vx -= ex * vz; wx -= ex * wz;
+          uy -= ey * uz; vy -= ey * vz; wy -= ey * wz;
         }
         ux *= gx; vx *= gx; wx *= gx;
         uy *= gy; vy *= gy; wy *= gy;
@@ -231,6 +288,13 @@ physics_column(const PhysArgs A) {
         sF[3][t] = ay * ((R)-2 * kv * syy);
         sF[4][t] = ax * (-kv * wx);
         sF[5][t] = ay * (-kv * wy);
+        if (WARP) {
+          // the zeta component of each flux, through J grad zeta
+          const R bx = -wi * wj * hy * zx * (R)0.5, by = -wi * wj * hx * zy * (R)0.5;
+          sF[WARP ? 6 : 0][t] = bx * ((R)-2 * kv * sxx) + by * ((R)-2 * kv * sxy);
+          sF[WARP ? 7 : 0][t] = bx * ((R)-2 * kv * sxy) + by * ((R)-2 * kv * syy);
+          sF[WARP ? 8 : 0][t] = bx * (-kv * wx) + by * (-kv * wy);
+        }
       }
       __syncthreads();
       if (act) {
@@ -241,6 +305,13 @@ physics_column(const PhysArgs A) {
           r[1] += Dwi * sF[0][lx] + Dwj * sF[1][ly];
           r[2] += Dwi * sF[2][lx] + Dwj * sF[3][ly];
           r[3] += Dwi * sF[4][lx] + Dwj * sF[5][ly];
+          if (WARP) {
+            const R Dwc = PTab<R>::Dw(N, c * n1 + m);
+            const int lz = i + n1 * j + Nq * m;
+            r[1] += Dwc * sF[WARP ? 6 : 0][lz];
+            r[2] += Dwc * sF[WARP ? 7 : 0][lz];
+            r[3] += Dwc * sF[WARP ? 8 : 0][lz];
+          }
         }
       }
     }
@@ -266,8 +337,14 @@ physics_column(const PhysArgs A) {
 template <int N, typename R>
 void launch_n(const PhysArgs& A, int eq, int ncol, cudaStream_t st) {
   constexpr int threads = ((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32;
-  if (eq == SEM_EQ_CONSERVATIVE) physics_column<N, 0, R><<<ncol, threads, 0, st>>>(A);
-  else physics_column<N, 1, R><<<ncol, threads, 0, st>>>(A);
+  if (A.metric) {
+    if (eq == SEM_EQ_CONSERVATIVE) physics_column<N, 0, R, true><<<ncol, threads, 0, st>>>(A);
+    else physics_column<N, 1, R, true><<<ncol, threads, 0, st>>>(A);
+  } else if (eq == SEM_EQ_CONSERVATIVE) {
+    physics_column<N, 0, R><<<ncol, threads, 0, st>>>(A);
+  } else {
+    physics_column<N, 1, R><<<ncol, threads, 0, st>>>(A);
+  }
 }
 
 // Mixed form, conservative set: the same terms with the thread layout of the
@@ -594,6 +671,15 @@ int launch_physics(Mesh& m, const sem_params& p, const void* q, bool mixed, void
   A.zk = D.zk;
   A.hzk = D.hzk;
   A.hzk32 = D.hzk32;
+  const bool w = m.warped();
+  A.metric = w ? (mixed ? (const void*)D.metric32 : (const void*)D.metric) : nullptr;
+  A.zG = w ? D.zG : nullptr;
+  A.zH = w ? D.zH : nullptr;
+  A.refG = w ? (mixed ? (const void*)D.refG32 : (const void*)D.refG) : nullptr;
+  A.refH = w ? (mixed ? (const void*)D.refH32 : (const void*)D.refH) : nullptr;
+  A.spg_gamma = p.sponge_gamma;
+  A.spg_depth = p.sponge_depth;
+  A.Lz = m.Lz;
   for (int l = 0; l < 16; ++l) {
     A.geo[l][0] = m.hx(l);
     A.geo[l][1] = m.hy(l);
@@ -601,7 +687,7 @@ int launch_physics(Mesh& m, const sem_params& p, const void* q, bool mixed, void
   }
   ProfScope ps("physics", st);
   const int ncol = (int)m.Ncol();
-  if (mixed && p.eqset == SEM_EQ_CONSERVATIVE) {
+  if (mixed && p.eqset == SEM_EQ_CONSERVATIVE && !w) {
     switch (m.N) {
       case 2: rc = launch_lines<2, 16, 4>(A, ncol, st); break;
       case 3: rc = launch_lines<3, 16, 2>(A, ncol, st); break;

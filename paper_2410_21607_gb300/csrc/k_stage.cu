@@ -1571,7 +1571,8 @@ static int launch_pencil_n(const VolArgs& A, int N, int nz, cudaStream_t st, int
 // the physics pass leaves out what it added (sponge_done, smag_done).
 static int element_terms(Mesh& m, const sem_params& p, VolArgs& A, bool& sponge_done, bool& smag_done) {
   sponge_done = smag_done = false;
-  if (p.eqset != SEM_EQ_CONSERVATIVE) return SEM_OK;
+  // warped layers: the physics pass adds every term (at each node's height)
+  if (p.eqset != SEM_EQ_CONSERVATIVE || m.warped()) return SEM_OK;
   int v = m.pencil_variant;
   if (v < 0 || v >= kNumPencil || kPencil[v].N != m.N) v = pencil_default(m.N, m.nz);
   if (v < 0 || kPencil[v].kind != 1) return SEM_OK;
@@ -1767,8 +1768,6 @@ int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float
                       cudaStream_t st) {
   int rc = upload_basis_constants();
   if (rc) return rc;
-  if (m.warped() && physics_on(p))
-    return fail(SEM_ERR_UNSUPPORTED, "warped layers: the stress, absorbing layer and heating are not built");
   DeviceTables& D = *m.dev;
   float* d = work32;
   float* qs32 = work32 + (size_t)kFields * m.NG;
@@ -2341,8 +2340,6 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
   int rc = upload_basis_constants();
   if (rc) return rc;
   if (m.NG * kFields >= (1ll << 31)) return fail(SEM_ERR_ARG, "mesh too large for 32-bit node indexing");
-  if (m.warped() && physics_on(p))
-    return fail(SEM_ERR_UNSUPPORTED, "warped layers: the stress, absorbing layer and heating are not built");
   DeviceTables& D = *m.dev;
   const bool mixed = p.precision == SEM_PREC_MIXED;
   const float* qs32 = s.qs32;

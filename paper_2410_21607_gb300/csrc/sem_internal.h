@@ -194,6 +194,7 @@ struct DeviceTables {
   bool ref_valid = false;
   // warped layers: per-node tables (null on box meshes)
   double* zG = nullptr;         // [NG] node heights
+  double* zH = nullptr;         // [Nhang][NZ] heights of the hanging lines' nodes
   double* metric = nullptr;     // [Ncol][Nq][nz][N+1][3] z_xi, z_eta, z_zeta
   float* metric32 = nullptr;
   double* Minv_g = nullptr;     // [NG] inverse lumped mass per node

@@ -159,12 +159,14 @@ def test_uniform_counts_and_info(sem):
     assert m.info.n_hanging_h == 0
 
 
-def _fake_checkpoint(path, ncol_leaves, NG, corrupt=None):
-    """A checkpoint file in the library's layout (header, leaves, layer faces,
-    state, FNV-1a)."""
+def _fake_checkpoint(path, ncol_leaves, NG, corrupt=None, warp=(0.0, 0, 0), version=3):
+    """A checkpoint file in the library's layout (header with the warped-layer
+    parameters, leaves, layer faces, state, FNV-1a)."""
     import struct
-    head = struct.pack("<8s4d8i3q", b"SEMCKPT2", 80e3, 80e3, 10e3, 1.5, 2, 2, 1, 4, 1, 1, 0, 0,
+    head = struct.pack("<8s4d8i3q", b"SEMCKPT%d" % version, 80e3, 80e3, 10e3, 1.5, 2, 2, 1, 4, 1, 1, 0, 0,
                        len(ncol_leaves), NG, 7)
+    if version >= 3:
+        head += struct.pack("<d2i", float(warp[0]), int(warp[1]), int(warp[2]))
     leaves = np.asarray(ncol_leaves, dtype=np.int32).tobytes()
     faces = np.array([0.0, 10e3]).tobytes()
     state = np.arange(5 * NG, dtype=np.float64).tobytes()
@@ -202,6 +204,24 @@ def test_checkpoint_reading_rejects_bad_files(sem, tmp_path):
     with pytest.raises(sem.SemError) as e:
         sem.sem_checkpoint_read_mesh(garbage)
     assert e.value.code == sem.SEM_ERR_IO
+    old = tmp_path / "v2.ckpt"                 # the format before warped layers
+    _fake_checkpoint(old, leaves, m.NG, version=2)
+    with pytest.raises(sem.SemError) as e:
+        sem.sem_checkpoint_read_mesh(old)
+    assert e.value.code == sem.SEM_ERR_IO and "earlier version" in str(e.value)
+
+
+def test_checkpoint_of_a_warped_mesh_rebuilds_it(sem, tmp_path):
+    """The warped-layer parameters travel in the checkpoint: the mesh read
+    back has the warped node heights of the mesh that wrote it."""
+    leaves = [(0, i, j) for j in range(2) for i in range(2)]
+    w = sem.sem_mesh_create(80e3, 80e3, 10e3, 2, 2, 1, 4, warp=(300.0, 1, 1))
+    path = tmp_path / "warped.ckpt"
+    _fake_checkpoint(path, leaves, w.NG, warp=(300.0, 1, 1))
+    m2, t, s = sem.sem_checkpoint_read_mesh(path)
+    np.testing.assert_array_equal(sem.sem_mesh_coords_host(m2), sem.sem_mesh_coords_host(w))
+    box = sem.sem_mesh_create(80e3, 80e3, 10e3, 2, 2, 1, 4)
+    assert np.abs(sem.sem_mesh_coords_host(m2)[2] - sem.sem_mesh_coords_host(box)[2]).max() > 50.0
 
 
 def test_one_time_setup_runs_once_per_device(sem):

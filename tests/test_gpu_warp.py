@@ -149,14 +149,117 @@ def test_warped_speed_criterion_and_diagnostics(sem):
     assert abs(d["max_wind"] - sp.max()) <= 1e-12 * sp.max()
 
 
+PHYS = dict(smag_cs=0.21, sponge_gamma=0.02, sponge_depth=6000.0)
+HEAT = dict(heat_q0=0.005, heat_r0=27.5e3, heat_width=10e3, heat_rmax=60e3, heat_ztop=10e3, heat_ramp=5.0)
+ADDED_TOL = 1e-3
+
+
+def _gpu_rhs(sem, m, q, eqset, prec, **phys):
+    p = sem.sem_params_default(eqset=0 if eqset == "C" else 1, precision=prec, **phys)
+    out = torch.full_like(q, float("nan"))
+    sem.sem_rhs(m, p, q, out)
+    return host(out)
+
+
+@pytest.mark.parametrize("name", ["warped-4x4x2-N4", "warped-twolevel-N4", "warped-twolevel-N3"])
+@pytest.mark.parametrize("eqset", ["C", "NC"])
+@pytest.mark.parametrize("terms", ["stress+layer", "heating"])
+def test_warped_physics_rhs_matches_oracle(sem, name, eqset, terms):
+    """The terms of the paper's runs on warped layers: horizontal stress at
+    constant height (through the metric), absorbing layer and heating at
+    each node's height.  Totals at 1e-12 (float64) and 1e-4 (mixed); the
+    added terms alone at 1e-9 (float64) and ADDED_TOL of their own norm
+    (mixed)."""
+    m, o, X, perm = make_pair(sem, **WMESH[name])
+    phys = dict(PHYS) if terms == "stress+layer" else dict(time=3.0, **HEAT)
+    q_o = random_state(o.XG, o.Lz, 25, eqset)
+    T_o = orhs.rhs(o, q_o, refstate.Params(**phys), eqset)
+    dT_o = T_o - orhs.rhs(o, q_o, PRM, eqset)
+    assert np.linalg.norm(dT_o) > 0
+    q = dev(q_o[:, perm])
+    for prec, tol, added in ((0, 1e-12, 1e-9), (1, 1e-4, ADDED_TOL)):
+        T = _gpu_rhs(sem, m, q, eqset, prec, **phys)
+        dT = T - _gpu_rhs(sem, m, q, eqset, prec)
+        assert np.all(group_rel_l2(T, T_o[:, perm]) <= tol), prec
+        for g in (slice(1, 4), slice(0, 1), slice(4, 5)):
+            ref = np.linalg.norm(dT_o[g])
+            if ref > 0:
+                assert np.linalg.norm(dT[g] - dT_o[g][:, perm]) <= added * ref, (prec, g)
+            else:
+                assert np.all(dT[g] == 0.0), (prec, g)
+    assert sem.sem_status(m) == 0
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_warped_physics_steps_match_oracle(sem, prec):
+    """Five steps of 1 s from the balanced vortex with the stress, the
+    absorbing layer and the heating (stage times) on a warped 2:1 mesh."""
+    m, o, X, perm = make_pair(sem, **WMESH["warped-twolevel-N4"])
+    phys = dict(PHYS, **HEAT)
+    q0 = vortex_state(o.XG, o.Lz)
+    q_ref = q0.copy()
+    for s_ in range(5):
+        q_ref = ork.rk_step(o, refstate.Params(time=float(s_), **phys), q_ref, 1.0)
+    q = dev(q0[:, perm])
+    p = sem.sem_params_default(precision=prec, **phys)
+    if prec == 0:
+        w1, w2 = torch.empty_like(q), torch.empty_like(q)
+    else:
+        q32 = torch.empty(q.shape, dtype=torch.float32, device="cuda")
+        work = torch.empty((10, m.NG), dtype=torch.float32, device="cuda")
+        sem.sem_mirror(m, q, q32)
+    for s_ in range(5):
+        p.time = float(s_)
+        if prec == 0:
+            sem.sem_step(m, p, q, w1, w2, 1.0)
+        else:
+            sem.sem_step_mixed(m, p, q, q32, work, 1.0)
+    got = host(q)
+    tol = 1e-10 if prec == 0 else 1e-4
+    assert np.all(group_rel_l2(full_fields(got, X[:, 2]), full_fields(q_ref[:, perm], X[:, 2])) <= tol)
+    assert np.all(increment_err(got, q0[:, perm], q_ref[:, perm]) <= tol)
+    assert sem.sem_status(m) == 0
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_warped_checkpoint_resume_is_bitwise(sem, prec, tmp_path):
+    """Four steps straight through equal two steps, a checkpoint, the mesh
+    and state read back (warped layers rebuilt from the file), and two more."""
+    m, o, X, perm = make_pair(sem, **WMESH["warped-twolevel-N4"])
+    q0 = dev(vortex_state(o.XG, o.Lz)[:, perm])
+    p = sem.sem_params_default(precision=prec)
+
+    def steps(mesh, q, n):
+        if prec == 0:
+            w1, w2 = torch.empty_like(q), torch.empty_like(q)
+            for _ in range(n):
+                sem.sem_step(mesh, p, q, w1, w2, 1.0)
+        else:
+            q32 = torch.empty(q.shape, dtype=torch.float32, device="cuda")
+            work = torch.empty((10, mesh.NG), dtype=torch.float32, device="cuda")
+            sem.sem_mirror(mesh, q, q32)
+            for _ in range(n):
+                sem.sem_step_mixed(mesh, p, q, q32, work, 1.0)
+        return q
+
+    a = steps(m, q0.clone(), 4)
+    b = steps(m, q0.clone(), 2)
+    path = tmp_path / "warped.ckpt"
+    sem.sem_checkpoint_write(m, b, path, time=2.0, step=2)
+    m2, t, s_ = sem.sem_checkpoint_read_mesh(path)
+    c = torch.empty((5, m2.NG), dtype=torch.float64, device="cuda")
+    sem.sem_checkpoint_read_state(path, m2, c)
+    c = steps(m2, c, 2)
+    torch.cuda.synchronize()
+    assert torch.equal(a, c)
+    box = sem.sem_mesh_create(300e3, 300e3, 12e3, 4, 4, 2, 4, leaves=two_level_leaves(), lvl_max=3)
+    with pytest.raises(sem.SemError):          # written for the warped mesh
+        sem.sem_checkpoint_read_state(path, box, c)
+
+
 def test_warped_refusals(sem):
     m, o, X, perm = make_pair(sem, **WMESH["warped-4x4x2-N4"])
     q = dev(random_state(o.XG, o.Lz, 5)[:, perm])
-    out = torch.empty_like(q)
-    for kw in (dict(smag_cs=0.21), dict(sponge_gamma=0.1, sponge_depth=3000.0), dict(heat_q0=1e-3)):
-        with pytest.raises(sem.SemError) as e:
-            sem.sem_rhs(m, sem.sem_params_default(**kw), q, out)
-        assert e.value.code == sem.SEM_ERR_UNSUPPORTED, kw
     with pytest.raises(sem.SemError) as e:
         p = sem.sem_params_default(thresholds=[1e-4, 2e-4, 3e-4], lvl_max=3, criterion=[1, 1, 1])
         sem.sem_adapt_flags(m, p, q, torch.empty(m.Ne, dtype=torch.int8, device="cuda"))

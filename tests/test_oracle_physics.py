@@ -219,3 +219,62 @@ def test_heating_enters_the_step_at_the_stage_times():
     Qs = [rhs.heating_rate(m.XG[:, 0], m.XG[:, 1], m.XG[:, 2], prm.at(prm.time + c * dt)) for c in (0, 1, 0.5)]
     simpson = dt * (Qs[0] + Qs[1] + 4 * Qs[2]) / 6
     np.testing.assert_allclose(q1[4], rho0 * simpson, rtol=1e-5, atol=1e-5 * np.abs(rho0 * simpson).max())
+
+
+# ---------------------------------------------------------------------------
+# warped layers (non-affine elements): the same properties with the general
+# isoparametric metric
+
+WARP = (600.0, 1, 1)
+
+
+@pytest.mark.parametrize("eqset", ["C", "NC"])
+def test_warped_sponge_and_heating_act_pointwise_at_the_node_heights(eqset):
+    """On a conforming warped mesh the lumped collocated sources are the
+    pointwise values at each global node's own height (a level height in
+    their place fails: the layer surfaces are curved)."""
+    m = mesh.OracleMesh(L, L, LZ, 3, 3, 3, 4, warp=WARP)
+    z = m.XG[:, 2]
+    prm = refstate.Params(sponge_gamma=0.01, sponge_depth=6000.0)
+    q = random_state(m.XG, LZ, 3, eqset)
+    T = visc_tendency(m, q, prm, eqset)
+    expect = -rhs.sponge_rate(z, LZ, prm)[None, :] * q
+    expect[3, m.z_bottom | m.z_top] = 0.0
+    np.testing.assert_allclose(T, expect, rtol=1e-10, atol=1e-12 * np.abs(expect).max())
+    # the curved layer surfaces put the nodes of one level at different
+    # heights, inside the layer where the rate varies
+    zb = m.XG_box[:, 2]
+    level = np.abs(zb - zb[np.argmin(np.abs(zb - (LZ - 3000.0)))]) < 1e-6
+    assert np.ptp(z[level]) > 100.0 and np.ptp(expect[0][level]) > 0.0
+    hm = mesh.OracleMesh(200e3, 200e3, 18e3, 4, 4, 3, 4, warp=WARP)
+    hp = refstate.Params(heat_q0=0.004, time=900.0)
+    Th = rhs.rhs(hm, np.zeros((5, hm.NG)), hp, eqset)
+    Q = rhs.heating_rate(hm.XG[:, 0], hm.XG[:, 1], hm.XG[:, 2], hp)
+    fac = refstate.reference_state(hm.XG[:, 2], hp)["rho0"] if eqset == "C" else 1.0
+    np.testing.assert_allclose(Th[4], fac * Q, rtol=1e-12, atol=1e-15 * np.abs(fac * Q).max())
+    assert np.all(Th[:4] == 0.0) and np.count_nonzero(Q) > 0
+
+
+@pytest.mark.parametrize("eqset,nc", [("C", False), ("NC", False), ("NC", True)])
+def test_warped_smagorinsky_energy_identity_and_dissipation(eqset, nc):
+    """The stress's energy identity with horizontal gradients taken at
+    constant height through the warped metric: it fixes the pairing of the
+    horizontal fluxes with the zeta derivatives of the test functions."""
+    m = (mesh.OracleMesh(L, L, LZ, 4, 4, 2, 4, leaves=two_level_leaves(), warp=WARP) if nc
+         else mesh.OracleMesh(L, L, LZ, 3, 3, 2, 4, warp=WARP))
+    prm = refstate.Params(smag_cs=0.21)
+    q = random_state(m.XG, LZ, 8, eqset)
+    lhs, rhs_ = _energy_identity(m, q, prm, eqset)
+    assert rhs_ < 0.0
+    assert abs(lhs - rhs_) <= 1e-10 * abs(rhs_)
+
+
+@pytest.mark.parametrize("eqset", ["C", "NC"])
+def test_warped_physics_keep_mass_conservation_and_rest_state(eqset):
+    m = mesh.OracleMesh(L, L, LZ, 4, 4, 2, 4, leaves=two_level_leaves(), warp=WARP)
+    prm = refstate.Params(smag_cs=0.21, sponge_gamma=0.01)
+    assert np.all(rhs.rhs(m, np.zeros((5, m.NG)), prm, eqset) == 0.0)
+    q = random_state(m.XG, LZ, 4, eqset)
+    Tv = visc_tendency(m, q, refstate.Params(smag_cs=0.21), eqset)
+    assert np.all(Tv[0] == 0.0) and np.all(Tv[4] == 0.0)
+    assert np.abs(Tv[1:4]).max() > 0.0
