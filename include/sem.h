@@ -94,10 +94,11 @@ typedef struct {
    * side, the stages and steps (float64 and mixed forms), the terms of the
    * paper's runs (the horizontal Smagorinsky stress with gradients at constant
    * height, the absorbing layer and the heating at each node's height), the
-   * speed criterion, coordinates, diagnostics and checkpoints are available;
-   * the vorticity and potential-vorticity criteria, adaptation
-   * (sem_transfer_plan) and batching give SEM_ERR_UNSUPPORTED, and the mixed
-   * conservative form uses the line-exchange element kernels only. */
+   * criteria (speed; vorticity and potential vorticity with derivatives at
+   * constant height), coordinates, diagnostics and checkpoints are available;
+   * adaptation (sem_transfer_plan) and batching give SEM_ERR_UNSUPPORTED, and
+   * the mixed conservative form uses the line-exchange element kernels
+   * only. */
   double warp_amplitude;
   int warp_kx, warp_ky;
 } sem_mesh_desc;

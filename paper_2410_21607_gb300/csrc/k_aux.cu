@@ -63,6 +63,9 @@ struct AdaptArgs {
   // the geometry always uses the column's level
   const int8_t* elem_level;
   int level_all;
+  // warped layers: z_xi, z_eta, z_zeta per node of each column line
+  // ([Ncol][Nq][nz][N+1][3]), else null
+  const double* metric;
 };
 
 template <int N, int EQ>
@@ -129,11 +132,25 @@ adapt_column(const AdaptArgs A) {
             d[qv][2] += Dc * sQ[qv][lz];
           }
         }
-        const double gx = A.gx[geo_lev], gy = A.gy[geo_lev], gz = 2.0 / A.hzk[k];
-        for (int qv = 0; qv < 4; ++qv) {
-          d[qv][0] *= gx;
-          d[qv][1] *= gy;
-          d[qv][2] *= gz;
+        const double gx = A.gx[geo_lev], gy = A.gy[geo_lev];
+        if (A.metric) {
+          // warped layers: derivatives at constant height through the node's
+          // metric, d/dx = (2/hx) (d/dxi - (z_xi / z_zeta) d/dzeta), d/dz = d/dzeta / z_zeta
+          const double* mt = A.metric + ((((long long)col * Nq + ab) * A.nz + k) * n1 + c) * 3;
+          const double zx = mt[0], zy = mt[1], zz = mt[2];
+          for (int qv = 0; qv < 4; ++qv) {
+            const double dz = d[qv][2] / zz;
+            d[qv][0] = gx * (d[qv][0] - zx * dz);
+            d[qv][1] = gy * (d[qv][1] - zy * dz);
+            d[qv][2] = dz;
+          }
+        } else {
+          const double gz = 2.0 / A.hzk[k];
+          for (int qv = 0; qv < 4; ++qv) {
+            d[qv][0] *= gx;
+            d[qv][1] *= gy;
+            d[qv][2] *= gz;
+          }
         }
         const double wz = d[1][0] - d[0][1];
         zeta = fabs(wz);
@@ -216,8 +233,7 @@ int launch_adapt(Mesh& m, const sem_params& p, const double* q, int8_t* flags, d
     A.gy[l] = 2.0 / m.hy(l);
   }
   A.hzk = D.hzk;
-  if (A.need_grad && m.warped())
-    return fail(SEM_ERR_UNSUPPORTED, "warped layers: the vorticity and potential-vorticity criteria are not built");
+  A.metric = m.warped() ? D.metric : nullptr;
   if (A.need_grad) {
     int rc = upload_aux_constants();
     if (rc) return rc;

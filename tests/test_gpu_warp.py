@@ -257,13 +257,41 @@ def test_warped_checkpoint_resume_is_bitwise(sem, prec, tmp_path):
         sem.sem_checkpoint_read_state(path, box, c)
 
 
+@pytest.mark.parametrize("name", ["warped-twolevel-N4", "warped-twolevel-N3"])
+@pytest.mark.parametrize("eqset", ["C", "NC"])
+@pytest.mark.parametrize("variables", [("vorticity",) * 3, ("pv",) * 3, ("speed", "vorticity", "pv")])
+def test_warped_alternative_criteria_match_oracle(sem, name, eqset, variables):
+    """Vorticity and potential vorticity on warped layers (derivatives at
+    constant height through the node metric): element maxima within 1e-10
+    of the oracle's and flags equal away from ties."""
+    crit = {"speed": sem.SEM_CRIT_SPEED, "vorticity": sem.SEM_CRIT_VORTICITY, "pv": sem.SEM_CRIT_PV}
+    m, o, X, perm = make_pair(sem, **WMESH[name])
+    q_o = random_state(o.XG, o.Lz, 33, eqset, amp=0.2)
+    lv = sem.sem_mesh_leaves_host(m)
+    oleaf = {tuple(l): c for c, l in enumerate(o.leaves)}
+    emap = np.array([oleaf[tuple(l)] * o.nz + k for l in lv for k in range(o.nz)])
+    maxima = {v: adapt.CRITERIA[v](o, q_o, PRM, eqset).max(axis=1) for v in set(variables)}
+    thr = [float(np.quantile(maxima[v], qq)) * (1 + 1e-6) for v, qq in zip(variables, (0.3, 0.6, 0.9))]
+    fl_o, cmax_o = adapt.criterion_flags(o, q_o, PRM, thr, 3, eqset, variables=list(variables))
+    p = sem.sem_params_default(eqset=0 if eqset == "C" else 1, thresholds=thr, lvl_max=3,
+                               criterion=[crit[v] for v in variables])
+    flags = torch.empty(m.Ne, dtype=torch.int8, device="cuda")
+    cmax = torch.empty(m.Ne, dtype=torch.float64, device="cuda")
+    sem.sem_adapt_flags(m, p, dev(q_o[:, perm]), flags, cmax)
+    fl, cm = host(flags), host(cmax)
+    np.testing.assert_allclose(cm, cmax_o[emap], rtol=1e-10, atol=1e-12 * np.abs(cmax_o).max())
+    levels = o.level[emap]
+    near = np.zeros(m.Ne, dtype=bool)
+    for lvl in range(4):
+        for t_idx in (lvl - 1, lvl):
+            if 0 <= t_idx < 3:
+                mx = maxima[variables[t_idx]][emap]
+                near |= (levels == lvl) & (np.abs(mx - thr[t_idx]) <= 1e-9 * abs(thr[t_idx]))
+    assert np.array_equal(fl[~near], fl_o[emap][~near])
+
+
 def test_warped_refusals(sem):
     m, o, X, perm = make_pair(sem, **WMESH["warped-4x4x2-N4"])
-    q = dev(random_state(o.XG, o.Lz, 5)[:, perm])
-    with pytest.raises(sem.SemError) as e:
-        p = sem.sem_params_default(thresholds=[1e-4, 2e-4, 3e-4], lvl_max=3, criterion=[1, 1, 1])
-        sem.sem_adapt_flags(m, p, q, torch.empty(m.Ne, dtype=torch.int8, device="cuda"))
-    assert e.value.code == sem.SEM_ERR_UNSUPPORTED
     with pytest.raises(sem.SemError) as e:
         sem.sem_batch_create([m])
     assert e.value.code == sem.SEM_ERR_UNSUPPORTED

@@ -83,3 +83,28 @@ def test_per_level_variables():
     f0, c0 = adapt.criterion_flags(m, q, PRM, [5.0, 10.0], 2)
     f1, c1 = adapt.criterion_flags(m, q, PRM, [5.0, 10.0], 2, variables=["speed", "speed"])
     assert np.array_equal(f0, f1) and np.array_equal(c0, c1)
+
+
+@pytest.mark.parametrize("eqset", ["C", "NC"])
+def test_warped_vorticity_is_taken_at_constant_height(eqset):
+    """On warped layers u = -omega y + a z, v = omega x + b z: the vertical
+    vorticity at constant height is exactly 2 omega, which holds only if the
+    horizontal derivatives carry the metric's correction -(z_xi / z_zeta)
+    d/dzeta (without it the shear a, b leaks in through the tilted layers).
+    The rigid rotation's potential vorticity (2 omega + f) dtheta0/dz / rho0
+    holds to 2e-4: the exponential theta0 is interpolated along curved
+    elements."""
+    m = mesh.OracleMesh(300e3, 300e3, 12e3, 3, 3, 2, 4, periodic=(False, False), warp=(600.0, 1, 1))
+    om, a, b = 3e-5, 2e-3, -1e-3
+    ref = refstate.reference_state(m.XG[:, 2], PRM)
+    x, y, z = m.XG[:, 0], m.XG[:, 1], m.XG[:, 2]
+    fac = ref["rho0"] if eqset == "C" else 1.0
+    q = np.zeros((5, m.NG))
+    q[1], q[2] = (-om * y + a * z) * fac, (om * x + b * z) * fac
+    zeta = adapt.criterion_vorticity(m, q, PRM, eqset)
+    np.testing.assert_allclose(zeta, 2 * om, rtol=1e-9)
+    # without the shear the potential vorticity has the rigid-rotation value
+    qr = rotation_state(m, om, eqset)
+    refl = refstate.reference_state(m.X[:, :, 2], PRM)
+    np.testing.assert_allclose(adapt.criterion_pv(m, qr, PRM, eqset),
+                               (2 * om + PRM.f) * refl["dtheta0"] / refl["rho0"], rtol=2e-4)
