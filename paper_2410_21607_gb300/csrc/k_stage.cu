@@ -1525,7 +1525,7 @@ static const PencilVariant kPencil[] = {
     {2, 16, 2, launch_pencil<2, 16, 2>},    {2, 16, 4, launch_lines<2, 16, 4>, 1},
     {2, 32, 2, launch_lines<2, 32, 2>, 1},
     {3, 16, 2, launch_pencil<3, 16, 2>},    {3, 16, 2, launch_lines<3, 16, 2>, 1},
-    {3, 8, 4, launch_lines<3, 8, 4>, 1},
+    {3, 8, 4, launch_lines<3, 8, 4>, 1},    {3, 8, 6, launch_lines<3, 8, 6>, 1},
     {4, 8, 2, launch_pencil<4, 8, 2>},      {4, 16, 2, launch_pencil<4, 16, 2>},
     {4, 16, 2, launch_lines<4, 16, 2>, 1, launch_lines_smag<4, 16, 2>},
     {4, 8, 4, launch_lines<4, 8, 4>, 1, launch_lines_smag<4, 8, 4>},
