@@ -220,7 +220,7 @@ int sem_rhs(sem_mesh* m, const sem_params* p, const double* q_dev, double* rhs_d
  * by any earlier device call on it (for example sem_mesh_coords), else
  * SEM_ERR_ARG, and those tables include the mesh's own residual scratch,
  * which stays allocated.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress, kept per device; the driver may load
+ * device address (cudaGetSymbolAddress, kept per device; the CUDA driver may load
  * the library's device code then); make that first call before any stream
  * capture.  A call whose reference-state parameters (g, R_d, c_p, p00,
  * theta_s, N_bv) differ from those of the mesh's previous call uploads the

@@ -74,7 +74,7 @@ def test_rhs_noalloc_matches_rhs_on_two_calls(sem, kind, precision):
 
 
 def test_rhs_noalloc_leaves_free_memory_unchanged(sem):
-    """After a first call (which may make the driver load the library's
+    """After a first call (which may make the CUDA driver load the library's
     device code with its array), further calls change the device's free
     memory by nothing."""
     from synth.vortex import random_state
