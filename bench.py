@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--no-amr", action="store_true")
     ap.add_argument("--no-physics", action="store_true")
     ap.add_argument("--no-warped", action="store_true")
+    ap.add_argument("--mlp-forward-only", action="store_true",
+                    help="time only the flag network's forwards on 2^20 feature rows and print that "
+                         "object (a short command for profiling them)")
     ap.add_argument("--kernel-row", type=int, default=None,
                     help="use this row of the element-kernel variant table instead of autotuning "
                          "(for profiler runs, whose per-launch overhead distorts the timings)")
@@ -617,6 +620,11 @@ def main():
         dist.barrier()
     from paper_2410_21607_gb300 import sem
     from synth.vortex import vortex_state
+
+    if a.mlp_forward_only:
+        if rank == 0:
+            print(json.dumps({"mlp_forward": mlp_forward_measure(sem, torch)}), flush=True)
+        return 0
 
     L, Lz, n, nz, N, dt = 2048e3, 24e3, 64, 16, 4, 0.25
     m = sem.sem_mesh_create(L, L, Lz, n, n, nz, N)
