@@ -1056,7 +1056,27 @@ __device__ __forceinline__ void smag_phases(const VolArgs& A, float* smem, const
 // Body shared by the single-mesh kernel (one CTA per column) and the batched
 // persistent kernel.  Threads t >= KL (N+1)^2 of a larger CTA take part in
 // the barriers only.
-template <int N, int KL, bool SMAG = false, bool WARP = false>
+// TMA (kind 4): the state runs of the CTA's non-hanging column lines are
+// staged in shared memory by bulk copies (cp.async.bulk, one per field and
+// line: the 16-byte-aligned window of at most KL N + 1 + 3 floats around the
+// chunk's levels), completing on an mbarrier; the copies of chunk ch + 1 are
+// issued once every thread has read chunk ch's staged values and run under
+// chunk ch's line exchange.  Hanging lines, a state array that is not 16-byte
+// aligned and a window that would run past the end of the array take the
+// plain loads.  The values, hence the arithmetic, are those of the plain
+// kernel.  The waits are bounded: a wait that runs out sets bit 2 of the
+// status word, waits once more for the copies in flight and leaves the
+// column's remaining chunks unwritten.
+template <int N, int KL>
+__host__ __device__ constexpr int lines_tma_sw() { return (KL * N + 1 + 3 + 3) / 4 * 4; }
+template <int N, int KL>
+__host__ __device__ constexpr int lines_tma_stage_off() { return (lines_smem_floats<N, KL>() + 3) / 4 * 4; }
+template <int N, int KL>
+__host__ __device__ constexpr int lines_tma_smem_floats() {
+  return lines_tma_stage_off<N, KL>() + kFields * (N + 1) * (N + 1) * lines_tma_sw<N, KL>() + 4;
+}
+
+template <int N, int KL, bool SMAG = false, bool WARP = false, bool TMA = false>
 __device__ __forceinline__ void lines_body(const VolArgs& A, const int col, float* smem, const int t) {
   constexpr int n1 = N + 1, Nq = n1 * n1;
   constexpr int LW = lines_lw<N>(), LS = lines_ls<N, KL>();
@@ -1081,11 +1101,60 @@ __device__ __forceinline__ void lines_body(const VolArgs& A, const int col, floa
   const float wi = c_wf[N][i], wj = c_wf[N][j];
   float* rc = (float*)A.rc;
   const int nchunk = (A.nz + KL - 1) / KL;
+  // TMA staging: window of field f, line ab at sQ + (f Nq + ab) SW
+  constexpr int SW = lines_tma_sw<N, KL>();
+  float* sQ = smem + lines_tma_stage_off<N, KL>();
+  const uint32_t bar = TMA ? tcg::smem_u32(sQ + kFields * Nq * SW) : 0u;
+  const float* qf = (const float*)A.q;
+  const long long qtot = (long long)kFields * A.NG;
+  const bool tma_ok = TMA && (((uintptr_t)A.q & 15) == 0);
+  // whether chunk chn's window of line hq fits the array (the last field's is the furthest)
+  auto staged = [&](int hq, int chn) {
+    const int nl = min(KL, A.nz - chn * KL) * N + 1;
+    return tma_ok && hq >= 0 &&
+           ((((long long)(kFields - 1) * A.NG + (long long)hq * A.NZ + chn * KL * N + nl + 3) & ~3ll) <= qtot);
+  };
+  auto issue = [&](int chn) {
+    if (t < kFields * Nq) {
+      const int f = t / Nq, abq = t - (t / Nq) * Nq;
+      const int hq = A.hmap[(long long)col * Nq + abq];
+      if (staged(hq, chn)) {
+        const int nl = min(KL, A.nz - chn * KL) * N + 1;
+        const long long off = (long long)f * A.NG + (long long)hq * A.NZ + chn * KL * N;
+        const long long ws = off & ~3ll, we = (off + nl + 3) & ~3ll;
+        const uint32_t bytes = (uint32_t)((we - ws) * 4);
+        tcg::fence_async_smem();
+        tcg::mbar_expect_tx(bar, bytes);
+        tcg::bulk_g2s(tcg::smem_u32(sQ + (f * Nq + abq) * SW), qf + ws, bytes, bar);
+      }
+    }
+  };
+  if constexpr (TMA) {
+    if (t == 0) tcg::mbar_init(bar, 1);
+    __syncthreads();
+    issue(0);
+    __syncthreads();
+    if (t == 0) tcg::mbar_arrive(bar);
+  }
   for (int ch = 0; ch < nchunk; ++ch) {
     const int k = ch * KL + kk;
     const bool act = part && k < A.nz;
     const int kz0 = k * N;
     const float hk = act ? __ldg(A.hzk32 + k) : 0.f;   // layer thickness
+    // this thread's staged window (TMA): its offset inside the window per field
+    bool st_line = false;
+    int dwin = 0;
+    if constexpr (TMA) {
+      if (!__syncthreads_and(tcg::mbar_wait(bar, (uint32_t)(ch & 1)))) {
+        // a wait ran out: record it, let the copies in flight land, stop
+        if (t == 0) atomicOr(A.status, 4);
+        tcg::mbar_wait(bar, (uint32_t)(ch & 1));
+        __syncthreads();
+        break;
+      }
+      st_line = part && staged(hm, ch);
+      dwin = (int)(((long long)hm * A.NZ + ch * KL * N) & 3);
+    }
     float rz[kFields][n1];
 #pragma unroll
     for (int f = 0; f < kFields; ++f)
@@ -1098,7 +1167,14 @@ __device__ __forceinline__ void lines_body(const VolArgs& A, const int col, floa
       for (int c = 0; c < n1; ++c) {
         float v[kFields];
         const int kz = kz0 + c;
-        load_node<N>(A, hm, kz, v);
+        if (TMA && st_line) {
+          // the staged window: field f starts (f NG) mod 4 floats later
+#pragma unroll
+          for (int f = 0; f < kFields; ++f)
+            v[f] = sQ[(f * Nq + ab) * SW + ((dwin + (int)(((long long)f * A.NG) & 3)) & 3) + kk * N + c];
+        } else {
+          load_node<N>(A, hm, kz, v);
+        }
         const float wc = c_wf[N][c];
         NodeTerms T;
         float wJn = wi * wj * wc * J * hk;
@@ -1140,6 +1216,9 @@ __device__ __forceinline__ void lines_body(const VolArgs& A, const int col, floa
       }
     }
     __syncthreads();
+    // every thread has read chunk ch's staged values: the next chunk's copies
+    // run under this chunk's line exchange
+    if (TMA && ch + 1 < nchunk) issue(ch + 1);
     if (act) {
       // x-line (lo, lc): nodes (m, lo, lc), m = 0..N
       float* bx = sX + kk * LS + lo * n1 * LW + lc;
@@ -1173,6 +1252,8 @@ __device__ __forceinline__ void lines_body(const VolArgs& A, const int col, floa
       }
     }
     __syncthreads();
+    // all of the next chunk's transaction counts are registered
+    if (TMA && ch + 1 < nchunk && t == 0) tcg::mbar_arrive(bar);
     if constexpr (SMAG) {
       if (act) {
 #pragma unroll
@@ -1238,6 +1319,14 @@ __global__ void __launch_bounds__(KL * (N + 1) * (N + 1), MB)
 volume_lines_mixed(const VolArgs A) {
   extern __shared__ __align__(16) float smem[];
   lines_body<N, KL>(A, blockIdx.x, smem, threadIdx.x);
+}
+
+// The same with the state staged by bulk copies (TMA, kind 4).
+template <int N, int KL, int MB>
+__global__ void __launch_bounds__(KL * (N + 1) * (N + 1), MB)
+volume_lines_tma(const VolArgs A) {
+  extern __shared__ __align__(16) float smem[];
+  lines_body<N, KL, false, false, true>(A, blockIdx.x, smem, threadIdx.x);
 }
 
 // The same on warped layers (non-affine elements).
@@ -1511,6 +1600,20 @@ static int launch_lines(const VolArgs& A, cudaStream_t st) {
   return SEM_OK;
 }
 
+template <int N, int KL, int MB>
+static int launch_lines_tma(const VolArgs& A, cudaStream_t st) {
+  constexpr size_t sm = sizeof(float) * lines_tma_smem_floats<N, KL>();
+  static DeviceOnce attr;
+  int rc = device_once(attr, [&] {
+    SEM_CUDA_TRY(cudaFuncSetAttribute(volume_lines_tma<N, KL, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    return SEM_OK;
+  });
+  if (rc) return rc;
+  ProfScope ps("volume_mixed", st);
+  volume_lines_tma<N, KL, MB><<<A.Ncol, KL * (N + 1) * (N + 1), sm, st>>>(A);
+  return SEM_OK;
+}
+
 // Launch variants of the pencil kernel: layers per CTA (KL) and the minimum
 // resident CTAs per SM the register allocation is sized for (MB).  The
 // autotuner (sem_autotune) times them on a mesh and keeps the fastest.
@@ -1518,7 +1621,8 @@ struct PencilVariant {
   int N, KL, MB;
   int (*launch)(const VolArgs&, cudaStream_t);
   int kind;         // 0: z-pencil volume_pencil_mixed; 1: line-exchange volume_lines_mixed;
-                    // 2: line exchange with the x, y contractions on tensor cores (volume_lines_tc)
+                    // 2: line exchange with the x, y contractions on tensor cores (volume_lines_tc);
+                    // 4: line exchange with the state staged by bulk copies (volume_lines_tma)
   int (*launch_smag)(const VolArgs&, cudaStream_t);   // with the stress added; null: none
 };
 static const PencilVariant kPencil[] = {
@@ -1533,6 +1637,7 @@ static const PencilVariant kPencil[] = {
     {4, 4, 8, launch_lines<4, 4, 8>, 1, launch_lines_smag<4, 4, 8>},
     {4, kTcKL, 3, launch_lines_tc<3>, 2},
     {4, 8, 3, launch_lines<4, 8, 3>, 1, launch_lines_smag<4, 8, 3>},
+    {4, 8, 3, launch_lines_tma<4, 8, 3>, 4},  {4, 8, 2, launch_lines_tma<4, 8, 2>, 4},
     {5, 8, 2, launch_pencil<5, 8, 2>},      {5, 8, 2, launch_lines<5, 8, 2>, 1},
     {5, 4, 4, launch_lines<5, 4, 4>, 1},
     {6, 4, 2, launch_pencil<6, 4, 2>},      {6, 8, 1, launch_lines<6, 8, 1>, 1},
@@ -1575,7 +1680,7 @@ static int element_terms(Mesh& m, const sem_params& p, VolArgs& A, bool& sponge_
   if (p.eqset != SEM_EQ_CONSERVATIVE || m.warped()) return SEM_OK;
   int v = m.pencil_variant;
   if (v < 0 || v >= kNumPencil || kPencil[v].N != m.N) v = pencil_default(m.N, m.nz);
-  if (v < 0 || kPencil[v].kind != 1) return SEM_OK;
+  if (v < 0 || (kPencil[v].kind != 1 && kPencil[v].kind != 4)) return SEM_OK;
   if (p.sponge_gamma > 0.0) {
     const int rc = ensure_sponge(m, p);
     if (rc) return rc;

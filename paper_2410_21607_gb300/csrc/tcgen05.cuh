@@ -1,6 +1,7 @@
 // Helpers for the fifth-generation tensor cores (tcgen05) on sm_103a: shared
 // memory matrix descriptors, instruction descriptors, the MMA, its commit to
-// an mbarrier and a bounded wait, tensor-memory loads.  Operands are K-major
+// an mbarrier and a bounded wait, tensor-memory loads; and the untiled bulk
+// copy (TMA) from global to shared memory with its mbarrier transactions.  Operands are K-major
 // without swizzle: core matrices of 8 rows x 16 bytes, `lbo` bytes between
 // core matrices adjacent in K and `sbo` bytes between core matrices adjacent
 // in M (or N).
@@ -65,6 +66,21 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar), "r"(count));
 }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// one arrival on an mbarrier (no transaction bytes)
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}" :: "r"(bar) : "memory");
+}
+// raise the transaction count the current phase of an mbarrier waits for
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+}
+// bulk copy (TMA, untiled) of `bytes` from global to this CTA's shared
+// memory, both addresses 16-byte aligned and `bytes` a multiple of 16; its
+// completion counts its bytes off the mbarrier's transaction count
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 // tensor memory of `ncols` columns (a power of 2 >= 32) for this CTA; one

@@ -143,7 +143,7 @@ def test_every_element_kernel_variant_matches_oracle(sem, name):
         assert np.all(err <= 1e-4), (row, rows[row] if row >= 0 else "default", err)
         if row >= 0:
             kinds.add(rows[row][3])
-    assert kinds == ({0, 1, 2} if m.N == 4 else {0, 1})
+    assert kinds == ({0, 1, 2, 4} if m.N == 4 else {0, 1})
     assert sem.sem_status(m) == 0
 
 
@@ -786,3 +786,38 @@ def test_merge_flags_every_combination(sem):
     t = lambda a: dev(a.astype(np.int8))
     got = host(sem.sem_merge_flags(t(c), t(pr), t(lv), lvl_max))
     assert np.array_equal(got, want.astype(np.int8))
+
+
+@pytest.mark.parametrize("name", ["twolevel-17-layers-N4", "uniform-6x6x4-N4"])
+def test_tma_staged_variant_equals_plain_variant(sem, name):
+    """The line-exchange variant that stages the state with bulk copies (TMA,
+    kind 4) reads the same values as the plain one with the same layers and
+    CTAs per SM: the stage's outputs are equal bit for bit, with a 16-byte
+    aligned mirror (staged) and with one offset by 4 bytes (the plain loads);
+    17 layers give three chunks and the prefetch between them, the two-level
+    mesh hanging lines that are not staged."""
+    spec = dict(MESHES.get(name, {}))
+    if name == "twolevel-17-layers-N4":
+        spec = dict(L=300e3, Lz=24e3, nx=4, nz=17, N=4, leaves=two_level_leaves())
+    m, o, X, perm = make_pair(sem, **spec)
+    q = dev(random_state(o.XG, o.Lz, 14)[:, perm])
+    p = sem.sem_params_default(precision=sem.SEM_PREC_MIXED)
+    q32 = torch.empty(q.shape, dtype=torch.float32, device="cuda")
+    sem.sem_mirror(m, q, q32)
+    rows, _ = sem.sem_autotune(m, p, q32, 1)
+    row = {(r[0], r[1], r[3]): k for k, r in enumerate(rows)}
+    big = torch.empty(q.numel() + 4, dtype=torch.float32, device="cuda")
+    shifted = big[1:1 + q.numel()].view(q.shape)      # 4 bytes past a 16-byte boundary
+    shifted.copy_(q32)
+    assert q32.data_ptr() % 16 == 0 and shifted.data_ptr() % 16 == 4
+    for mb in (3, 2):
+        for mirror in (q32, shifted):
+            outs = []
+            for kind in (1, 4):
+                sem.sem_autotune_select(m, row[(8, mb, kind)])
+                out, out32 = torch.empty_like(q), torch.empty_like(q32)
+                sem.sem_rk_stage_mixed(m, p, 0, q, q, mirror, out, out32, 0.5)
+                outs.append((out, out32))
+            torch.cuda.synchronize()
+            assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1]), (mb, mirror.data_ptr() % 16)
+    assert sem.sem_status(m) == 0
