@@ -433,7 +433,9 @@ typedef struct {
   int chosen;                          /* index into the arrays below */
   int layers_per_cta[SEM_TUNE_MAX];
   int min_ctas_per_sm[SEM_TUNE_MAX];
-  int kind[SEM_TUNE_MAX];              /* 0: z-pencil kernel, 1: line-exchange kernel */
+  int kind[SEM_TUNE_MAX];              /* 0: z-pencil kernel, 1: line-exchange kernel,
+                                          2: line exchange with the x, y contractions on tensor cores,
+                                          4: line exchange with the state staged by bulk copies (TMA) */
   double ms[SEM_TUNE_MAX];             /* mean event time per launch */
 } sem_tune_out;
 int sem_autotune(sem_mesh* m, const sem_params* p, const float* q32_dev, int reps,

@@ -443,7 +443,9 @@ def sem_profile_end():
 def sem_autotune(mesh, params, q32, reps=5, stream=None):
     """Time the element-kernel variants on this mesh and keep the fastest.
     Returns [(layers_per_cta, min_ctas_per_sm, ms, kind)] and the chosen index
-    (kind 0: z-pencil kernel, 1: line-exchange kernel)."""
+    (kind 0: z-pencil kernel, 1: line-exchange kernel, 2: line exchange with
+    the x, y contractions on tensor cores, 4: line exchange with the state
+    staged by bulk copies)."""
     _f32(q32, mesh.field_shape)
     out = TuneOut()
     _check(LIB.sem_autotune(mesh.h, C.byref(params), _ptr(q32), int(reps), C.byref(out),
