@@ -1101,7 +1101,9 @@ __device__ __forceinline__ void lines_body(const VolArgs& A, const int col, floa
   const float wi = c_wf[N][i], wj = c_wf[N][j];
   float* rc = (float*)A.rc;
   const int nchunk = (A.nz + KL - 1) / KL;
-  // TMA staging: window of field f, line ab at sQ + (f Nq + ab) SW
+  // TMA staging: window of field f, line ab at sQ + (f Nq + ab) SW; thread
+  // t < 5 Nq issues the copy of (field t / Nq, line t mod Nq)
+  static_assert(!TMA || (KL >= kFields && !SMAG && !WARP), "TMA staging needs a thread per field and line");
   constexpr int SW = lines_tma_sw<N, KL>();
   float* sQ = smem + lines_tma_stage_off<N, KL>();
   const uint32_t bar = TMA ? tcg::smem_u32(sQ + kFields * Nq * SW) : 0u;
