@@ -254,8 +254,9 @@ int sem_rk_stage_mixed(sem_mesh* m, const sem_params* p, int stage, const double
                        const double* qs_dev, const float* qs32_dev, double* qout_dev,
                        float* qout32_dev, double dt, cudaStream_t stream);
 
-/* A whole SSP-RK3 step of the mixed form, conservative set, in increment
- * form: with d_s = q_s - q_n,
+/* A whole SSP-RK3 step of the mixed form, either equation set (the
+ * conservative set through the autotuned element kernel, the paper's set
+ * through the column element kernel), in increment form: with d_s = q_s - q_n,
  *   d_1 = dt L(q_n), d_2 = (d_1 + dt L(q_1)) / 4, d_3 = 2 (d_2 + dt L(q_2)) / 3,
  *   q_{n+1} = q_n + d_3,
  * which is the Shu-Osher SSP-RK3 step rewritten exactly.  The increments d_s

@@ -489,8 +489,7 @@ int sem_step_mixed(sem_mesh* mh, const sem_params* p, double* q, float* q32, flo
                    double dt, cudaStream_t st) {
   int rc = prepare(mh, p);
   if (rc) return rc;
-  if (p->precision != SEM_PREC_MIXED || p->eqset != SEM_EQ_CONSERVATIVE)
-    return fail(SEM_ERR_ARG, "sem_step_mixed needs SEM_PREC_MIXED and the conservative set");
+  if (p->precision != SEM_PREC_MIXED) return fail(SEM_ERR_ARG, "sem_step_mixed needs SEM_PREC_MIXED");
   if (!q || !q32 || !work32) return fail(SEM_ERR_ARG, "NULL argument");
   if (mh->m.NG * kFields >= (1ll << 31)) return fail(SEM_ERR_ARG, "mesh too large for 32-bit indexing");
   return launch_step_mixed(mh->m, *p, q, q32, work32, dt, st);

@@ -435,6 +435,8 @@ struct DssArgs {
   const void* Minv_h;     // double or float
   const void* Minv_z;
   const int4* qt_rec_unit;  // FP64 form: unit-weight Q_h^T records
+  const int4* qt_rec_src;   // mixed form: compact Q_h^T records (sources, -2: use the lists)
+  const float4* qt_rec_w;   //   and their float32 weights
   const void* Minv_g;       // warped layers: inverse lumped mass per node (double or float), else null
   const double* qn;
   const double* qs;
@@ -562,24 +564,44 @@ __global__ void __launch_bounds__(256) dss_stage_mixed(const DssArgs A) {
   const float* mh = (const float*)A.Minv_h;
   const float* mz = (const float*)A.Minv_z;
   const float cdt = (float)A.cdt;
+  // 32-bit node indices (the caller checks 5 NG < 2^31): the division by NZ
+  // runs on the integer pipe
+  const unsigned NZ = (unsigned)A.NZ, NG = (unsigned)A.NG;
+  const long long NGl = A.NG;
+  const int NZr = A.NZr;
   int bad = 0;
-  for (long long gidx = (long long)blockIdx.x * blockDim.x + threadIdx.x; gidx < A.NG;
-       gidx += (long long)gridDim.x * blockDim.x) {
-    const long long h = gidx / A.NZ;
-    const int kz = (int)(gidx - h * A.NZ);
-    const int beg = __ldg(A.qt_ptr + h), end = __ldg(A.qt_ptr + h + 1);
+  for (unsigned gidx = blockIdx.x * blockDim.x + threadIdx.x; gidx < NG; gidx += gridDim.x * blockDim.x) {
+    const unsigned h = gidx / NZ;
+    const int kz = (int)(gidx - h * NZ);
     const float s = WARP ? cdt * __ldg((const float*)A.Minv_g + gidx) : cdt * (__ldg(mh + h) * __ldg(mz + kz));
-    const bool lid = (kz == 0) || (kz == A.NZ - 1);
+    const bool lid = (kz == 0) || (kz == (int)NZ - 1);
+    // Q_h^T gather in the order of the CSR lists: from the compact record
+    // (sources and weights after one load each), else from the lists
     float acc[kFields] = {0, 0, 0, 0, 0};
-    for (int e = beg; e < end; ++e) {
-      const float w = __ldg(qtw + e);
-      const float* p = rc + (long long)__ldg(A.qt_src + e) * kFields * A.NZr + kz;
+    const int4 s4 = __ldg(A.qt_rec_src + h);
+    if (s4.x >= 0) {
+      const float4 w4 = __ldg(A.qt_rec_w + h);
+      const int src[4] = {s4.x, s4.y, s4.z, s4.w};
+      const float ww[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-      for (int fl = 0; fl < kFields; ++fl) acc[fl] = fmaf(w, __ldg(p + (long long)fl * A.NZr), acc[fl]);
+      for (int e = 0; e < 4; ++e) {
+        if (src[e] < 0) break;
+        const float* p = rc + (size_t)src[e] * kFields * NZr + kz;
+#pragma unroll
+        for (int fl = 0; fl < kFields; ++fl) acc[fl] = fmaf(ww[e], __ldg(p + fl * NZr), acc[fl]);
+      }
+    } else {
+      const int beg = __ldg(A.qt_ptr + h), end = __ldg(A.qt_ptr + h + 1);
+      for (int e = beg; e < end; ++e) {
+        const float w = __ldg(qtw + e);
+        const float* p = rc + (size_t)__ldg(A.qt_src + e) * kFields * NZr + kz;
+#pragma unroll
+        for (int fl = 0; fl < kFields; ++fl) acc[fl] = fmaf(w, __ldg(p + fl * NZr), acc[fl]);
+      }
     }
 #pragma unroll
     for (int fl = 0; fl < kFields; ++fl) {
-      const long long o = (long long)fl * A.NG + gidx;
+      const long long o = (long long)fl * NGl + gidx;
       const float inc = (fl == 3 && lid) ? 0.f : acc[fl] * s;
       const double incd = f2d_bits(inc);
       double val;
@@ -1883,7 +1905,17 @@ int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float
     VolArgs A = make_vol_args(m, p, stage == 0 ? (const void*)q32 : (const void*)qs32, true, nullptr);
     bool sponge_done = false, smag_done = false;
     if ((rc = element_terms(m, p, A, sponge_done, smag_done))) return rc;
-    if ((rc = launch_pencil_n(A, m.N, m.nz, st, m.pencil_variant, smag_done))) return rc;
+    if (p.eqset == SEM_EQ_CONSERVATIVE) {
+      if ((rc = launch_pencil_n(A, m.N, m.nz, st, m.pencil_variant, smag_done))) return rc;
+    } else switch (m.N) {
+      // the paper's set: the column element kernel (same residual layout)
+      case 2: launch_volume_n<2>(A, p.eqset, true, st); break;
+      case 3: launch_volume_n<3>(A, p.eqset, true, st); break;
+      case 4: launch_volume_n<4>(A, p.eqset, true, st); break;
+      case 5: launch_volume_n<5>(A, p.eqset, true, st); break;
+      case 6: launch_volume_n<6>(A, p.eqset, true, st); break;
+      default: return fail(SEM_ERR_UNSUPPORTED, "order N not compiled");
+    }
     SEM_CUDA_TRY(cudaGetLastError());
     if (physics_on(p) &&
         (rc = launch_physics(m, p, A.q, true, nullptr, p.time + (stage == 0 ? 0.0 : (stage == 1 ? dt : 0.5 * dt)),
@@ -2482,6 +2514,8 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
   B.Minv_h = mixed ? (const void*)D.Minv_h32 : (const void*)D.Minv_h;
   B.Minv_z = mixed ? (const void*)D.Minv_z32 : (const void*)D.Minv_z;
   B.qt_rec_unit = reinterpret_cast<const int4*>(D.qt_rec_unit);
+  B.qt_rec_src = reinterpret_cast<const int4*>(D.qt_rec_src);
+  B.qt_rec_w = reinterpret_cast<const float4*>(D.qt_rec_w);
   B.Minv_g = !m.warped() ? nullptr : (mixed ? (const void*)D.Minv_g32 : (const void*)D.Minv_g);
   B.qn = s.qn;
   B.qs = s.qs;
@@ -2499,9 +2533,9 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
   {
     ProfScope ps(mixed ? "dss_rk_mixed" : "dss_rk_fp64", st);
     if (mixed && B.Minv_g)
-      dss_stage_mixed<true><<<grid_cap(m.NG), 256, 0, st>>>(B);
+      dss_stage_mixed<true><<<grid_cap(m.NG, 64), 256, 0, st>>>(B);
     else if (mixed)
-      dss_stage_mixed<<<grid_cap(m.NG), 256, 0, st>>>(B);
+      dss_stage_mixed<<<grid_cap(m.NG, 64), 256, 0, st>>>(B);
     else {
       const size_t sm = sizeof(double) * m.NZ;
       if (sm > 48 * 1024) return fail(SEM_ERR_UNSUPPORTED, "more than 6144 vertical levels");

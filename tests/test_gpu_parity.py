@@ -821,3 +821,42 @@ def test_tma_staged_variant_equals_plain_variant(sem, name):
             torch.cuda.synchronize()
             assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1]), (mb, mirror.data_ptr() % 16)
     assert sem.sem_status(m) == 0
+
+
+@pytest.mark.parametrize("name", ["uniform-6x6x4-N4", "twolevel-N4", "twolevel-N3-open", "uniform-5x4x3-N6",
+                                  "stretched-twolevel-N4"])
+def test_step_mixed_paper_set_matches_oracle(sem, name):
+    """sem_step_mixed with the paper's set (rho', u, v, w, theta'): the column
+    element kernel feeds the same increment-form stages; ten steps against
+    the oracle's, 1e-4 in the full fields and in the change, and against the
+    mixed stage-by-stage form (sem_rk_stage_mixed) at 1e-5 of the change."""
+    m, o, X, perm = make_pair(sem, **MESHES[name])
+    q_o = vortex_state(o.XG, o.Lz, eqset="NC")
+    dt = 0.5 if name in ("uniform-5x4x3-N6", "stretched-twolevel-N4") else 1.0
+    q_ref = q_o.copy()
+    for _ in range(10):
+        q_ref = ork.rk_step(o, PRM, q_ref, dt, eqset="NC")
+    p = sem.sem_params_default(eqset=1, precision=sem.SEM_PREC_MIXED)
+    q = dev(q_o[:, perm])
+    q32 = torch.empty(q.shape, dtype=torch.float32, device="cuda")
+    work = torch.empty((10, m.NG), dtype=torch.float32, device="cuda")
+    sem.sem_mirror(m, q, q32)
+    for _ in range(10):
+        sem.sem_step_mixed(m, p, q, q32, work, dt)
+    got = host(q)
+    z = X[:, 2]
+    assert np.all(group_rel_l2(full_fields(got, z, "NC"), full_fields(q_ref[:, perm], z, "NC")) <= 1e-4)
+    assert np.all(increment_err(got, q_o[:, perm], q_ref[:, perm]) <= 1e-4)
+    # the stage-by-stage mixed form (float64 stage states) on the same steps
+    qs = dev(q_o[:, perm])
+    w1, w2 = torch.empty_like(qs), torch.empty_like(qs)
+    m1, m2 = torch.empty(q32.shape, dtype=torch.float32, device="cuda"), torch.empty_like(q32)
+    m0 = torch.empty_like(q32)
+    for _ in range(10):
+        sem.sem_mirror(m, qs, m0)
+        sem.sem_rk_stage_mixed(m, p, 0, qs, qs, m0, w1, m1, dt)
+        sem.sem_rk_stage_mixed(m, p, 1, qs, w1, m1, w2, m2, dt)
+        sem.sem_rk_stage_mixed(m, p, 2, qs, w2, m2, w1, m1, dt)
+        qs.copy_(w1)
+    assert np.all(increment_err(got, q_o[:, perm], host(qs)) <= 1e-5)
+    assert sem.sem_status(m) == 0
