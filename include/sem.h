@@ -422,12 +422,14 @@ int sem_peak_probe(int precision, double* tflops_host, cudaStream_t stream);
 int sem_selftest_device_once(int n_devices, int n_threads, int* init_calls_host);
 
 /* Autotuner of the mixed-form element kernel.  Times every launch variant
- * compiled for the mesh's order (layers of a column per CTA, and the number
- * of CTAs per SM the register budget is sized for) on the float32 state
- * mirror q32_dev, `reps` launches each after two warm-up launches, keeps the
- * fastest for this mesh (used by sem_rk_stage, sem_rk_stage_mixed and
- * sem_step_mixed afterwards) and reports all timings.  Synchronises the
- * stream; overwrites the mesh's residual scratch. */
+ * compiled for the mesh's order and p->eqset's equation set (layers of a
+ * column per CTA, and the number of CTAs per SM the register budget is sized
+ * for) on the float32 state mirror q32_dev, `reps` launches each after two
+ * warm-up launches, keeps the fastest for this mesh and that set (used by
+ * sem_rk_stage, sem_rk_stage_mixed and sem_step_mixed afterwards; the two
+ * sets' choices are kept apart) and reports all timings.  The paper's set on
+ * warped layers has one kernel and no table: SEM_ERR_UNSUPPORTED.
+ * Synchronises the stream; overwrites the mesh's residual scratch. */
 #define SEM_TUNE_MAX 16
 typedef struct {
   int n_variants;
@@ -436,18 +438,20 @@ typedef struct {
   int min_ctas_per_sm[SEM_TUNE_MAX];
   int kind[SEM_TUNE_MAX];              /* 0: z-pencil kernel, 1: line-exchange kernel,
                                           2: line exchange with the x, y contractions on tensor cores,
-                                          4: line exchange with the state staged by bulk copies (TMA) */
+                                          4: line exchange with the state staged by bulk copies (TMA),
+                                          5: line exchange for the paper's equation set */
   double ms[SEM_TUNE_MAX];             /* mean event time per launch */
 } sem_tune_out;
 int sem_autotune(sem_mesh* m, const sem_params* p, const float* q32_dev, int reps,
                  sem_tune_out* out_host, cudaStream_t stream);
 /* Selects row `row` of the table sem_autotune reports for this mesh's order
- * (same order, 0 <= row < n_variants) as the mesh's element-kernel variant,
- * or the untuned default for row = -1; no timing and no device work.  For
- * tests that run every variant, and for callers that cache a tuning result.
- * The paper has no counterpart (launch configuration only).  SEM_ERR_ARG for
- * a row outside the table. */
-int sem_autotune_select(sem_mesh* m, int row);
+ * and equation set `eqset` (SEM_EQ_*; 0 <= row < n_variants) as the mesh's
+ * element-kernel variant for that set, or the untuned default for row = -1;
+ * no timing and no device work.  For tests that run every variant, and for
+ * callers that cache a tuning result.  The paper has no counterpart (launch
+ * configuration only).  SEM_ERR_ARG for a row outside the table or an
+ * unknown set. */
+int sem_autotune_select(sem_mesh* m, int eqset, int row);
 
 /* Checkpoint / resume.  sem_checkpoint_write copies the float64 state to the
  * host (synchronises the stream) and writes the mesh description, its leaf

@@ -504,9 +504,10 @@ int sem_autotune(sem_mesh* mh, const sem_params* p, const float* q32, int reps, 
   return autotune_pencil(mh->m, *p, q32, reps, out, st);
 }
 
-int sem_autotune_select(sem_mesh* mh, int row) {
+int sem_autotune_select(sem_mesh* mh, int eqset, int row) {
   if (!mh) return fail(SEM_ERR_ARG, "bad argument");
-  return select_pencil(mh->m, row);
+  if (eqset != SEM_EQ_CONSERVATIVE && eqset != SEM_EQ_NONCONSERVATIVE) return fail(SEM_ERR_ARG, "unknown equation set");
+  return select_pencil(mh->m, eqset, row);
 }
 
 int sem_batch_create(sem_mesh* const* meshes, int n, sem_batch** out) {

@@ -1370,6 +1370,229 @@ volume_lines_smag(const VolArgs A) {
 }
 
 // ---------------------------------------------------------------------------
+// Mixed form, the paper's equation set (Sec. 2: mass in flux form; momentum
+// and potential temperature in advective form, in the primitive perturbation
+// variables rho', u, v, w, theta'): line-exchange element kernel.
+//
+// Same thread roles and contraction skeleton as lines_body, with a different
+// pointwise part.  The z-line owner forms at each node of its line the
+// weighted mass-flux components and the five quantities u, v, w, p', theta';
+// the x- and y-line owners apply the weak derivative to their line's mass
+// flux and the strong derivative D to the five quantities; the z-line owner
+// takes the z derivatives from the quantities it kept in registers and forms
+// the advective residuals node by node, as volume_column does for this set.
+// A layer's top-node residual is complete only after that combination, so it
+// passes to the layer above through shared memory after one more barrier.
+// Box meshes only (warped layers take volume_column).
+template <int N>
+__host__ __device__ constexpr int nc_lw() { return (6 * (N + 1)) | 1; }
+template <int N, int KL>
+__host__ __device__ constexpr int nc_ls() {
+  return (N + 1) * (N + 1) * nc_lw<N>() + ((32 / KL - ((N + 1) * (N + 1) * nc_lw<N>()) % 32) % 32 + 32) % 32;
+}
+template <int N, int KL>
+__host__ __device__ constexpr int nc_smem_floats() {
+  return 2 * KL * nc_ls<N, KL>() + kFields * KL * (N + 1) * (N + 1) + 2 * kFields * (N + 1) * (N + 1) +
+         2 * (N + 1) * KL * (N + 1) * (N + 1) + 2 * 5 * (KL * N + 1);
+}
+
+template <int N, int KL>
+__device__ __forceinline__ void lines_nc_body(const VolArgs& A, const int col, float* smem, const int t) {
+  constexpr int n1 = N + 1, Nq = n1 * n1;
+  constexpr int LW = nc_lw<N>(), LS = nc_ls<N, KL>();
+  float* sX = smem;                       // [kk][LS]: per line ab, [6][n1]: mass flux x, u, v, w, p', theta'
+  float* sY = sX + KL * LS;               // [kk][LS]: the same for y
+  float* sT = sY + KL * LS;               // [f][kk][ab]: full top-node residual of each layer
+  float* sP = sT + kFields * KL * Nq;     // [2][f][ab]: top-node carry between chunks
+  float* sV = sP + 2 * kFields * Nq;      // [2][c][t]: 1 / rho and rho' of the thread's nodes
+  constexpr int NL = KL * N + 1;          // levels of a chunk
+  float* sR = sV + 2 * n1 * KL * Nq;      // [2][5][NL]: the chunk's reference rows, double-buffered:
+                                          // theta0, p0, rho0, 1/(rho theta)0, dtheta0/dz
+  const bool part = t < KL * Nq;
+  const int kk = t % KL, ab = part ? t / KL : 0;
+  const int i = ab % n1, j = ab / n1;
+  const int lc = ab % n1, lo = ab / n1;   // exchange phase: x-line (j, c) = (lo, lc), y-line (i, c) = (lo, lc)
+  const int lev = A.col_level[col];
+  const float* geo = A.geof[lev];
+  const float sx = geo[4], sy = geo[5], sz = geo[6], J = geo[3];
+  const float gx = 2.f / geo[0], gy = 2.f / geo[1];
+  constexpr int NT = KL * Nq;
+  const int hm = part ? A.hmap[(long long)col * Nq + ab] : 0;
+  const float wi = c_wf[N][i], wj = c_wf[N][j];
+  const float fc = A.ff, g = A.gf;
+  float* rc = (float*)A.rc;
+  const int nchunk = (A.nz + KL - 1) / KL;
+  // reference rows of chunk chn into buffer chn & 1 (levels past the top repeat it)
+  auto stage_ref = [&](int chn) {
+    float* R = sR + (chn & 1) * 5 * NL;
+    for (int e = t; e < 5 * NL; e += blockDim.x) {
+      const int f = e / NL, z = e - (e / NL) * NL;
+      const int kz = min(chn * KL * N + z, A.NZ - 1);
+      constexpr int fld[5] = {0, 2, 3, 6, 5};
+      R[e] = __ldg(A.ref32 + (long long)kz * kRef + fld[f]);
+    }
+  };
+  stage_ref(0);
+  __syncthreads();
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const int k = ch * KL + kk;
+    const bool act = part && k < A.nz;
+    const int kz0 = k * N;
+    const float hk = act ? __ldg(A.hzk32 + k) : 1.f;   // layer thickness
+    const float* R = sR + (ch & 1) * 5 * NL + kk * N;   // + f NL + c
+    float qz[5][n1];   // u, v, w, p', theta' on this thread's z-line
+    float rm[n1];      // z part of the weak mass-flux contraction
+#pragma unroll
+    for (int c = 0; c < n1; ++c) {
+      rm[c] = 0.f;
+#pragma unroll
+      for (int f = 0; f < 5; ++f) qz[f][c] = 0.f;
+    }
+    float* zX = sX + kk * LS + ab * LW;   // this thread's z-line, + s n1 + c
+    float* zY = sY + kk * LS + ab * LW;
+    if (act) {
+#pragma unroll
+      for (int c = 0; c < n1; ++c) {
+        float v[kFields];
+        const int kz = kz0 + c;
+        load_node<N>(A, hm, kz, v);
+        const float th0 = R[c], p0 = R[NL + c], rho0 = R[2 * NL + c], inv_rt0 = R[3 * NL + c];
+        const float rp = v[0], u = v[1], vv = v[2], w = v[3], thp = v[4];
+        const float rho = rho0 + rp;
+        const float inv = __frcp_rn(rho);
+        const float rtp = fmaf(rho0, thp, rp * (th0 + thp));   // (rho theta)'
+        const float pp = p0 * pow1p_m1(rtp * inv_rt0, A.bin, A.gammaf);
+        const float wc = c_wf[N][c];
+        zX[c] = rho * u * (wj * wc * sx * hk);
+        zY[c] = rho * vv * (wi * wc * sy * hk);
+        const float Fz = rho * w * (wi * wj * sz);
+#pragma unroll
+        for (int c2 = 0; c2 < n1; ++c2) rm[c2] = fmaf(c_Dwf[N][c2 * n1 + c], Fz, rm[c2]);
+        qz[0][c] = u;
+        qz[1][c] = vv;
+        qz[2][c] = w;
+        qz[3][c] = pp;
+        qz[4][c] = thp;
+        sV[c * NT + t] = inv;
+        sV[(n1 + c) * NT + t] = rp;
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+          zX[(f + 1) * n1 + c] = qz[f][c];
+          zY[(f + 1) * n1 + c] = qz[f][c];
+        }
+      }
+    }
+    __syncthreads();
+    // the next chunk's reference rows load under this chunk's line exchange
+    if (ch + 1 < nchunk) stage_ref(ch + 1);
+    if (act) {
+      // x-line (lo, lc): nodes (m, lo, lc); slot 0 weak, slots 1..5 strong
+      float* bx = sX + kk * LS + lo * n1 * LW + lc;
+      float* by = sY + kk * LS + lo * LW + lc;
+#pragma unroll
+      for (int s = 0; s < 6; ++s) {
+        float F[n1];
+#pragma unroll
+        for (int m = 0; m < n1; ++m) F[m] = bx[m * LW + s * n1];
+#pragma unroll
+        for (int i2 = 0; i2 < n1; ++i2) {
+          float acc = 0.f;
+#pragma unroll
+          for (int m = 0; m < n1; ++m)
+            acc = fmaf(s == 0 ? c_Dwf[N][i2 * n1 + m] : c_Df[N][i2 * n1 + m], F[m], acc);
+          bx[i2 * LW + s * n1] = acc;
+        }
+      }
+      // y-line (lo, lc): nodes (lo, m, lc)
+#pragma unroll
+      for (int s = 0; s < 6; ++s) {
+        float F[n1];
+#pragma unroll
+        for (int m = 0; m < n1; ++m) F[m] = by[m * n1 * LW + s * n1];
+#pragma unroll
+        for (int j2 = 0; j2 < n1; ++j2) {
+          float acc = 0.f;
+#pragma unroll
+          for (int m = 0; m < n1; ++m)
+            acc = fmaf(s == 0 ? c_Dwf[N][j2 * n1 + m] : c_Df[N][j2 * n1 + m], F[m], acc);
+          by[j2 * n1 * LW + s * n1] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    // residuals of the bottom and top nodes (kept for the vertical DSS); the
+    // inner nodes' go to the residual array as they are formed
+    float rb[kFields], rt[kFields];
+    float* dst = rc + ((long long)((long long)col * Nq + ab) * kFields) * A.NZr + kz0;
+    if (act) {
+      const float gz = 2.f / hk;
+      const float wJ1 = wi * wj * J * hk;
+#pragma unroll
+      for (int c = 0; c < n1; ++c) {
+        // derivatives of u, v, w, p', theta' at node c: x, y from the line
+        // owners, z from this thread's own line
+        float dx[5], dy[5], dz[5];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+          float a = 0.f;
+#pragma unroll
+          for (int m = 0; m < n1; ++m) a = fmaf(c_Df[N][c * n1 + m], qz[f][m], a);
+          dx[f] = zX[(f + 1) * n1 + c] * gx;
+          dy[f] = zY[(f + 1) * n1 + c] * gy;
+          dz[f] = a * gz;
+        }
+        const float u = qz[0][c], vv = qz[1][c], w = qz[2][c], inv = sV[c * NT + t];
+        const float wJ = wJ1 * c_wf[N][c];
+        const float th0dz = R[4 * NL + c];
+        float adv[5];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) adv[f] = fmaf(w, dz[f], fmaf(vv, dy[f], u * dx[f]));
+        const float r[kFields] = {rm[c] + zX[c] + zY[c], wJ * (-adv[0] - dx[3] * inv + fc * vv),
+                                  wJ * (-adv[1] - dy[3] * inv - fc * u),
+                                  wJ * (-adv[2] - dz[3] * inv - sV[(n1 + c) * NT + t] * inv * g), wJ * (-w * th0dz - adv[4])};
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) {
+          if (c == 0) rb[f] = r[f];
+          else if (c == N) rt[f] = r[f];
+          else dst[(long long)f * A.NZr + c] = r[f];
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) sT[(f * KL + kk) * Nq + ab] = rt[f];
+    }
+    __syncthreads();
+    if (act) {
+      // vertical DSS: the bottom node takes the full top-node value of the
+      // layer below (this chunk: sT; the previous chunk's last layer: sP)
+      if (kk > 0) {
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) rb[f] += sT[(f * KL + kk - 1) * Nq + ab];
+      } else if (ch > 0) {
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) rb[f] += sP[((ch - 1) & 1) * kFields * Nq + f * Nq + ab];
+      }
+      if (kk == KL - 1) {
+#pragma unroll
+        for (int f = 0; f < kFields; ++f) sP[(ch & 1) * kFields * Nq + f * Nq + ab] = rt[f];
+      }
+      const bool top = (k == A.nz - 1);
+#pragma unroll
+      for (int f = 0; f < kFields; ++f) {
+        dst[(long long)f * A.NZr] = rb[f];
+        if (top) dst[(long long)f * A.NZr + N] = rt[f];
+      }
+    }
+  }
+}
+
+template <int N, int KL, int MB>
+__global__ void __launch_bounds__(KL * (N + 1) * (N + 1), MB)
+volume_lines_nc(const VolArgs A) {
+  extern __shared__ __align__(16) float smem[];
+  lines_nc_body<N, KL>(A, blockIdx.x, smem, threadIdx.x);
+}
+
+// ---------------------------------------------------------------------------
 // Tensor-core variant of the line-exchange element kernel (kind 2, order 4).
 //
 // The x and y contractions of a layer chunk run on the fifth-generation
@@ -1638,6 +1861,20 @@ static int launch_lines_tma(const VolArgs& A, cudaStream_t st) {
   return SEM_OK;
 }
 
+template <int N, int KL, int MB>
+static int launch_lines_nc(const VolArgs& A, cudaStream_t st) {
+  constexpr size_t sm = sizeof(float) * nc_smem_floats<N, KL>();
+  static DeviceOnce attr;
+  int rc = device_once(attr, [&] {
+    SEM_CUDA_TRY(cudaFuncSetAttribute(volume_lines_nc<N, KL, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    return SEM_OK;
+  });
+  if (rc) return rc;
+  ProfScope ps("volume_mixed", st);
+  volume_lines_nc<N, KL, MB><<<A.Ncol, KL * (N + 1) * (N + 1), sm, st>>>(A);
+  return SEM_OK;
+}
+
 // Launch variants of the pencil kernel: layers per CTA (KL) and the minimum
 // resident CTAs per SM the register allocation is sized for (MB).  The
 // autotuner (sem_autotune) times them on a mesh and keeps the fastest.
@@ -1646,7 +1883,8 @@ struct PencilVariant {
   int (*launch)(const VolArgs&, cudaStream_t);
   int kind;         // 0: z-pencil volume_pencil_mixed; 1: line-exchange volume_lines_mixed;
                     // 2: line exchange with the x, y contractions on tensor cores (volume_lines_tc);
-                    // 4: line exchange with the state staged by bulk copies (volume_lines_tma)
+                    // 4: line exchange with the state staged by bulk copies (volume_lines_tma);
+                    // 5: line exchange for the paper's equation set (volume_lines_nc)
   int (*launch_smag)(const VolArgs&, cudaStream_t);   // with the stress added; null: none
 };
 static const PencilVariant kPencil[] = {
@@ -1666,15 +1904,21 @@ static const PencilVariant kPencil[] = {
     {5, 4, 4, launch_lines<5, 4, 4>, 1},
     {6, 4, 2, launch_pencil<6, 4, 2>},      {6, 8, 1, launch_lines<6, 8, 1>, 1},
     {6, 4, 2, launch_lines<6, 4, 2>, 1},
+    // the paper's equation set
+    {2, 16, 4, launch_lines_nc<2, 16, 4>, 5}, {3, 8, 4, launch_lines_nc<3, 8, 4>, 5},
+    {4, 8, 3, launch_lines_nc<4, 8, 3>, 5},   {4, 8, 2, launch_lines_nc<4, 8, 2>, 5},
+    {4, 5, 5, launch_lines_nc<4, 5, 5>, 5},   {4, 16, 2, launch_lines_nc<4, 16, 2>, 5},
+    {5, 4, 3, launch_lines_nc<5, 4, 3>, 5},   {6, 4, 2, launch_lines_nc<6, 4, 2>, 5},
 };
 constexpr int kNumPencil = sizeof(kPencil) / sizeof(kPencil[0]);
 
-// default choice before tuning: the line-exchange variant with the most
-// layers per CTA that fit nz (ties: more CTAs per SM), else the fewest layers
-static int pencil_default(int N, int nz) {
+// default choice before tuning: the line-exchange variant (kind 1, or 5 for
+// the paper's set) with the most layers per CTA that fit nz (ties: more CTAs
+// per SM), else the fewest layers
+static int pencil_default(int N, int nz, int kind = 1) {
   int best = -1;
   for (int v = 0; v < kNumPencil; ++v) {
-    if (kPencil[v].N != N || kPencil[v].kind != 1) continue;
+    if (kPencil[v].N != N || kPencil[v].kind != kind) continue;
     if (best < 0) { best = v; continue; }
     const PencilVariant& a = kPencil[v];
     const PencilVariant& b = kPencil[best];
@@ -1686,11 +1930,36 @@ static int pencil_default(int N, int nz) {
 
 static int launch_pencil_n(const VolArgs& A, int N, int nz, cudaStream_t st, int variant = -1,
                            bool smag = false) {
-  if (variant < 0 || variant >= kNumPencil || kPencil[variant].N != N) variant = pencil_default(N, nz);
+  if (variant < 0 || variant >= kNumPencil || kPencil[variant].N != N || kPencil[variant].kind == 5)
+    variant = pencil_default(N, nz);
   // warped layers: the line-exchange kernels only
   if (A.metric32 && variant >= 0 && kPencil[variant].kind != 1) variant = pencil_default(N, nz);
   if (variant < 0) return fail(SEM_ERR_UNSUPPORTED, "order N not compiled");
   if (smag) return kPencil[variant].launch_smag(A, st);
+  return kPencil[variant].launch(A, st);
+}
+
+// The paper's set, mixed form: the line-exchange rows (kind 5) on box
+// meshes, volume_column on warped layers.
+template <int N>
+static int launch_nc_column(const VolArgs& A, cudaStream_t st) {
+  launch_volume_n<N>(A, SEM_EQ_NONCONSERVATIVE, true, st);
+  return SEM_OK;
+}
+static int launch_nc_n(const VolArgs& A, int N, int nz, cudaStream_t st, int variant = -1) {
+  if (A.metric32) {
+    switch (N) {
+      case 2: return launch_nc_column<2>(A, st);
+      case 3: return launch_nc_column<3>(A, st);
+      case 4: return launch_nc_column<4>(A, st);
+      case 5: return launch_nc_column<5>(A, st);
+      case 6: return launch_nc_column<6>(A, st);
+      default: return fail(SEM_ERR_UNSUPPORTED, "order N not compiled");
+    }
+  }
+  if (variant < 0 || variant >= kNumPencil || kPencil[variant].N != N || kPencil[variant].kind != 5)
+    variant = pencil_default(N, nz, 5);
+  if (variant < 0) return fail(SEM_ERR_UNSUPPORTED, "order N not compiled");
   return kPencil[variant].launch(A, st);
 }
 
@@ -1907,14 +2176,9 @@ int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float
     if ((rc = element_terms(m, p, A, sponge_done, smag_done))) return rc;
     if (p.eqset == SEM_EQ_CONSERVATIVE) {
       if ((rc = launch_pencil_n(A, m.N, m.nz, st, m.pencil_variant, smag_done))) return rc;
-    } else switch (m.N) {
-      // the paper's set: the column element kernel (same residual layout)
-      case 2: launch_volume_n<2>(A, p.eqset, true, st); break;
-      case 3: launch_volume_n<3>(A, p.eqset, true, st); break;
-      case 4: launch_volume_n<4>(A, p.eqset, true, st); break;
-      case 5: launch_volume_n<5>(A, p.eqset, true, st); break;
-      case 6: launch_volume_n<6>(A, p.eqset, true, st); break;
-      default: return fail(SEM_ERR_UNSUPPORTED, "order N not compiled");
+    } else {
+      // the paper's set (same residual layout)
+      if ((rc = launch_nc_n(A, m.N, m.nz, st, m.nc_variant))) return rc;
     }
     SEM_CUDA_TRY(cudaGetLastError());
     if (physics_on(p) &&
@@ -1959,12 +2223,24 @@ int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float
   return SEM_OK;
 }
 
-// Autotuner: time every pencil variant compiled for the mesh's order on the
-// given state (float32 mirror) and keep the fastest for this mesh.
+// Rows of the variant table for a mesh and equation set: the conservative
+// set's kernels (kinds 0, 1, 2, 4; warped layers: kind 1 only) or the paper's
+// set's (kind 5; box meshes only).
+static bool tune_row(const Mesh& m, int eqset, int v) {
+  if (kPencil[v].N != m.N) return false;
+  if (eqset != SEM_EQ_CONSERVATIVE) return kPencil[v].kind == 5 && !m.warped();
+  if (kPencil[v].kind == 5) return false;
+  return !m.warped() || kPencil[v].kind == 1;
+}
+
+// Autotuner: time every element-kernel variant compiled for the mesh's order
+// and the parameters' equation set on the given state (float32 mirror) and
+// keep the fastest for this mesh and set.
 int autotune_pencil(Mesh& m, const sem_params& p, const float* q32, int reps, sem_tune_out* out,
                     cudaStream_t st) {
   int rc = upload_basis_constants();
   if (rc) return rc;
+  const int eqset = p.eqset;
   VolArgs A = make_vol_args(m, p, q32, true, nullptr);
   cudaEvent_t e0, e1;
   SEM_CUDA_TRY(cudaEventCreate(&e0));
@@ -1973,8 +2249,7 @@ int autotune_pencil(Mesh& m, const sem_params& p, const float* q32, int reps, se
   float best_ms = 0.f;
   out->n_variants = 0;
   for (int v = 0; v < kNumPencil && out->n_variants < SEM_TUNE_MAX; ++v) {
-    if (kPencil[v].N != m.N) continue;
-    if (m.warped() && kPencil[v].kind != 1) continue;   // warped layers: line exchange only
+    if (!tune_row(m, eqset, v)) continue;
     for (int w = 0; w < 2; ++w) kPencil[v].launch(A, st);
     cudaEventRecord(e0, st);
     for (int r = 0; r < reps; ++r) kPencil[v].launch(A, st);
@@ -2001,23 +2276,27 @@ int autotune_pencil(Mesh& m, const sem_params& p, const float* q32, int reps, se
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (best < 0) return fail(SEM_ERR_UNSUPPORTED, "no variant for this order");
-  m.pencil_variant = best;
+  if (best < 0)
+    return fail(SEM_ERR_UNSUPPORTED, eqset != SEM_EQ_CONSERVATIVE && m.warped()
+                                         ? "the paper's set on warped layers has one element kernel"
+                                         : "no variant for this order");
+  (eqset == SEM_EQ_CONSERVATIVE ? m.pencil_variant : m.nc_variant) = best;
   return SEM_OK;
 }
 
-// Row `row` of the autotuner's table for the mesh's order (-1: default).
-int select_pencil(Mesh& m, int row) {
+// Row `row` of the autotuner's table for the mesh's order and the equation
+// set (-1: default).
+int select_pencil(Mesh& m, int eqset, int row) {
+  int& sel = eqset == SEM_EQ_CONSERVATIVE ? m.pencil_variant : m.nc_variant;
   if (row == -1) {
-    m.pencil_variant = -1;
+    sel = -1;
     return SEM_OK;
   }
   int k = 0;
   for (int v = 0; v < kNumPencil && k < SEM_TUNE_MAX; ++v) {
-    if (kPencil[v].N != m.N) continue;
-    if (m.warped() && kPencil[v].kind != 1) continue;   // the rows sem_autotune lists
+    if (!tune_row(m, eqset, v)) continue;   // the rows sem_autotune lists
     if (k == row) {
-      m.pencil_variant = v;
+      sel = v;
       return SEM_OK;
     }
     ++k;
@@ -2493,6 +2772,8 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
   if (mixed && eq == SEM_EQ_CONSERVATIVE) {
     if ((rc = element_terms(m, p, A, sponge_done, smag_done))) return rc;
     if ((rc = launch_pencil_n(A, m.N, m.nz, st, m.pencil_variant, smag_done))) return rc;
+  } else if (mixed) {
+    if ((rc = launch_nc_n(A, m.N, m.nz, st, m.nc_variant))) return rc;
   } else switch (m.N) {
     case 2: launch_volume_n<2>(A, eq, mixed, st); break;
     case 3: launch_volume_n<3>(A, eq, mixed, st); break;

@@ -112,6 +112,7 @@ struct Mesh {
   long long serial = 0;
   // element-kernel launch variant chosen by the autotuner (-1: default)
   int pencil_variant = -1;
+  int nc_variant = -1;      // the same for the paper's equation set
   // device
   DeviceTables* dev = nullptr;
   int dev_id = -1;
@@ -262,7 +263,7 @@ int mlp_status(void* m, int* status, cudaStream_t st);
 int mlp_features_api(Mesh& mesh, const double* q, const float* scales, float* F, cudaStream_t st);
 int autotune_pencil(Mesh& m, const sem_params& p, const float* q32, int reps, sem_tune_out* out,
                     cudaStream_t st);
-int select_pencil(Mesh& m, int row);
+int select_pencil(Mesh& m, int eqset, int row);
 int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float* work32, double dt,
                       cudaStream_t st);
 // terms of the paper's runs (k_physics.cu): adds the Smagorinsky stress and the

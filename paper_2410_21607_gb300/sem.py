@@ -140,7 +140,7 @@ def _load():
         "sem_checkpoint_read_mesh": (i, [C.c_char_p, C.POINTER(vp), C.POINTER(d), C.POINTER(C.c_longlong)]),
         "sem_checkpoint_read_state": (i, [C.c_char_p, vp, vp, vp]),
         "sem_autotune": (i, [vp, C.POINTER(Params), vp, i, C.POINTER(TuneOut), vp]),
-        "sem_autotune_select": (i, [vp, i]),
+        "sem_autotune_select": (i, [vp, i, i]),
         "sem_selftest_device_once": (i, [i, i, vp]),
         "sem_peak_probe": (i, [i, C.POINTER(d), vp]),
         "sem_adapt_flags_levels": (i, [vp, C.POINTER(Params), vp, vp, i, vp, vp, vp]),
@@ -445,7 +445,8 @@ def sem_autotune(mesh, params, q32, reps=5, stream=None):
     Returns [(layers_per_cta, min_ctas_per_sm, ms, kind)] and the chosen index
     (kind 0: z-pencil kernel, 1: line-exchange kernel, 2: line exchange with
     the x, y contractions on tensor cores, 4: line exchange with the state
-    staged by bulk copies)."""
+    staged by bulk copies, 5: line exchange for the paper's equation set).
+    The table is the one of params.eqset's equation set."""
     _f32(q32, mesh.field_shape)
     out = TuneOut()
     _check(LIB.sem_autotune(mesh.h, C.byref(params), _ptr(q32), int(reps), C.byref(out),
@@ -455,9 +456,10 @@ def sem_autotune(mesh, params, q32, reps=5, stream=None):
     return rows, out.chosen
 
 
-def sem_autotune_select(mesh, row):
-    """Use row `row` of sem_autotune's table (-1: the untuned default)."""
-    _check(LIB.sem_autotune_select(mesh.h, int(row)))
+def sem_autotune_select(mesh, row, eqset=0):
+    """Use row `row` of sem_autotune's table for equation set `eqset`
+    (0: conservative, 1: the paper's set; row -1: the untuned default)."""
+    _check(LIB.sem_autotune_select(mesh.h, int(eqset), int(row)))
 
 
 class Batch:
