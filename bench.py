@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--no-amr", action="store_true")
     ap.add_argument("--no-physics", action="store_true")
     ap.add_argument("--no-warped", action="store_true")
+    ap.add_argument("--no-paper-set", action="store_true")
     ap.add_argument("--mlp-forward-only", action="store_true",
                     help="time only the flag network's forwards on 2^20 feature rows and print that "
                          "object (a short command for profiling them)")
@@ -481,6 +482,71 @@ def warped_measure(sem, torch, steps=20, warmup=3, gate_steps=100, amplitude=600
                                        "kind": r[3]} for r in rows], "chosen": chosen},
             "alg_bytes": {"element_pass": elem, "stage": stage, "metric": metric_bytes,
                           "reference_state": ref_bytes},
+            "stage_frac": stage / (ms / 3 * 1e-3) / 1e9 / hbm, "kernels": kern,
+            "gate": gate, "status": sem.sem_status(m)}
+
+
+def paper_set_measure(sem, torch, steps=20, warmup=3, gate_steps=100):
+    """The benchmark mesh (64x64x16, N = 4) with the paper's own equation set
+    (mass in flux form, momentum and theta' in advective form, variables
+    rho', u, v, w, theta'): mixed increment-form steps, autotuned among that
+    set's line-exchange variants; per-kernel durations against the same
+    algorithmic bytes as the conservative set (the state and residual arrays
+    have the same shapes); the max-wind gate against the float64 form."""
+    from synth.vortex import vortex_state
+    L, Lz, n, nz, N, dt = 2048e3, 24e3, 64, 16, 4, 0.25
+    m = sem.sem_mesh_create(L, L, Lz, n, n, nz, N)
+    q0 = torch.from_numpy(vortex_state(sem.sem_mesh_coords_host(m).T, Lz, eqset="NC")).cuda()
+    p = sem.sem_params_default(eqset=1, precision=sem.SEM_PREC_MIXED)
+    p64 = sem.sem_params_default(eqset=1, precision=sem.SEM_PREC_FP64)
+    stream = torch.cuda.current_stream()
+    q = q0.clone()
+    q32 = torch.empty(q.shape, dtype=torch.float32, device="cuda")
+    work = torch.empty((10, m.NG), dtype=torch.float32, device="cuda")
+    sem.sem_mirror(m, q, q32, stream)
+    rows, chosen = sem.sem_autotune(m, p, q32, 5, stream)
+    for _ in range(warmup):
+        sem.sem_step_mixed(m, p, q, q32, work, dt, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        sem.sem_step_mixed(m, p, q, q32, work, dt, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    sem.sem_profile_begin()
+    for _ in range(steps):
+        sem.sem_step_mixed(m, p, q, q32, work, dt, stream)
+    torch.cuda.synchronize()
+    pr = sem.sem_profile_end()
+    NG, NL = m.NG, m.Ne * (N + 1) ** 3
+    elem, stage = 20 * NG + 4 * NL, 124 * NG + 4 * NL
+    hbm, _ = peaks()
+    kern = {}
+    for name, (nl, tot) in pr.items():
+        if name == "mirror":
+            continue
+        avg = tot / max(nl, 1)
+        ab = elem if name.startswith("volume") else stage - elem
+        kern[name] = {"launches": nl, "ms_avg": avg, "alg_bytes": ab,
+                      "frac": ab / (avg * 1e-3) / 1e9 / hbm}
+    gate = None
+    if gate_steps > 0:
+        qm, qd = q0.clone(), q0.clone()
+        sem.sem_mirror(m, qm, q32, stream)
+        w1, w2 = torch.empty_like(qd), torch.empty_like(qd)
+        for _ in range(gate_steps):
+            sem.sem_step_mixed(m, p, qm, q32, work, dt, stream)
+            sem.sem_step(m, p64, qd, w1, w2, dt, stream)
+        dm, dd = sem.sem_diag(m, p64, qm), sem.sem_diag(m, p64, qd)
+        gate = {"steps": gate_steps, "max_wind_fp64": dd["max_wind"],
+                "max_wind_rel_err": abs(dm["max_wind"] - dd["max_wind"]) / dd["max_wind"]}
+    return {"workload": "uniform-64x64x16-N4, the paper's equation set",
+            "ms_per_step": ms, "value": 3 * 5 * NL / (ms * 1e-3),
+            "autotune": {"variants": [{"layers_per_cta": r[0], "min_ctas_per_sm": r[1], "ms": r[2],
+                                       "kind": r[3]} for r in rows], "chosen": chosen},
+            "alg_bytes": {"element_pass": elem, "stage": stage},
             "stage_frac": stage / (ms / 3 * 1e-3) / 1e9 / hbm, "kernels": kern,
             "gate": gate, "status": sem.sem_status(m)}
 
@@ -906,6 +972,9 @@ def main():
     warped_res = None
     if not a.no_warped and a.form == "mixed":
         warped_res = warped_measure(sem, torch, gate_steps=a.gate_steps)
+    paper_res = None
+    if not a.no_paper_set and a.form == "mixed":
+        paper_res = paper_set_measure(sem, torch, gate_steps=a.gate_steps)
     amr_res = None
     if not a.no_amr and a.form == "mixed":
         amr_res = amr_measure(sem, torch)
@@ -940,6 +1009,7 @@ def main():
             "gate": gate,
             "roofline": roof, "kernels": kernels, "autotune": tune, "batched": batched,
             "learned": learned_res, "amr": amr_res, "physics": physics_res, "warped": warped_res,
+            "paper_set": paper_res,
             "cpu_baseline": cpu,
             "e2e": {"value": job_throughput(dof_stage * 3, world, e2e_ms), "unit": "DOF-updates/s",
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,

@@ -1907,7 +1907,7 @@ static const PencilVariant kPencil[] = {
     // the paper's equation set
     {2, 16, 4, launch_lines_nc<2, 16, 4>, 5}, {3, 8, 4, launch_lines_nc<3, 8, 4>, 5},
     {4, 8, 3, launch_lines_nc<4, 8, 3>, 5},   {4, 8, 2, launch_lines_nc<4, 8, 2>, 5},
-    {4, 5, 5, launch_lines_nc<4, 5, 5>, 5},   {4, 16, 2, launch_lines_nc<4, 16, 2>, 5},
+    {4, 6, 4, launch_lines_nc<4, 6, 4>, 5},   {4, 16, 2, launch_lines_nc<4, 16, 2>, 5},
     {5, 4, 3, launch_lines_nc<5, 4, 3>, 5},   {6, 4, 2, launch_lines_nc<6, 4, 2>, 5},
 };
 constexpr int kNumPencil = sizeof(kPencil) / sizeof(kPencil[0]);
