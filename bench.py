@@ -486,16 +486,18 @@ def warped_measure(sem, torch, steps=20, warmup=3, gate_steps=100, amplitude=600
             "gate": gate, "status": sem.sem_status(m)}
 
 
-def paper_set_measure(sem, torch, steps=20, warmup=3, gate_steps=100):
+def paper_set_measure(sem, torch, steps=20, warmup=3, gate_steps=100, warp=None):
     """The benchmark mesh (64x64x16, N = 4) with the paper's own equation set
     (mass in flux form, momentum and theta' in advective form, variables
     rho', u, v, w, theta'): mixed increment-form steps, autotuned among that
     set's line-exchange variants; per-kernel durations against the same
     algorithmic bytes as the conservative set (the state and residual arrays
-    have the same shapes); the max-wind gate against the float64 form."""
+    have the same shapes; on warped layers plus the float32 metric terms and
+    the reference state per node, as in warped_measure); the max-wind gate
+    against the float64 form.  warp = (amplitude, kx, ky): warped layers."""
     from synth.vortex import vortex_state
     L, Lz, n, nz, N, dt = 2048e3, 24e3, 64, 16, 4, 0.25
-    m = sem.sem_mesh_create(L, L, Lz, n, n, nz, N)
+    m = sem.sem_mesh_create(L, L, Lz, n, n, nz, N, warp=warp)
     q0 = torch.from_numpy(vortex_state(sem.sem_mesh_coords_host(m).T, Lz, eqset="NC")).cuda()
     p = sem.sem_params_default(eqset=1, precision=sem.SEM_PREC_MIXED)
     p64 = sem.sem_params_default(eqset=1, precision=sem.SEM_PREC_FP64)
@@ -520,8 +522,9 @@ def paper_set_measure(sem, torch, steps=20, warmup=3, gate_steps=100):
         sem.sem_step_mixed(m, p, q, q32, work, dt, stream)
     torch.cuda.synchronize()
     pr = sem.sem_profile_end()
-    NG, NL = m.NG, m.Ne * (N + 1) ** 3
-    elem, stage = 20 * NG + 4 * NL, 124 * NG + 4 * NL
+    NG, NL, Ncol, Nq = m.NG, m.Ne * (N + 1) ** 3, m.Ncol, (N + 1) ** 2
+    extra = 0 if warp is None else 12 * Ncol * Nq * nz * (N + 1) + 16 * NG
+    elem, stage = 20 * NG + 4 * NL + extra, 124 * NG + 4 * NL + extra
     hbm, _ = peaks()
     kern = {}
     for name, (nl, tot) in pr.items():
@@ -542,7 +545,9 @@ def paper_set_measure(sem, torch, steps=20, warmup=3, gate_steps=100):
         dm, dd = sem.sem_diag(m, p64, qm), sem.sem_diag(m, p64, qd)
         gate = {"steps": gate_steps, "max_wind_fp64": dd["max_wind"],
                 "max_wind_rel_err": abs(dm["max_wind"] - dd["max_wind"]) / dd["max_wind"]}
-    return {"workload": "uniform-64x64x16-N4, the paper's equation set",
+    what = "" if warp is None else (f" on warped layers (amplitude {warp[0]:g} m, {warp[1]} x {warp[2]} "
+                                    "periods, flat lids)")
+    return {"workload": "uniform-64x64x16-N4, the paper's equation set" + what,
             "ms_per_step": ms, "value": 3 * 5 * NL / (ms * 1e-3),
             "autotune": {"variants": [{"layers_per_cta": r[0], "min_ctas_per_sm": r[1], "ms": r[2],
                                        "kind": r[3]} for r in rows], "chosen": chosen},
@@ -975,6 +980,8 @@ def main():
     paper_res = None
     if not a.no_paper_set and a.form == "mixed":
         paper_res = paper_set_measure(sem, torch, gate_steps=a.gate_steps)
+        if not a.no_warped:
+            paper_res["warped"] = paper_set_measure(sem, torch, gate_steps=a.gate_steps, warp=(600.0, 4, 4))
     amr_res = None
     if not a.no_amr and a.form == "mixed":
         amr_res = amr_measure(sem, torch)

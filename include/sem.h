@@ -427,9 +427,9 @@ int sem_selftest_device_once(int n_devices, int n_threads, int* init_calls_host)
  * for) on the float32 state mirror q32_dev, `reps` launches each after two
  * warm-up launches, keeps the fastest for this mesh and that set (used by
  * sem_rk_stage, sem_rk_stage_mixed and sem_step_mixed afterwards; the two
- * sets' choices are kept apart) and reports all timings.  The paper's set on
- * warped layers has one kernel and no table: SEM_ERR_UNSUPPORTED.
- * Synchronises the stream; overwrites the mesh's residual scratch. */
+ * sets' choices are kept apart) and reports all timings.  Warped layers: the
+ * line-exchange rows only.  Synchronises the stream; overwrites the mesh's
+ * residual scratch. */
 #define SEM_TUNE_MAX 16
 typedef struct {
   int n_variants;

@@ -1,6 +1,6 @@
 // Right-hand side and Runge-Kutta stage kernels.
 //
-//   volume_column<N, EQ, R>: one CTA per leaf column marches up its nz
+//   volume_column<N, EQ, R> (the float64 form): one CTA per leaf column marches up its nz
 //     layers.  Per element it gathers the state through the column's
 //     horizontal map (hanging rows interpolated, Sec. 3.1), forms the
 //     pointwise fluxes and sources of the split equations (Sec. 2), contracts
@@ -626,24 +626,22 @@ __global__ void __launch_bounds__(256) mirror_kernel(const double* q, float* q32
     q32[i] = d2f_bits(q[i]);
 }
 
-template <int N, int EQ, typename R>
+// The float64 form's element kernel (both sets, box or warped layers); the
+// mixed form runs the line-exchange kernels of the variant table instead.
+template <int N, int EQ>
 static void launch_volume(const VolArgs& A, cudaStream_t st) {
   constexpr int P = (N + 1) * (N + 1) * (N + 1);
   constexpr int nt = (P + 31) / 32 * 32;
-  ProfScope ps(sizeof(R) == 8 ? "volume_fp64" : "volume_mixed", st);
+  ProfScope ps("volume_fp64", st);
   if (A.metric)
-    volume_column<N, EQ, R, true><<<A.Ncol, nt, 0, st>>>(A);
+    volume_column<N, EQ, double, true><<<A.Ncol, nt, 0, st>>>(A);
   else
-    volume_column<N, EQ, R><<<A.Ncol, nt, 0, st>>>(A);
+    volume_column<N, EQ, double><<<A.Ncol, nt, 0, st>>>(A);
 }
 
 template <int N>
-static void launch_volume_n(const VolArgs& A, int eq, bool mixed, cudaStream_t st) {
-  if (eq == 0) {
-    if (mixed) launch_volume<N, 0, float>(A, st); else launch_volume<N, 0, double>(A, st);
-  } else {
-    if (mixed) launch_volume<N, 1, float>(A, st); else launch_volume<N, 1, double>(A, st);
-  }
+static void launch_volume_fp64(const VolArgs& A, int eq, cudaStream_t st) {
+  if (eq == 0) launch_volume<N, 0>(A, st); else launch_volume<N, 1>(A, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -1383,7 +1381,11 @@ volume_lines_smag(const VolArgs A) {
 // the advective residuals node by node, as volume_column does for this set.
 // A layer's top-node residual is complete only after that combination, so it
 // passes to the layer above through shared memory after one more barrier.
-// Box meshes only (warped layers take volume_column).
+// W: warped layers, as volume_column's warped branch: the weak mass flux is the
+// contravariant one (the z component takes the x and y fluxes with the weights
+// of J grad zeta), the strong derivatives are taken at constant height
+// (d/dx = 2/hx (d/dxi - z_xi/z_zeta d/dzeta) and so on), and the reference
+// state is the one at each node's height.
 template <int N>
 __host__ __device__ constexpr int nc_lw() { return (6 * (N + 1)) | 1; }
 template <int N, int KL>
@@ -1396,7 +1398,7 @@ __host__ __device__ constexpr int nc_smem_floats() {
          2 * (N + 1) * KL * (N + 1) * (N + 1) + 2 * 5 * (KL * N + 1);
 }
 
-template <int N, int KL>
+template <int N, int KL, bool WARP = false>
 __device__ __forceinline__ void lines_nc_body(const VolArgs& A, const int col, float* smem, const int t) {
   constexpr int n1 = N + 1, Nq = n1 * n1;
   constexpr int LW = nc_lw<N>(), LS = nc_ls<N, KL>();
@@ -1420,8 +1422,17 @@ __device__ __forceinline__ void lines_nc_body(const VolArgs& A, const int col, f
   const int hm = part ? A.hmap[(long long)col * Nq + ab] : 0;
   const float wi = c_wf[N][i], wj = c_wf[N][j];
   const float fc = A.ff, g = A.gf;
+  const float hx = geo[0], hy = geo[1];
   float* rc = (float*)A.rc;
   const int nchunk = (A.nz + KL - 1) / KL;
+  // W: reference row at a node's own height; metric terms z_xi, z_eta, z_zeta of a node
+  auto ref_at = [&](int kz) {
+    return hm >= 0 ? A.refG32 + ((long long)hm * A.NZ + kz) * kRef
+                   : A.refH32 + ((long long)(-1 - hm) * A.NZ + kz) * kRef;
+  };
+  auto metric_at = [&](int k, int c) {
+    return A.metric32 + ((((long long)col * Nq + ab) * A.nz + k) * n1 + c) * 3;
+  };
   // reference rows of chunk chn into buffer chn & 1 (levels past the top repeat it)
   auto stage_ref = [&](int chn) {
     float* R = sR + (chn & 1) * 5 * NL;
@@ -1432,8 +1443,10 @@ __device__ __forceinline__ void lines_nc_body(const VolArgs& A, const int col, f
       R[e] = __ldg(A.ref32 + (long long)kz * kRef + fld[f]);
     }
   };
-  stage_ref(0);
-  __syncthreads();
+  if constexpr (!WARP) {
+    stage_ref(0);
+    __syncthreads();
+  }
   for (int ch = 0; ch < nchunk; ++ch) {
     const int k = ch * KL + kk;
     const bool act = part && k < A.nz;
@@ -1456,16 +1469,34 @@ __device__ __forceinline__ void lines_nc_body(const VolArgs& A, const int col, f
         float v[kFields];
         const int kz = kz0 + c;
         load_node<N>(A, hm, kz, v);
-        const float th0 = R[c], p0 = R[NL + c], rho0 = R[2 * NL + c], inv_rt0 = R[3 * NL + c];
+        const float wc = c_wf[N][c];
+        float th0, p0, rho0, inv_rt0, ax, ay, cxw = 0.f, cyw = 0.f;
+        if constexpr (!WARP) {
+          th0 = R[c], p0 = R[NL + c], rho0 = R[2 * NL + c], inv_rt0 = R[3 * NL + c];
+          ax = wj * wc * sx * hk;
+          ay = wi * wc * sy * hk;
+        } else {
+          // reference row: theta0, pi0, p0, rho0 | (rho theta)0, dtheta0/dz, 1/(rho theta)0, z
+          const float* rf = ref_at(kz);
+          const float4 r0 = __ldg(reinterpret_cast<const float4*>(rf));
+          const float4 r1 = __ldg(reinterpret_cast<const float4*>(rf + 4));
+          th0 = r0.x, p0 = r0.z, rho0 = r0.w, inv_rt0 = r1.z;
+          const float* mt = metric_at(k, c);
+          const float zx = __ldg(mt), zy = __ldg(mt + 1), zz = __ldg(mt + 2);
+          ax = wj * wc * 0.5f * hy * zz;        // weighted J grad xi . e_x
+          ay = wi * wc * 0.5f * hx * zz;        // weighted J grad eta . e_y
+          cxw = -0.5f * hy * zx * wi * wj;      // weighted J grad zeta . e_x
+          cyw = -0.5f * hx * zy * wi * wj;      // weighted J grad zeta . e_y
+        }
         const float rp = v[0], u = v[1], vv = v[2], w = v[3], thp = v[4];
         const float rho = rho0 + rp;
         const float inv = __frcp_rn(rho);
         const float rtp = fmaf(rho0, thp, rp * (th0 + thp));   // (rho theta)'
         const float pp = p0 * pow1p_m1(rtp * inv_rt0, A.bin, A.gammaf);
-        const float wc = c_wf[N][c];
-        zX[c] = rho * u * (wj * wc * sx * hk);
-        zY[c] = rho * vv * (wi * wc * sy * hk);
-        const float Fz = rho * w * (wi * wj * sz);
+        zX[c] = rho * u * ax;
+        zY[c] = rho * vv * ay;
+        float Fz = rho * w * (wi * wj * sz);
+        if constexpr (WARP) Fz = fmaf(rho * u, cxw, fmaf(rho * vv, cyw, Fz));
 #pragma unroll
         for (int c2 = 0; c2 < n1; ++c2) rm[c2] = fmaf(c_Dwf[N][c2 * n1 + c], Fz, rm[c2]);
         qz[0][c] = u;
@@ -1484,7 +1515,7 @@ __device__ __forceinline__ void lines_nc_body(const VolArgs& A, const int col, f
     }
     __syncthreads();
     // the next chunk's reference rows load under this chunk's line exchange
-    if (ch + 1 < nchunk) stage_ref(ch + 1);
+    if (!WARP && ch + 1 < nchunk) stage_ref(ch + 1);
     if (act) {
       // x-line (lo, lc): nodes (m, lo, lc); slot 0 weak, slots 1..5 strong
       float* bx = sX + kk * LS + lo * n1 * LW + lc;
@@ -1532,18 +1563,36 @@ __device__ __forceinline__ void lines_nc_body(const VolArgs& A, const int col, f
         // derivatives of u, v, w, p', theta' at node c: x, y from the line
         // owners, z from this thread's own line
         float dx[5], dy[5], dz[5];
+        float wJ, th0dz;
+        if constexpr (!WARP) {
 #pragma unroll
-        for (int f = 0; f < 5; ++f) {
-          float a = 0.f;
+          for (int f = 0; f < 5; ++f) {
+            float a = 0.f;
 #pragma unroll
-          for (int m = 0; m < n1; ++m) a = fmaf(c_Df[N][c * n1 + m], qz[f][m], a);
-          dx[f] = zX[(f + 1) * n1 + c] * gx;
-          dy[f] = zY[(f + 1) * n1 + c] * gy;
-          dz[f] = a * gz;
+            for (int m = 0; m < n1; ++m) a = fmaf(c_Df[N][c * n1 + m], qz[f][m], a);
+            dx[f] = zX[(f + 1) * n1 + c] * gx;
+            dy[f] = zY[(f + 1) * n1 + c] * gy;
+            dz[f] = a * gz;
+          }
+          wJ = wJ1 * c_wf[N][c];
+          th0dz = R[4 * NL + c];
+        } else {
+          const float* mt = metric_at(k, c);
+          const float zx = __ldg(mt), zy = __ldg(mt + 1), zz = __ldg(mt + 2);
+          const float gzw = 1.f / zz, rzx = zx / zz, rzy = zy / zz;
+#pragma unroll
+          for (int f = 0; f < 5; ++f) {
+            float a = 0.f;
+#pragma unroll
+            for (int m = 0; m < n1; ++m) a = fmaf(c_Df[N][c * n1 + m], qz[f][m], a);
+            dx[f] = (zX[(f + 1) * n1 + c] - rzx * a) * gx;
+            dy[f] = (zY[(f + 1) * n1 + c] - rzy * a) * gy;
+            dz[f] = a * gzw;
+          }
+          wJ = wi * wj * c_wf[N][c] * sz * zz;
+          th0dz = __ldg(ref_at(kz0 + c) + 5);
         }
         const float u = qz[0][c], vv = qz[1][c], w = qz[2][c], inv = sV[c * NT + t];
-        const float wJ = wJ1 * c_wf[N][c];
-        const float th0dz = R[4 * NL + c];
         float adv[5];
 #pragma unroll
         for (int f = 0; f < 5; ++f) adv[f] = fmaf(w, dz[f], fmaf(vv, dy[f], u * dx[f]));
@@ -1590,6 +1639,14 @@ __global__ void __launch_bounds__(KL * (N + 1) * (N + 1), MB)
 volume_lines_nc(const VolArgs A) {
   extern __shared__ __align__(16) float smem[];
   lines_nc_body<N, KL>(A, blockIdx.x, smem, threadIdx.x);
+}
+
+// The same on warped layers (non-affine elements).
+template <int N, int KL, int MB>
+__global__ void __launch_bounds__(KL * (N + 1) * (N + 1), MB)
+volume_lines_nc_warp(const VolArgs A) {
+  extern __shared__ __align__(16) float smem[];
+  lines_nc_body<N, KL, true>(A, blockIdx.x, smem, threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1867,11 +1924,15 @@ static int launch_lines_nc(const VolArgs& A, cudaStream_t st) {
   static DeviceOnce attr;
   int rc = device_once(attr, [&] {
     SEM_CUDA_TRY(cudaFuncSetAttribute(volume_lines_nc<N, KL, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    SEM_CUDA_TRY(cudaFuncSetAttribute(volume_lines_nc_warp<N, KL, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     return SEM_OK;
   });
   if (rc) return rc;
   ProfScope ps("volume_mixed", st);
-  volume_lines_nc<N, KL, MB><<<A.Ncol, KL * (N + 1) * (N + 1), sm, st>>>(A);
+  if (A.metric32)
+    volume_lines_nc_warp<N, KL, MB><<<A.Ncol, KL * (N + 1) * (N + 1), sm, st>>>(A);
+  else
+    volume_lines_nc<N, KL, MB><<<A.Ncol, KL * (N + 1) * (N + 1), sm, st>>>(A);
   return SEM_OK;
 }
 
@@ -1939,24 +2000,9 @@ static int launch_pencil_n(const VolArgs& A, int N, int nz, cudaStream_t st, int
   return kPencil[variant].launch(A, st);
 }
 
-// The paper's set, mixed form: the line-exchange rows (kind 5) on box
-// meshes, volume_column on warped layers.
-template <int N>
-static int launch_nc_column(const VolArgs& A, cudaStream_t st) {
-  launch_volume_n<N>(A, SEM_EQ_NONCONSERVATIVE, true, st);
-  return SEM_OK;
-}
+// The paper's set, mixed form: the line-exchange rows (kind 5), box or
+// warped layers.
 static int launch_nc_n(const VolArgs& A, int N, int nz, cudaStream_t st, int variant = -1) {
-  if (A.metric32) {
-    switch (N) {
-      case 2: return launch_nc_column<2>(A, st);
-      case 3: return launch_nc_column<3>(A, st);
-      case 4: return launch_nc_column<4>(A, st);
-      case 5: return launch_nc_column<5>(A, st);
-      case 6: return launch_nc_column<6>(A, st);
-      default: return fail(SEM_ERR_UNSUPPORTED, "order N not compiled");
-    }
-  }
   if (variant < 0 || variant >= kNumPencil || kPencil[variant].N != N || kPencil[variant].kind != 5)
     variant = pencil_default(N, nz, 5);
   if (variant < 0) return fail(SEM_ERR_UNSUPPORTED, "order N not compiled");
@@ -2225,10 +2271,10 @@ int launch_step_mixed(Mesh& m, const sem_params& p, double* q, float* q32, float
 
 // Rows of the variant table for a mesh and equation set: the conservative
 // set's kernels (kinds 0, 1, 2, 4; warped layers: kind 1 only) or the paper's
-// set's (kind 5; box meshes only).
+// set's (kind 5).
 static bool tune_row(const Mesh& m, int eqset, int v) {
   if (kPencil[v].N != m.N) return false;
-  if (eqset != SEM_EQ_CONSERVATIVE) return kPencil[v].kind == 5 && !m.warped();
+  if (eqset != SEM_EQ_CONSERVATIVE) return kPencil[v].kind == 5;
   if (kPencil[v].kind == 5) return false;
   return !m.warped() || kPencil[v].kind == 1;
 }
@@ -2276,10 +2322,7 @@ int autotune_pencil(Mesh& m, const sem_params& p, const float* q32, int reps, se
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (best < 0)
-    return fail(SEM_ERR_UNSUPPORTED, eqset != SEM_EQ_CONSERVATIVE && m.warped()
-                                         ? "the paper's set on warped layers has one element kernel"
-                                         : "no variant for this order");
+  if (best < 0) return fail(SEM_ERR_UNSUPPORTED, "no variant for this order");
   (eqset == SEM_EQ_CONSERVATIVE ? m.pencil_variant : m.nc_variant) = best;
   return SEM_OK;
 }
@@ -2775,11 +2818,11 @@ int launch_rhs_stage(Mesh& m, const sem_params& p, const StageArgs& s, cudaStrea
   } else if (mixed) {
     if ((rc = launch_nc_n(A, m.N, m.nz, st, m.nc_variant))) return rc;
   } else switch (m.N) {
-    case 2: launch_volume_n<2>(A, eq, mixed, st); break;
-    case 3: launch_volume_n<3>(A, eq, mixed, st); break;
-    case 4: launch_volume_n<4>(A, eq, mixed, st); break;
-    case 5: launch_volume_n<5>(A, eq, mixed, st); break;
-    case 6: launch_volume_n<6>(A, eq, mixed, st); break;
+    case 2: launch_volume_fp64<2>(A, eq, st); break;
+    case 3: launch_volume_fp64<3>(A, eq, st); break;
+    case 4: launch_volume_fp64<4>(A, eq, st); break;
+    case 5: launch_volume_fp64<5>(A, eq, st); break;
+    case 6: launch_volume_fp64<6>(A, eq, st); break;
     default: return fail(SEM_ERR_UNSUPPORTED, "order N not compiled");
   }
   SEM_CUDA_TRY(cudaGetLastError());

@@ -160,12 +160,16 @@ def test_autotune_select_rejects_rows_outside_the_table(sem):
     with pytest.raises(sem.SemError) as e:     # no such equation set
         sem.sem_autotune_select(m, 0, eqset=2)
     assert e.value.code == sem.SEM_ERR_ARG
-    # warped layers: the paper's set has no table
+    # warped layers: the paper's set keeps its four rows, the conservative set
+    # its line-exchange rows only (five at order 4)
     w = sem.sem_mesh_create(80e3, 80e3, 10e3, 2, 2, 2, 4, warp=(500.0, 1, 1))
-    sem.sem_autotune_select(w, -1, eqset=1)
-    with pytest.raises(sem.SemError) as e:
-        sem.sem_autotune_select(w, 0, eqset=1)
-    assert e.value.code == sem.SEM_ERR_ARG
+    for row in (-1, 0, 3):
+        sem.sem_autotune_select(w, row, eqset=1)
+    sem.sem_autotune_select(w, 4, eqset=0)
+    for eq, bad in ((1, 4), (0, 5)):
+        with pytest.raises(sem.SemError) as e:
+            sem.sem_autotune_select(w, bad, eqset=eq)
+        assert e.value.code == sem.SEM_ERR_ARG
 
 
 def test_uniform_counts_and_info(sem):

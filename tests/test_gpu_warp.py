@@ -78,6 +78,55 @@ def test_warped_every_line_variant_matches_oracle(sem):
         assert np.all(group_rel_l2(host(out), T_o[:, perm]) <= 1e-4), rows[row]
 
 
+@pytest.mark.parametrize("name", ["warped-twolevel-17-layers-N4", "warped-twolevel-N3", "warped-4x4x2-N4"])
+def test_warped_every_paper_set_variant_matches_oracle(sem, name):
+    """The paper's set on warped layers: every line-exchange variant of its
+    table (kind 5) gives the mixed tendency within 1e-4 of the oracle, for a
+    random state and for the balanced vortex."""
+    m, o, X, perm = make_pair(sem, **WMESH[name])
+    p = sem.sem_params_default(eqset=1, precision=sem.SEM_PREC_MIXED)
+    states = (random_state(o.XG, o.Lz, 53, "NC"), vortex_state(o.XG, o.Lz, eqset="NC"))
+    q32 = torch.empty((5, m.NG), dtype=torch.float32, device="cuda")
+    sem.sem_mirror(m, dev(states[0][:, perm]), q32)
+    rows, _ = sem.sem_autotune(m, p, q32, 1)
+    assert rows and {r[3] for r in rows} == {5}
+    for row in list(range(len(rows))) + [-1]:
+        sem.sem_autotune_select(m, row, eqset=1)
+        for q_o in states:
+            T_o = orhs.rhs(o, q_o, PRM, "NC")
+            q = dev(q_o[:, perm])
+            out = torch.full_like(q, float("nan"))
+            sem.sem_rhs(m, p, q, out)
+            err = group_rel_l2(host(out), T_o[:, perm])
+            assert np.all(err <= 1e-4), (row, err)
+    assert sem.sem_status(m) == 0
+
+
+@pytest.mark.parametrize("name", ["warped-4x4x2-N4", "warped-twolevel-N4"])
+@pytest.mark.parametrize("eqset", ["C", "NC"])
+def test_warped_mixed_steps_both_sets_match_oracle(sem, name, eqset):
+    """Five mixed increment-form steps of 1 s from the balanced vortex in
+    either equation set: within 1e-4 of the oracle's steps in the full fields
+    and in the change."""
+    m, o, X, perm = make_pair(sem, **WMESH[name])
+    q_o = vortex_state(o.XG, o.Lz, eqset=eqset)
+    q_ref = q_o.copy()
+    for _ in range(5):
+        q_ref = ork.rk_step(o, PRM, q_ref, 1.0, eqset)
+    q = dev(q_o[:, perm])
+    p = sem.sem_params_default(eqset=0 if eqset == "C" else 1, precision=sem.SEM_PREC_MIXED)
+    q32 = torch.empty(q.shape, dtype=torch.float32, device="cuda")
+    work = torch.empty((10, m.NG), dtype=torch.float32, device="cuda")
+    sem.sem_mirror(m, q, q32)
+    for _ in range(5):
+        sem.sem_step_mixed(m, p, q, q32, work, 1.0)
+    got = host(q)
+    z = X[:, 2]
+    assert np.all(group_rel_l2(full_fields(got, z, eqset), full_fields(q_ref[:, perm], z, eqset)) <= 1e-4)
+    assert np.all(increment_err(got, q_o[:, perm], q_ref[:, perm]) <= 1e-4)
+    assert sem.sem_status(m) == 0
+
+
 @pytest.mark.parametrize("name", ["warped-4x4x2-N4", "warped-twolevel-N4"])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_warped_steps_match_oracle(sem, name, prec):
