@@ -214,10 +214,11 @@ def cpu_one_thread(n=16):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def batched_measure(sem, torch, steps=10, warmup=3, refine=True, rates=None):
+def batched_measure(sem, torch, steps=10, warmup=3, refine=True, rates=None, eqset=0):
     """The 16-instance batched workload: one CUDA-graph launch per step over
     all instances (persistent element kernel + gather/increment kernel per
-    stage) against stepping the instances one after another."""
+    stage) against stepping the instances one after another; eqset 1: the
+    paper's equation set."""
     from synth.vortex import VortexSpec, vortex_state
     from synth.workloads import batched_instances, geometric_flags
     insts = batched_instances()
@@ -225,14 +226,15 @@ def batched_measure(sem, torch, steps=10, warmup=3, refine=True, rates=None):
         import dataclasses
         insts = [dataclasses.replace(it, levels=0) for it in insts]
     meshes, qs, q32, work, dts, dof, init = [], [], [], [], [], 0, []
-    p = sem.sem_params_default(precision=sem.SEM_PREC_MIXED)
+    p = sem.sem_params_default(eqset=eqset, precision=sem.SEM_PREC_MIXED)
     for k, it in enumerate(insts):
         m = sem.sem_mesh_create(it.L, it.L, it.Lz, it.nx, it.nx, it.nz, it.N, lvl_max=max(it.levels, 1))
         for _ in range(it.levels):
             lv = [tuple(x) for x in sem.sem_mesh_leaves_host(m)]
             m = sem.sem_transfer_plan(m, geometric_flags(lv, it.nx, it.nz, it.L, 3 * it.rmw, it.levels))
         spec = VortexSpec(vmax=it.vmax, rmw=it.rmw, seed=1000 + k)
-        q = torch.from_numpy(vortex_state(sem.sem_mesh_coords_host(m).T, it.Lz, spec)).cuda()
+        q = torch.from_numpy(vortex_state(sem.sem_mesh_coords_host(m).T, it.Lz, spec,
+                                          eqset="NC" if eqset else "C")).cuda()
         meshes.append(m)
         init.append(q.clone())
         qs.append(q)
@@ -270,7 +272,7 @@ def batched_measure(sem, torch, steps=10, warmup=3, refine=True, rates=None):
     # max-wind gate: every instance after gate_steps batched (graph) steps
     # against its float64 single-mesh run from the same initial state
     gate_steps = 20
-    p64 = sem.sem_params_default(precision=sem.SEM_PREC_FP64)
+    p64 = sem.sem_params_default(eqset=eqset, precision=sem.SEM_PREC_FP64)
     for k, m in enumerate(meshes):
         qs[k].copy_(init[k])
         sem.sem_mirror(m, qs[k], q32[k], stream)
@@ -292,11 +294,12 @@ def batched_measure(sem, torch, steps=10, warmup=3, refine=True, rates=None):
     # total DOF-updates over the sum of each instance's DOF-updates at its
     # order's rate
     expected = None
-    if rates:
+    if rates and not eqset:
         dofs = [15 * m.Ne * (it.N + 1) ** 3 for m, it in zip(meshes, insts)]
         expected = sum(dofs) / sum(d / rates[it.N] for d, it in zip(dofs, insts))
     return {"workload": "16 seeded instances, bases 8..48, N 3..6, "
-                        + ("0..3 levels" if refine else "unrefined"),
+                        + ("0..3 levels" if refine else "unrefined")
+                        + (", the paper's equation set" if eqset else ""),
             "expected_from_order_rates": expected,
             "instances": len(insts), "elements": int(sum(m.Ne for m in meshes)),
             "dof_per_stage": dof, "ms_per_step_graph": ms_graph, "ms_per_step_batched_no_graph": ms_nograph,
@@ -971,6 +974,8 @@ def main():
         batched = ([batched_measure(sem, torch, rates=rates)] if a.batched in ("both", "refined") else []) + \
                   ([batched_measure(sem, torch, refine=False, rates=rates)]
                    if a.batched in ("both", "unrefined") else [])
+        if a.batched in ("both", "unrefined"):
+            batched.append(batched_measure(sem, torch, refine=False, eqset=1))
         batched.append({"order_rates_dof_updates_per_s": {str(k): v for k, v in rates.items()},
                         "how": "single uniform mesh per order, autotuned mixed steps"})
 

@@ -271,13 +271,16 @@ int sem_step_mixed(sem_mesh* m, const sem_params* p, double* q_dev, float* q32_d
  * orders N = 2..6, any refinement levels).  Per stage, one persistent element
  * kernel walks all columns of all meshes from a work queue (costliest columns
  * first) and one gather/increment kernel covers the concatenated global nodes;
- * a step is the increment form of sem_step_mixed for every instance.  The
- * meshes must outlive the batch.  sem_batch_step_mixed takes per-instance
- * arrays (q[k] float64 [5][NG_k], q32[k] its float32 mirror, work32[k] float32
- * 2 x [5][NG_k]) and time steps dt[k]; with use_graph != 0 the step's launches
- * are captured once into a CUDA graph and replayed (re-captured when an array
- * pointer, a dt or a physical parameter changes).  sem_batch_status reads and
- * clears the batch's non-finite flag (synchronises). */
+ * a step is the increment form of sem_step_mixed for every instance, in
+ * p->eqset's equation set (either set; p->precision must be SEM_PREC_MIXED,
+ * else SEM_ERR_ARG; box meshes only, and no Smagorinsky stress or absorbing
+ * layer: SEM_ERR_UNSUPPORTED).  The meshes must outlive the batch.
+ * sem_batch_step_mixed takes per-instance arrays (q[k] float64 [5][NG_k],
+ * q32[k] its float32 mirror, work32[k] float32 2 x [5][NG_k]) and time steps
+ * dt[k]; with use_graph != 0 the step's launches are captured once into a CUDA
+ * graph and replayed (re-captured when an array pointer, a dt, a physical
+ * parameter or the equation set changes).  sem_batch_status reads and clears
+ * the batch's non-finite flag (synchronises). */
 typedef struct sem_batch sem_batch;
 int sem_batch_create(sem_mesh* const* meshes, int n, sem_batch** out);
 void sem_batch_destroy(sem_batch* b);

@@ -542,8 +542,7 @@ int sem_batch_step_mixed(sem_batch* b, const sem_params* p, double* const* q, fl
   if (!b || !p || !q || !q32 || !work32 || !dt) return fail(SEM_ERR_ARG, "NULL argument");
   int rc = check_params(p);
   if (rc) return rc;
-  if (p->precision != SEM_PREC_MIXED || p->eqset != SEM_EQ_CONSERVATIVE)
-    return fail(SEM_ERR_ARG, "batched steps need SEM_PREC_MIXED and the conservative set");
+  if (p->precision != SEM_PREC_MIXED) return fail(SEM_ERR_ARG, "batched steps need SEM_PREC_MIXED");
   for (int k = 0; k < b->n; ++k)
     if (!q[k] || !q32[k] || !work32[k]) return fail(SEM_ERR_ARG, "NULL array");
   return batch_step_mixed(b->impl, *p, q, q32, work32, dt, use_graph, st);

@@ -1300,7 +1300,9 @@ __device__ __forceinline__ void lines_body(const VolArgs& A, const int col, floa
       }
       // vertical DSS: the bottom node takes the full top-node value of the
       // layer below (its z part from sT, its x and y parts still in sX, sY;
-      // with SMAG all of it from sT)
+      // with SMAG all of it from sT), summed as z + (x + y) like the value
+      // the layer below forms itself and hands on between chunks, so that
+      // the result does not depend on where the chunks split the column
       if (kk > 0 && SMAG) {
 #pragma unroll
         for (int f = 0; f < kFields; ++f) rz[f][0] += sT[(f * KL + kk - 1) * Nq + ab];
@@ -1309,7 +1311,7 @@ __device__ __forceinline__ void lines_body(const VolArgs& A, const int col, floa
         const float* pY = sY + (kk - 1) * LS + ab * LW;
 #pragma unroll
         for (int f = 0; f < kFields; ++f)
-          rz[f][0] += sT[(f * KL + kk - 1) * Nq + ab] + pX[f * n1 + N] + pY[f * n1 + N];
+          rz[f][0] += sT[(f * KL + kk - 1) * Nq + ab] + (pX[f * n1 + N] + pY[f * n1 + N]);
       } else if (ch > 0) {
 #pragma unroll
         for (int f = 0; f < kFields; ++f) rz[f][0] += sP[((ch - 1) & 1) * kFields * Nq + f * Nq + ab];
@@ -1830,9 +1832,10 @@ __global__ void __launch_bounds__(kTcThreads, MB) volume_lines_tc(const VolArgs 
       if (kk > 0) {
         const float* pX = stX + (kk - 1) * LS + ab * LW;
         const float* pY = stY + (kk - 1) * LS + ab * LW;
+        // z + (x + y), as the layer below forms its top-node value
 #pragma unroll
         for (int f = 0; f < kFields; ++f)
-          rz[f][0] += sT[(f * KL + kk - 1) * Nq + ab] + pX[f * n1 + N] + pY[f * n1 + N];
+          rz[f][0] += sT[(f * KL + kk - 1) * Nq + ab] + (pX[f * n1 + N] + pY[f * n1 + N]);
       } else if (ch > 0) {
 #pragma unroll
         for (int f = 0; f < kFields; ++f) rz[f][0] += sP[((ch - 1) & 1) * kFields * Nq + f * Nq + ab];
@@ -2387,6 +2390,33 @@ volume_batch_mixed(const VolArgs* __restrict__ insts, const int* __restrict__ in
   }
 }
 
+// The same queue with the paper's equation set (the line-exchange body of
+// volume_lines_nc).
+template <int BT, int MB>
+__global__ void __launch_bounds__(BT, MB)
+volume_batch_nc(const VolArgs* __restrict__ insts, const int* __restrict__ inst_N,
+                const int2* __restrict__ tiles, int ntiles, int* counter) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ int s_tile;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= ntiles) break;
+    const int2 tl = tiles[tile];
+    const VolArgs& A = insts[tl.x];
+    switch (inst_N[tl.x]) {
+      case 2: lines_nc_body<2, batch_kl(2, BT)>(A, tl.y, smem, threadIdx.x); break;
+      case 3: lines_nc_body<3, batch_kl(3, BT)>(A, tl.y, smem, threadIdx.x); break;
+      case 4: lines_nc_body<4, batch_kl(4, BT)>(A, tl.y, smem, threadIdx.x); break;
+      case 5: lines_nc_body<5, batch_kl(5, BT)>(A, tl.y, smem, threadIdx.x); break;
+      case 6: lines_nc_body<6, batch_kl(6, BT)>(A, tl.y, smem, threadIdx.x); break;
+      default: break;
+    }
+  }
+}
+
 template <int BT>
 static size_t batch_smem() {
   size_t m = lines_smem_floats<2, batch_kl(2, BT)>();
@@ -2396,19 +2426,31 @@ static size_t batch_smem() {
   m = std::max(m, (size_t)lines_smem_floats<6, batch_kl(6, BT)>());
   return m * sizeof(float);
 }
+template <int BT>
+static size_t batch_smem_nc() {
+  size_t m = nc_smem_floats<2, batch_kl(2, BT)>();
+  m = std::max(m, (size_t)nc_smem_floats<3, batch_kl(3, BT)>());
+  m = std::max(m, (size_t)nc_smem_floats<4, batch_kl(4, BT)>());
+  m = std::max(m, (size_t)nc_smem_floats<5, batch_kl(5, BT)>());
+  m = std::max(m, (size_t)nc_smem_floats<6, batch_kl(6, BT)>());
+  return m * sizeof(float);
+}
 
 // Launch configurations of the batched element kernel (threads per CTA and
-// the CTAs per SM its registers are sized for); chosen by timing at set-up.
+// the CTAs per SM its registers are sized for), for the conservative set and
+// for the paper's set; chosen by timing at set-up, per set.
 struct BatchVariant {
   int BT, MB;
   void (*kernel)(const VolArgs*, const int*, const int2*, int, int*);
   size_t (*smem)();
+  void (*kernel_nc)(const VolArgs*, const int*, const int2*, int, int*);
+  size_t (*smem_nc)();
 };
 static const BatchVariant kBatch[] = {
-    {400, 1, volume_batch_mixed<400, 1>, batch_smem<400>},
-    {200, 2, volume_batch_mixed<200, 2>, batch_smem<200>},
-    {200, 3, volume_batch_mixed<200, 3>, batch_smem<200>},
-    {256, 2, volume_batch_mixed<256, 2>, batch_smem<256>},
+    {400, 1, volume_batch_mixed<400, 1>, batch_smem<400>, volume_batch_nc<400, 1>, batch_smem_nc<400>},
+    {200, 2, volume_batch_mixed<200, 2>, batch_smem<200>, volume_batch_nc<200, 2>, batch_smem_nc<200>},
+    {200, 3, volume_batch_mixed<200, 3>, batch_smem<200>, volume_batch_nc<200, 3>, batch_smem_nc<200>},
+    {256, 2, volume_batch_mixed<256, 2>, batch_smem<256>, volume_batch_nc<256, 2>, batch_smem_nc<256>},
 };
 constexpr int kNumBatch = sizeof(kBatch) / sizeof(kBatch[0]);
 
@@ -2454,14 +2496,15 @@ struct BatchImpl {
   cudaGraph_t graph = nullptr;
   std::vector<const void*> key;  // arrays and dt the device tables were built for
   std::vector<double> key_dt;
-  double key_par[7] = {0};
+  double key_par[8] = {0};
   int nsm = 152;
   std::vector<IncArgs> h_inc;  // host copy of the increment-kernel arguments [3][n]
   int nsmall = 0;
-  int variant = -1;          // batched element-kernel configuration (kBatch)
+  int eq = SEM_EQ_CONSERVATIVE;  // equation set of the current tables and graph
+  int variant[2] = {-1, -1};     // batched element-kernel configuration (kBatch), per set
   std::vector<char> big;     // instances launched with their own tuned kernel
   std::vector<VolArgs> h_vol;  // host copy of the element-kernel arguments [2][n]
-  float variant_ms[kNumBatch] = {0};
+  float variant_ms[2][kNumBatch] = {{0}};
 };
 
 static void batch_free(BatchImpl* b) {
@@ -2559,9 +2602,13 @@ int batch_create(Mesh* const* meshes, int n, void** out) {
       if (e == cudaSuccess) b->br_done.push_back(ev);
     }
   }
-  for (int v = 0; v < kNumBatch && e == cudaSuccess; ++v)
+  for (int v = 0; v < kNumBatch && e == cudaSuccess; ++v) {
     e = cudaFuncSetAttribute(kBatch[v].kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kBatch[v].smem());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kBatch[v].kernel_nc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kBatch[v].smem_nc());
+  }
   if (e != cudaSuccess) {
     batch_free(b);
     delete b;
@@ -2584,7 +2631,10 @@ void batch_destroy(void* h) {
 static void batch_volume(BatchImpl* b, int v, const VolArgs* vol, int* counter, cudaStream_t st) {
   const BatchVariant& V = kBatch[v];
   const int vgrid = std::min(b->ntiles, b->nsm * V.MB);
-  V.kernel<<<vgrid, V.BT, V.smem(), st>>>(vol, b->d_N, b->d_tiles, b->ntiles, counter);
+  if (b->eq == SEM_EQ_CONSERVATIVE)
+    V.kernel<<<vgrid, V.BT, V.smem(), st>>>(vol, b->d_N, b->d_tiles, b->ntiles, counter);
+  else
+    V.kernel_nc<<<vgrid, V.BT, V.smem_nc(), st>>>(vol, b->d_N, b->d_tiles, b->ntiles, counter);
 }
 
 // time every configuration of the element kernel on stage-0 inputs (side
@@ -2611,10 +2661,11 @@ static int batch_tune(BatchImpl* b, cudaStream_t st) {
     }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    b->variant_ms[v] = ms / 3.f;
-    if (b->variant < 0 || b->variant_ms[v] < best) {
-      best = b->variant_ms[v];
-      b->variant = v;
+    const int q = b->eq == SEM_EQ_CONSERVATIVE ? 0 : 1;
+    b->variant_ms[q][v] = ms / 3.f;
+    if (b->variant[q] < 0 || b->variant_ms[q][v] < best) {
+      best = b->variant_ms[q][v];
+      b->variant[q] = v;
     }
   }
   cudaEventDestroy(e0);
@@ -2638,7 +2689,10 @@ static void batch_enqueue(BatchImpl* b, cudaStream_t st) {
     cudaStream_t s2 = b->branch[k] ? b->br[bi++ % nbr] : st;
     Mesh& m = *b->meshes[k];
     for (int stage = 0; stage < 3; ++stage) {
-      launch_pencil_n(b->h_vol[(stage == 0 ? 0 : n) + k], m.N, m.nz, s2, m.pencil_variant);
+      if (b->eq == SEM_EQ_CONSERVATIVE)
+        launch_pencil_n(b->h_vol[(stage == 0 ? 0 : n) + k], m.N, m.nz, s2, m.pencil_variant);
+      else
+        launch_nc_n(b->h_vol[(stage == 0 ? 0 : n) + k], m.N, m.nz, s2, m.nc_variant);
       const IncArgs& B = b->h_inc[stage * n + k];
       const int blocks = grid_cap(B.NG, 64);   // as in the single-mesh step
       if (stage == 0) dss_inc<0><<<blocks, 256, 0, s2>>>(B);
@@ -2650,7 +2704,8 @@ static void batch_enqueue(BatchImpl* b, cudaStream_t st) {
   for (int stage = 0; stage < 3; ++stage) {
     if (b->ntiles > 0) {
       cudaMemsetAsync(b->d_counter + stage, 0, sizeof(int), st);
-      batch_volume(b, b->variant, b->d_vol + (stage == 0 ? 0 : n), b->d_counter + stage, st);
+      batch_volume(b, b->variant[b->eq == SEM_EQ_CONSERVATIVE ? 0 : 1], b->d_vol + (stage == 0 ? 0 : n),
+                   b->d_counter + stage, st);
     }
     const int ns = b->nsmall;
     if (ns > 0 && b->total_nodes > 0) {
@@ -2678,9 +2733,10 @@ int batch_step_mixed(void* h, const sem_params& p, double* const* q, float* cons
     key.push_back(work32[k]);
   }
   std::vector<double> kdt(dt, dt + n);
-  const double par[7] = {p.g, p.f, p.R_d, p.c_p, p.p00, p.theta_s, p.N_bv};
+  const double par[8] = {p.g, p.f, p.R_d, p.c_p, p.p00, p.theta_s, p.N_bv, (double)p.eqset};
   const bool same = key == b->key && kdt == b->key_dt && std::memcmp(par, b->key_par, sizeof(par)) == 0;
   if (!same) {
+    b->eq = p.eqset;
     std::vector<VolArgs> vol(2 * n);
     std::vector<IncArgs> inc(3 * n);
     for (int k = 0; k < n; ++k) {
@@ -2729,7 +2785,8 @@ int batch_step_mixed(void* h, const sem_params& p, double* const* q, float* cons
     b->h_inc = inc;
     b->h_vol = vol;
     for (int k = 0; k < n; ++k)
-      if (b->big[k] && b->meshes[k]->pencil_variant < 0) {
+      if (b->big[k] && (p.eqset == SEM_EQ_CONSERVATIVE ? b->meshes[k]->pencil_variant
+                                                       : b->meshes[k]->nc_variant) < 0) {
         sem_tune_out tout;
         std::memset(&tout, 0, sizeof(tout));
         int rc = autotune_pencil(*b->meshes[k], p, q32[k], 3, &tout, st);
@@ -2746,7 +2803,7 @@ int batch_step_mixed(void* h, const sem_params& p, double* const* q, float* cons
       cudaGraphDestroy(b->graph);
       b->graph = nullptr;
     }
-    if (b->variant < 0 && b->ntiles > 0) {
+    if (b->variant[b->eq == SEM_EQ_CONSERVATIVE ? 0 : 1] < 0 && b->ntiles > 0) {
       int rc = batch_tune(b, st);
       if (rc) return rc;
     }
@@ -2771,11 +2828,12 @@ int batch_step_mixed(void* h, const sem_params& p, double* const* q, float* cons
 
 int batch_tuning(void* h, int* variant, int* bt, int* mb, float* ms, int max) {
   BatchImpl* b = (BatchImpl*)h;
-  *variant = b->variant;
+  const int q = b->eq == SEM_EQ_CONSERVATIVE ? 0 : 1;
+  *variant = b->variant[q];
   for (int v = 0; v < kNumBatch && v < max; ++v) {
     bt[v] = kBatch[v].BT;
     mb[v] = kBatch[v].MB;
-    ms[v] = b->variant_ms[v];
+    ms[v] = b->variant_ms[q][v];
   }
   return kNumBatch < max ? kNumBatch : max;
 }

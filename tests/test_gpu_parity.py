@@ -135,6 +135,7 @@ def test_every_element_kernel_variant_matches_oracle(sem, name):
     rows, _ = sem.sem_autotune(m, p, q32, 1)
     assert len(rows) >= 2
     kinds = set()
+    lines = []
     for row in list(range(len(rows))) + [-1]:
         sem.sem_autotune_select(m, row)
         out = torch.full_like(q, float("nan"))
@@ -143,7 +144,13 @@ def test_every_element_kernel_variant_matches_oracle(sem, name):
         assert np.all(err <= 1e-4), (row, rows[row] if row >= 0 else "default", err)
         if row >= 0:
             kinds.add(rows[row][3])
+            if rows[row][3] in (1, 4):
+                lines.append((rows[row], out.clone()))
     assert kinds == ({0, 1, 2, 4} if m.N == 4 else {0, 1})
+    # the line-exchange variants do the same arithmetic per node whatever the
+    # layers per CTA (the face shared by two chunks is summed as inside one)
+    for r, o in lines[1:]:
+        assert torch.equal(o, lines[0][1]), (r, lines[0][0])
     assert sem.sem_status(m) == 0
 
 
@@ -169,12 +176,17 @@ def test_every_paper_set_variant_matches_oracle(sem, name):
     rows, chosen = sem.sem_autotune(m, p, q32, 1)
     assert rows and {r[3] for r in rows} == {5}
     assert len(rows) == (4 if m.N == 4 else 1)
+    outs = []
     for row in list(range(len(rows))) + [-1]:
         sem.sem_autotune_select(m, row, eqset=1)
         out = torch.full_like(q, float("nan"))
         sem.sem_rhs(m, p, q, out)
         err = group_rel_l2(host(out), T_o[:, perm])
         assert np.all(err <= 1e-4), (row, rows[row] if row >= 0 else "default", err)
+        outs.append(out.clone())
+    # the same arithmetic per node whatever the layers per CTA
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
     assert sem.sem_status(m) == 0
 
 
@@ -709,6 +721,76 @@ def test_batched_steps_match_oracle(sem, use_graph, with_big):
         assert np.all(err <= 1e-4), (k, specs[k], err)
         inc = increment_err(got, q_o[:, perm], q_ref[:, perm])
         assert np.all(inc <= 1e-4), (k, specs[k], inc)
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batched_paper_set_matches_oracle_and_single_mesh_steps(sem, use_graph):
+    """The batched step with the paper's equation set (the persistent queue
+    over that set's line-exchange body): meshes of orders 3 to 6, refined by
+    one level (2:1 faces), an unrefined one with 17 layers, and two meshes
+    large enough for their own launches.  After two steps every instance is
+    within 1e-4 of two float64 oracle steps (full fields and change) and
+    within 1e-13 of stepping each mesh alone; a conservative-set step of the
+    same batch afterwards still matches its single-mesh steps (the tables,
+    tuning and graph follow the set)."""
+    specs = [(4, 2, 3, 300e3, 1), (4, 2, 4, 300e3, 1), (3, 2, 5, 300e3, 1),
+             (3, 2, 6, 300e3, 1), (5, 17, 4, 300e3, 0), (18, 1, 2, 300e3, 0), (20, 2, 3, 300e3, 0)]
+    dts = [0.5, 0.5, 0.4, 0.25, 0.5, 0.5, 0.5]
+    meshes = [_instance_mesh(sem, nx, nz, N, L, lev, 120e3) for nx, nz, N, L, lev in specs]
+    assert min(m.Ncol for m in meshes[-2:]) >= 2 * torch.cuda.get_device_properties(0).multi_processor_count
+    p = sem.sem_params_default(eqset=1, precision=sem.SEM_PREC_MIXED)
+    oracles, perms, init = [], [], []
+    for k, (m, (nx, nz, N, L, lev)) in enumerate(zip(meshes, specs)):
+        o = om.OracleMesh(L, L, 24e3, nx, nx, nz, N, leaves=[tuple(x) for x in sem.sem_mesh_leaves_host(m)])
+        perm = node_perm(sem.sem_mesh_coords_host(m), o.XG)
+        q_o = random_state(o.XG, 24e3, 60 + k, "NC")
+        oracles.append((o, q_o))
+        perms.append(perm)
+        init.append(dev(q_o[:, perm]))
+
+    def fresh(states):
+        qs = [q.clone() for q in states]
+        q32 = [torch.empty(q.shape, dtype=torch.float32, device="cuda") for q in qs]
+        work = [torch.empty((10, q.shape[1]), dtype=torch.float32, device="cuda") for q in qs]
+        for m, q, a in zip(meshes, qs, q32):
+            sem.sem_mirror(m, q, a)
+        return qs, q32, work
+
+    qb, b32, wb = fresh(init)
+    batch = sem.sem_batch_create(meshes)
+    for _ in range(2):
+        sem.sem_batch_step_mixed(batch, p, qb, b32, wb, dts, use_graph=use_graph)
+    assert sem.sem_batch_status(batch) == 0
+    qa, a32, wa = fresh(init)
+    for _ in range(2):
+        for k, m in enumerate(meshes):
+            sem.sem_step_mixed(m, p, qa[k], a32[k], wa[k], dts[k])
+    torch.cuda.synchronize()
+    for k, ((o, q_o), perm) in enumerate(zip(oracles, perms)):
+        q_ref = q_o
+        for _ in range(2):
+            q_ref = ork.rk_step(o, PRM, q_ref, dts[k], "NC")
+        got = host(qb[k])
+        z = o.XG[perm, 2]
+        err = group_rel_l2(full_fields(got, z, "NC"), full_fields(q_ref[:, perm], z, "NC"))
+        assert np.all(err <= 1e-4), (k, specs[k], err)
+        inc = increment_err(got, q_o[:, perm], q_ref[:, perm])
+        assert np.all(inc <= 1e-4), (k, specs[k], inc)
+        d = (qa[k] - qb[k]).abs().max().item()
+        assert d <= 1e-13 * qa[k].abs().max().item(), (k, d)
+    # the same batch with the conservative set
+    pc = sem.sem_params_default(precision=sem.SEM_PREC_MIXED)
+    initc = [dev(random_state(sem.sem_mesh_coords_host(m).T, 24e3, 80 + k)) for k, m in enumerate(meshes)]
+    qb, b32, wb = fresh(initc)
+    sem.sem_batch_step_mixed(batch, pc, qb, b32, wb, dts, use_graph=use_graph)
+    qa, a32, wa = fresh(initc)
+    for k, m in enumerate(meshes):
+        sem.sem_step_mixed(m, pc, qa[k], a32[k], wa[k], dts[k])
+    torch.cuda.synchronize()
+    for k in range(len(meshes)):
+        d = (qa[k] - qb[k]).abs().max().item()
+        assert d <= 1e-13 * qa[k].abs().max().item(), (k, d)
+    assert sem.sem_batch_status(batch) == 0
 
 
 def test_mixed_pressure_both_branches(sem):
