@@ -39,11 +39,11 @@ def pair(sem):
     return m, o, perm, q_o
 
 
-def full(q, z):
+def full(q, z, eqset="C"):
     ref = refstate.reference_state(z, PRM)
     out = q.copy()
     out[0] += ref["rho0"]
-    out[4] += ref["rhotheta0"]
+    out[4] += ref["rhotheta0"] if eqset == "C" else ref["theta0"]
     return out
 
 
@@ -64,6 +64,31 @@ def test_fullsize_mixed_step_matches_oracle(sem, pair):
     assert np.all(err <= 1e-4), err
     inc = group_rel_l2(got - q_o[:, perm], q_ref[:, perm] - q_o[:, perm])
     assert np.all(inc <= 1e-4), inc       # the step's own increment, not only the state
+    assert sem.sem_status(m) == 0
+
+
+def test_fullsize_paper_set_mixed_step_matches_oracle(sem, pair):
+    """The paper's equation set at full size: one mixed increment-form step
+    (autotuned among that set's line-exchange variants) against one oracle
+    step at every node, in the full fields and in the step's increment."""
+    m, o, perm, _ = pair
+    q_o = vortex_state(o.XG, LZ, eqset="NC")
+    q_ref = ork.rk_step(o, PRM, q_o, DT, "NC")
+    p = sem.sem_params_default(eqset=1, precision=sem.SEM_PREC_MIXED)
+    q = torch.from_numpy(np.ascontiguousarray(q_o[:, perm])).cuda()
+    q32 = torch.empty(q.shape, dtype=torch.float32, device="cuda")
+    work = torch.empty((10, m.NG), dtype=torch.float32, device="cuda")
+    sem.sem_mirror(m, q, q32)
+    rows, _ = sem.sem_autotune(m, p, q32, 2)
+    assert {r[3] for r in rows} == {5}
+    sem.sem_step_mixed(m, p, q, q32, work, DT)
+    torch.cuda.synchronize()
+    got = q.cpu().numpy()
+    z = o.XG[perm, 2]
+    err = group_rel_l2(full(got, z, "NC"), full(q_ref[:, perm], z, "NC"))
+    assert np.all(err <= 1e-4), err
+    inc = group_rel_l2(got - q_o[:, perm], q_ref[:, perm] - q_o[:, perm])
+    assert np.all(inc <= 1e-4), inc
     assert sem.sem_status(m) == 0
 
 
