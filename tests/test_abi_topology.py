@@ -172,6 +172,20 @@ def test_autotune_select_rejects_rows_outside_the_table(sem):
         assert e.value.code == sem.SEM_ERR_ARG
 
 
+@pytest.mark.parametrize("N,n_c,n_nc", [(2, 3, 1), (3, 4, 1), (4, 10, 4), (5, 3, 1), (6, 3, 1)])
+def test_variant_tables_per_order_and_set(sem, N, n_c, n_nc):
+    """Every compiled order has rows in both equation sets' variant tables
+    (the conservative set's z-pencil and line-exchange kernels, and order 4's
+    tensor-core and TMA variants; the paper's set's line-exchange kernels):
+    the last row is accepted, the one after it refused (host only)."""
+    m = sem.sem_mesh_create(80e3, 80e3, 10e3, 2, 2, 1, N)
+    for eq, n in ((0, n_c), (1, n_nc)):
+        sem.sem_autotune_select(m, n - 1, eqset=eq)
+        with pytest.raises(sem.SemError) as e:
+            sem.sem_autotune_select(m, n, eqset=eq)
+        assert e.value.code == sem.SEM_ERR_ARG
+
+
 def test_uniform_counts_and_info(sem):
     m = sem.sem_mesh_create(2048e3, 2048e3, 24e3, 64, 64, 16, 4)
     assert (m.Ne, m.NG, m.NH, m.NZ) == (65536, 4259840, 65536, 65)
